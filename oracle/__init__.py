@@ -1,0 +1,237 @@
+"""FP64 CPU oracle of the spectral-element Poisson solve -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library
+(``paper_2207_07098_gb300``) never imports, links or falls back to it, and the
+two share no code; only the seeded input generators in ``workloads`` serve
+both.
+
+The arithmetic lives in ``sem_oracle.c`` (plain sequential loops, FP64),
+built into ``liboracle.so`` by :func:`build` and reached through ctypes.
+Each routine restates a definition of Karp et al. (Sec. II-A: GLL basis,
+derivative matrix D, geometric factors G, local operator A^e = D^T G D,
+QQ^T; Sec. II-B: Jacobi-preconditioned CG).
+
+What pins the oracle to something other than itself (tests/test_oracle_*.py):
+
+* GLL: sum of weights = 2; closed-form nodes and weights for N = 1..4
+  (tests/golden/gll_closed_forms.txt); exact quadrature of x^k, k <= 2N-1;
+  symmetric nodes.
+* D: exact derivative of every polynomial of degree <= N; zero row sums;
+  centro-symmetry; 1-D stiffness D^T W D equal to closed forms (N = 1, 2) and
+  to exact integrals of Lagrange-basis derivatives built with numpy
+  polynomials.
+* Geometry: closed form for affine elements; total volume (unit cube, also
+  deformed; annulus = 255 pi).
+* A: kernel contains constants (Neumann); closed Kronecker form on affine
+  meshes; symmetry; positive definiteness on the masked space; entrywise
+  equality with a dense matrix assembled from explicit Kronecker products,
+  numpy Jacobians and an explicit Q on 1-8 deformed elements.
+* QQ^T: multiplicities 1/2/4/8 from mesh structure; sum invariance.
+* Jacobi: diagonal of the dense assembled matrix.
+* PCG: dense direct solve on tiny meshes; spectral convergence to
+  sin(pi x) sin(pi y) sin(pi z); at most n_free iterations on tiny meshes.
+* IR: reaches the FP64 solution; monotone outer residuals.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_SRC = os.path.join(_HERE, "sem_oracle.c")
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so (gcc, -O2, OpenMP, no FMA contraction)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "sem_oracle.h"))):
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+               _SRC, "-o", _SO + ".tmp", "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(_SO + ".tmp", _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    _lib = configure(ctypes.CDLL(_SO))
+    return _lib
+
+
+def configure(lib):
+    """Declare the C signatures on a loaded oracle library."""
+    lib.or_gll.argtypes = [ctypes.c_int, _dp, _dp]
+    lib.or_dmat.argtypes = [ctypes.c_int, _dp, _dp]
+    lib.or_setup.restype = ctypes.c_void_p
+    lib.or_setup.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _i64p, _u8p, _dp]
+    lib.or_free.argtypes = [ctypes.c_void_p]
+    lib.or_n_local.restype = ctypes.c_int64
+    lib.or_n_local.argtypes = [ctypes.c_void_p]
+    lib.or_n_unique.restype = ctypes.c_int64
+    lib.or_n_unique.argtypes = [ctypes.c_void_p]
+    for name in ("or_get_mult", "or_get_minv", "or_get_dmat"):
+        getattr(lib, name).argtypes = [ctypes.c_void_p, _dp]
+    lib.or_get_geom.argtypes = [ctypes.c_void_p, _dp, _dp]
+    lib.or_ax_local.argtypes = [ctypes.c_void_p, _dp, _dp]
+    lib.or_ax.argtypes = [ctypes.c_void_p, _dp, _dp]
+    lib.or_gs.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int]
+    lib.or_mass.argtypes = [ctypes.c_void_p, _dp, _dp, ctypes.c_int]
+    lib.or_dot.restype = ctypes.c_double
+    lib.or_dot.argtypes = [ctypes.c_void_p, _dp, _dp]
+    lib.or_pcg.restype = ctypes.c_int
+    lib.or_pcg.argtypes = [ctypes.c_void_p, _dp, _dp, ctypes.c_double, ctypes.c_int, _ip, _dp, _dp]
+    lib.or_ir.restype = ctypes.c_int
+    lib.or_ir.argtypes = [ctypes.c_void_p, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                          ctypes.c_int, ctypes.c_int, _ip, _ip, _dp, _dp]
+    lib.or_threads.restype = ctypes.c_int
+    return lib
+
+
+def _d(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dp)
+
+
+def threads() -> int:
+    """OpenMP threads the oracle's element loops use."""
+    return _load().or_threads()
+
+
+def gll(N: int):
+    """GLL nodes and weights of order N (Newton on P_N', long double)."""
+    lib = _load()
+    xi = np.zeros(N + 1)
+    rho = np.zeros(N + 1)
+    lib.or_gll(N, _d(xi), _d(rho))
+    return xi, rho
+
+
+def dmat(N: int, xi: np.ndarray | None = None) -> np.ndarray:
+    """Derivative matrix D[i, j] = l_j'(xi_i)."""
+    lib = _load()
+    if xi is None:
+        xi, _ = gll(N)
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    D = np.zeros((N + 1, N + 1))
+    lib.or_dmat(N, _d(xi), _d(D))
+    return D
+
+
+class Problem:
+    """The discrete Poisson problem of one mesh, held by the C oracle."""
+
+    def __init__(self, mesh, h1: np.ndarray | None = None):
+        lib = _load()
+        self.lib = lib
+        self.mesh = mesh
+        self.E, self.lx = mesh.E, mesh.lx
+        coords = np.ascontiguousarray(mesh.coords, dtype=np.float64)
+        gid = np.ascontiguousarray(mesh.gid, dtype=np.int64)
+        mask = np.ascontiguousarray(mesh.mask, dtype=np.uint8)
+        self._h1 = None if h1 is None else np.ascontiguousarray(h1, dtype=np.float64)
+        self.h = lib.or_setup(mesh.E, mesh.lx, _d(coords), gid.ctypes.data_as(_i64p),
+                              mask.ctypes.data_as(_u8p),
+                              None if self._h1 is None else _d(self._h1))
+        if not self.h:
+            raise ValueError("oracle set-up rejected the mesh (J <= 0, lx out of range or "
+                             "mask differing between copies of a node)")
+        self.n = int(lib.or_n_local(self.h))
+        self.n_unique = int(lib.or_n_unique(self.h))
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.lib.or_free(h)
+            self.h = None
+
+    # set-up data --------------------------------------------------------
+    def geom(self):
+        G = np.zeros((6, self.n))
+        B = np.zeros(self.n)
+        self.lib.or_get_geom(self.h, _d(G), _d(B))
+        return G, B
+
+    def mult(self):
+        m = np.zeros(self.n)
+        self.lib.or_get_mult(self.h, _d(m))
+        return m
+
+    def minv(self):
+        m = np.zeros(self.n)
+        self.lib.or_get_minv(self.h, _d(m))
+        return m
+
+    def dmat(self):
+        D = np.zeros((self.lx, self.lx))
+        self.lib.or_get_dmat(self.h, _d(D))
+        return D
+
+    # operators ----------------------------------------------------------
+    def ax_local(self, u):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        w = np.zeros(self.n)
+        self.lib.or_ax_local(self.h, _d(u), _d(w))
+        return w
+
+    def ax(self, u):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        w = np.zeros(self.n)
+        self.lib.or_ax(self.h, _d(u), _d(w))
+        return w
+
+    def gs(self, u, mask: bool = True):
+        w = np.array(u, dtype=np.float64, copy=True)
+        self.lib.or_gs(self.h, _d(w), 1 if mask else 0)
+        return w
+
+    def mass(self, u, assemble: bool = True):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        w = np.zeros(self.n)
+        self.lib.or_mass(self.h, _d(u), _d(w), 1 if assemble else 0)
+        return w
+
+    def dot(self, a, b) -> float:
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        return float(self.lib.or_dot(self.h, _d(a), _d(b)))
+
+    # solvers ------------------------------------------------------------
+    def pcg(self, b, x0=None, tol: float = 1e-10, max_iter: int = 100000, hist: bool = False):
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros(self.n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        h = np.zeros(max_iter) if hist else None
+        st = self.lib.or_pcg(self.h, _d(b), _d(x), tol, max_iter, ctypes.byref(it),
+                             ctypes.byref(rr), None if h is None else _d(h))
+        info = dict(status=int(st), iters=int(it.value), relres=float(rr.value))
+        if hist:
+            info["hist"] = h[: it.value]
+        return x, info
+
+    def ir(self, b, x0=None, tol: float = 1e-10, inner_tol: float = 1e-5, max_outer: int = 50,
+           max_inner: int = 100000):
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros(self.n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+        oi = ctypes.c_int(0)
+        ii = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        hist = np.zeros(max_outer + 1)
+        st = self.lib.or_ir(self.h, _d(b), _d(x), tol, inner_tol, max_outer, max_inner,
+                            ctypes.byref(oi), ctypes.byref(ii), ctypes.byref(rr), _d(hist))
+        return x, dict(status=int(st), outer=int(oi.value), inner=int(ii.value),
+                       relres=float(rr.value), outer_hist=hist[: oi.value])
