@@ -1,0 +1,218 @@
+/*
+ * sem.h -- C ABI of libsem, a GB300 (sm_103a) library for the
+ * spectral-element pressure-Poisson solve of Karp et al., "Large-Scale Direct
+ * Numerical Simulations of Turbulence Using GPUs and Modern Fortran"
+ * (arXiv 2207.07098).
+ *
+ * The library solves  mask * QQ^T A_L x = b  where
+ *   A_L   is the block-diagonal matrix of the element operators
+ *         A^e = D^T G^e D, scaled by a coefficient h1 at every quadrature
+ *         point (Sec. II-A, eq. "disclap" and the definitions of D and G^e
+ *         below it; h1 as in the Helmholtz operator of the same section),
+ *   QQ^T  is the gather-scatter (direct-stiffness summation) over nodes that
+ *         several elements share (Sec. II-A, "QQ^T A_L u_L = A u_L"),
+ *   mask  zeroes homogeneous Dirichlet nodes,
+ * with Jacobi-preconditioned conjugate gradients (Sec. II-B, P-CG), in FP64
+ * or with FP64 iterative refinement around an FP32 inner CG.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Local vectors have n_L = E * lx^3 entries in element-major layout
+ *   [e][k][j][i] (i fastest), lx = N + 1 GLL points per direction.  For a
+ *   batch handle, the local vectors of all solves are concatenated in solve
+ *   order.
+ * - Vector arguments of sem_ax, sem_gs, sem_mass, sem_dot and the getters are
+ *   DEVICE pointers (e.g. torch tensors' data_ptr()) of the element type that
+ *   the precision argument names (double for SEM_FP64, float otherwise),
+ *   16-byte aligned.  sem_cg_solve and sem_cg_solve_batch accept host or
+ *   device pointers for x and b (host buffers are copied in and out inside
+ *   the call).  Set-up arrays (coordinates, ids, mask, h1) are HOST pointers.
+ * - The caller owns every pointer it passes; the handle owns everything the
+ *   library allocates (geometric factors, preconditioner, gather-scatter
+ *   lists, solver work vectors) and sem_destroy frees it.
+ * - All work is enqueued on the given stream (0 = legacy default stream).
+ *   Calls that return results to the host (sem_cg_solve*) synchronise it.
+ * - Every call returns a sem_status.  On failure sem_last_error() returns a
+ *   message for the calling thread.  A handle is not thread-safe: calls on
+ *   one handle must be serialised by the caller.
+ */
+#ifndef SEM_H
+#define SEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SEM_API __attribute__((visibility("default")))
+
+/* Opaque handle: one mesh (sem_setup) or a batch of meshes (sem_setup_batch)
+ * with everything the library derived from it. */
+typedef struct sem_handle sem_handle;
+
+typedef enum sem_status {
+    SEM_OK = 0,
+    SEM_EINVAL = 1,       /* bad argument, mesh or alignment */
+    SEM_ENOMEM = 2,       /* device or host allocation failed */
+    SEM_ECUDA = 3,        /* a CUDA runtime call failed */
+    SEM_ENOTCONV = 4,     /* max iterations reached; outputs are valid iterates */
+    SEM_EBREAKDOWN = 5,   /* p^T A p <= 0 or a non-finite scalar in CG */
+    SEM_ESTAGNATE = 6,    /* refinement step failed to halve the FP64 residual */
+    SEM_ETIMEOUT = 7      /* a bounded device-side wait expired */
+} sem_status;
+
+/* Arithmetic of one operator application or of the inner solve. */
+typedef enum sem_precision {
+    SEM_FP64 = 0,        /* double data, FP64-accurate arithmetic */
+    SEM_FP32 = 1,        /* float data, FP32 arithmetic and accumulation */
+    SEM_FP64_NATIVE = 2  /* double data, plain FP64 CUDA-core arithmetic */
+} sem_precision;
+
+typedef enum sem_solve_mode {
+    SEM_MODE_FP64 = 0,     /* plain FP64 Jacobi-PCG */
+    SEM_MODE_MIXED_IR = 1  /* FP64 refinement around an FP32 inner Jacobi-PCG */
+} sem_solve_mode;
+
+typedef struct sem_info {
+    int nsolve;              /* 1 for sem_setup, number of meshes for a batch */
+    int E;                   /* elements (sum over the batch) */
+    int lx;                  /* points per direction (0 for a mixed-order batch) */
+    int64_t n_local;         /* local points E * lx^3 (sum over the batch) */
+    int64_t n_unique;        /* distinct global nodes */
+    int64_t n_free;          /* distinct global nodes with mask = 1 */
+    int64_t n_shared;        /* local points that belong to a node with >= 2 copies */
+    size_t device_bytes;     /* device memory held by the handle */
+} sem_info;
+
+typedef struct sem_solve_opts {
+    double tol;          /* relative residual ||b - A x|| / ||b|| to reach (1e-10) */
+    int max_iter;        /* max CG iterations (FP64 mode) or inner iterations per
+                            refinement step (mixed mode) */
+    int mode;            /* sem_solve_mode */
+    double inner_tol;    /* mixed mode: inner relative tolerance (1e-5) */
+    int max_outer;       /* mixed mode: max refinement steps (30) */
+    int precision;       /* FP64 mode: SEM_FP64 or SEM_FP64_NATIVE operator */
+    int use_graph;       /* capture the CG iterations in CUDA graphs (1) */
+    int graph_chunk;     /* CG iterations per graph launch between host checks (32) */
+} sem_solve_opts;
+
+typedef struct sem_solve_stats {
+    int status;               /* sem_status of this solve */
+    int iterations;           /* CG iterations (all inner iterations in mixed mode) */
+    int outer_iterations;     /* refinement steps (0 in FP64 mode) */
+    double relres;            /* TRUE residual ||b - A x|| / ||b||, recomputed in FP64 */
+    double relres_recursive;  /* last recursive residual estimate of the CG loop */
+    double time_ms;           /* device time of the solve (CUDA events) */
+} sem_solve_stats;
+
+/* Mesh of one member of a batch (host pointers; see sem_setup). */
+typedef struct sem_mesh_desc {
+    int E;
+    int lx;
+    const double* coords;   /* [3][E][lx^3] */
+    const int64_t* gid;     /* [E lx^3] */
+    const uint8_t* mask;    /* [E lx^3] */
+    const double* h1;       /* [E lx^3] or NULL for h1 = 1 */
+} sem_mesh_desc;
+
+/* Fill *opts with the defaults listed above. */
+SEM_API void sem_solve_opts_default(sem_solve_opts* opts);
+
+/* Message of the last failed call on this thread ("" if none). */
+SEM_API const char* sem_last_error(void);
+
+/* GLL nodes xi[lx], weights rho[lx] and derivative matrix D[lx*lx]
+ * (D[i*lx+j] = l_j'(xi_i)) on [-1,1] (Sec. II-A: GLL points xi_i and the
+ * differentiation matrix D).  Host pointers; any may be NULL.
+ * 2 <= lx <= 16, else SEM_EINVAL. */
+SEM_API int sem_gll(int lx, double* xi, double* rho, double* D);
+
+/* Build a handle for one mesh (Sec. II-A).
+ *   E       number of hexahedral elements (>= 1)
+ *   lx      points per direction, 2..16
+ *   coords  HOST [3][E][lx^3] node coordinates x, y, z
+ *   gid     HOST [E lx^3] global node ids: equal ids <=> same node (this is Q)
+ *   mask    HOST [E lx^3] 0 on homogeneous Dirichlet nodes, 1 elsewhere
+ *   h1      HOST [E lx^3] coefficient at every node, or NULL for h1 = 1
+ *   flags   0 (reserved)
+ * Computes on the device the geometric factors G_st = rho rho rho J
+ * sum_l dr_s/dx_l dr_t/dx_l (h1 folded in), the mass B = rho rho rho J and
+ * the Jacobi diagonal, and on the host the gather-scatter lists.
+ * Errors: SEM_EINVAL for bad sizes, a mask that differs between copies of
+ * a node, or a non-positive Jacobian; SEM_ENOMEM; SEM_ECUDA.  On error *h is
+ * NULL and nothing is leaked.  Synchronises the stream. */
+SEM_API int sem_setup(sem_handle** h, int E, int lx, const double* coords,
+                      const int64_t* gid, const uint8_t* mask, const double* h1,
+                      int flags, cudaStream_t stream);
+
+/* Build one handle for nsolve independent meshes (orders may differ).
+ * Global ids are local to each mesh.  Same errors as sem_setup. */
+SEM_API int sem_setup_batch(sem_handle** h, int nsolve, const sem_mesh_desc* meshes,
+                            int flags, cudaStream_t stream);
+
+/* Free everything the handle owns.  NULL is accepted. */
+SEM_API int sem_destroy(sem_handle* h);
+
+/* Sizes and memory of a handle. */
+SEM_API int sem_get_info(const sem_handle* h, sem_info* info);
+
+/* Per-solve local offsets of a batch handle: offsets[s] = first local index
+ * of solve s, offsets[nsolve] = n_local (host array of nsolve+1 entries). */
+SEM_API int sem_get_offsets(const sem_handle* h, int64_t* offsets);
+
+/* w = A_L u (assemble = 0) or w = mask * QQ^T A_L u (assemble = 1)
+ * (Sec. II-A, eq. disclap and A = QQ^T A_L).  u, w: device [n_local] of the
+ * precision's type; w must not alias u. */
+SEM_API int sem_ax(sem_handle* h, void* w, const void* u, int precision, int assemble,
+                   cudaStream_t stream);
+
+/* u <- QQ^T u in place, then u <- mask * u if apply_mask (Sec. II-A).  Copies
+ * of a node are summed in ascending local index, so the result is
+ * bit-reproducible.  u: device [n_local], double (SEM_FP64*) or float. */
+SEM_API int sem_gs(sem_handle* h, void* u, int precision, int apply_mask, cudaStream_t stream);
+
+/* w = B u (diagonal mass, B = rho rho rho J), then mask * QQ^T if assemble.
+ * Used to form right-hand sides b = mask QQ^T (B f). */
+SEM_API int sem_mass(sem_handle* h, void* w, const void* u, int precision, int assemble,
+                     cudaStream_t stream);
+
+/* result[0] = <a, b> over unique nodes = sum_L a_L b_L / mult_L, accumulated
+ * in FP64 in a fixed order (deterministic).  a, b: device double [n_local];
+ * result: device double[1] (batch handle: double[nsolve], one per solve). */
+SEM_API int sem_dot(sem_handle* h, const double* a, const double* b, double* result,
+                    cudaStream_t stream);
+
+/* Copies of set-up data (device outputs):
+ *   G  [E][6][lx^3] factors h1*G11, h1*G12, h1*G13, h1*G22, h1*G23, h1*G33
+ *   B  [n_local] mass rho rho rho J
+ * Either pointer may be NULL.  Single-mesh handles only. */
+SEM_API int sem_get_geometry(const sem_handle* h, double* G, double* B, cudaStream_t stream);
+
+/* Jacobi preconditioner Minv = mask / (QQ^T diag(A_L)) (device double [n_local]). */
+SEM_API int sem_get_jacobi(const sem_handle* h, double* minv, cudaStream_t stream);
+
+/* Solve mask QQ^T A_L x = b with Jacobi-PCG (Sec. II-B) or mixed-precision
+ * refinement.  x: [n_local] initial guess in, solution out; b: [n_local]
+ * assembled right-hand side (equal on all copies of a node, 0 on Dirichlet
+ * nodes).  Host or device pointers.  opts NULL = defaults; stats may be NULL.
+ * Returns SEM_OK, SEM_ENOTCONV, SEM_EBREAKDOWN or SEM_ESTAGNATE (x holds the
+ * last iterate), or an error.  Synchronises the stream. */
+SEM_API int sem_cg_solve(sem_handle* h, double* x, const double* b, const sem_solve_opts* opts,
+                         sem_solve_stats* stats, cudaStream_t stream);
+
+/* All solves of a batch handle at once: x, b concatenated [n_local];
+ * stats: host array of nsolve entries (may be NULL).  Every CG iteration
+ * advances all unconverged solves with one set of launches.  Returns the
+ * worst status over the batch. */
+SEM_API int sem_cg_solve_batch(sem_handle* h, double* x, const double* b,
+                               const sem_solve_opts* opts, sem_solve_stats* stats,
+                               cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEM_H */

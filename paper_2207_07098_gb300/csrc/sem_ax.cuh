@@ -1,0 +1,198 @@
+// Template of the matrix-free local operator kernels (see sem_ax.cu for the
+// description); instantiated per precision in sem_ax_f64.cu and sem_ax_f32.cu.
+#pragma once
+
+#include <algorithm>
+
+#include "sem_device.cuh"
+#include "sem_internal.h"
+
+namespace sem {
+
+template <int LX>
+struct AxCfg {
+    static constexpr int N2 = LX * LX;
+    static constexpr int N3 = LX * LX * LX;
+    static constexpr int EPC = (256 / N2) > 0 ? (256 / N2) : 1;
+    static constexpr int USED = EPC * N2;
+    static constexpr int THREADS = ((USED + 31) / 32) * 32;
+    static constexpr int DP = LX + 1;  // padded row of D in shared memory
+};
+
+template <typename T>
+struct AxParams {
+    const T* u;   // input (plain variant)
+    T* w;         // output
+    const T* G;   // [E][6][lx^3], h1 folded in
+    const T* D;   // [lx][lx]
+    int64_t E;
+    // fused CG variant: u = z + beta p, p <- u, partial <p, w>
+    const T* z;
+    T* p;
+    CGState* st;
+    double* partials;
+    unsigned int* counter;
+    int dry;  // 1: only prepare the kernel (attributes, occupancy); no launch
+};
+
+template <typename T, int LX>
+constexpr size_t ax_smem_bytes() {
+    return sizeof(T) * ((size_t)LX * AxCfg<LX>::DP + 3 * (size_t)AxCfg<LX>::EPC * AxCfg<LX>::N3);
+}
+
+template <typename T, int LX, bool FUSED>
+__global__ void __launch_bounds__(AxCfg<LX>::THREADS) ax_kernel(AxParams<T> a) {
+    using C = AxCfg<LX>;
+    constexpr int N2 = C::N2, N3 = C::N3, EPC = C::EPC, DP = C::DP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sD = reinterpret_cast<T*>(smem_raw);
+    T* su = sD + LX * DP;
+    T* sr = su + EPC * N3;
+    T* ss = sr + EPC * N3;
+
+    double beta = 0.0;
+    bool first = false;
+    if (FUSED) {
+        if (a.st->done) return;  // uniform over the grid
+        beta = cg_beta(a.st);
+        first = (a.st->iter == 0);
+    }
+    for (int t = threadIdx.x; t < LX * LX; t += blockDim.x) sD[(t / LX) * DP + (t % LX)] = a.D[t];
+
+    const int tid = threadIdx.x;
+    const int el = tid / N2;
+    const int ij = tid - el * N2;
+    const int i = ij % LX, j = ij / LX;
+    const bool active = el < EPC;
+    const int so = (active ? el : 0) * N3;  // this thread's element slot in shared memory
+    const int64_t ngroups = (a.E + EPC - 1) / EPC;
+    double pap = 0.0;
+    const T tbeta = (T)beta;
+    __syncthreads();
+
+    for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
+        const int64_t e = g * EPC + el;
+        const bool valid = active && e < a.E;
+        const int64_t base = e * N3 + ij;
+        T ucol[LX];
+#pragma unroll
+        for (int k = 0; k < LX; k++) {
+            T v = T(0);
+            if (valid) {
+                if (FUSED) {
+                    const T zz = ld_stream(a.z + base + k * N2);
+                    const T pp = first ? T(0) : a.p[base + k * N2];
+                    v = fma(tbeta, pp, zz);
+                    a.p[base + k * N2] = v;
+                } else {
+                    v = ld_stream(a.u + base + k * N2);
+                }
+            }
+            ucol[k] = v;
+            if (active) su[so + k * N2 + ij] = v;
+        }
+        __syncthreads();
+        T wt[LX];
+        const T* Ge = a.G + e * 6 * N3 + ij;
+#pragma unroll
+        for (int k = 0; k < LX; k++) {
+            T ur = T(0), us = T(0), ut = T(0);
+#pragma unroll
+            for (int l = 0; l < LX; l++) {
+                ur = fma(sD[i * DP + l], su[so + k * N2 + j * LX + l], ur);
+                us = fma(sD[j * DP + l], su[so + k * N2 + l * LX + i], us);
+                ut = fma(sD[k * DP + l], ucol[l], ut);
+            }
+            T g11 = T(0), g12 = T(0), g13 = T(0), g22 = T(0), g23 = T(0), g33 = T(0);
+            if (valid) {
+                g11 = ld_stream(Ge + 0 * N3 + k * N2);
+                g12 = ld_stream(Ge + 1 * N3 + k * N2);
+                g13 = ld_stream(Ge + 2 * N3 + k * N2);
+                g22 = ld_stream(Ge + 3 * N3 + k * N2);
+                g23 = ld_stream(Ge + 4 * N3 + k * N2);
+                g33 = ld_stream(Ge + 5 * N3 + k * N2);
+            }
+            const T wr = fma(g11, ur, fma(g12, us, g13 * ut));
+            const T ws = fma(g12, ur, fma(g22, us, g23 * ut));
+            wt[k] = fma(g13, ur, fma(g23, us, g33 * ut));
+            if (active) {
+                sr[so + k * N2 + ij] = wr;
+                ss[so + k * N2 + ij] = ws;
+            }
+        }
+        __syncthreads();
+        T pw = T(0);
+#pragma unroll
+        for (int k = 0; k < LX; k++) {
+            T acc = T(0);
+#pragma unroll
+            for (int l = 0; l < LX; l++) {
+                acc = fma(sD[l * DP + i], sr[so + k * N2 + j * LX + l], acc);
+                acc = fma(sD[l * DP + j], ss[so + k * N2 + l * LX + i], acc);
+                acc = fma(sD[l * DP + k], wt[l], acc);
+            }
+            if (valid) {
+                st_stream(a.w + base + k * N2, acc);
+                if (FUSED) pw = fma(ucol[k], acc, pw);
+            }
+        }
+        if (FUSED) pap += (double)pw;
+        __syncthreads();
+    }
+    if (FUSED) {
+        double v[1] = {pap};
+        CGState* st = a.st;
+        grid_sum_finalize<1>(v, a.partials, a.counter, [&](double (&acc)[1]) { cg_set_alpha(st, acc[0]); });
+    }
+}
+
+template <typename T, int LX, bool FUSED>
+inline int launch_ax_t(sem_handle* h, const AxParams<T>& a, cudaStream_t s) {
+    using C = AxCfg<LX>;
+    constexpr size_t smem = ax_smem_bytes<T, LX>();
+    static int per_sm = -1;  // occupancy of this instantiation (same device for the process)
+    if (per_sm < 0) {
+        cudaFuncSetAttribute(ax_kernel<T, LX, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ax_kernel<T, LX, FUSED>, C::THREADS, smem);
+        per_sm = nb > 0 ? nb : 1;
+    }
+    if (a.dry) return SEM_OK;
+    const int64_t ngroups = (a.E + C::EPC - 1) / C::EPC;
+    int64_t grid = std::min<int64_t>(ngroups, (int64_t)h->sm_count * per_sm);
+    grid = std::max<int64_t>(1, std::min<int64_t>(grid, kMaxPartials));
+    ax_kernel<T, LX, FUSED><<<(int)grid, C::THREADS, smem, s>>>(a);
+    SEM_LAUNCH_CHECK("ax_kernel");
+    return SEM_OK;
+}
+
+template <typename T, bool FUSED>
+inline int dispatch_ax(sem_handle* h, int lx, const AxParams<T>& a, cudaStream_t s) {
+    switch (lx) {
+        case 2: return launch_ax_t<T, 2, FUSED>(h, a, s);
+        case 3: return launch_ax_t<T, 3, FUSED>(h, a, s);
+        case 4: return launch_ax_t<T, 4, FUSED>(h, a, s);
+        case 5: return launch_ax_t<T, 5, FUSED>(h, a, s);
+        case 6: return launch_ax_t<T, 6, FUSED>(h, a, s);
+        case 7: return launch_ax_t<T, 7, FUSED>(h, a, s);
+        case 8: return launch_ax_t<T, 8, FUSED>(h, a, s);
+        case 9: return launch_ax_t<T, 9, FUSED>(h, a, s);
+        case 10: return launch_ax_t<T, 10, FUSED>(h, a, s);
+        case 11: return launch_ax_t<T, 11, FUSED>(h, a, s);
+        case 12: return launch_ax_t<T, 12, FUSED>(h, a, s);
+        case 13: return launch_ax_t<T, 13, FUSED>(h, a, s);
+        case 14: return launch_ax_t<T, 14, FUSED>(h, a, s);
+        case 15: return launch_ax_t<T, 15, FUSED>(h, a, s);
+        case 16: return launch_ax_t<T, 16, FUSED>(h, a, s);
+        default: return fail(SEM_EINVAL, "lx out of range");
+    }
+}
+
+
+// per-precision entry points (sem_ax_f64.cu, sem_ax_f32.cu)
+int dispatch_ax_f64(sem_handle* h, int lx, const AxParams<double>& a, bool fused, cudaStream_t s);
+int dispatch_ax_f64_plain(sem_handle* h, int lx, const AxParams<double>& a, cudaStream_t s);
+int dispatch_ax_f32_plain(sem_handle* h, int lx, const AxParams<float>& a, cudaStream_t s);
+int dispatch_ax_f32(sem_handle* h, int lx, const AxParams<float>& a, bool fused, cudaStream_t s);
+
+}  // namespace sem

@@ -1,0 +1,411 @@
+// Jacobi-preconditioned conjugate gradients (Sec. II-B of Karp et al.) and
+// FP64 iterative refinement around an FP32 inner CG.
+//
+// One CG iteration is three launches, captured in CUDA graphs:
+//   K-A  p = z + beta p;  w = A_L p;  alpha = rho / <p, w>     (sem_ax.cu)
+//   K-B  w = mask QQ^T w                                       (sem_gs.cu)
+//   K-C  x += alpha p;  r -= alpha w;  z = Minv r;  rho = <r, z>, rr = <r, r>
+// The scalars live in device memory (CGState) and are produced by the last
+// CTA of each reducing launch in a fixed order, so a solve is bit-reproducible.
+// Each launch returns at once when the solve is already done, so a graph of
+// several iterations can run past convergence without changing the result;
+// the host reads the state between graph launches.
+#include <cmath>
+#include <cstring>
+
+#include "sem_device.cuh"
+#include "sem_internal.h"
+
+namespace sem {
+
+template <typename T>
+struct VecT;
+template <>
+struct VecT<double> {
+    using V = double2;
+    using M = uchar2;
+    static constexpr int W = 2;
+};
+template <>
+struct VecT<float> {
+    using V = float4;
+    using M = uchar4;
+    static constexpr int W = 4;
+};
+
+template <typename T>
+struct UpdParams {
+    T* x;
+    const T* p;
+    T* r;
+    const T* w;
+    T* z;
+    const T* minv;
+    const uint8_t* mult;
+    int64_t n;
+    CGState* st;
+    double* partials;
+    unsigned int* counter;
+};
+
+template <typename T>
+__device__ __forceinline__ void upd_point(T& x, T p, T& r, T w, T& z, T mi, T inv, T ta, T& rz, T& rr) {
+    x = fma(ta, p, x);
+    r = fma(-ta, w, r);
+    z = mi * r;
+    rz = fma(r * z, inv, rz);
+    rr = fma(r * r, inv, rr);
+}
+
+// K-C: x += alpha p; r -= alpha w; z = Minv r; partial sums of <r,z>, <r,r>
+// (weights 1/mult).  Per-thread sums of W points in T, then FP64.
+template <typename T>
+__global__ void __launch_bounds__(256) cg_update_kernel(UpdParams<T> a) {
+    using VT = VecT<T>;
+    using V = typename VT::V;
+    using M = typename VT::M;
+    constexpr int W = VT::W;
+    if (a.st->done) return;
+    const T ta = (T)a.st->alpha;
+    __shared__ T inv[256];
+    for (int m = threadIdx.x; m < 256; m += blockDim.x) inv[m] = m ? (T)(1.0 / m) : T(0);
+    __syncthreads();
+    double rz = 0.0, rr = 0.0;
+    const int64_t nv = a.n / W;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv; q += (int64_t)gridDim.x * blockDim.x) {
+        V x = reinterpret_cast<const V*>(a.x)[q];
+        const V p = ld_stream(reinterpret_cast<const V*>(a.p) + q);
+        V r = reinterpret_cast<const V*>(a.r)[q];
+        const V w = ld_stream(reinterpret_cast<const V*>(a.w) + q);
+        const V mi = ld_stream(reinterpret_cast<const V*>(a.minv) + q);
+        const M mu = reinterpret_cast<const M*>(a.mult)[q];
+        V z;
+        T lrz = T(0), lrr = T(0);
+        T* xs = reinterpret_cast<T*>(&x);
+        const T* ps = reinterpret_cast<const T*>(&p);
+        T* rs = reinterpret_cast<T*>(&r);
+        const T* ws = reinterpret_cast<const T*>(&w);
+        const T* ms = reinterpret_cast<const T*>(&mi);
+        T* zs = reinterpret_cast<T*>(&z);
+        const unsigned char* us = reinterpret_cast<const unsigned char*>(&mu);
+#pragma unroll
+        for (int c = 0; c < W; c++) upd_point<T>(xs[c], ps[c], rs[c], ws[c], zs[c], ms[c], inv[us[c]], ta, lrz, lrr);
+        reinterpret_cast<V*>(a.x)[q] = x;
+        reinterpret_cast<V*>(a.r)[q] = r;
+        reinterpret_cast<V*>(a.z)[q] = z;
+        rz += (double)lrz;
+        rr += (double)lrr;
+    }
+    if (blockIdx.x == 0) {  // scalar tail
+        for (int64_t L = nv * W + threadIdx.x; L < a.n; L += blockDim.x) {
+            T x = a.x[L], r = a.r[L], z;
+            T lrz = T(0), lrr = T(0);
+            upd_point<T>(x, a.p[L], r, a.w[L], z, a.minv[L], inv[a.mult[L]], ta, lrz, lrr);
+            a.x[L] = x;
+            a.r[L] = r;
+            a.z[L] = z;
+            rz += (double)lrz;
+            rr += (double)lrr;
+        }
+    }
+    double v[2] = {rz, rr};
+    CGState* st = a.st;
+    grid_sum_finalize<2>(v, a.partials, a.counter, [&](double (&acc)[2]) { cg_set_rho(st, acc[0], acc[1]); });
+}
+
+// CG start: z = Minv r; rho = <r,z>, rr = <r,r>, bb = <b,b>; state reset.
+template <typename T>
+__global__ void __launch_bounds__(256) cg_init_kernel(const T* __restrict__ b, const T* __restrict__ r,
+                                                      T* __restrict__ z, const T* __restrict__ minv,
+                                                      const uint8_t* __restrict__ mult, int64_t n, double tol,
+                                                      int max_iter, CGState* st, double* partials,
+                                                      unsigned int* counter) {
+    __shared__ double inv[256];
+    for (int m = threadIdx.x; m < 256; m += blockDim.x) inv[m] = m ? 1.0 / m : 0.0;
+    __syncthreads();
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < n; L += (int64_t)gridDim.x * blockDim.x) {
+        const double rv = (double)r[L];
+        const T zv = minv[L] * r[L];
+        z[L] = zv;
+        const double iv = inv[mult[L]];
+        v[0] = fma(rv * (double)zv, iv, v[0]);
+        v[1] = fma(rv * rv, iv, v[1]);
+        const double bv = (double)b[L];
+        v[2] = fma(bv * bv, iv, v[2]);
+    }
+    grid_sum_finalize<3>(v, partials, counter, [&](double (&acc)[3]) {
+        st->rho = acc[0];
+        st->rho_old = 1.0;
+        st->rr = acc[1];
+        st->bb = acc[2];
+        st->tol2 = tol * tol * acc[2];
+        st->alpha = 0.0;
+        st->pap = 0.0;
+        st->iter = 0;
+        st->max_iter = max_iter;
+        const bool conv = (acc[2] == 0.0 || acc[1] <= st->tol2);
+        st->done = (conv || max_iter <= 0) ? 1 : 0;
+        st->status = (conv || max_iter > 0) ? SEM_OK : SEM_ENOTCONV;
+    });
+}
+
+// r = b - w (FP64), out[0] = <r, r>, out[1] = <b, b>
+__global__ void __launch_bounds__(256) resid_kernel(const double* __restrict__ b, const double* __restrict__ w,
+                                                    double* __restrict__ r, const uint8_t* __restrict__ mult,
+                                                    int64_t n, double* partials, unsigned int* counter,
+                                                    double* out) {
+    __shared__ double inv[256];
+    for (int m = threadIdx.x; m < 256; m += blockDim.x) inv[m] = m ? 1.0 / m : 0.0;
+    __syncthreads();
+    double v[2] = {0.0, 0.0};
+    for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < n; L += (int64_t)gridDim.x * blockDim.x) {
+        const double bv = b[L];
+        const double rv = bv - w[L];
+        r[L] = rv;
+        const double iv = inv[mult[L]];
+        v[0] = fma(rv * rv, iv, v[0]);
+        v[1] = fma(bv * bv, iv, v[1]);
+    }
+    grid_sum_finalize<2>(v, partials, counter, [&](double (&acc)[2]) {
+        out[0] = acc[0];
+        out[1] = acc[1];
+    });
+}
+
+// Refinement: b32 = r32 = float(r / ||r||), d32 = 0 (||r||^2 in rr_in[0]).
+__global__ void ir_prepare_kernel(const double* __restrict__ r, const double* rr_in, float* __restrict__ b32,
+                                  float* __restrict__ r32, float* __restrict__ d32, int64_t n) {
+    const double s = 1.0 / sqrt(rr_in[0]);
+    for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < n; L += (int64_t)gridDim.x * blockDim.x) {
+        const float v = (float)(r[L] * s);
+        b32[L] = v;
+        r32[L] = v;
+        d32[L] = 0.0f;
+    }
+}
+
+// Refinement: x += ||r|| d32
+__global__ void ir_correct_kernel(double* __restrict__ x, const float* __restrict__ d32, const double* rr_in,
+                                  int64_t n) {
+    const double s = sqrt(rr_in[0]);
+    for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < n; L += (int64_t)gridDim.x * blockDim.x)
+        x[L] = fma(s, (double)d32[L], x[L]);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+int launch_cg_update(sem_handle* h, int precision, cudaStream_t s) {
+    const int grid = grid_for(h, h->n_local / 4 + 1, 256, 8);
+    if (precision == SEM_FP32) {
+        UpdParams<float> a = {h->ws.d32, h->ws.p32, h->ws.r32, h->ws.w32, h->ws.z32, h->minv32, h->mult,
+                              h->n_local, h->state + 1, h->partials, h->counters + 3};
+        cg_update_kernel<float><<<grid, 256, 0, s>>>(a);
+    } else {
+        UpdParams<double> a = {h->ws.x, h->ws.p, h->ws.r, h->ws.w, h->ws.z, h->minv64, h->mult,
+                               h->n_local, h->state, h->partials, h->counters + 3};
+        cg_update_kernel<double><<<grid, 256, 0, s>>>(a);
+    }
+    SEM_LAUNCH_CHECK("cg_update_kernel");
+    return SEM_OK;
+}
+
+static int launch_iteration(sem_handle* h, int precision, cudaStream_t s) {
+    int rc = launch_cg_pupdate_ax(h, precision, s);
+    if (!rc) rc = launch_gs(h, precision == SEM_FP32 ? (void*)h->ws.w32 : (void*)h->ws.w, precision == SEM_FP32,
+                            true, s);
+    if (!rc) rc = launch_cg_update(h, precision, s);
+    return rc;
+}
+
+static int get_graph(sem_handle* h, int precision, int chunk, cudaGraphExec_t* out) {
+    GraphCache& g = h->graph;
+    if (g.exec && g.key_prec == precision && g.key_chunk == chunk) {
+        *out = g.exec;
+        return SEM_OK;
+    }
+    if (g.exec) {
+        cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+    }
+    if (!h->capture_stream) SEM_CUDA_TRY(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+    int prc = prepare_cg_kernels(h);
+    if (prc) return prc;
+    cudaStream_t cs = h->capture_stream;
+    SEM_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int rc = SEM_OK;
+    for (int it = 0; it < chunk && rc == SEM_OK; it++) rc = launch_iteration(h, precision, cs);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        g.exec = nullptr;
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    g.key_prec = precision;
+    g.key_chunk = chunk;
+    *out = g.exec;
+    return SEM_OK;
+}
+
+// Run CG iterations on state slot `slot` until done.  Returns SEM_OK or an
+// error; the solve status is in the state.
+static int run_cg_loop(sem_handle* h, int precision, const sem_solve_opts& o, int slot, cudaStream_t s,
+                       CGState* out) {
+    const int chunk = std::max(1, std::min(o.graph_chunk, 1024));
+    cudaGraphExec_t exec = nullptr;
+    if (o.use_graph) {
+        int rc = get_graph(h, precision, chunk, &exec);
+        if (rc) return rc;
+    }
+    SEM_CUDA_TRY(cudaMemcpyAsync(out, h->state + slot, sizeof(CGState), cudaMemcpyDeviceToHost, s));
+    SEM_CUDA_TRY(cudaStreamSynchronize(s));
+    const int64_t max_rounds = (int64_t)out->max_iter / chunk + 3;
+    for (int64_t round = 0; !out->done && round < max_rounds; round++) {
+        if (exec) {
+            SEM_CUDA_TRY(cudaGraphLaunch(exec, s));
+        } else {
+            for (int it = 0; it < chunk; it++) {
+                int rc = launch_iteration(h, precision, s);
+                if (rc) return rc;
+            }
+        }
+        SEM_CUDA_TRY(cudaMemcpyAsync(out, h->state + slot, sizeof(CGState), cudaMemcpyDeviceToHost, s));
+        SEM_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    if (!out->done) return fail(SEM_ETIMEOUT, "CG loop did not finish within its iteration budget");
+    return SEM_OK;
+}
+
+// rr_bb[0] = ||b - A x||^2, rr_bb[1] = ||b||^2 (unique-node norm), r = b - A x
+static int true_residual(sem_handle* h, const double* x, const double* b, double* rr_bb, cudaStream_t s) {
+    int rc = launch_ax_local(h, x, h->ws.w, SEM_FP64, s);
+    if (!rc) rc = launch_gs(h, h->ws.w, false, true, s);
+    if (rc) return rc;
+    resid_kernel<<<grid_for(h, h->n_local, 256, 4), 256, 0, s>>>(b, h->ws.w, h->ws.r, h->mult, h->n_local,
+                                                                 h->partials, h->counters + 4, rr_bb);
+    SEM_LAUNCH_CHECK("resid_kernel");
+    return SEM_OK;
+}
+
+static bool is_host_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+static int solve_single(sem_handle* h, double* x_user, const double* b_user, const sem_solve_opts& o,
+                        sem_solve_stats* stats, cudaStream_t s) {
+    int rc = ensure_workspace(h, o.mode == SEM_MODE_MIXED_IR);
+    if (rc) return rc;
+    const int64_t n = h->n_local;
+    const size_t bytes = sizeof(double) * n;
+    const bool xh = is_host_ptr(x_user), bh = is_host_ptr(b_user);
+    cudaEvent_t ev0, ev1;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    cudaEventRecord(ev0, s);
+    SEM_CUDA_TRY(cudaMemcpyAsync(h->ws.x, x_user, bytes, xh ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    SEM_CUDA_TRY(cudaMemcpyAsync(h->ws.b, b_user, bytes, bh ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    double* rrbb = h->scratch;  // [0] rr, [1] bb
+    sem_solve_stats st = {};
+    CGState hs;
+    int status = SEM_OK;
+    if (o.mode == SEM_MODE_FP64) {
+        const int prec = o.precision == SEM_FP64_NATIVE ? SEM_FP64_NATIVE : SEM_FP64;
+        if ((rc = true_residual(h, h->ws.x, h->ws.b, rrbb, s))) return rc;
+        cg_init_kernel<double><<<grid_for(h, n, 256, 4), 256, 0, s>>>(
+            h->ws.b, h->ws.r, h->ws.z, h->minv64, h->mult, n, o.tol, o.max_iter, h->state, h->partials,
+            h->counters + 5);
+        SEM_LAUNCH_CHECK("cg_init_kernel");
+        if ((rc = run_cg_loop(h, prec, o, 0, s, &hs))) return rc;
+        st.iterations = hs.iter;
+        st.relres_recursive = hs.bb > 0 ? std::sqrt(hs.rr / hs.bb) : 0.0;
+        status = hs.status;
+    } else {
+        // FP64 refinement around an FP32 inner CG
+        double prev = INFINITY;
+        int outer = 0, inner = 0;
+        for (;;) {
+            if ((rc = true_residual(h, h->ws.x, h->ws.b, rrbb, s))) return rc;
+            double hb[2];
+            SEM_CUDA_TRY(cudaMemcpyAsync(hb, rrbb, sizeof(hb), cudaMemcpyDeviceToHost, s));
+            SEM_CUDA_TRY(cudaStreamSynchronize(s));
+            const double rel = hb[1] > 0 ? std::sqrt(hb[0] / hb[1]) : 0.0;
+            st.relres_recursive = rel;
+            if (hb[1] == 0.0 || rel <= o.tol) { status = SEM_OK; break; }
+            if (!std::isfinite(rel)) { status = SEM_EBREAKDOWN; break; }
+            if (outer >= o.max_outer) { status = SEM_ENOTCONV; break; }
+            if (outer > 0 && rel > 0.5 * prev) { status = SEM_ESTAGNATE; break; }
+            prev = rel;
+            ir_prepare_kernel<<<grid_for(h, n, 256, 8), 256, 0, s>>>(h->ws.r, rrbb, h->ws.b32, h->ws.r32,
+                                                                     h->ws.d32, n);
+            cg_init_kernel<float><<<grid_for(h, n, 256, 4), 256, 0, s>>>(
+                h->ws.b32, h->ws.r32, h->ws.z32, h->minv32, h->mult, n, o.inner_tol, o.max_iter, h->state + 1,
+                h->partials, h->counters + 5);
+            SEM_LAUNCH_CHECK("ir prepare");
+            if ((rc = run_cg_loop(h, SEM_FP32, o, 1, s, &hs))) return rc;
+            inner += hs.iter;
+            ir_correct_kernel<<<grid_for(h, n, 256, 8), 256, 0, s>>>(h->ws.x, h->ws.d32, rrbb, n);
+            SEM_LAUNCH_CHECK("ir_correct_kernel");
+            outer++;
+        }
+        st.iterations = inner;
+        st.outer_iterations = outer;
+    }
+    // true FP64 residual of the final iterate
+    if ((rc = true_residual(h, h->ws.x, h->ws.b, rrbb, s))) return rc;
+    double hb[2];
+    SEM_CUDA_TRY(cudaMemcpyAsync(hb, rrbb, sizeof(hb), cudaMemcpyDeviceToHost, s));
+    SEM_CUDA_TRY(cudaMemcpyAsync(x_user, h->ws.x, bytes, xh ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+    cudaEventRecord(ev1, s);
+    SEM_CUDA_TRY(cudaStreamSynchronize(s));
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    st.relres = hb[1] > 0 ? std::sqrt(hb[0] / hb[1]) : 0.0;
+    st.time_ms = ms;
+    st.status = status;
+    if (stats) *stats = st;
+    if (status != SEM_OK) {
+        const char* what = status == SEM_ENOTCONV   ? "not converged within max_iter / max_outer"
+                           : status == SEM_EBREAKDOWN ? "CG breakdown (p^T A p <= 0 or non-finite scalar)"
+                                                      : "refinement stagnated";
+        set_error(what);
+    }
+    return status;
+}
+
+}  // namespace sem
+
+using namespace sem;
+
+extern "C" {
+
+SEM_API int sem_cg_solve(sem_handle* h, double* x, const double* b, const sem_solve_opts* opts,
+                         sem_solve_stats* stats, cudaStream_t s) {
+    if (!h || !x || !b) return fail(SEM_EINVAL, "null argument");
+    if (h->nsolve != 1) return fail(SEM_EINVAL, "batch handle: use sem_cg_solve_batch");
+    sem_solve_opts o;
+    sem_solve_opts_default(&o);
+    if (opts) o = *opts;
+    if (!(o.tol > 0.0) || o.max_iter < 0 || (o.mode != SEM_MODE_FP64 && o.mode != SEM_MODE_MIXED_IR))
+        return fail(SEM_EINVAL, "bad solve options");
+    if (o.mode == SEM_MODE_MIXED_IR && !(o.inner_tol > 0.0 && o.inner_tol < 1.0))
+        return fail(SEM_EINVAL, "inner_tol must be in (0, 1)");
+    return solve_single(h, x, b, o, stats, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+// Device helpers shared by the kernels of libsem: deterministic block and grid
+// reductions, streaming loads, and the CG scalar updates.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "sem_internal.h"
+
+namespace sem {
+
+template <typename T>
+__device__ __forceinline__ T ld_stream(const T* p) { return __ldcs(p); }
+template <typename T>
+__device__ __forceinline__ void st_stream(T* p, T v) { __stcs(p, v); }
+
+// Sum of NV values over the block (blockDim.x a multiple of 32, <= 1024).
+// Fixed shuffle/tree order: bit-reproducible for a fixed block size.  The
+// result is valid in thread 0.  `red` holds NV*32 doubles of shared memory.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* red) {
+#pragma unroll
+    for (int q = 0; q < NV; q++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; q++) red[q * 32 + wid] = v[q];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; q++) {
+            v[q] = lane < nw ? red[q * 32 + lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+        }
+    }
+}
+
+// Grid-wide deterministic sum: every block writes its block sum to
+// partials[q * kMaxPartials + blockIdx.x]; the last block to arrive (a ticket
+// counter decides who, not what is summed) adds the partials in block order
+// and calls fin(sums) in thread 0, then resets the counter for the next
+// launch.  Returns nothing; fin runs exactly once per launch.
+template <int NV, typename Fin>
+__device__ __forceinline__ void grid_sum_finalize(double (&v)[NV], double* partials,
+                                                  unsigned int* counter, Fin fin) {
+    __shared__ double red[NV * 32];
+    __shared__ int is_last;
+    block_sum<NV>(v, red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; q++) partials[q * kMaxPartials + blockIdx.x] = v[q];
+        __threadfence();
+        const unsigned int t = atomicAdd(counter, 1u);
+        is_last = (t == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (is_last) {
+        __threadfence();
+        double acc[NV];
+#pragma unroll
+        for (int q = 0; q < NV; q++) acc[q] = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+#pragma unroll
+            for (int q = 0; q < NV; q++) acc[q] += __ldcg(&partials[q * kMaxPartials + b]);
+        block_sum<NV>(acc, red);
+        if (threadIdx.x == 0) {
+            fin(acc);
+            *counter = 0u;
+        }
+    }
+}
+
+// CG scalar step after <p, A p> is known (Sec. II-B, P-CG).
+__device__ __forceinline__ void cg_set_alpha(CGState* st, double pap) {
+    st->pap = pap;
+    if (!(pap > 0.0) || !isfinite(pap)) {
+        st->alpha = 0.0;
+        st->done = 1;
+        st->status = SEM_EBREAKDOWN;
+    } else {
+        st->alpha = st->rho / pap;
+    }
+}
+
+// CG scalar step after <r, z> and <r, r> of the new residual are known.
+__device__ __forceinline__ void cg_set_rho(CGState* st, double rz, double rr) {
+    st->rho_old = st->rho;
+    st->rho = rz;
+    st->rr = rr;
+    st->iter += 1;
+    if (!isfinite(rr) || !isfinite(rz)) {
+        st->done = 1;
+        st->status = SEM_EBREAKDOWN;
+    } else if (rr <= st->tol2) {
+        st->done = 1;
+        st->status = SEM_OK;
+    } else if (st->iter >= st->max_iter) {
+        st->done = 1;
+        st->status = SEM_ENOTCONV;
+    }
+}
+
+__device__ __forceinline__ double cg_beta(const CGState* st) {
+    return st->iter == 0 ? 0.0 : st->rho / st->rho_old;
+}
+
+}  // namespace sem

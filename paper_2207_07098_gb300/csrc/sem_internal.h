@@ -1,0 +1,182 @@
+// Internal declarations of libsem: the handle, error plumbing, and device
+// helpers shared by the translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sem.h"
+
+namespace sem {
+
+constexpr int kMaxLx = 16;
+constexpr int kReduceThreads = 256;
+constexpr int kMaxPartials = 4096;  // upper bound on CTAs of a reducing launch
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define SEM_CUDA_TRY(call)                                  \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return ::sem::cuda_fail(e_, #call); \
+    } while (0)
+
+#define SEM_LAUNCH_CHECK(what)                              \
+    do {                                                    \
+        cudaError_t e_ = cudaGetLastError();                \
+        if (e_ != cudaSuccess) return ::sem::cuda_fail(e_, what); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// solver scalars living in device memory (one per solve)
+// ---------------------------------------------------------------------------
+struct CGState {
+    double rho;       // <r, z> of the current iterate
+    double rho_old;   // <r, z> of the previous iterate
+    double alpha;     // step length of the current iteration
+    double pap;       // <p, A p>
+    double rr;        // <r, r>
+    double bb;        // <b, b>
+    double tol2;      // (tol * ||b||)^2 threshold on rr, set at init
+    double scale;     // refinement: ||r|| of the outer residual
+    int iter;         // iterations done
+    int max_iter;
+    int done;         // 1 once converged, failed or out of iterations
+    int status;       // SEM_OK / SEM_ENOTCONV / SEM_EBREAKDOWN
+};
+
+// ---------------------------------------------------------------------------
+// one mesh (a handle holds one, or many for a batch)
+// ---------------------------------------------------------------------------
+struct MeshPart {
+    int E = 0;
+    int lx = 0;
+    int64_t elem_off = 0;  // first element in the handle's element numbering
+    int64_t loc_off = 0;   // first local index
+    int64_t n_local = 0;
+    int64_t n_unique = 0;
+    int64_t n_free = 0;
+};
+
+// Gather-scatter lists: every node with >= 2 copies is one segment
+// (local indices ascending).  Segments of free nodes come first, then those of
+// Dirichlet nodes; `zero` lists Dirichlet nodes with a single copy.
+struct GSLists {
+    int* seg_off = nullptr;   // [nseg + 1]
+    int* seg_idx = nullptr;   // [n_shared]
+    int* zero_idx = nullptr;  // [nzero]
+    int* seg_solve = nullptr; // batch: solve of each segment (unused for one mesh)
+    int64_t nseg_free = 0;
+    int64_t nseg = 0;
+    int64_t n_shared = 0;
+    int64_t nzero = 0;
+};
+
+struct Workspace {
+    // FP64 CG vectors
+    double* r = nullptr;
+    double* p = nullptr;
+    double* z = nullptr;
+    double* w = nullptr;
+    double* x = nullptr;
+    double* b = nullptr;
+    // FP32 inner vectors
+    float* r32 = nullptr;
+    float* p32 = nullptr;
+    float* z32 = nullptr;
+    float* w32 = nullptr;
+    float* d32 = nullptr;
+    float* b32 = nullptr;
+    bool have64 = false, have32 = false;
+};
+
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    int key_prec = -1;
+    int key_chunk = 0;
+    const void* key_ptr = nullptr;
+};
+
+}  // namespace sem
+
+struct sem_handle {
+    int device = 0;
+    int sm_count = 0;
+    int nsolve = 1;
+    int E = 0;           // total elements
+    int lx = 0;          // common lx (0 for a mixed-order batch)
+    int64_t n_local = 0;
+    int64_t n_unique = 0;
+    int64_t n_free = 0;
+    std::vector<sem::MeshPart> parts;
+    // basis per lx (index lx): D in FP64 and FP32
+    double* D64[sem::kMaxLx + 1] = {};
+    float* D32[sem::kMaxLx + 1] = {};
+    // set-up data
+    double* G64 = nullptr;     // [E][6][lx^3], h1 folded in
+    float* G32 = nullptr;
+    double* B64 = nullptr;     // [n_local] mass
+    double* minv64 = nullptr;  // [n_local]
+    float* minv32 = nullptr;
+    uint8_t* mult = nullptr;   // [n_local] copies of the node
+    uint8_t* mask = nullptr;   // [n_local]
+    sem::GSLists gs;
+    // reductions and solver state
+    double* partials = nullptr;       // [kMaxPartials * 4]
+    unsigned int* counters = nullptr; // [16]
+    sem::CGState* state = nullptr;    // [nsolve]
+    sem::CGState* state_host = nullptr;  // pinned mirror [nsolve]
+    double* scratch = nullptr;        // [64] small device scratch
+    sem::Workspace ws;
+    sem::GraphCache graph;
+    cudaStream_t capture_stream = nullptr;
+    size_t device_bytes = 0;
+};
+
+namespace sem {
+
+// allocation helper that records bytes in the handle
+template <typename T>
+int dalloc(sem_handle* h, T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return SEM_OK;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(SEM_ENOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    h->device_bytes += count * sizeof(T);
+    return SEM_OK;
+}
+
+int ensure_workspace(sem_handle* h, bool fp32);
+
+// ---- launches implemented in the .cu files (all enqueue on `s`) ----------
+// ax: w = A_L u (local).  T = double or float.  `native` selects the plain
+// FP64 kernel for double.
+int launch_ax_local(sem_handle* h, const void* u, void* w, int precision, cudaStream_t s);
+// gs (+ mask)
+int launch_gs(sem_handle* h, void* u, bool fp32, bool apply_mask, cudaStream_t s);
+// w = B u
+int launch_mass(sem_handle* h, const double* u, double* w, cudaStream_t s);
+int launch_mass32(sem_handle* h, const float* u, float* w, cudaStream_t s);
+// fused CG pieces
+int launch_cg_pupdate_ax(sem_handle* h, int precision, cudaStream_t s);   // K-A
+int launch_cg_update(sem_handle* h, int precision, cudaStream_t s);       // K-C
+int launch_cg_init(sem_handle* h, int precision, cudaStream_t s);         // z, rho, rr, bb
+int launch_dot(sem_handle* h, const double* a, const double* b, double* out, cudaStream_t s);
+int launch_residual(sem_handle* h, const double* b, const double* ax, double* r,
+                    double* rr_out, cudaStream_t s);  // r = b - ax, rr_out[0] = <r,r>
+int grid_for(sem_handle* h, int64_t work_items, int threads, int per_sm);
+int prepare_cg_kernels(sem_handle* h);
+
+}  // namespace sem

@@ -1,0 +1,606 @@
+// Set-up of libsem handles: GLL basis, gather-scatter lists, geometric
+// factors, mass and Jacobi diagonal (Sec. II-A and II-B of Karp et al.).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "sem_device.cuh"
+#include "sem_internal.h"
+
+namespace sem {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+int cuda_fail(cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return SEM_ECUDA;
+}
+
+int grid_for(sem_handle* h, int64_t work_items, int threads, int per_sm) {
+    int64_t blocks = (work_items + threads - 1) / threads;
+    int64_t cap = (int64_t)h->sm_count * per_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    if (blocks > kMaxPartials) blocks = kMaxPartials;
+    return (int)blocks;
+}
+
+// ---------------------------------------------------------------------------
+// GLL basis.  Nodes: -1, 1 and the roots of P_N'.  Here they are found as the
+// roots of q = P_{N+1} - P_{N-1}, which vanishes exactly at the N+1 GLL nodes
+// because P_{N+1} - P_{N-1} = (2N+1)/(N(N+1)) (x^2 - 1) P_N'; Newton uses
+// q' = (2N+1) P_N.  Weights 2/(N(N+1) P_N^2); D_ij = l_j'(xi_i).
+// ---------------------------------------------------------------------------
+static void legendre_upto(int n, long double x, long double* P) {  // P[0..n]
+    P[0] = 1.0L;
+    if (n >= 1) P[1] = x;
+    for (int m = 1; m < n; m++) P[m + 1] = ((2 * m + 1) * x * P[m] - m * P[m - 1]) / (m + 1);
+}
+
+static void gll_basis(int lx, double* xi, double* rho, double* D) {
+    const int N = lx - 1;
+    long double P[kMaxLx + 2];
+    std::vector<long double> x(lx), PN(lx);
+    const long double pi = 3.14159265358979323846264338327950288L;
+    for (int i = 0; i <= N; i++) {
+        long double t = -cosl(pi * (long double)i / (long double)N);
+        if (i > 0 && i < N) {
+            for (int it = 0; it < 60; it++) {
+                legendre_upto(N + 1, t, P);
+                long double q = P[N + 1] - P[N - 1];
+                long double dq = (2 * N + 1) * P[N];
+                long double step = q / dq;
+                t -= step;
+                if (fabsl(step) <= 4e-19L * (1.0L + fabsl(t))) break;
+            }
+        }
+        x[i] = t;
+        legendre_upto(N, t, P);
+        PN[i] = P[N];
+    }
+    for (int i = 0; i <= N; i++) {
+        if (xi) xi[i] = (double)x[i];
+        if (rho) rho[i] = (double)(2.0L / ((long double)N * (N + 1) * PN[i] * PN[i]));
+    }
+    if (D) {
+        for (int i = 0; i <= N; i++)
+            for (int j = 0; j <= N; j++) {
+                long double v;
+                if (i != j)
+                    v = PN[i] / (PN[j] * (x[i] - x[j]));
+                else if (i == 0)
+                    v = -0.25L * N * (N + 1);
+                else if (i == N)
+                    v = 0.25L * N * (N + 1);
+                else
+                    v = 0.0L;
+                D[i * lx + j] = (double)v;
+            }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// set-up kernels (one thread per local point; run once, not on the hot path)
+// ---------------------------------------------------------------------------
+struct GeomArgs {
+    const double* X;      // [3][n_local] (of this part)
+    const double* h1;     // [n_local] or null
+    const double* D;      // [lx][lx]
+    const double* rho;    // [lx]
+    double* G;            // [E][6][lx^3] (this part)
+    double* B;            // [n_local]
+    int E, lx;
+    int* bad;             // set to 1 on a non-positive Jacobian
+};
+
+__global__ void geometry_kernel(GeomArgs a) {
+    const int lx = a.lx, n3 = lx * lx * lx;
+    const int64_t n = (int64_t)a.E * n3;
+    for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < n;
+         L += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = L / n3;
+        const int q = (int)(L - e * n3);
+        const int i = q % lx, j = (q / lx) % lx, k = q / (lx * lx);
+        double d[3][3];
+        for (int m = 0; m < 3; m++) {
+            const double* c = a.X + (int64_t)m * n + e * n3;
+            double dr = 0.0, ds = 0.0, dt = 0.0;
+            for (int l = 0; l < lx; l++) {
+                dr = fma(a.D[i * lx + l], c[(k * lx + j) * lx + l], dr);
+                ds = fma(a.D[j * lx + l], c[(k * lx + l) * lx + i], ds);
+                dt = fma(a.D[k * lx + l], c[(l * lx + j) * lx + i], dt);
+            }
+            d[m][0] = dr;
+            d[m][1] = ds;
+            d[m][2] = dt;
+        }
+        // cofactors of the Jacobian matrix dx/dr (rows x,y,z; columns r,s,t)
+        const double c00 = d[1][1] * d[2][2] - d[1][2] * d[2][1];
+        const double c01 = d[1][2] * d[2][0] - d[1][0] * d[2][2];
+        const double c02 = d[1][0] * d[2][1] - d[1][1] * d[2][0];
+        const double J = d[0][0] * c00 + d[0][1] * c01 + d[0][2] * c02;
+        if (!(J > 0.0)) {
+            *a.bad = 1;
+            continue;
+        }
+        // gradients of r, s, t: rows of the inverse = columns of adj / J
+        double g[3][3];
+        g[0][0] = c00;
+        g[0][1] = d[0][2] * d[2][1] - d[0][1] * d[2][2];
+        g[0][2] = d[0][1] * d[1][2] - d[0][2] * d[1][1];
+        g[1][0] = c01;
+        g[1][1] = d[0][0] * d[2][2] - d[0][2] * d[2][0];
+        g[1][2] = d[0][2] * d[1][0] - d[0][0] * d[1][2];
+        g[2][0] = c02;
+        g[2][1] = d[0][1] * d[2][0] - d[0][0] * d[2][1];
+        g[2][2] = d[0][0] * d[1][1] - d[0][1] * d[1][0];
+        const double wq = a.rho[i] * a.rho[j] * a.rho[k];
+        const double hh = a.h1 ? a.h1[L] : 1.0;
+        // G_st = w J (grad r_s . grad r_t) = w (adj_s . adj_t) / J
+        const double s = wq * hh / J;
+        double* Ge = a.G + e * 6 * n3 + q;
+        const int ss[6] = {0, 0, 0, 1, 1, 2}, tt[6] = {0, 1, 2, 1, 2, 2};
+        for (int c = 0; c < 6; c++) {
+            const double dot = g[ss[c]][0] * g[tt[c]][0] + g[ss[c]][1] * g[tt[c]][1] +
+                               g[ss[c]][2] * g[tt[c]][2];
+            Ge[c * n3] = s * dot;
+        }
+        a.B[L] = wq * J;
+    }
+}
+
+// Local diagonal of A^e with the folded factors (h1 G):
+// d = sum_l D_li^2 G11(l,j,k) + D_lj^2 G22(i,l,k) + D_lk^2 G33(i,j,l)
+//   + 2 (D_ii D_jj G12 + D_ii D_kk G13 + D_jj D_kk G23)(i,j,k)
+__global__ void jacobi_local_kernel(const double* G, const double* D, int E, int lx, double* d) {
+    const int n3 = lx * lx * lx;
+    const int64_t n = (int64_t)E * n3;
+    for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < n;
+         L += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = L / n3;
+        const int q = (int)(L - e * n3);
+        const int i = q % lx, j = (q / lx) % lx, k = q / (lx * lx);
+        const double* Ge = G + e * 6 * n3;
+        double s = 0.0;
+        for (int l = 0; l < lx; l++) {
+            const double a = D[l * lx + i], b = D[l * lx + j], c = D[l * lx + k];
+            s = fma(a * a, Ge[0 * n3 + (k * lx + j) * lx + l], s);
+            s = fma(b * b, Ge[3 * n3 + (k * lx + l) * lx + i], s);
+            s = fma(c * c, Ge[5 * n3 + (l * lx + j) * lx + i], s);
+        }
+        const double dii = D[i * lx + i], djj = D[j * lx + j], dkk = D[k * lx + k];
+        s += 2.0 * (dii * djj * Ge[1 * n3 + q] + dii * dkk * Ge[2 * n3 + q] + djj * dkk * Ge[4 * n3 + q]);
+        d[L] = s;
+    }
+}
+
+__global__ void jacobi_invert_kernel(const double* d, const uint8_t* mask, int64_t n, double* minv,
+                                     float* minv32) {
+    for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < n;
+         L += (int64_t)gridDim.x * blockDim.x) {
+        const double v = mask[L] ? 1.0 / d[L] : 0.0;
+        minv[L] = v;
+        minv32[L] = (float)v;
+    }
+}
+
+__global__ void to_float_kernel(const double* a, float* b, int64_t n) {
+    for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < n;
+         L += (int64_t)gridDim.x * blockDim.x)
+        b[L] = (float)a[L];
+}
+
+// ---------------------------------------------------------------------------
+// host: stable LSD radix sort of (key, local index) pairs by key
+// ---------------------------------------------------------------------------
+static void radix_sort_pairs(std::vector<uint64_t>& key, std::vector<int32_t>& val) {
+    const size_t n = key.size();
+    if (n < 2) return;
+    uint64_t mx = 0;
+    for (uint64_t k : key) mx = std::max(mx, k);
+    int bits = 0;
+    while (bits < 64 && (mx >> bits) != 0) bits++;
+    std::vector<uint64_t> k2(n);
+    std::vector<int32_t> v2(n);
+    std::vector<size_t> cnt(1 << 16);
+    for (int shift = 0; shift < bits; shift += 16) {
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (size_t q = 0; q < n; q++) cnt[(key[q] >> shift) & 0xFFFF]++;
+        size_t acc = 0;
+        for (auto& c : cnt) {
+            size_t t = c;
+            c = acc;
+            acc += t;
+        }
+        for (size_t q = 0; q < n; q++) {
+            size_t pos = cnt[(key[q] >> shift) & 0xFFFF]++;
+            k2[pos] = key[q];
+            v2[pos] = val[q];
+        }
+        key.swap(k2);
+        val.swap(v2);
+    }
+}
+
+// Gather-scatter lists of one mesh, appended to host vectors (indices offset
+// by loc_off).  Returns SEM_OK or SEM_EINVAL.
+struct HostGS {
+    std::vector<int32_t> free_off, free_idx, dir_off, dir_idx, zero;
+    std::vector<int32_t> free_solve, dir_solve;
+    std::vector<uint8_t> mult;
+};
+
+static int build_gs_part(const MeshPart& part, int solve, const int64_t* gid, const uint8_t* mask,
+                         HostGS& out, int64_t* n_unique, int64_t* n_free) {
+    const int64_t n = part.n_local;
+    int64_t gmin = INT64_MAX;
+    for (int64_t L = 0; L < n; L++) gmin = std::min(gmin, gid[L]);
+    std::vector<uint64_t> key(n);
+    std::vector<int32_t> val(n);
+    for (int64_t L = 0; L < n; L++) {
+        key[L] = (uint64_t)(gid[L] - gmin);
+        val[L] = (int32_t)L;
+    }
+    radix_sort_pairs(key, val);
+    int64_t nu = 0, nf = 0;
+    for (int64_t a = 0; a < n;) {
+        int64_t b = a + 1;
+        while (b < n && key[b] == key[a]) b++;
+        const int cnt = (int)(b - a);
+        if (cnt > 255) return fail(SEM_EINVAL, "a node has more than 255 local copies");
+        const uint8_t m0 = mask[val[a]] ? 1 : 0;
+        for (int64_t c = a; c < b; c++) {
+            if ((mask[val[c]] ? 1 : 0) != m0)
+                return fail(SEM_EINVAL, "Dirichlet mask differs between copies of a node");
+            out.mult[part.loc_off + val[c]] = (uint8_t)cnt;
+        }
+        nu++;
+        if (m0) nf++;
+        if (cnt >= 2) {
+            auto& off = m0 ? out.free_off : out.dir_off;
+            auto& idx = m0 ? out.free_idx : out.dir_idx;
+            auto& sol = m0 ? out.free_solve : out.dir_solve;
+            off.push_back((int32_t)idx.size());
+            sol.push_back(solve);
+            for (int64_t c = a; c < b; c++) idx.push_back((int32_t)(part.loc_off + val[c]));
+        } else if (!m0) {
+            out.zero.push_back((int32_t)(part.loc_off + val[a]));
+        }
+        a = b;
+    }
+    *n_unique = nu;
+    *n_free = nf;
+    return SEM_OK;
+}
+
+static void free_handle(sem_handle* h) {
+    if (!h) return;
+    for (int l = 0; l <= kMaxLx; l++) {
+        cudaFree(h->D64[l]);
+        cudaFree(h->D32[l]);
+    }
+    cudaFree(h->G64);
+    cudaFree(h->G32);
+    cudaFree(h->B64);
+    cudaFree(h->minv64);
+    cudaFree(h->minv32);
+    cudaFree(h->mult);
+    cudaFree(h->mask);
+    cudaFree(h->gs.seg_off);
+    cudaFree(h->gs.seg_idx);
+    cudaFree(h->gs.zero_idx);
+    cudaFree(h->gs.seg_solve);
+    cudaFree(h->partials);
+    cudaFree(h->counters);
+    cudaFree(h->state);
+    cudaFree(h->scratch);
+    if (h->state_host) cudaFreeHost(h->state_host);
+    Workspace& w = h->ws;
+    cudaFree(w.r); cudaFree(w.p); cudaFree(w.z); cudaFree(w.w); cudaFree(w.x); cudaFree(w.b);
+    cudaFree(w.r32); cudaFree(w.p32); cudaFree(w.z32); cudaFree(w.w32); cudaFree(w.d32); cudaFree(w.b32);
+    if (h->graph.exec) cudaGraphExecDestroy(h->graph.exec);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+    delete h;
+}
+
+int ensure_workspace(sem_handle* h, bool fp32) {
+    Workspace& w = h->ws;
+    const size_t n = (size_t)h->n_local;
+    int rc;
+    if (!w.have64) {
+        if ((rc = dalloc(h, &w.r, n)) || (rc = dalloc(h, &w.p, n)) || (rc = dalloc(h, &w.z, n)) ||
+            (rc = dalloc(h, &w.w, n)) || (rc = dalloc(h, &w.x, n)) || (rc = dalloc(h, &w.b, n)))
+            return rc;
+        w.have64 = true;
+    }
+    if (fp32 && !w.have32) {
+        if ((rc = dalloc(h, &w.r32, n)) || (rc = dalloc(h, &w.p32, n)) || (rc = dalloc(h, &w.z32, n)) ||
+            (rc = dalloc(h, &w.w32, n)) || (rc = dalloc(h, &w.d32, n)) || (rc = dalloc(h, &w.b32, n)))
+            return rc;
+        w.have32 = true;
+    }
+    return SEM_OK;
+}
+
+static bool host_pointer(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+static int setup_common(sem_handle** out, int nsolve, const sem_mesh_desc* meshes, cudaStream_t s) {
+    *out = nullptr;
+    if (nsolve < 1 || !meshes) return fail(SEM_EINVAL, "nsolve must be >= 1");
+    int64_t n_local = 0, E = 0;
+    for (int q = 0; q < nsolve; q++) {
+        const sem_mesh_desc& m = meshes[q];
+        if (m.E < 1 || m.lx < 2 || m.lx > kMaxLx)
+            return fail(SEM_EINVAL, "each mesh needs E >= 1 and 2 <= lx <= 16");
+        if (!m.coords || !m.gid || !m.mask) return fail(SEM_EINVAL, "coords, gid and mask are required");
+        if (!host_pointer(m.coords) || !host_pointer(m.gid) || !host_pointer(m.mask) ||
+            (m.h1 && !host_pointer(m.h1)))
+            return fail(SEM_EINVAL, "set-up arrays must be host pointers");
+        n_local += (int64_t)m.E * m.lx * m.lx * m.lx;
+        E += m.E;
+    }
+    if (n_local >= ((int64_t)1 << 31) - 64)
+        return fail(SEM_EINVAL, "n_local must be below 2^31 (32-bit local indices)");
+    sem_handle* h = new sem_handle();
+    int rc = SEM_OK;
+    auto bail = [&](int code) {
+        free_handle(h);
+        return code;
+    };
+    if (cudaGetDevice(&h->device) != cudaSuccess) return bail(fail(SEM_ECUDA, "no CUDA device"));
+    cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+    h->nsolve = nsolve;
+    h->E = (int)E;
+    h->n_local = n_local;
+    h->lx = meshes[0].lx;
+    for (int q = 1; q < nsolve; q++)
+        if (meshes[q].lx != h->lx) h->lx = 0;
+    // parts
+    int64_t eoff = 0, loff = 0;
+    for (int q = 0; q < nsolve; q++) {
+        MeshPart p;
+        p.E = meshes[q].E;
+        p.lx = meshes[q].lx;
+        p.elem_off = eoff;
+        p.loc_off = loff;
+        p.n_local = (int64_t)p.E * p.lx * p.lx * p.lx;
+        h->parts.push_back(p);
+        eoff += p.E;
+        loff += p.n_local;
+    }
+    // gather-scatter lists
+    HostGS hg;
+    hg.mult.assign(n_local, 1);
+    std::vector<uint8_t> mask_all(n_local);
+    for (int q = 0; q < nsolve; q++) {
+        MeshPart& p = h->parts[q];
+        if ((rc = build_gs_part(p, q, meshes[q].gid, meshes[q].mask, hg, &p.n_unique, &p.n_free)))
+            return bail(rc);
+        for (int64_t L = 0; L < p.n_local; L++) mask_all[p.loc_off + L] = meshes[q].mask[L] ? 1 : 0;
+        h->n_unique += p.n_unique;
+        h->n_free += p.n_free;
+    }
+    GSLists& g = h->gs;
+    g.nseg_free = (int64_t)hg.free_off.size();
+    g.nseg = g.nseg_free + (int64_t)hg.dir_off.size();
+    g.n_shared = (int64_t)(hg.free_idx.size() + hg.dir_idx.size());
+    g.nzero = (int64_t)hg.zero.size();
+    std::vector<int32_t> off(g.nseg + 1), idx(g.n_shared), sol(g.nseg);
+    {
+        int64_t c = 0;
+        for (size_t q = 0; q < hg.free_off.size(); q++) { off[c] = hg.free_off[q]; sol[c] = hg.free_solve[q]; c++; }
+        const int32_t base = (int32_t)hg.free_idx.size();
+        for (size_t q = 0; q < hg.dir_off.size(); q++) { off[c] = base + hg.dir_off[q]; sol[c] = hg.dir_solve[q]; c++; }
+        off[g.nseg] = (int32_t)g.n_shared;
+        std::copy(hg.free_idx.begin(), hg.free_idx.end(), idx.begin());
+        std::copy(hg.dir_idx.begin(), hg.dir_idx.end(), idx.begin() + base);
+    }
+    if ((rc = dalloc(h, &g.seg_off, off.size())) || (rc = dalloc(h, &g.seg_idx, idx.size() + 1)) ||
+        (rc = dalloc(h, &g.zero_idx, hg.zero.size() + 1)) || (rc = dalloc(h, &g.seg_solve, sol.size() + 1)) ||
+        (rc = dalloc(h, &h->mult, n_local)) || (rc = dalloc(h, &h->mask, n_local)) ||
+        (rc = dalloc(h, &h->G64, (size_t)6 * n_local)) || (rc = dalloc(h, &h->G32, (size_t)6 * n_local)) ||
+        (rc = dalloc(h, &h->B64, n_local)) || (rc = dalloc(h, &h->minv64, n_local)) ||
+        (rc = dalloc(h, &h->minv32, n_local)) || (rc = dalloc(h, &h->partials, (size_t)kMaxPartials * 4)) ||
+        (rc = dalloc(h, &h->counters, 16)) || (rc = dalloc(h, &h->state, (size_t)nsolve + 2)) ||
+        (rc = dalloc(h, &h->scratch, 64)))
+        return bail(rc);
+    if (cudaMallocHost((void**)&h->state_host, sizeof(CGState) * (nsolve + 2)) != cudaSuccess)
+        return bail(fail(SEM_ENOMEM, "cudaMallocHost failed"));
+#define UP(dst, src, bytes)                                                               \
+    do {                                                                                  \
+        if ((bytes) > 0) {                                                                \
+            cudaError_t e_ = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s); \
+            if (e_ != cudaSuccess) return bail(cuda_fail(e_, "upload"));                  \
+        }                                                                                 \
+    } while (0)
+    UP(g.seg_off, off.data(), off.size() * 4);
+    UP(g.seg_idx, idx.data(), idx.size() * 4);
+    UP(g.zero_idx, hg.zero.data(), hg.zero.size() * 4);
+    UP(g.seg_solve, sol.data(), sol.size() * 4);
+    UP(h->mult, hg.mult.data(), (size_t)n_local);
+    UP(h->mask, mask_all.data(), (size_t)n_local);
+    if (cudaMemsetAsync(h->counters, 0, 16 * sizeof(unsigned), s) != cudaSuccess)
+        return bail(fail(SEM_ECUDA, "memset"));
+    // basis per order
+    for (int q = 0; q < nsolve; q++) {
+        const int lx = h->parts[q].lx;
+        if (h->D64[lx]) continue;
+        double Dh[kMaxLx * kMaxLx];
+        float Df[kMaxLx * kMaxLx];
+        gll_basis(lx, nullptr, nullptr, Dh);
+        for (int t = 0; t < lx * lx; t++) Df[t] = (float)Dh[t];
+        if ((rc = dalloc(h, &h->D64[lx], (size_t)lx * lx)) || (rc = dalloc(h, &h->D32[lx], (size_t)lx * lx)))
+            return bail(rc);
+        UP(h->D64[lx], Dh, sizeof(double) * lx * lx);
+        UP(h->D32[lx], Df, sizeof(float) * lx * lx);
+    }
+    // geometry, mass, Jacobi diagonal: one part at a time through a staging buffer
+    int64_t maxn = 0;
+    for (auto& p : h->parts) maxn = std::max(maxn, p.n_local);
+    double *dX = nullptr, *dh1 = nullptr, *drho = nullptr, *dd = nullptr;
+    int* dbad = nullptr;
+    cudaError_t e1 = cudaMalloc((void**)&dX, sizeof(double) * 3 * maxn);
+    cudaError_t e2 = cudaMalloc((void**)&dh1, sizeof(double) * maxn);
+    cudaError_t e3 = cudaMalloc((void**)&drho, sizeof(double) * kMaxLx);
+    cudaError_t e4 = cudaMalloc((void**)&dbad, sizeof(int));
+    cudaError_t e5 = cudaMalloc((void**)&dd, sizeof(double) * n_local);
+    auto free_tmp = [&]() {
+        cudaFree(dX); cudaFree(dh1); cudaFree(drho); cudaFree(dbad); cudaFree(dd);
+    };
+    if (e1 || e2 || e3 || e4 || e5) {
+        free_tmp();
+        cudaGetLastError();
+        return bail(fail(SEM_ENOMEM, "set-up staging allocation failed"));
+    }
+    int bad = 0;
+    cudaMemsetAsync(dbad, 0, sizeof(int), s);
+    for (int q = 0; q < nsolve && rc == SEM_OK; q++) {
+        const MeshPart& p = h->parts[q];
+        double rho[kMaxLx];
+        gll_basis(p.lx, nullptr, rho, nullptr);
+        cudaMemcpyAsync(drho, rho, sizeof(double) * p.lx, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(dX, meshes[q].coords, sizeof(double) * 3 * p.n_local, cudaMemcpyHostToDevice, s);
+        if (meshes[q].h1)
+            cudaMemcpyAsync(dh1, meshes[q].h1, sizeof(double) * p.n_local, cudaMemcpyHostToDevice, s);
+        GeomArgs a;
+        a.X = dX;
+        a.h1 = meshes[q].h1 ? dh1 : nullptr;
+        a.D = h->D64[p.lx];
+        a.rho = drho;
+        a.G = h->G64 + 6 * p.loc_off;
+        a.B = h->B64 + p.loc_off;
+        a.E = p.E;
+        a.lx = p.lx;
+        a.bad = dbad;
+        geometry_kernel<<<grid_for(h, p.n_local, 256, 8), 256, 0, s>>>(a);
+        jacobi_local_kernel<<<grid_for(h, p.n_local, 256, 8), 256, 0, s>>>(
+            h->G64 + 6 * p.loc_off, h->D64[p.lx], p.E, p.lx, dd + p.loc_off);
+        // the staging buffers are reused by the next part: wait for this one
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "geometry kernels");
+    }
+    if (rc == SEM_OK) {
+        cudaMemcpyAsync(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        if (bad) rc = fail(SEM_EINVAL, "non-positive Jacobian at some node (tangled or left-handed element)");
+    }
+    if (rc == SEM_OK) rc = launch_gs(h, dd, false, false, s);
+    if (rc == SEM_OK) {
+        jacobi_invert_kernel<<<grid_for(h, n_local, 256, 8), 256, 0, s>>>(dd, h->mask, n_local, h->minv64,
+                                                                           h->minv32);
+        to_float_kernel<<<grid_for(h, 6 * n_local, 256, 8), 256, 0, s>>>(h->G64, h->G32, 6 * n_local);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "jacobi set-up");
+    }
+    free_tmp();
+    if (rc != SEM_OK) return bail(rc);
+    *out = h;
+    return SEM_OK;
+#undef UP
+}
+
+}  // namespace sem
+
+using namespace sem;
+
+extern "C" {
+
+SEM_API const char* sem_last_error(void) { return g_err.c_str(); }
+
+SEM_API void sem_solve_opts_default(sem_solve_opts* o) {
+    if (!o) return;
+    o->tol = 1e-10;
+    o->max_iter = 100000;
+    o->mode = SEM_MODE_FP64;
+    o->inner_tol = 1e-5;
+    o->max_outer = 30;
+    o->precision = SEM_FP64;
+    o->use_graph = 1;
+    o->graph_chunk = 32;
+}
+
+SEM_API int sem_gll(int lx, double* xi, double* rho, double* D) {
+    if (lx < 2 || lx > kMaxLx) return fail(SEM_EINVAL, "lx must be in [2, 16]");
+    gll_basis(lx, xi, rho, D);
+    return SEM_OK;
+}
+
+SEM_API int sem_setup(sem_handle** h, int E, int lx, const double* coords, const int64_t* gid,
+                      const uint8_t* mask, const double* h1, int flags, cudaStream_t stream) {
+    if (!h) return fail(SEM_EINVAL, "null handle pointer");
+    (void)flags;
+    sem_mesh_desc m;
+    m.E = E;
+    m.lx = lx;
+    m.coords = coords;
+    m.gid = gid;
+    m.mask = mask;
+    m.h1 = h1;
+    return setup_common(h, 1, &m, stream);
+}
+
+SEM_API int sem_setup_batch(sem_handle** h, int nsolve, const sem_mesh_desc* meshes, int flags,
+                            cudaStream_t stream) {
+    if (!h) return fail(SEM_EINVAL, "null handle pointer");
+    (void)flags;
+    return setup_common(h, nsolve, meshes, stream);
+}
+
+SEM_API int sem_destroy(sem_handle* h) {
+    if (h) {
+        cudaDeviceSynchronize();
+        free_handle(h);
+    }
+    return SEM_OK;
+}
+
+SEM_API int sem_get_info(const sem_handle* h, sem_info* info) {
+    if (!h || !info) return fail(SEM_EINVAL, "null argument");
+    info->nsolve = h->nsolve;
+    info->E = h->E;
+    info->lx = h->lx;
+    info->n_local = h->n_local;
+    info->n_unique = h->n_unique;
+    info->n_free = h->n_free;
+    info->n_shared = h->gs.n_shared;
+    info->device_bytes = h->device_bytes;
+    return SEM_OK;
+}
+
+SEM_API int sem_get_offsets(const sem_handle* h, int64_t* offsets) {
+    if (!h || !offsets) return fail(SEM_EINVAL, "null argument");
+    for (int q = 0; q < h->nsolve; q++) offsets[q] = h->parts[q].loc_off;
+    offsets[h->nsolve] = h->n_local;
+    return SEM_OK;
+}
+
+SEM_API int sem_get_geometry(const sem_handle* h, double* G, double* B, cudaStream_t s) {
+    if (!h) return fail(SEM_EINVAL, "null handle");
+    if (G) SEM_CUDA_TRY(cudaMemcpyAsync(G, h->G64, sizeof(double) * 6 * h->n_local, cudaMemcpyDeviceToDevice, s));
+    if (B) SEM_CUDA_TRY(cudaMemcpyAsync(B, h->B64, sizeof(double) * h->n_local, cudaMemcpyDeviceToDevice, s));
+    return SEM_OK;
+}
+
+SEM_API int sem_get_jacobi(const sem_handle* h, double* minv, cudaStream_t s) {
+    if (!h || !minv) return fail(SEM_EINVAL, "null argument");
+    SEM_CUDA_TRY(cudaMemcpyAsync(minv, h->minv64, sizeof(double) * h->n_local, cudaMemcpyDeviceToDevice, s));
+    return SEM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,164 @@
+"""GPU parity of the operator pieces (through the C ABI) against the FP64 oracle:
+GLL basis, geometric factors, Jacobi diagonal, local and assembled ax_helm in
+FP64 (1e-12 relative) and FP32, gather-scatter (bit-exact in FP64), mass and
+the unique-node inner product."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+import paper_2207_07098_gb300 as S
+from gpu_helpers import Handle, rel_err
+
+pytestmark = pytest.mark.gpu
+
+TOL_AX64 = 1e-12     # relative, 2-norm and max-norm, per application
+TOL_AX32 = 5e-6      # FP32 operator vs FP64 oracle (reported; FP32 rounding of G, D, u)
+
+
+def _case(kind, dims, N, seed=0):
+    if kind == "affine":
+        m = W.box_mesh(*dims, N)
+        return m, None
+    if kind == "deformed":
+        m = W.box_mesh(*dims, N, amp=0.05)
+        return m, W.h1_wavy(m)
+    if kind == "jitter":
+        m = W.box_mesh(*dims, N, amp=0.1, jitter=0.02, seed=seed)
+        return m, W.h1_wavy(m)
+    if kind == "annulus":
+        m = W.annulus_mesh(n_theta=dims[0], n_r=dims[1], n_z=dims[2], N=N)
+        return m, None
+    raise ValueError(kind)
+
+
+# element counts chosen to leave ragged last groups of elements per CTA
+CASES = [
+    ("affine", (1, 1, 1), 1), ("deformed", (3, 2, 1), 2), ("jitter", (3, 3, 2), 3), ("deformed", (5, 3, 2), 4),
+    ("jitter", (3, 2, 3), 5), ("deformed", (4, 3, 3), 6), ("jitter", (3, 3, 3), 7), ("deformed", (5, 4, 3), 7),
+    ("annulus", (8, 3, 2), 7), ("deformed", (2, 3, 2), 8), ("jitter", (2, 2, 3), 9), ("deformed", (2, 2, 1), 11),
+    ("deformed", (1, 2, 1), 15),
+]
+
+
+@pytest.mark.parametrize("lx", [2, 3, 5, 8, 10, 16])
+def test_gll_basis_matches_oracle(lx):
+    xi, rho, D = S.sem_gll(lx)
+    xo, ro = oracle.gll(lx - 1)
+    np.testing.assert_allclose(xi, xo, atol=2e-16 * lx)
+    np.testing.assert_allclose(rho, ro, rtol=1e-14)
+    np.testing.assert_allclose(D, oracle.dmat(lx - 1), atol=1e-14 * lx * lx)
+
+
+@pytest.mark.parametrize("kind,dims,N", CASES)
+def test_geometry_mass_jacobi(kind, dims, N):
+    m, h1 = _case(kind, dims, N)
+    P = oracle.Problem(m, h1)
+    H = Handle(m, h1)
+    G, B = H.geometry()
+    Go, Bo = P.geom()
+    hh = np.ones(m.n_local) if h1 is None else h1
+    scale = np.max(np.abs(Go[[0, 3, 5]] * hh))
+    assert np.max(np.abs(G - Go * hh[None, :])) <= 1e-13 * scale
+    np.testing.assert_allclose(B, Bo, rtol=1e-13, atol=1e-16 * np.max(Bo))
+    mi, mo = H.jacobi(), P.minv()
+    np.testing.assert_array_equal(mi == 0, mo == 0)
+    np.testing.assert_allclose(mi, mo, rtol=1e-12)
+    info = H.info
+    assert info["n_unique"] == P.n_unique
+    assert info["n_free"] == int(np.unique(m.gid[m.mask > 0]).shape[0])
+
+
+@pytest.mark.parametrize("kind,dims,N", CASES)
+def test_ax_fp64_local_and_assembled(kind, dims, N):
+    m, h1 = _case(kind, dims, N)
+    P = oracle.Problem(m, h1)
+    H = Handle(m, h1)
+    u = W.random_local_field(m, 11)
+    for prec in (S.SEM_FP64, S.SEM_FP64_NATIVE):
+        e2, einf = rel_err(H.ax(u, prec, assemble=0), P.ax_local(u))
+        assert e2 <= TOL_AX64 and einf <= TOL_AX64, (e2, einf)
+    uc = W.random_local_field(m, 12, continuous=True)
+    e2, einf = rel_err(H.ax(uc, S.SEM_FP64, assemble=1), P.ax(uc))
+    assert e2 <= TOL_AX64 and einf <= TOL_AX64, (e2, einf)
+
+
+@pytest.mark.parametrize("kind,dims,N", CASES[1::2])
+def test_ax_fp32(kind, dims, N):
+    m, h1 = _case(kind, dims, N)
+    P = oracle.Problem(m, h1)
+    H = Handle(m, h1)
+    u = W.random_local_field(m, 13, continuous=True)
+    e2, einf = rel_err(H.ax(u, S.SEM_FP32, assemble=1), P.ax(u))
+    assert e2 <= TOL_AX32 * N and einf <= 10 * TOL_AX32 * N, (e2, einf)
+
+
+@pytest.mark.parametrize("kind,dims,N", CASES)
+def test_gs_bit_exact_and_mask(kind, dims, N):
+    m, h1 = _case(kind, dims, N)
+    P = oracle.Problem(m, h1)
+    H = Handle(m, h1)
+    w = W.random_local_field(m, 14)
+    # copies are summed in ascending local index on both sides: identical rounding
+    assert np.array_equal(H.gs(w, mask=1), P.gs(w, mask=True))
+    assert np.array_equal(H.gs(w, mask=0), P.gs(w, mask=False))
+    g32 = H.gs(w.astype(np.float32), precision=S.SEM_FP32, mask=1)
+    e2, _ = rel_err(g32, P.gs(w, mask=True))
+    assert e2 < 1e-6
+
+
+@pytest.mark.parametrize("kind,dims,N", CASES[::3])
+def test_mass_and_dot(kind, dims, N):
+    m, h1 = _case(kind, dims, N)
+    P = oracle.Problem(m, h1)
+    H = Handle(m, h1)
+    f = W.forcing_sines(m)
+    e2, einf = rel_err(H.mass(f, assemble=1), P.mass(f, assemble=True))
+    assert e2 <= 1e-14 and einf <= 1e-14
+    a = W.random_local_field(m, 15, continuous=True)
+    b = W.random_local_field(m, 16, continuous=True)
+    d = H.dot(a, b)[0]
+    assert abs(d - P.dot(a, b)) <= 1e-13 * np.sum(np.abs(a * b) / P.mult())
+
+
+def test_ax_deterministic():
+    m, h1 = _case("jitter", (4, 3, 3), 7)
+    H = Handle(m, h1)
+    u = W.random_local_field(m, 17, continuous=True)
+    a = H.ax(u)
+    for _ in range(3):
+        assert np.array_equal(H.ax(u), a)
+
+
+def test_ax_full_size_deformed_cube():
+    """The 32^3-element, N = 7 deformed cube with h1 (16.8 M points): every
+    output of one assembled FP64 application against the oracle."""
+    m, h1, _ = W.deformed_cube(32, 7, seed=2)
+    P = oracle.Problem(m, h1)
+    H = Handle(m, h1)
+    u = W.random_local_field(m, 18, continuous=True)
+    e2, einf = rel_err(H.ax(u), P.ax(u))
+    assert e2 <= TOL_AX64 and einf <= TOL_AX64, (e2, einf)
+    e2, einf = rel_err(H.ax(u, S.SEM_FP32), P.ax(u))
+    assert e2 <= 1e-5, e2
+
+
+def test_invalid_inputs_rejected():
+    m = W.box_mesh(2, 2, 2, 3)
+    with pytest.raises(S.SemError) as ei:
+        S.sem_setup(m.E, 17, m.coords, m.gid, m.mask)
+    assert ei.value.status == S.SEM_EINVAL
+    bad = m.mask.copy()
+    # a Dirichlet flag on one copy only of a shared interior node
+    _, first, cnt = np.unique(m.gid, return_index=True, return_counts=True)
+    shared = first[(cnt > 1) & (m.mask[first] > 0)][0]
+    bad[shared] = 0
+    with pytest.raises(S.SemError) as ei:
+        S.sem_setup(m.E, m.lx, m.coords, m.gid, bad)
+    assert ei.value.status == S.SEM_EINVAL
+    # a left-handed element (x mirrored): non-positive Jacobian
+    c = m.coords.copy()
+    c[0] = -c[0]
+    with pytest.raises(S.SemError) as ei:
+        S.sem_setup(m.E, m.lx, c, m.gid, m.mask)
+    assert ei.value.status == S.SEM_EINVAL
