@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 spectral-element Poisson solve.
+
+Workload (default): the 32^3-element deformed unit cube of order N = 7
+(32,768 hex elements, lx = 8, 16,777,216 local points), nodes displaced by
+0.05 h sin(2 pi x) sin(2 pi y) sin(2 pi z), h1 = 1 + 0.5 sin(4 pi x) cos(2 pi y),
+six geometric factors stored per point, seeded N(0,1) right-hand side per
+global node, Dirichlet on all faces.  Synthetic, generated by ``workloads``.
+
+One step = one complete solve of that problem to a relative residual of 1e-10
+(true FP64 residual ||b - A x|| / ||b||), with the selected solver (default:
+FP64 iterative refinement around an FP32 inner Jacobi-PCG; ``--solver fp64``
+for plain FP64 Jacobi-PCG).  Metric: Poisson GDOF/s = n_local x CG iterations
+/ solve time (the paper counts E (N+1)^3 points).  Inputs are resident in HBM
+and larger than L2 (the FP64 factors alone are 805 MB).
+
+Prints ONE JSON line.  ``--impl reference`` times the FP64 CPU oracle instead
+(on the host cores, a bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "Poisson GDOF/s (FP64 vs mixed, to 1e-10 rel. residual); ax_helm % HBM peak"
+UNIT = "GDOF/s"
+L2_NOTE = "inputs larger than L2 (FP64 factors 805 MB, FP32 factors 403 MB); no flush"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--solver", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--n", type=int, default=32, help="elements per direction of the cube")
+    ap.add_argument("--order", type=int, default=7)
+    ap.add_argument("--no-extras", action="store_true", help="skip the comparison solves and ax-only bench")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4) if r[5 + q].lower() == "active"})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+def _workload(args):
+    m, h1, b = W.deformed_cube(args.n, args.order, seed=2)
+    name = f"deformed cube {args.n}^3 hex, N={args.order}, h1 wavy, random RHS"
+    return m, h1, b, name
+
+
+def _config(args, m, extra=None):
+    c = {"workload": f"deformed_cube_{args.n}^3_N{args.order}", "elements": m.E, "lx": m.lx,
+         "n_local": m.n_local, "tol": 1e-10, "solver": "mixed_ir" if args.solver == "mixed" else "fp64_pcg",
+         "preconditioner": "point Jacobi (exact assembled diagonal)", "l2": L2_NOTE}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def _oracle_sample(m, h1, b, target_s: float):
+    """Time the FP64 CPU oracle on a bounded number of PCG iterations of the
+    full workload.  Returns (GDOF/s, iterations, seconds, threads, setup_s)."""
+    import oracle
+    t0 = time.perf_counter()
+    P = oracle.Problem(m, h1)
+    setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    P.pcg(b, tol=1e-30, max_iter=1)
+    t1 = time.perf_counter() - t0
+    k = max(1, int(round(target_s / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    _, info = P.pcg(b, tol=1e-30, max_iter=k)
+    dt = time.perf_counter() - t0
+    return m.n_local * info["iters"] / dt / 1e9, info["iters"], dt, oracle.threads(), setup
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    m, h1, b, _ = _workload(args)
+    import oracle
+    P = oracle.Problem(m, h1)
+    t0 = time.perf_counter()
+    P.pcg(b, tol=1e-30, max_iter=1)
+    t1 = time.perf_counter() - t0
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    k = max(1, int(budget / max(t1, 1e-3)))
+    for _ in range(args.warmup):
+        P.pcg(b, tol=1e-30, max_iter=k)
+    t0 = time.perf_counter()
+    its = 0
+    for _ in range(args.steps):
+        _, info = P.pcg(b, tol=1e-30, max_iter=k)
+        its += info["iters"]
+    dt = time.perf_counter() - t0
+    val = m.n_local * its / dt / 1e9
+    sample = f"{k} FP64 Jacobi-PCG iterations of the full workload per step (oracle, plain C loops)"
+    out = {"metric": METRIC, "value": val, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": _config(args, m, {"solver": "oracle_fp64_pcg_sample"}),
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def _traffic_for(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel's
+    source is unchanged since the capture (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh).get(kernel)
+        if not rec or rec.get("workload") != workload:
+            return None
+        src = os.path.join(ROOT, rec["source"])
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        return rec["bytes_per_launch"] if h == rec.get("source_sha") else None
+    except Exception:
+        return None
+
+
+def run_ours(args):
+    import torch
+    import paper_2207_07098_gb300 as S
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    S.load()
+    m, h1, b, _ = _workload(args)
+    n = m.n_local
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    h = S.sem_setup(m.E, m.lx, m.coords, m.gid, m.mask, h1)
+    setup_s = time.perf_counter() - t0
+    info = S.sem_get_info(h)
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros(n, dtype=torch.float64, device="cuda")
+    mode = S.SEM_MODE_MIXED_IR if args.solver == "mixed" else S.SEM_MODE_FP64
+    opts = {"mode": mode, "tol": 1e-10, "inner_tol": 1e-5}
+
+    def step():
+        xd.zero_()
+        return S.sem_cg_solve(h, xd, bd, opts)
+
+    for _ in range(max(3, args.warmup)):
+        st = step()
+    assert st["status"] == S.SEM_OK and st["relres"] <= 1e-10, st
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = [step() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    iters = sum(s["iterations"] for s in stats)
+    launches = sum(s["kernel_launches"] for s in stats)
+    worst = max(s["relres"] for s in stats)
+    value = ws * n * iters / (ms * 1e-3) / 1e9
+
+    # e2e: the same solves through the C ABI with pinned host buffers (copies inside)
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+    bh = torch.from_numpy(b).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e_it = 0
+    for _ in range(args.steps):
+        xh.zero_()
+        s = S.sem_cg_solve(h, xh, bh, opts)
+        e_it += s["iterations"]
+    torch.cuda.synchronize()
+    e_dt = time.perf_counter() - t0
+    e2e = {"value": ws * n * e_it / e_dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * n,
+           "d2h_bytes_per_step": 8 * n}
+
+    peak, peak_kind = _peaks()
+    # dominant kernel: the fused p-update + ax_helm launch (K-A) of the CG loop
+    samples = [s["ax_ms"] for s in stats if s["ax_samples"] > 0]
+    ax_ms = statistics.mean(samples) if samples else None
+    ka_bytes_pt = 9 * (4 if args.solver == "mixed" else 8)  # read z, p, 6 G; write p, w (h1 folded)
+    ka_bytes = ka_bytes_pt * n
+    achieved = ka_bytes / (ax_ms * 1e-3) / 1e9 if ax_ms else None
+    kname = "ax_kernel<float,8,true>" if args.solver == "mixed" else "ax_kernel<double,8,true>"
+    traffic = _traffic_for(kname, f"deformed_cube_{args.n}^3_N{args.order}")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None,
+                "traffic": traffic, "kernel": kname, "algorithmic_bytes_per_launch": ka_bytes,
+                "launch_ms": ax_ms, "peak_kind": peak_kind}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64" if args.solver == "mixed" else "f64", "data": "synthetic",
+           "config": _config(args, m, {"inner_tol": 1e-5 if args.solver == "mixed" else None,
+                                       "n_unique_free": info["n_free"], "parallelism": f"replicas x{ws}"}),
+           "iterations_per_solve": iters / args.steps, "outer_per_solve": stats[-1]["outer_iterations"],
+           "relres_max": worst, "gpu_launches": launches, "e2e": e2e, "roofline": roofline, "clocks": clk,
+           "setup_s": setup_s}
+
+    if rank == 0 and not args.no_extras:
+        out["extras"] = _extras(S, torch, h, m, bd, n, args, peak, stats, ms)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, k, dt, thr, osetup = _oracle_sample(m, h1, b, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+                               "sample": f"{k} FP64 Jacobi-PCG iterations of the full workload "
+                                         f"({dt:.1f} s; oracle set-up {osetup:.1f} s not counted)"}
+    S.sem_destroy(h)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def _extras(S, torch, h, m, bd, n, args, peak, stats, ms_timed):
+    """FP64 vs mixed solves, 200 FP64 CG iterations, and the ax_helm-only bench."""
+    ex = {}
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    res = {}
+    for name, mode, prec in (("fp64", S.SEM_MODE_FP64, S.SEM_FP64), ("mixed", S.SEM_MODE_MIXED_IR, S.SEM_FP64)):
+        x.zero_()
+        st = S.sem_cg_solve(h, x, bd, {"mode": mode, "precision": prec, "tol": 1e-10, "inner_tol": 1e-5})
+        res[name] = {"time_ms": st["time_ms"], "iterations": st["iterations"], "outer": st["outer_iterations"],
+                     "relres": st["relres"], "gdof_s": n * st["iterations"] / (st["time_ms"] * 1e-3) / 1e9,
+                     "ax_ms": st["ax_ms"]}
+    res["speedup_mixed_vs_fp64"] = res["fp64"]["time_ms"] / res["mixed"]["time_ms"]
+    ex["solves_to_1e-10"] = res
+    x.zero_()
+    st = S.sem_cg_solve(h, x, bd, {"mode": S.SEM_MODE_FP64, "tol": 1e-30, "max_iter": 200})
+    ex["cg200_fp64"] = {"time_ms": st["time_ms"], "iterations": st["iterations"],
+                        "gdof_s": n * st["iterations"] / (st["time_ms"] * 1e-3) / 1e9}
+    # ax_helm-only: plain local operator, back-to-back launches, CUDA events on the launching stream
+    stream = torch.cuda.current_stream()
+    axr = {}
+    for name, prec, dt, bpp in (("fp64", S.SEM_FP64, torch.float64, 64), ("fp32", S.SEM_FP32, torch.float32, 32)):
+        u = torch.randn(n, dtype=dt, device="cuda")
+        w = torch.empty_like(u)
+        for _ in range(3):
+            S.sem_ax(h, w, u, prec, 0)
+        reps = 20
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            S.sem_ax(h, w, u, prec, 0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / reps
+        gbs = bpp * n / (t * 1e-3) / 1e9
+        axr[name] = {"ms": t, "gb_s": gbs, "frac_hbm": gbs / peak, "bytes_per_point": bpp}
+    ex["ax_helm_only"] = axr
+    return ex
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -106,6 +106,10 @@ typedef struct sem_solve_stats {
     double relres;            /* TRUE residual ||b - A x|| / ||b||, recomputed in FP64 */
     double relres_recursive;  /* last recursive residual estimate of the CG loop */
     double time_ms;           /* device time of the solve (CUDA events) */
+    int64_t kernel_launches;  /* kernels this solve launched (graph nodes included) */
+    double ax_ms;             /* mean duration of the fused p-update + ax_helm kernel, sampled
+                                 with CUDA events once per graph launch (0 if not sampled) */
+    int ax_samples;           /* number of such samples */
 } sem_solve_stats;
 
 /* Mesh of one member of a batch (host pointers; see sem_setup). */

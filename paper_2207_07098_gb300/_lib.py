@@ -42,7 +42,8 @@ class sem_solve_opts(ctypes.Structure):
 
 class sem_solve_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("outer_iterations", ctypes.c_int),
-                ("relres", ctypes.c_double), ("relres_recursive", ctypes.c_double), ("time_ms", ctypes.c_double)]
+                ("relres", ctypes.c_double), ("relres_recursive", ctypes.c_double), ("time_ms", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64), ("ax_ms", ctypes.c_double), ("ax_samples", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

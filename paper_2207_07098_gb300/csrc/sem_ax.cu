@@ -97,12 +97,14 @@ __global__ void mass_kernel(const T* __restrict__ u, const double* __restrict__ 
 int launch_mass(sem_handle* h, const double* u, double* w, cudaStream_t s) {
     mass_kernel<double><<<grid_for(h, h->n_local, 256, 8), 256, 0, s>>>(u, h->B64, w, h->n_local);
     SEM_LAUNCH_CHECK("mass_kernel");
+    h->launches++;
     return SEM_OK;
 }
 
 int launch_mass32(sem_handle* h, const float* u, float* w, cudaStream_t s) {
     mass_kernel<float><<<grid_for(h, h->n_local, 256, 8), 256, 0, s>>>(u, h->B64, w, h->n_local);
     SEM_LAUNCH_CHECK("mass_kernel");
+    h->launches++;
     return SEM_OK;
 }
 

@@ -163,6 +163,7 @@ inline int launch_ax_t(sem_handle* h, const AxParams<T>& a, cudaStream_t s) {
     grid = std::max<int64_t>(1, std::min<int64_t>(grid, kMaxPartials));
     ax_kernel<T, LX, FUSED><<<(int)grid, C::THREADS, smem, s>>>(a);
     SEM_LAUNCH_CHECK("ax_kernel");
+    h->launches++;
     return SEM_OK;
 }
 

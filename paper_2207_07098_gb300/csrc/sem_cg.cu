@@ -209,6 +209,7 @@ int launch_cg_update(sem_handle* h, int precision, cudaStream_t s) {
         cg_update_kernel<double><<<grid, 256, 0, s>>>(a);
     }
     SEM_LAUNCH_CHECK("cg_update_kernel");
+    h->launches++;
     return SEM_OK;
 }
 
@@ -233,10 +234,21 @@ static int get_graph(sem_handle* h, int precision, int chunk, cudaGraphExec_t* o
     if (!h->capture_stream) SEM_CUDA_TRY(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
     int prc = prepare_cg_kernels(h);
     if (prc) return prc;
+    for (auto& ev : h->ax_ev)
+        if (!ev) SEM_CUDA_TRY(cudaEventCreate(&ev));
     cudaStream_t cs = h->capture_stream;
+    const int64_t launches_before = h->launches;  // captured kernels are counted per graph launch
     SEM_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     int rc = SEM_OK;
-    for (int it = 0; it < chunk && rc == SEM_OK; it++) rc = launch_iteration(h, precision, cs);
+    for (int it = 0; it < chunk && rc == SEM_OK; it++) {
+        if (it == 0 && cudaEventRecordWithFlags(h->ax_ev[0], cs, cudaEventRecordExternal) != cudaSuccess) rc = fail(SEM_ECUDA, "event record");
+        if (!rc) rc = launch_cg_pupdate_ax(h, precision, cs);
+        if (it == 0 && !rc && cudaEventRecordWithFlags(h->ax_ev[1], cs, cudaEventRecordExternal) != cudaSuccess) rc = fail(SEM_ECUDA, "event record");
+        if (!rc) rc = launch_gs(h, precision == SEM_FP32 ? (void*)h->ws.w32 : (void*)h->ws.w, precision == SEM_FP32,
+                                true, cs);
+        if (!rc) rc = launch_cg_update(h, precision, cs);
+    }
+    h->launches = launches_before;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &graph);
     if (rc) {
@@ -256,10 +268,16 @@ static int get_graph(sem_handle* h, int precision, int chunk, cudaGraphExec_t* o
     return SEM_OK;
 }
 
+struct AxTiming {
+    double ms = 0.0;
+    int samples = 0;
+};
+
 // Run CG iterations on state slot `slot` until done.  Returns SEM_OK or an
-// error; the solve status is in the state.
+// error; the solve status is in the state.  With graphs, the duration of the
+// first K-A of every graph launch is added to `tm`.
 static int run_cg_loop(sem_handle* h, int precision, const sem_solve_opts& o, int slot, cudaStream_t s,
-                       CGState* out) {
+                       CGState* out, AxTiming* tm) {
     const int chunk = std::max(1, std::min(o.graph_chunk, 1024));
     cudaGraphExec_t exec = nullptr;
     if (o.use_graph) {
@@ -272,6 +290,7 @@ static int run_cg_loop(sem_handle* h, int precision, const sem_solve_opts& o, in
     for (int64_t round = 0; !out->done && round < max_rounds; round++) {
         if (exec) {
             SEM_CUDA_TRY(cudaGraphLaunch(exec, s));
+            h->launches += 3 * (int64_t)chunk;
         } else {
             for (int it = 0; it < chunk; it++) {
                 int rc = launch_iteration(h, precision, s);
@@ -280,6 +299,15 @@ static int run_cg_loop(sem_handle* h, int precision, const sem_solve_opts& o, in
         }
         SEM_CUDA_TRY(cudaMemcpyAsync(out, h->state + slot, sizeof(CGState), cudaMemcpyDeviceToHost, s));
         SEM_CUDA_TRY(cudaStreamSynchronize(s));
+        if (exec && tm) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, h->ax_ev[0], h->ax_ev[1]) == cudaSuccess) {
+                tm->ms += ms;
+                tm->samples++;
+            } else {
+                cudaGetLastError();
+            }
+        }
     }
     if (!out->done) return fail(SEM_ETIMEOUT, "CG loop did not finish within its iteration budget");
     return SEM_OK;
@@ -293,6 +321,7 @@ static int true_residual(sem_handle* h, const double* x, const double* b, double
     resid_kernel<<<grid_for(h, h->n_local, 256, 4), 256, 0, s>>>(b, h->ws.w, h->ws.r, h->mult, h->n_local,
                                                                  h->partials, h->counters + 4, rr_bb);
     SEM_LAUNCH_CHECK("resid_kernel");
+    h->launches++;
     return SEM_OK;
 }
 
@@ -320,6 +349,8 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
     SEM_CUDA_TRY(cudaMemcpyAsync(h->ws.b, b_user, bytes, bh ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
     double* rrbb = h->scratch;  // [0] rr, [1] bb
     sem_solve_stats st = {};
+    AxTiming tm;
+    const int64_t launches0 = h->launches;
     CGState hs;
     int status = SEM_OK;
     if (o.mode == SEM_MODE_FP64) {
@@ -329,7 +360,8 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
             h->ws.b, h->ws.r, h->ws.z, h->minv64, h->mult, n, o.tol, o.max_iter, h->state, h->partials,
             h->counters + 5);
         SEM_LAUNCH_CHECK("cg_init_kernel");
-        if ((rc = run_cg_loop(h, prec, o, 0, s, &hs))) return rc;
+        h->launches++;
+        if ((rc = run_cg_loop(h, prec, o, 0, s, &hs, &tm))) return rc;
         st.iterations = hs.iter;
         st.relres_recursive = hs.bb > 0 ? std::sqrt(hs.rr / hs.bb) : 0.0;
         status = hs.status;
@@ -355,10 +387,12 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
                 h->ws.b32, h->ws.r32, h->ws.z32, h->minv32, h->mult, n, o.inner_tol, o.max_iter, h->state + 1,
                 h->partials, h->counters + 5);
             SEM_LAUNCH_CHECK("ir prepare");
-            if ((rc = run_cg_loop(h, SEM_FP32, o, 1, s, &hs))) return rc;
+            h->launches += 2;
+            if ((rc = run_cg_loop(h, SEM_FP32, o, 1, s, &hs, &tm))) return rc;
             inner += hs.iter;
             ir_correct_kernel<<<grid_for(h, n, 256, 8), 256, 0, s>>>(h->ws.x, h->ws.d32, rrbb, n);
             SEM_LAUNCH_CHECK("ir_correct_kernel");
+            h->launches++;
             outer++;
         }
         st.iterations = inner;
@@ -378,6 +412,9 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
     st.relres = hb[1] > 0 ? std::sqrt(hb[0] / hb[1]) : 0.0;
     st.time_ms = ms;
     st.status = status;
+    st.kernel_launches = h->launches - launches0;
+    st.ax_samples = tm.samples;
+    st.ax_ms = tm.samples ? tm.ms / tm.samples : 0.0;
     if (stats) *stats = st;
     if (status != SEM_OK) {
         const char* what = status == SEM_ENOTCONV   ? "not converged within max_iter / max_outer"

@@ -44,6 +44,7 @@ int launch_gs(sem_handle* h, void* u, bool fp32, bool apply_mask, cudaStream_t s
         gs_kernel<double><<<grid, 256, 0, s>>>((double*)u, g.seg_off, g.seg_idx, g.nseg_free, g.nseg,
                                                g.zero_idx, g.nzero, apply_mask ? 1 : 0);
     SEM_LAUNCH_CHECK("gs_kernel");
+    h->launches++;
     return SEM_OK;
 }
 
@@ -68,6 +69,7 @@ int launch_dot(sem_handle* h, const double* a, const double* b, double* out, cud
         dot_kernel<<<grid, 256, 0, s>>>(a + p.loc_off, b + p.loc_off, h->mult + p.loc_off, p.n_local,
                                         h->partials, h->counters + 1, out + q);
         SEM_LAUNCH_CHECK("dot_kernel");
+        h->launches++;
     }
     return SEM_OK;
 }

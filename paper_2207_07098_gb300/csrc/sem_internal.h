@@ -138,6 +138,8 @@ struct sem_handle {
     sem::Workspace ws;
     sem::GraphCache graph;
     cudaStream_t capture_stream = nullptr;
+    cudaEvent_t ax_ev[2] = {nullptr, nullptr};  // bracket the first K-A of each graph
+    int64_t launches = 0;                        // kernels launched by this handle
     size_t device_bytes = 0;
 };
 

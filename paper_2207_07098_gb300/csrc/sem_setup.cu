@@ -309,6 +309,8 @@ static void free_handle(sem_handle* h) {
     cudaFree(w.r32); cudaFree(w.p32); cudaFree(w.z32); cudaFree(w.w32); cudaFree(w.d32); cudaFree(w.b32);
     if (h->graph.exec) cudaGraphExecDestroy(h->graph.exec);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+    for (auto& ev : h->ax_ev)
+        if (ev) cudaEventDestroy(ev);
     delete h;
 }
 
