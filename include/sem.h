@@ -189,6 +189,29 @@ SEM_API int sem_mass(sem_handle* h, void* w, const void* u, int precision, int a
 SEM_API int sem_dot(sem_handle* h, const double* a, const double* b, double* result,
                     cudaStream_t stream);
 
+/* result[q] = <a, b> over the unique nodes of mesh q, like sem_dot, but the
+ * call allocates nothing and uses no memory owned by the handle: its scratch
+ * (one FP64 partial sum per CTA and a ticket counter) is a fixed device
+ * array inside the library.  The paper has no counterpart; this exists for
+ * callers that cannot call cudaMalloc at the point where they need the
+ * product -- code recording a CUDA graph by stream capture (allocation is
+ * refused during a capture), applications whose device memory is held by
+ * their own pool allocator, latency-critical loops (cudaMalloc/cudaFree can
+ * synchronise the device).
+ *   h       handle from sem_setup / sem_setup_batch (read only)
+ *   a, b    device double [n_local]
+ *   result  device double[nsolve]
+ * Each CTA sums a fixed chunk of 32768 points, so the result is the same on
+ * every GPU; it equals sem_dot's up to rounding order.  Limit: at most
+ * 134,217,728 local points per mesh (4096 partial sums; the array takes
+ * 33 KB on every GPU that loads the library, until the process exits), else
+ * SEM_EINVAL.  The first call on each device looks up the array's device
+ * address; make that first call before any stream capture.  All calls share
+ * the array: each clears its counter first, and calls that overlap on the GPU
+ * (unordered streams) race and give wrong results. */
+SEM_API int sem_dot_noalloc(const sem_handle* h, const double* a, const double* b, double* result,
+                            cudaStream_t stream);
+
 /* Copies of set-up data (device outputs):
  *   G  [E][6][lx^3] factors h1*G11, h1*G12, h1*G13, h1*G22, h1*G23, h1*G33
  *   B  [n_local] mass rho rho rho J

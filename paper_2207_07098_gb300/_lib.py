@@ -71,6 +71,7 @@ _SIGS = {
     "sem_gs": (_I, [_VP, _VP, _I, _I, _VP]),
     "sem_mass": (_I, [_VP, _VP, _VP, _I, _I, _VP]),
     "sem_dot": (_I, [_VP, _VP, _VP, _VP, _VP]),
+    "sem_dot_noalloc": (_I, [_VP, _VP, _VP, _VP, _VP]),
     "sem_get_geometry": (_I, [_VP, _VP, _VP, _VP]),
     "sem_get_jacobi": (_I, [_VP, _VP, _VP]),
     "sem_cg_solve": (_I, [_VP, _VP, _VP, ctypes.POINTER(sem_solve_opts), ctypes.POINTER(sem_solve_stats), _VP]),
@@ -211,6 +212,12 @@ def sem_mass(h, w, u, precision: int = SEM_FP64, assemble: int = 1, stream=None)
 
 def sem_dot(h, a, b, result, stream=None) -> None:
     _check(load().sem_dot(ctypes.c_void_p(h), _ptr(a), _ptr(b), _ptr(result), _stream(stream)))
+
+
+def sem_dot_noalloc(h, a, b, result, stream=None) -> None:
+    """Like sem_dot, with the scratch in a fixed device array of the library
+    (no allocation; see include/sem.h for the limit and the sharing rules)."""
+    _check(load().sem_dot_noalloc(ctypes.c_void_p(h), _ptr(a), _ptr(b), _ptr(result), _stream(stream)))
 
 
 def sem_get_geometry(h, G=None, B=None, stream=None) -> None:
