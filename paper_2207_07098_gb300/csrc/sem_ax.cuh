@@ -40,16 +40,139 @@ constexpr size_t ax_smem_bytes() {
     return sizeof(T) * ((size_t)LX * AxCfg<LX>::DP + 3 * (size_t)AxCfg<LX>::EPC * AxCfg<LX>::N3);
 }
 
+// Shared-memory carve-up of one CTA: D (padded rows), then EPC element slots
+// of u, wr and ws.
+template <typename T, int LX>
+struct AxSmem {
+    T* sD;
+    T* su;
+    T* sr;
+    T* ss;
+    __device__ __forceinline__ explicit AxSmem(unsigned char* raw) {
+        using C = AxCfg<LX>;
+        sD = reinterpret_cast<T*>(raw);
+        su = sD + LX * C::DP;
+        sr = su + C::EPC * C::N3;
+        ss = sr + C::EPC * C::N3;
+    }
+};
+
+// Thread coordinates inside a CTA: element slot `el`, column (i, j).
+template <int LX>
+struct AxThread {
+    int el, ij, i, j, so;
+    bool active;
+    __device__ __forceinline__ AxThread() {
+        using C = AxCfg<LX>;
+        el = threadIdx.x / C::N2;
+        ij = threadIdx.x - el * C::N2;
+        i = ij % LX;
+        j = ij / LX;
+        active = el < C::EPC;
+        so = (active ? el : 0) * C::N3;
+    }
+};
+
+template <typename T, int LX>
+__device__ __forceinline__ void ax_load_d(T* sD, const T* D) {
+    constexpr int DP = AxCfg<LX>::DP;
+    for (int t = threadIdx.x; t < LX * LX; t += blockDim.x) sD[(t / LX) * DP + (t % LX)] = D[t];
+}
+
+// One group of up to EPC elements.  Element `e` of this thread (relative to
+// the pointers) is processed when `valid`.  Plain: w = A_L u.  FUSED:
+// u = z + beta p (p <- u; old p ignored on the first iteration), w = A_L u,
+// and the thread's partial sum of u.w is returned.  Contains two
+// __syncthreads(); every thread of the CTA must call it.
+template <typename T, int LX, bool FUSED>
+__device__ __forceinline__ T ax_group(const AxSmem<T, LX>& sm, const AxThread<LX>& th, int64_t e, bool valid,
+                                      const T* __restrict__ u, const T* __restrict__ z, T* __restrict__ p,
+                                      T* __restrict__ w, const T* __restrict__ G, T tbeta, bool first) {
+    using C = AxCfg<LX>;
+    constexpr int N2 = C::N2, N3 = C::N3, DP = C::DP;
+    const T* sD = sm.sD;
+    T* su = sm.su;
+    T* sr = sm.sr;
+    T* ss = sm.ss;
+    const int so = th.so, ij = th.ij, i = th.i, j = th.j;
+    const int64_t base = e * N3 + ij;
+    T ucol[LX];
+    // all loads of the column first, then the p stores: no load waits on a store
+#pragma unroll
+    for (int k = 0; k < LX; k++) {
+        if (FUSED) {
+            ucol[k] = valid ? ld_stream(z + base + k * N2) : T(0);
+        } else {
+            ucol[k] = valid ? ld_stream(u + base + k * N2) : T(0);
+        }
+    }
+    if (FUSED) {
+        T pold[LX];
+#pragma unroll
+        for (int k = 0; k < LX; k++) pold[k] = (valid && !first) ? p[base + k * N2] : T(0);
+#pragma unroll
+        for (int k = 0; k < LX; k++) {
+            ucol[k] = fma(tbeta, pold[k], ucol[k]);
+            if (valid) p[base + k * N2] = ucol[k];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < LX; k++)
+        if (th.active) su[so + k * N2 + ij] = ucol[k];
+    __syncthreads();
+    T wt[LX];
+    const T* Ge = G + e * 6 * N3 + ij;
+#pragma unroll
+    for (int k = 0; k < LX; k++) {
+        T ur = T(0), us = T(0), ut = T(0);
+#pragma unroll
+        for (int l = 0; l < LX; l++) {
+            ur = fma(sD[i * DP + l], su[so + k * N2 + j * LX + l], ur);
+            us = fma(sD[j * DP + l], su[so + k * N2 + l * LX + i], us);
+            ut = fma(sD[k * DP + l], ucol[l], ut);
+        }
+        T g11 = T(0), g12 = T(0), g13 = T(0), g22 = T(0), g23 = T(0), g33 = T(0);
+        if (valid) {
+            g11 = ld_stream(Ge + 0 * N3 + k * N2);
+            g12 = ld_stream(Ge + 1 * N3 + k * N2);
+            g13 = ld_stream(Ge + 2 * N3 + k * N2);
+            g22 = ld_stream(Ge + 3 * N3 + k * N2);
+            g23 = ld_stream(Ge + 4 * N3 + k * N2);
+            g33 = ld_stream(Ge + 5 * N3 + k * N2);
+        }
+        const T wr = fma(g11, ur, fma(g12, us, g13 * ut));
+        const T ws = fma(g12, ur, fma(g22, us, g23 * ut));
+        wt[k] = fma(g13, ur, fma(g23, us, g33 * ut));
+        if (th.active) {
+            sr[so + k * N2 + ij] = wr;
+            ss[so + k * N2 + ij] = ws;
+        }
+    }
+    __syncthreads();
+    T pw = T(0);
+#pragma unroll
+    for (int k = 0; k < LX; k++) {
+        T acc = T(0);
+#pragma unroll
+        for (int l = 0; l < LX; l++) {
+            acc = fma(sD[l * DP + i], sr[so + k * N2 + j * LX + l], acc);
+            acc = fma(sD[l * DP + j], ss[so + k * N2 + l * LX + i], acc);
+            acc = fma(sD[l * DP + k], wt[l], acc);
+        }
+        if (valid) {
+            st_stream(w + base + k * N2, acc);
+            if (FUSED) pw = fma(ucol[k], acc, pw);
+        }
+    }
+    return pw;
+}
+
 template <typename T, int LX, bool FUSED>
 __global__ void __launch_bounds__(AxCfg<LX>::THREADS) ax_kernel(AxParams<T> a) {
     using C = AxCfg<LX>;
-    constexpr int N2 = C::N2, N3 = C::N3, EPC = C::EPC, DP = C::DP;
+    constexpr int EPC = C::EPC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sD = reinterpret_cast<T*>(smem_raw);
-    T* su = sD + LX * DP;
-    T* sr = su + EPC * N3;
-    T* ss = sr + EPC * N3;
-
+    const AxSmem<T, LX> sm(smem_raw);
     double beta = 0.0;
     bool first = false;
     if (FUSED) {
@@ -57,85 +180,16 @@ __global__ void __launch_bounds__(AxCfg<LX>::THREADS) ax_kernel(AxParams<T> a) {
         beta = cg_beta(a.st);
         first = (a.st->iter == 0);
     }
-    for (int t = threadIdx.x; t < LX * LX; t += blockDim.x) sD[(t / LX) * DP + (t % LX)] = a.D[t];
-
-    const int tid = threadIdx.x;
-    const int el = tid / N2;
-    const int ij = tid - el * N2;
-    const int i = ij % LX, j = ij / LX;
-    const bool active = el < EPC;
-    const int so = (active ? el : 0) * N3;  // this thread's element slot in shared memory
+    ax_load_d<T, LX>(sm.sD, a.D);
+    const AxThread<LX> th;
     const int64_t ngroups = (a.E + EPC - 1) / EPC;
     double pap = 0.0;
     const T tbeta = (T)beta;
     __syncthreads();
-
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
-        const int64_t e = g * EPC + el;
-        const bool valid = active && e < a.E;
-        const int64_t base = e * N3 + ij;
-        T ucol[LX];
-#pragma unroll
-        for (int k = 0; k < LX; k++) {
-            T v = T(0);
-            if (valid) {
-                if (FUSED) {
-                    const T zz = ld_stream(a.z + base + k * N2);
-                    const T pp = first ? T(0) : a.p[base + k * N2];
-                    v = fma(tbeta, pp, zz);
-                    a.p[base + k * N2] = v;
-                } else {
-                    v = ld_stream(a.u + base + k * N2);
-                }
-            }
-            ucol[k] = v;
-            if (active) su[so + k * N2 + ij] = v;
-        }
-        __syncthreads();
-        T wt[LX];
-        const T* Ge = a.G + e * 6 * N3 + ij;
-#pragma unroll
-        for (int k = 0; k < LX; k++) {
-            T ur = T(0), us = T(0), ut = T(0);
-#pragma unroll
-            for (int l = 0; l < LX; l++) {
-                ur = fma(sD[i * DP + l], su[so + k * N2 + j * LX + l], ur);
-                us = fma(sD[j * DP + l], su[so + k * N2 + l * LX + i], us);
-                ut = fma(sD[k * DP + l], ucol[l], ut);
-            }
-            T g11 = T(0), g12 = T(0), g13 = T(0), g22 = T(0), g23 = T(0), g33 = T(0);
-            if (valid) {
-                g11 = ld_stream(Ge + 0 * N3 + k * N2);
-                g12 = ld_stream(Ge + 1 * N3 + k * N2);
-                g13 = ld_stream(Ge + 2 * N3 + k * N2);
-                g22 = ld_stream(Ge + 3 * N3 + k * N2);
-                g23 = ld_stream(Ge + 4 * N3 + k * N2);
-                g33 = ld_stream(Ge + 5 * N3 + k * N2);
-            }
-            const T wr = fma(g11, ur, fma(g12, us, g13 * ut));
-            const T ws = fma(g12, ur, fma(g22, us, g23 * ut));
-            wt[k] = fma(g13, ur, fma(g23, us, g33 * ut));
-            if (active) {
-                sr[so + k * N2 + ij] = wr;
-                ss[so + k * N2 + ij] = ws;
-            }
-        }
-        __syncthreads();
-        T pw = T(0);
-#pragma unroll
-        for (int k = 0; k < LX; k++) {
-            T acc = T(0);
-#pragma unroll
-            for (int l = 0; l < LX; l++) {
-                acc = fma(sD[l * DP + i], sr[so + k * N2 + j * LX + l], acc);
-                acc = fma(sD[l * DP + j], ss[so + k * N2 + l * LX + i], acc);
-                acc = fma(sD[l * DP + k], wt[l], acc);
-            }
-            if (valid) {
-                st_stream(a.w + base + k * N2, acc);
-                if (FUSED) pw = fma(ucol[k], acc, pw);
-            }
-        }
+        const int64_t e = g * EPC + th.el;
+        const bool valid = th.active && e < a.E;
+        const T pw = ax_group<T, LX, FUSED>(sm, th, e, valid, a.u, a.z, a.p, a.w, a.G, tbeta, first);
         if (FUSED) pap += (double)pw;
         __syncthreads();
     }

@@ -1,6 +1,581 @@
-// Batched solves over many independent meshes (placeholder until the
-// persistent batched kernels land).
+// Batched Poisson solves over many independent meshes of different sizes and
+// orders (one handle from sem_setup_batch).  Every CG iteration advances all
+// unconverged solves with one set of launches: the fused p-update + ax_helm
+// (one persistent launch per order present, over the element groups of every
+// solve of that order), the gather-scatter over all meshes, and the x/r/z
+// update over point tiles.  Each solve keeps its own scalars (CGState) and is
+// reduced in a fixed order, so every member of a batch is bit-reproducible;
+// converged solves are skipped.  The iterations are captured in CUDA graphs.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "sem_batch.cuh"
 #include "sem_internal.h"
+
+namespace sem {
+
+struct TileList {
+    const int64_t* tloc;
+    const int* tlen;
+    const int* tsolve;
+    int64_t ntiles;
+    const int* stfirst;
+    const int* stcount;
+    double* tpart;
+    unsigned int* scount;
+};
+
+// Per-tile partials -> per-solve sums in tile order, by the CTA that finishes
+// the solve's last tile.  Returns true in thread 0 of that CTA with sums in acc.
+template <int NV>
+__device__ __forceinline__ bool tile_finalize(const TileList& tl, int64_t t, int s, double (&v)[NV],
+                                              double (&acc)[NV], double* red, int* is_last) {
+    block_sum<NV>(v, red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; q++) tl.tpart[t * 3 + q] = v[q];
+        __threadfence();
+        *is_last = (atomicAdd(&tl.scount[s], 1u) == (unsigned)tl.stcount[s] - 1u) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!*is_last) return false;
+    __threadfence();
+    const int f = tl.stfirst[s], c = tl.stcount[s];
+#pragma unroll
+    for (int q = 0; q < NV; q++) acc[q] = 0.0;
+    for (int k = threadIdx.x; k < c; k += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < NV; q++) acc[q] += __ldcg(&tl.tpart[(int64_t)(f + k) * 3 + q]);
+    block_sum<NV>(acc, red);
+    if (threadIdx.x == 0) {
+        tl.scount[s] = 0u;
+        return true;
+    }
+    return false;
+}
+
+// K-C over tiles: x += alpha p; r -= alpha w; z = Minv r; <r,z>, <r,r> per solve.
+template <typename T>
+__global__ void __launch_bounds__(256) upd_batch_kernel(T* x, const T* p, T* r, const T* w, T* z, const T* minv,
+                                                         const uint8_t* mult, CGState* st_base, TileList tl) {
+    __shared__ T inv[256];
+    __shared__ double red[64];
+    __shared__ int is_last;
+    for (int m = threadIdx.x; m < 256; m += blockDim.x) inv[m] = m ? (T)(1.0 / m) : T(0);
+    __syncthreads();
+    for (int64_t t = blockIdx.x; t < tl.ntiles; t += gridDim.x) {
+        const int s = tl.tsolve[t];
+        CGState* st = st_base + s;
+        if (st->done) continue;
+        const T ta = (T)st->alpha;
+        const int64_t l0 = tl.tloc[t], l1 = l0 + tl.tlen[t];
+        T lrz = T(0), lrr = T(0);
+        for (int64_t L = l0 + threadIdx.x; L < l1; L += blockDim.x) {
+            const T xv = fma(ta, p[L], x[L]);
+            const T rv = fma(-ta, w[L], r[L]);
+            const T zv = minv[L] * rv;
+            x[L] = xv;
+            r[L] = rv;
+            z[L] = zv;
+            const T iv = inv[mult[L]];
+            lrz = fma(rv * zv, iv, lrz);
+            lrr = fma(rv * rv, iv, lrr);
+        }
+        double v[2] = {(double)lrz, (double)lrr}, acc[2];
+        if (tile_finalize<2>(tl, t, s, v, acc, red, &is_last)) cg_set_rho(st, acc[0], acc[1]);
+        __syncthreads();
+    }
+}
+
+// CG start per solve: z = Minv r; rho, rr, bb.  Solves with act[s] == 0 are
+// marked done without work.
+template <typename T>
+__global__ void __launch_bounds__(256) init_batch_kernel(const T* b, const T* r, T* z, const T* minv,
+                                                          const uint8_t* mult, CGState* st_base, TileList tl,
+                                                          const int* act, double tol, int max_iter) {
+    __shared__ double inv[256];
+    __shared__ double red[96];
+    __shared__ int is_last;
+    for (int m = threadIdx.x; m < 256; m += blockDim.x) inv[m] = m ? 1.0 / m : 0.0;
+    __syncthreads();
+    for (int64_t t = blockIdx.x; t < tl.ntiles; t += gridDim.x) {
+        const int s = tl.tsolve[t];
+        CGState* st = st_base + s;
+        if (act && !act[s]) {
+            if (threadIdx.x == 0 && t == tl.stfirst[s]) {
+                st->done = 1;
+                st->status = SEM_OK;
+                st->iter = 0;
+                st->max_iter = max_iter;
+            }
+            continue;
+        }
+        const int64_t l0 = tl.tloc[t], l1 = l0 + tl.tlen[t];
+        double v[3] = {0.0, 0.0, 0.0}, acc[3];
+        for (int64_t L = l0 + threadIdx.x; L < l1; L += blockDim.x) {
+            const T zv = minv[L] * r[L];
+            z[L] = zv;
+            const double rv = (double)r[L], bv = (double)b[L], iv = inv[mult[L]];
+            v[0] = fma(rv * (double)zv, iv, v[0]);
+            v[1] = fma(rv * rv, iv, v[1]);
+            v[2] = fma(bv * bv, iv, v[2]);
+        }
+        if (tile_finalize<3>(tl, t, s, v, acc, red, &is_last)) {
+            st->rho = acc[0];
+            st->rho_old = 1.0;
+            st->rr = acc[1];
+            st->bb = acc[2];
+            st->tol2 = tol * tol * acc[2];
+            st->alpha = 0.0;
+            st->pap = 0.0;
+            st->iter = 0;
+            st->max_iter = max_iter;
+            const bool conv = (acc[2] == 0.0 || acc[1] <= st->tol2);
+            st->done = (conv || max_iter <= 0) ? 1 : 0;
+            st->status = (conv || max_iter > 0) ? SEM_OK : SEM_ENOTCONV;
+        }
+        __syncthreads();
+    }
+}
+
+// r = b - w in FP64; rrbb[2s] = <r,r>, rrbb[2s+1] = <b,b> per solve.
+__global__ void __launch_bounds__(256) resid_batch_kernel(const double* b, const double* w, double* r,
+                                                           const uint8_t* mult, TileList tl, double* rrbb) {
+    __shared__ double inv[256];
+    __shared__ double red[64];
+    __shared__ int is_last;
+    for (int m = threadIdx.x; m < 256; m += blockDim.x) inv[m] = m ? 1.0 / m : 0.0;
+    __syncthreads();
+    for (int64_t t = blockIdx.x; t < tl.ntiles; t += gridDim.x) {
+        const int s = tl.tsolve[t];
+        const int64_t l0 = tl.tloc[t], l1 = l0 + tl.tlen[t];
+        double v[2] = {0.0, 0.0}, acc[2];
+        for (int64_t L = l0 + threadIdx.x; L < l1; L += blockDim.x) {
+            const double bv = b[L], rv = bv - w[L];
+            r[L] = rv;
+            const double iv = inv[mult[L]];
+            v[0] = fma(rv * rv, iv, v[0]);
+            v[1] = fma(bv * bv, iv, v[1]);
+        }
+        if (tile_finalize<2>(tl, t, s, v, acc, red, &is_last)) {
+            rrbb[2 * s] = acc[0];
+            rrbb[2 * s + 1] = acc[1];
+        }
+        __syncthreads();
+    }
+}
+
+// Refinement, per active solve: b32 = r32 = float(r / ||r||), d32 = 0.
+__global__ void prepare_batch_kernel(const double* r, float* b32, float* r32, float* d32, TileList tl,
+                                     const int* act, const double* rrbb) {
+    for (int64_t t = blockIdx.x; t < tl.ntiles; t += gridDim.x) {
+        const int s = tl.tsolve[t];
+        if (!act[s]) continue;
+        const double sc = 1.0 / sqrt(rrbb[2 * s]);
+        const int64_t l0 = tl.tloc[t], l1 = l0 + tl.tlen[t];
+        for (int64_t L = l0 + threadIdx.x; L < l1; L += blockDim.x) {
+            const float v = (float)(r[L] * sc);
+            b32[L] = v;
+            r32[L] = v;
+            d32[L] = 0.0f;
+        }
+    }
+}
+
+// Refinement, per active solve: x += ||r|| d32.
+__global__ void correct_batch_kernel(double* x, const float* d32, TileList tl, const int* act, const double* rrbb) {
+    for (int64_t t = blockIdx.x; t < tl.ntiles; t += gridDim.x) {
+        const int s = tl.tsolve[t];
+        if (!act[s]) continue;
+        const double sc = sqrt(rrbb[2 * s]);
+        const int64_t l0 = tl.tloc[t], l1 = l0 + tl.tlen[t];
+        for (int64_t L = l0 + threadIdx.x; L < l1; L += blockDim.x) x[L] = fma(sc, (double)d32[L], x[L]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+static int epc_of(int lx) { return std::max(1, 256 / (lx * lx)); }
+
+static int build_plan(sem_handle* h) {
+    BatchPlan& bp = h->batch;
+    if (bp.ready) return SEM_OK;
+    const int ns = h->nsolve;
+    std::vector<int> lxs;
+    for (auto& p : h->parts) lxs.push_back(p.lx);
+    std::sort(lxs.begin(), lxs.end());
+    lxs.erase(std::unique(lxs.begin(), lxs.end()), lxs.end());
+    std::vector<int> sgfirst(ns), sgcount(ns);
+    int64_t goff = 0;
+    int rc;
+    for (int lx : lxs) {
+        const int epc = epc_of(lx);
+        const int64_t n3 = (int64_t)lx * lx * lx;
+        std::vector<int64_t> loc;
+        std::vector<int> cnt, sol;
+        for (int q = 0; q < ns; q++) {
+            const MeshPart& p = h->parts[q];
+            if (p.lx != lx) continue;
+            sgfirst[q] = (int)(goff + (int64_t)loc.size());
+            for (int e0 = 0; e0 < p.E; e0 += epc) {
+                loc.push_back(p.loc_off + (int64_t)e0 * n3);
+                cnt.push_back(std::min(epc, p.E - e0));
+                sol.push_back(q);
+            }
+            sgcount[q] = (int)(goff + (int64_t)loc.size()) - sgfirst[q];
+        }
+        LxGroups g;
+        g.lx = lx;
+        g.ngroups = (int64_t)loc.size();
+        g.goff = goff;
+        if ((rc = dalloc(h, &g.loc, loc.size())) || (rc = dalloc(h, &g.cnt, cnt.size())) ||
+            (rc = dalloc(h, &g.solve, sol.size())))
+            return rc;
+        SEM_CUDA_TRY(cudaMemcpy(g.loc, loc.data(), loc.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+        SEM_CUDA_TRY(cudaMemcpy(g.cnt, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice));
+        SEM_CUDA_TRY(cudaMemcpy(g.solve, sol.data(), sol.size() * sizeof(int), cudaMemcpyHostToDevice));
+        goff += g.ngroups;
+        bp.lxg.push_back(g);
+    }
+    bp.ngroups = goff;
+    std::vector<int64_t> tloc;
+    std::vector<int> tlen, tsol, stfirst(ns), stcount(ns);
+    for (int q = 0; q < ns; q++) {
+        const MeshPart& p = h->parts[q];
+        stfirst[q] = (int)tloc.size();
+        for (int64_t a = 0; a < p.n_local; a += kTile) {
+            tloc.push_back(p.loc_off + a);
+            tlen.push_back((int)std::min<int64_t>(kTile, p.n_local - a));
+            tsol.push_back(q);
+        }
+        stcount[q] = (int)tloc.size() - stfirst[q];
+    }
+    bp.ntiles = (int64_t)tloc.size();
+    if ((rc = dalloc(h, &bp.sgfirst, ns)) || (rc = dalloc(h, &bp.sgcount, ns)) ||
+        (rc = dalloc(h, &bp.tloc, tloc.size())) || (rc = dalloc(h, &bp.tlen, tlen.size())) ||
+        (rc = dalloc(h, &bp.tsolve, tsol.size())) || (rc = dalloc(h, &bp.stfirst, ns)) ||
+        (rc = dalloc(h, &bp.stcount, ns)) || (rc = dalloc(h, &bp.gpart, (size_t)bp.ngroups)) ||
+        (rc = dalloc(h, &bp.tpart, (size_t)bp.ntiles * 3)) || (rc = dalloc(h, &bp.scount, ns)) ||
+        (rc = dalloc(h, &bp.rrbb, (size_t)2 * ns)) || (rc = dalloc(h, &bp.act, ns)))
+        return rc;
+    SEM_CUDA_TRY(cudaMemcpy(bp.sgfirst, sgfirst.data(), ns * sizeof(int), cudaMemcpyHostToDevice));
+    SEM_CUDA_TRY(cudaMemcpy(bp.sgcount, sgcount.data(), ns * sizeof(int), cudaMemcpyHostToDevice));
+    SEM_CUDA_TRY(cudaMemcpy(bp.tloc, tloc.data(), tloc.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    SEM_CUDA_TRY(cudaMemcpy(bp.tlen, tlen.data(), tlen.size() * sizeof(int), cudaMemcpyHostToDevice));
+    SEM_CUDA_TRY(cudaMemcpy(bp.tsolve, tsol.data(), tsol.size() * sizeof(int), cudaMemcpyHostToDevice));
+    SEM_CUDA_TRY(cudaMemcpy(bp.stfirst, stfirst.data(), ns * sizeof(int), cudaMemcpyHostToDevice));
+    SEM_CUDA_TRY(cudaMemcpy(bp.stcount, stcount.data(), ns * sizeof(int), cudaMemcpyHostToDevice));
+    SEM_CUDA_TRY(cudaMemset(bp.scount, 0, ns * sizeof(unsigned)));
+    bp.ready = true;
+    return SEM_OK;
+}
+
+static TileList tiles(sem_handle* h) {
+    BatchPlan& bp = h->batch;
+    return TileList{bp.tloc, bp.tlen, bp.tsolve, bp.ntiles, bp.stfirst, bp.stcount, bp.tpart, bp.scount};
+}
+
+static int grid_tiles(sem_handle* h) { return grid_for(h, h->batch.ntiles * 256, 256, 8); }
+
+// K-A over every order present: fused (CG state slot base `st`) or plain.
+static int batch_ax(sem_handle* h, bool fp32, bool fused, const void* u, CGState* st, cudaStream_t s) {
+    BatchPlan& bp = h->batch;
+    for (const LxGroups& g : bp.lxg) {
+        int rc;
+        if (fp32) {
+            BatchAxParams<float> a = {};
+            a.u = (const float*)u;
+            a.z = h->ws.z32;
+            a.p = h->ws.p32;
+            a.w = h->ws.w32;
+            a.G = h->G32;
+            a.D = h->D32[g.lx];
+            a.loc = g.loc; a.cnt = g.cnt; a.solve = g.solve; a.ngroups = g.ngroups; a.goff = g.goff;
+            a.st = st; a.sgfirst = bp.sgfirst; a.sgcount = bp.sgcount; a.gpart = bp.gpart; a.scount = bp.scount;
+            rc = dispatch_ax_batch_f32(h, g.lx, a, fused, s);
+        } else {
+            BatchAxParams<double> a = {};
+            a.u = (const double*)u;
+            a.z = h->ws.z;
+            a.p = h->ws.p;
+            a.w = h->ws.w;
+            a.G = h->G64;
+            a.D = h->D64[g.lx];
+            a.loc = g.loc; a.cnt = g.cnt; a.solve = g.solve; a.ngroups = g.ngroups; a.goff = g.goff;
+            a.st = st; a.sgfirst = bp.sgfirst; a.sgcount = bp.sgcount; a.gpart = bp.gpart; a.scount = bp.scount;
+            rc = dispatch_ax_batch_f64(h, g.lx, a, fused, s);
+        }
+        if (rc) return rc;
+    }
+    return SEM_OK;
+}
+
+static int prepare_batch_kernels(sem_handle* h) {
+    for (const LxGroups& g : h->batch.lxg) {
+        BatchAxParams<double> a = {};
+        a.dry = 1;
+        BatchAxParams<float> b = {};
+        b.dry = 1;
+        int rc = dispatch_ax_batch_f64(h, g.lx, a, true, 0);
+        if (!rc) rc = dispatch_ax_batch_f64(h, g.lx, a, false, 0);
+        if (!rc) rc = dispatch_ax_batch_f32(h, g.lx, b, true, 0);
+        if (!rc) rc = dispatch_ax_batch_f32(h, g.lx, b, false, 0);
+        if (rc) return rc;
+    }
+    return SEM_OK;
+}
+
+static int batch_iteration(sem_handle* h, bool fp32, CGState* st, cudaStream_t s) {
+    int rc = batch_ax(h, fp32, true, nullptr, st, s);
+    if (rc) return rc;
+    if ((rc = launch_gs(h, fp32 ? (void*)h->ws.w32 : (void*)h->ws.w, fp32, true, s))) return rc;
+    if (fp32)
+        upd_batch_kernel<float><<<grid_tiles(h), 256, 0, s>>>(h->ws.d32, h->ws.p32, h->ws.r32, h->ws.w32, h->ws.z32,
+                                                               h->minv32, h->mult, st, tiles(h));
+    else
+        upd_batch_kernel<double><<<grid_tiles(h), 256, 0, s>>>(h->ws.x, h->ws.p, h->ws.r, h->ws.w, h->ws.z,
+                                                                h->minv64, h->mult, st, tiles(h));
+    SEM_LAUNCH_CHECK("upd_batch_kernel");
+    h->launches++;
+    return SEM_OK;
+}
+
+static int batch_graph(sem_handle* h, bool fp32, CGState* st, int chunk, cudaGraphExec_t* out, int* per_launch) {
+    GraphCache& g = h->graph;
+    const int key = 100 + (fp32 ? 1 : 0);
+    if (g.exec && g.key_prec == key && g.key_chunk == chunk && g.key_ptr == st) {
+        *out = g.exec;
+        *per_launch = (int)h->batch.lxg.size() + 2;
+        return SEM_OK;
+    }
+    if (g.exec) {
+        cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+    }
+    if (!h->capture_stream) SEM_CUDA_TRY(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+    int rc = prepare_batch_kernels(h);
+    if (rc) return rc;
+    for (auto& ev : h->ax_ev)
+        if (!ev) SEM_CUDA_TRY(cudaEventCreate(&ev));
+    cudaStream_t cs = h->capture_stream;
+    const int64_t before = h->launches;
+    SEM_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    for (int it = 0; it < chunk && rc == SEM_OK; it++) {
+        if (it == 0 && cudaEventRecordWithFlags(h->ax_ev[0], cs, cudaEventRecordExternal) != cudaSuccess)
+            rc = fail(SEM_ECUDA, "event record");
+        if (!rc) rc = batch_ax(h, fp32, true, nullptr, st, cs);
+        if (it == 0 && !rc && cudaEventRecordWithFlags(h->ax_ev[1], cs, cudaEventRecordExternal) != cudaSuccess)
+            rc = fail(SEM_ECUDA, "event record");
+        if (!rc) rc = launch_gs(h, fp32 ? (void*)h->ws.w32 : (void*)h->ws.w, fp32, true, cs);
+        if (!rc) {
+            if (fp32)
+                upd_batch_kernel<float><<<grid_tiles(h), 256, 0, cs>>>(h->ws.d32, h->ws.p32, h->ws.r32, h->ws.w32,
+                                                                        h->ws.z32, h->minv32, h->mult, st, tiles(h));
+            else
+                upd_batch_kernel<double><<<grid_tiles(h), 256, 0, cs>>>(h->ws.x, h->ws.p, h->ws.r, h->ws.w, h->ws.z,
+                                                                         h->minv64, h->mult, st, tiles(h));
+            if (cudaGetLastError() != cudaSuccess) rc = fail(SEM_ECUDA, "upd_batch_kernel launch");
+        }
+    }
+    h->launches = before;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        g.exec = nullptr;
+        return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    g.key_prec = key;
+    g.key_chunk = chunk;
+    g.key_ptr = st;
+    *out = g.exec;
+    *per_launch = (int)h->batch.lxg.size() + 2;
+    return SEM_OK;
+}
+
+// Iterate until every state in [st, st + ns) is done.
+static int batch_loop(sem_handle* h, bool fp32, CGState* st, const sem_solve_opts& o, cudaStream_t s,
+                      std::vector<CGState>& hs, double* ax_ms_sum, int* ax_samples) {
+    const int ns = h->nsolve;
+    const int chunk = std::max(1, std::min(o.graph_chunk, 1024));
+    cudaGraphExec_t exec = nullptr;
+    int per_launch = 0;
+    if (o.use_graph) {
+        int rc = batch_graph(h, fp32, st, chunk, &exec, &per_launch);
+        if (rc) return rc;
+    }
+    auto read = [&]() -> int {
+        SEM_CUDA_TRY(cudaMemcpyAsync(h->state_host, st, sizeof(CGState) * ns, cudaMemcpyDeviceToHost, s));
+        SEM_CUDA_TRY(cudaStreamSynchronize(s));
+        std::copy(h->state_host, h->state_host + ns, hs.begin());
+        return SEM_OK;
+    };
+    int rc = read();
+    if (rc) return rc;
+    auto all_done = [&]() {
+        for (auto& x : hs)
+            if (!x.done) return false;
+        return true;
+    };
+    const int64_t max_rounds = (int64_t)o.max_iter / chunk + 3;
+    for (int64_t round = 0; !all_done() && round < max_rounds; round++) {
+        if (exec) {
+            SEM_CUDA_TRY(cudaGraphLaunch(exec, s));
+            h->launches += (int64_t)per_launch * chunk;
+        } else {
+            for (int it = 0; it < chunk; it++)
+                if ((rc = batch_iteration(h, fp32, st, s))) return rc;
+        }
+        if ((rc = read())) return rc;
+        if (exec) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, h->ax_ev[0], h->ax_ev[1]) == cudaSuccess) {
+                *ax_ms_sum += ms;
+                (*ax_samples)++;
+            } else {
+                cudaGetLastError();
+            }
+        }
+    }
+    if (!all_done()) return fail(SEM_ETIMEOUT, "batched CG loop did not finish within its iteration budget");
+    return SEM_OK;
+}
+
+static int batch_true_residual(sem_handle* h, cudaStream_t s) {
+    int rc = batch_ax(h, false, false, h->ws.x, nullptr, s);
+    if (!rc) rc = launch_gs(h, h->ws.w, false, true, s);
+    if (rc) return rc;
+    resid_batch_kernel<<<grid_tiles(h), 256, 0, s>>>(h->ws.b, h->ws.w, h->ws.r, h->mult, tiles(h), h->batch.rrbb);
+    SEM_LAUNCH_CHECK("resid_batch_kernel");
+    h->launches++;
+    return SEM_OK;
+}
+
+static bool host_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+static int solve_batch(sem_handle* h, double* x_user, const double* b_user, const sem_solve_opts& o,
+                       sem_solve_stats* stats, cudaStream_t s) {
+    int rc = ensure_workspace(h, o.mode == SEM_MODE_MIXED_IR);
+    if (!rc) rc = build_plan(h);
+    if (rc) return rc;
+    const int ns = h->nsolve;
+    const int64_t n = h->n_local;
+    const size_t bytes = sizeof(double) * n;
+    BatchPlan& bp = h->batch;
+    const bool xh = host_ptr(x_user), bh = host_ptr(b_user);
+    const int64_t launches0 = h->launches;
+    cudaEvent_t ev0, ev1;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    cudaEventRecord(ev0, s);
+    SEM_CUDA_TRY(cudaMemcpyAsync(h->ws.x, x_user, bytes, xh ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    SEM_CUDA_TRY(cudaMemcpyAsync(h->ws.b, b_user, bytes, bh ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    std::vector<CGState> hs(ns);
+    std::vector<int> status(ns, SEM_OK), iters(ns, 0), outer(ns, 0);
+    std::vector<double> rrbb(2 * ns);
+    double ax_sum = 0.0;
+    int ax_n = 0;
+    auto read_rrbb = [&]() -> int {
+        SEM_CUDA_TRY(cudaMemcpyAsync(rrbb.data(), bp.rrbb, sizeof(double) * 2 * ns, cudaMemcpyDeviceToHost, s));
+        SEM_CUDA_TRY(cudaStreamSynchronize(s));
+        return SEM_OK;
+    };
+    if ((rc = batch_true_residual(h, s))) return rc;
+    if (o.mode == SEM_MODE_FP64) {
+        init_batch_kernel<double><<<grid_tiles(h), 256, 0, s>>>(h->ws.b, h->ws.r, h->ws.z, h->minv64, h->mult, h->state,
+                                                                 tiles(h), nullptr, o.tol, o.max_iter);
+        SEM_LAUNCH_CHECK("init_batch_kernel");
+        h->launches++;
+        if ((rc = batch_loop(h, false, h->state, o, s, hs, &ax_sum, &ax_n))) return rc;
+        for (int q = 0; q < ns; q++) {
+            status[q] = hs[q].status;
+            iters[q] = hs[q].iter;
+        }
+        if ((rc = batch_true_residual(h, s)) || (rc = read_rrbb())) return rc;
+    } else {
+        std::vector<double> prev(ns, INFINITY);
+        std::vector<int> act(ns, 0), fin(ns, 0);
+        if ((rc = read_rrbb())) return rc;
+        CGState* inner = h->state + ns;
+        for (int round = 0;; round++) {
+            int nact = 0;
+            for (int q = 0; q < ns; q++) {
+                act[q] = 0;
+                if (fin[q]) continue;
+                const double bb = rrbb[2 * q + 1];
+                const double rel = bb > 0 ? std::sqrt(rrbb[2 * q] / bb) : 0.0;
+                if (bb == 0.0 || rel <= o.tol) { status[q] = SEM_OK; fin[q] = 1; }
+                else if (!std::isfinite(rel)) { status[q] = SEM_EBREAKDOWN; fin[q] = 1; }
+                else if (outer[q] >= o.max_outer) { status[q] = SEM_ENOTCONV; fin[q] = 1; }
+                else if (outer[q] > 0 && rel > 0.5 * prev[q]) { status[q] = SEM_ESTAGNATE; fin[q] = 1; }
+                else { act[q] = 1; prev[q] = rel; nact++; }
+            }
+            if (nact == 0) break;
+            SEM_CUDA_TRY(cudaMemcpyAsync(bp.act, act.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
+            prepare_batch_kernel<<<grid_tiles(h), 256, 0, s>>>(h->ws.r, h->ws.b32, h->ws.r32, h->ws.d32, tiles(h),
+                                                               bp.act, bp.rrbb);
+            init_batch_kernel<float><<<grid_tiles(h), 256, 0, s>>>(h->ws.b32, h->ws.r32, h->ws.z32, h->minv32, h->mult,
+                                                                    inner, tiles(h), bp.act, o.inner_tol, o.max_iter);
+            SEM_LAUNCH_CHECK("batch refinement prepare");
+            h->launches += 2;
+            if ((rc = batch_loop(h, true, inner, o, s, hs, &ax_sum, &ax_n))) return rc;
+            for (int q = 0; q < ns; q++)
+                if (act[q]) {
+                    iters[q] += hs[q].iter;
+                    outer[q]++;
+                }
+            correct_batch_kernel<<<grid_tiles(h), 256, 0, s>>>(h->ws.x, h->ws.d32, tiles(h), bp.act, bp.rrbb);
+            SEM_LAUNCH_CHECK("correct_batch_kernel");
+            h->launches++;
+            if ((rc = batch_true_residual(h, s)) || (rc = read_rrbb())) return rc;
+        }
+    }
+    SEM_CUDA_TRY(cudaMemcpyAsync(x_user, h->ws.x, bytes, xh ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+    cudaEventRecord(ev1, s);
+    SEM_CUDA_TRY(cudaStreamSynchronize(s));
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    int worst = SEM_OK;
+    for (int q = 0; q < ns; q++) {
+        if (status[q] != SEM_OK && (worst == SEM_OK || status[q] > worst)) worst = status[q];
+        if (stats) {
+            sem_solve_stats& st = stats[q];
+            st = sem_solve_stats{};
+            st.status = status[q];
+            st.iterations = iters[q];
+            st.outer_iterations = o.mode == SEM_MODE_MIXED_IR ? outer[q] : 0;
+            const double bb = rrbb[2 * q + 1];
+            st.relres = bb > 0 ? std::sqrt(rrbb[2 * q] / bb) : 0.0;
+            st.relres_recursive = o.mode == SEM_MODE_FP64 && hs[q].bb > 0 ? std::sqrt(hs[q].rr / hs[q].bb) : st.relres;
+            st.time_ms = ms;
+            st.kernel_launches = h->launches - launches0;
+            st.ax_samples = ax_n;
+            st.ax_ms = ax_n ? ax_sum / ax_n : 0.0;
+        }
+    }
+    if (worst != SEM_OK) set_error("at least one solve of the batch did not converge (see per-solve stats)");
+    return worst;
+}
+
+}  // namespace sem
 
 using namespace sem;
 
@@ -8,9 +583,15 @@ extern "C" {
 
 SEM_API int sem_cg_solve_batch(sem_handle* h, double* x, const double* b, const sem_solve_opts* opts,
                                sem_solve_stats* stats, cudaStream_t s) {
-    (void)x; (void)b; (void)opts; (void)stats; (void)s;
-    if (!h) return fail(SEM_EINVAL, "null handle");
-    return fail(SEM_EINVAL, "batched solve not available in this build");
+    if (!h || !x || !b) return fail(SEM_EINVAL, "null argument");
+    sem_solve_opts o;
+    sem_solve_opts_default(&o);
+    if (opts) o = *opts;
+    if (!(o.tol > 0.0) || o.max_iter < 0 || (o.mode != SEM_MODE_FP64 && o.mode != SEM_MODE_MIXED_IR))
+        return fail(SEM_EINVAL, "bad solve options");
+    if (o.mode == SEM_MODE_MIXED_IR && !(o.inner_tol > 0.0 && o.inner_tol < 1.0))
+        return fail(SEM_EINVAL, "inner_tol must be in (0, 1)");
+    return solve_batch(h, x, b, o, stats, s);
 }
 
 }  // extern "C"

@@ -1,0 +1,128 @@
+// Kernels of the batched solve over many independent meshes: the local
+// operator over a list of element groups (one launch per order present, every
+// unconverged solve of that order in the same persistent launch), with the
+// per-solve CG scalars in device memory.  Each solve's <p, A p> is summed from
+// its group partials in group order by the CTA that finishes the solve's last
+// group, so every solve of a batch is bit-reproducible.
+#pragma once
+
+#include "sem_ax.cuh"
+
+namespace sem {
+
+template <typename T>
+struct BatchAxParams {
+    const T* u;            // plain variant input
+    const T* z;            // fused variant
+    T* p;
+    T* w;
+    const T* G;
+    const T* D;
+    const int64_t* loc;    // group lists of this order
+    const int* cnt;
+    const int* solve;
+    int64_t ngroups;
+    int64_t goff;
+    CGState* st;           // per-solve states
+    const int* sgfirst;
+    const int* sgcount;
+    double* gpart;
+    unsigned int* scount;
+    int dry;
+};
+
+template <typename T, int LX, bool FUSED>
+__global__ void __launch_bounds__(AxCfg<LX>::THREADS) ax_batch_kernel(BatchAxParams<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const AxSmem<T, LX> sm(smem_raw);
+    __shared__ double red[32];
+    __shared__ int is_last;
+    ax_load_d<T, LX>(sm.sD, a.D);
+    const AxThread<LX> th;
+    __syncthreads();
+    for (int64_t g = blockIdx.x; g < a.ngroups; g += gridDim.x) {
+        const int s = a.solve[g];
+        CGState* st = a.st + s;
+        double beta = 0.0;
+        bool first = false;
+        if (FUSED) {
+            // no write to this solve's state can happen before all its groups are done
+            if (st->done) continue;
+            beta = cg_beta(st);
+            first = (st->iter == 0);
+        }
+        const int64_t loc = a.loc[g];
+        const bool valid = th.active && th.el < a.cnt[g];
+        const T pw = ax_group<T, LX, FUSED>(sm, th, th.el, valid, FUSED ? nullptr : a.u + loc,
+                                            FUSED ? a.z + loc : nullptr, FUSED ? a.p + loc : nullptr,
+                                            a.w + loc, a.G + 6 * loc, (T)beta, first);
+        if (FUSED) {
+            double v[1] = {(double)pw};
+            block_sum<1>(v, red);
+            if (threadIdx.x == 0) {
+                a.gpart[a.goff + g] = v[0];
+                __threadfence();
+                is_last = (atomicAdd(&a.scount[s], 1u) == (unsigned)a.sgcount[s] - 1u) ? 1 : 0;
+            }
+            __syncthreads();
+            if (is_last) {
+                __threadfence();
+                const int f = a.sgfirst[s], c = a.sgcount[s];
+                double acc[1] = {0.0};
+                for (int q = threadIdx.x; q < c; q += blockDim.x) acc[0] += __ldcg(&a.gpart[f + q]);
+                block_sum<1>(acc, red);
+                if (threadIdx.x == 0) {
+                    cg_set_alpha(st, acc[0]);
+                    a.scount[s] = 0u;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, int LX, bool FUSED>
+inline int launch_ax_batch_t(sem_handle* h, const BatchAxParams<T>& a, cudaStream_t s) {
+    using C = AxCfg<LX>;
+    constexpr size_t smem = ax_smem_bytes<T, LX>();
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        cudaFuncSetAttribute(ax_batch_kernel<T, LX, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ax_batch_kernel<T, LX, FUSED>, C::THREADS, smem);
+        per_sm = nb > 0 ? nb : 1;
+    }
+    if (a.dry || a.ngroups == 0) return SEM_OK;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(a.ngroups, (int64_t)h->sm_count * per_sm));
+    ax_batch_kernel<T, LX, FUSED><<<(int)grid, C::THREADS, smem, s>>>(a);
+    SEM_LAUNCH_CHECK("ax_batch_kernel");
+    h->launches++;
+    return SEM_OK;
+}
+
+template <typename T, bool FUSED>
+inline int dispatch_ax_batch(sem_handle* h, int lx, const BatchAxParams<T>& a, cudaStream_t s) {
+    switch (lx) {
+        case 2: return launch_ax_batch_t<T, 2, FUSED>(h, a, s);
+        case 3: return launch_ax_batch_t<T, 3, FUSED>(h, a, s);
+        case 4: return launch_ax_batch_t<T, 4, FUSED>(h, a, s);
+        case 5: return launch_ax_batch_t<T, 5, FUSED>(h, a, s);
+        case 6: return launch_ax_batch_t<T, 6, FUSED>(h, a, s);
+        case 7: return launch_ax_batch_t<T, 7, FUSED>(h, a, s);
+        case 8: return launch_ax_batch_t<T, 8, FUSED>(h, a, s);
+        case 9: return launch_ax_batch_t<T, 9, FUSED>(h, a, s);
+        case 10: return launch_ax_batch_t<T, 10, FUSED>(h, a, s);
+        case 11: return launch_ax_batch_t<T, 11, FUSED>(h, a, s);
+        case 12: return launch_ax_batch_t<T, 12, FUSED>(h, a, s);
+        case 13: return launch_ax_batch_t<T, 13, FUSED>(h, a, s);
+        case 14: return launch_ax_batch_t<T, 14, FUSED>(h, a, s);
+        case 15: return launch_ax_batch_t<T, 15, FUSED>(h, a, s);
+        case 16: return launch_ax_batch_t<T, 16, FUSED>(h, a, s);
+        default: return fail(SEM_EINVAL, "lx out of range");
+    }
+}
+
+int dispatch_ax_batch_f64(sem_handle* h, int lx, const BatchAxParams<double>& a, bool fused, cudaStream_t s);
+int dispatch_ax_batch_f32(sem_handle* h, int lx, const BatchAxParams<float>& a, bool fused, cudaStream_t s);
+
+}  // namespace sem

@@ -98,6 +98,42 @@ struct Workspace {
     bool have64 = false, have32 = false;
 };
 
+// Work lists of a batch handle (device arrays).
+//  * K-A groups: for every order lx present, EPC(lx) consecutive elements of one
+//    solve per group; groups of a solve are contiguous.  A group's partial sum
+//    goes to gpart[global group index].
+//  * point tiles: up to kTile consecutive local points of one solve, for the
+//    vector updates and reductions; partials tpart[tile][3].
+struct LxGroups {
+    int lx = 0;
+    int64_t ngroups = 0;
+    int64_t goff = 0;         // global index of this list's first group
+    int64_t* loc = nullptr;   // [ngroups] local index of the group's first element
+    int* cnt = nullptr;       // [ngroups] elements in the group
+    int* solve = nullptr;     // [ngroups]
+};
+
+struct BatchPlan {
+    std::vector<LxGroups> lxg;
+    int64_t ngroups = 0;
+    int* sgfirst = nullptr;   // [nsolve] first global group of the solve
+    int* sgcount = nullptr;   // [nsolve]
+    int64_t ntiles = 0;
+    int64_t* tloc = nullptr;  // [ntiles]
+    int* tlen = nullptr;      // [ntiles]
+    int* tsolve = nullptr;    // [ntiles]
+    int* stfirst = nullptr;   // [nsolve]
+    int* stcount = nullptr;   // [nsolve]
+    double* gpart = nullptr;  // [ngroups]
+    double* tpart = nullptr;  // [ntiles * 3]
+    unsigned int* scount = nullptr;  // [nsolve] per-solve ticket counters
+    double* rrbb = nullptr;   // [nsolve * 2]
+    int* act = nullptr;       // [nsolve] solves taking part in an inner solve
+    bool ready = false;
+};
+
+constexpr int kTile = 4096;
+
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     int key_prec = -1;
@@ -132,11 +168,12 @@ struct sem_handle {
     // reductions and solver state
     double* partials = nullptr;       // [kMaxPartials * 4]
     unsigned int* counters = nullptr; // [16]
-    sem::CGState* state = nullptr;    // [nsolve]
-    sem::CGState* state_host = nullptr;  // pinned mirror [nsolve]
+    sem::CGState* state = nullptr;       // [2 nsolve + 2]: solve / outer states, then inner states
+    sem::CGState* state_host = nullptr;  // pinned mirror
     double* scratch = nullptr;        // [64] small device scratch
     sem::Workspace ws;
     sem::GraphCache graph;
+    sem::BatchPlan batch;
     cudaStream_t capture_stream = nullptr;
     cudaEvent_t ax_ev[2] = {nullptr, nullptr};  // bracket the first K-A of each graph
     int64_t launches = 0;                        // kernels launched by this handle

@@ -307,6 +307,13 @@ static void free_handle(sem_handle* h) {
     Workspace& w = h->ws;
     cudaFree(w.r); cudaFree(w.p); cudaFree(w.z); cudaFree(w.w); cudaFree(w.x); cudaFree(w.b);
     cudaFree(w.r32); cudaFree(w.p32); cudaFree(w.z32); cudaFree(w.w32); cudaFree(w.d32); cudaFree(w.b32);
+    BatchPlan& bp = h->batch;
+    for (auto& g : bp.lxg) {
+        cudaFree(g.loc); cudaFree(g.cnt); cudaFree(g.solve);
+    }
+    cudaFree(bp.sgfirst); cudaFree(bp.sgcount); cudaFree(bp.tloc); cudaFree(bp.tlen); cudaFree(bp.tsolve);
+    cudaFree(bp.stfirst); cudaFree(bp.stcount); cudaFree(bp.gpart); cudaFree(bp.tpart); cudaFree(bp.scount);
+    cudaFree(bp.rrbb); cudaFree(bp.act);
     if (h->graph.exec) cudaGraphExecDestroy(h->graph.exec);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     for (auto& ev : h->ax_ev)
@@ -419,10 +426,10 @@ static int setup_common(sem_handle** out, int nsolve, const sem_mesh_desc* meshe
         (rc = dalloc(h, &h->G64, (size_t)6 * n_local)) || (rc = dalloc(h, &h->G32, (size_t)6 * n_local)) ||
         (rc = dalloc(h, &h->B64, n_local)) || (rc = dalloc(h, &h->minv64, n_local)) ||
         (rc = dalloc(h, &h->minv32, n_local)) || (rc = dalloc(h, &h->partials, (size_t)kMaxPartials * 4)) ||
-        (rc = dalloc(h, &h->counters, 16)) || (rc = dalloc(h, &h->state, (size_t)nsolve + 2)) ||
+        (rc = dalloc(h, &h->counters, 16)) || (rc = dalloc(h, &h->state, (size_t)2 * nsolve + 2)) ||
         (rc = dalloc(h, &h->scratch, 64)))
         return bail(rc);
-    if (cudaMallocHost((void**)&h->state_host, sizeof(CGState) * (nsolve + 2)) != cudaSuccess)
+    if (cudaMallocHost((void**)&h->state_host, sizeof(CGState) * (2 * nsolve + 2)) != cudaSuccess)
         return bail(fail(SEM_ENOMEM, "cudaMallocHost failed"));
 #define UP(dst, src, bytes)                                                               \
     do {                                                                                  \
