@@ -62,6 +62,19 @@ def _dist():
     return ws, rank, local
 
 
+def combine_ranks(ms: float, units: float, dist=None, device=None):
+    """Whole-job figures over ranks: time = max over ranks, units = sum.
+    Each rank solves its own replica (no data-path collective)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms, units
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -243,15 +256,12 @@ def run_ours(args):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms_local = ev0.elapsed_time(ev1)
     iters = sum(s["iterations"] for s in stats)
     launches = sum(s["kernel_launches"] for s in stats)
     worst = max(s["relres"] for s in stats)
-    value = ws * n * iters / (ms * 1e-3) / 1e9
+    ms, units = combine_ranks(ms_local, float(n * iters), dist, "cuda")
+    value = units / (ms * 1e-3) / 1e9
 
     # e2e: the same solves through the C ABI with pinned host buffers (copies inside)
     xh = torch.zeros(n, dtype=torch.float64).pin_memory()
@@ -275,7 +285,12 @@ def run_ours(args):
     ka_bytes_pt = 9 * (4 if args.solver == "mixed" else 8)  # read z, p, 6 G; write p, w (h1 folded)
     ka_bytes = ka_bytes_pt * n
     achieved = ka_bytes / (ax_ms * 1e-3) / 1e9 if ax_ms else None
-    kname = "ax_kernel<float,8,true>" if args.solver == "mixed" else "ax_kernel<double,8,true>"
+    variant = stats[-1].get("ax_variant", 0)
+    tname = "float" if args.solver == "mixed" else "double"
+    cfgs = {1: (1, 3), 2: (2, 2), 3: (2, 3), 4: (4, 2)}
+    kname = (f"ax_kernel<{tname},{m.lx},true>" if variant == 0 else
+             f"ax_df_kernel<{m.lx},true>" if variant == 5 else
+             f"ax_bulk_kernel<{tname},{m.lx},{cfgs[variant][0]},{cfgs[variant][1]},true>")
     traffic = _traffic_for(kname, f"deformed_cube_{args.n}^3_N{args.order}")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None,
@@ -343,6 +358,28 @@ def _extras(S, torch, h, m, bd, n, args, peak, stats, ms_timed):
         gbs = bpp * n / (t * 1e-3) / 1e9
         axr[name] = {"ms": t, "gb_s": gbs, "frac_hbm": gbs / peak, "bytes_per_point": bpp}
     ex["ax_helm_only"] = axr
+    # every operator variant (pinned at set-up), plain ax_helm, both precisions
+    var = {}
+    for v in range(6):
+        hv = S.sem_setup(m.E, m.lx, m.coords, m.gid, m.mask, None, S.SEM_FLAG_VARIANT(v))
+        row = {}
+        for name, prec, dt, bpp in (("fp64", S.SEM_FP64, torch.float64, 64), ("fp32", S.SEM_FP32, torch.float32, 32)):
+            u = torch.randn(n, dtype=dt, device="cuda")
+            w = torch.empty_like(u)
+            for _ in range(3):
+                S.sem_ax(hv, w, u, prec, 0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(10):
+                S.sem_ax(hv, w, u, prec, 0)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 10
+            row[name] = {"ms": t, "gb_s": bpp * n / (t * 1e-3) / 1e9}
+        S.sem_destroy(hv)
+        var[str(v)] = row
+    ex["ax_variants"] = var
     return ex
 
 

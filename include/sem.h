@@ -97,6 +97,8 @@ typedef struct sem_solve_opts {
     int precision;       /* FP64 mode: SEM_FP64 or SEM_FP64_NATIVE operator */
     int use_graph;       /* capture the CG iterations in CUDA graphs (1) */
     int graph_chunk;     /* CG iterations per graph launch between host checks (32) */
+    int autotune;        /* time the operator-kernel variants on this handle's data at the
+                            first solve of each precision and keep the fastest (1) */
 } sem_solve_opts;
 
 typedef struct sem_solve_stats {
@@ -110,6 +112,9 @@ typedef struct sem_solve_stats {
     double ax_ms;             /* mean duration of the fused p-update + ax_helm kernel, sampled
                                  with CUDA events once per graph launch (0 if not sampled) */
     int ax_samples;           /* number of such samples */
+    int ax_variant;           /* operator kernel used by the CG loop: 0 = shared-slab staging,
+                                 1..4 = bulk-copy staging (elements per CTA, stages) =
+                                 (1,3), (2,2), (2,3), (4,2) */
 } sem_solve_stats;
 
 /* Mesh of one member of a batch (host pointers; see sem_setup). */
@@ -121,6 +126,9 @@ typedef struct sem_mesh_desc {
     const uint8_t* mask;    /* [E lx^3] */
     const double* h1;       /* [E lx^3] or NULL for h1 = 1 */
 } sem_mesh_desc;
+
+/* Set-up flag: pin operator kernel variant v (0..4) for every precision. */
+#define SEM_FLAG_VARIANT(v) ((int)(((v) + 1) & 0xF))
 
 /* Fill *opts with the defaults listed above. */
 SEM_API void sem_solve_opts_default(sem_solve_opts* opts);
@@ -141,7 +149,10 @@ SEM_API int sem_gll(int lx, double* xi, double* rho, double* D);
  *   gid     HOST [E lx^3] global node ids: equal ids <=> same node (this is Q)
  *   mask    HOST [E lx^3] 0 on homogeneous Dirichlet nodes, 1 elsewhere
  *   h1      HOST [E lx^3] coefficient at every node, or NULL for h1 = 1
- *   flags   0 (reserved)
+ *   flags   0, or SEM_FLAG_VARIANT(v) to pin the operator kernel variant v
+ *           (0 = shared-slab staging, 1..4 = bulk-copy staging, see
+ *           sem_solve_stats.ax_variant) instead of autotuning it; variants
+ *           1..4 apply to lx in {4, 6, 8, 10, 12} and fall back to 0 elsewhere
  * Computes on the device the geometric factors G_st = rho rho rho J
  * sum_l dr_s/dx_l dr_t/dx_l (h1 folded in), the mass B = rho rho rho J and
  * the Jacobi diagonal, and on the host the gather-scatter lists.

@@ -10,9 +10,54 @@
 // six factors G are streamed once per point (coalesced along i), the
 // weighted derivatives wr, ws go back to shared memory and the transposed
 // contraction produces w.
+#include <type_traits>
+
 #include "sem_ax.cuh"
+#include "sem_ax_df.cuh"
 
 namespace sem {
+
+int* device_error_word(sem_handle* h) { return reinterpret_cast<int*>(h->scratch + 8); }
+
+int ax_variant_for(const sem_handle* h, int lx, bool fp32) {
+    const int v = h->ax_variant[fp32 ? 1 : 0][lx];
+    if (v == kDfVariant) return (!fp32 && lx <= 12) ? v : 0;
+    return (v > 0 && bulk_fits(lx, v, fp32)) ? v : 0;
+}
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+template <typename T>
+static int dispatch_variant(sem_handle* h, int lx, AxParams<T> a, bool fused, int variant, cudaStream_t s) {
+    if constexpr (std::is_same<T, double>::value) {
+        if (variant == kDfVariant && lx <= 12) {
+            DfParams d = {};
+            d.u = a.u;
+            d.z = a.z;
+            d.p = a.p;
+            d.w = a.w;
+            d.G2 = h->G2 + (a.G - h->G64) * 2;  // same element offset in the 12-plane layout
+            d.D2 = h->D2[lx];
+            d.E = a.E;
+            d.st = a.st;
+            d.partials = a.partials;
+            d.counter = a.counter;
+            d.dry = a.dry;
+            return dispatch_ax_df_entry(h, lx, d, fused, s);
+        }
+    }
+    if (variant == kDfVariant) variant = 0;
+    a.variant = variant;
+    a.err = device_error_word(h);
+    const bool bulk_ok = variant > 0 && bulk_fits(lx, variant, sizeof(T) == 4) && aligned16(a.w) &&
+                         (fused ? (aligned16(a.z) && aligned16(a.p)) : aligned16(a.u)) && aligned16(a.G);
+    if (!bulk_ok) a.variant = 0;
+    if constexpr (std::is_same<T, double>::value) {
+        return bulk_ok ? dispatch_ax_bulk_f64(h, lx, a, fused, s) : dispatch_ax_f64(h, lx, a, fused, s);
+    } else {
+        return bulk_ok ? dispatch_ax_bulk_f32(h, lx, a, fused, s) : dispatch_ax_f32(h, lx, a, fused, s);
+    }
+}
 
 int launch_ax_local(sem_handle* h, const void* u, void* w, int precision, cudaStream_t s) {
     for (int q = 0; q < h->nsolve; q++) {
@@ -25,7 +70,7 @@ int launch_ax_local(sem_handle* h, const void* u, void* w, int precision, cudaSt
             a.G = h->G32 + 6 * p.loc_off;
             a.D = h->D32[p.lx];
             a.E = p.E;
-            rc = dispatch_ax_f32(h, p.lx, a, false, s);
+            rc = dispatch_variant<float>(h, p.lx, a, false, ax_variant_for(h, p.lx, true), s);
         } else {
             AxParams<double> a = {};
             a.u = (const double*)u + p.loc_off;
@@ -33,7 +78,8 @@ int launch_ax_local(sem_handle* h, const void* u, void* w, int precision, cudaSt
             a.G = h->G64 + 6 * p.loc_off;
             a.D = h->D64[p.lx];
             a.E = p.E;
-            rc = dispatch_ax_f64(h, p.lx, a, false, s);
+            const int v = precision == SEM_FP64_NATIVE ? 0 : ax_variant_for(h, p.lx, false);
+            rc = dispatch_variant<double>(h, p.lx, a, false, v, s);
         }
         if (rc) return rc;
     }
@@ -55,7 +101,7 @@ int launch_cg_pupdate_ax(sem_handle* h, int precision, cudaStream_t s) {
         a.st = h->state + 1;
         a.partials = h->partials;
         a.counter = h->counters + 2;
-        return dispatch_ax_f32(h, p.lx, a, true, s);
+        return dispatch_variant<float>(h, p.lx, a, true, ax_variant_for(h, p.lx, true), s);
     }
     AxParams<double> a = {};
     a.w = h->ws.w;
@@ -67,23 +113,105 @@ int launch_cg_pupdate_ax(sem_handle* h, int precision, cudaStream_t s) {
     a.st = h->state;
     a.partials = h->partials;
     a.counter = h->counters + 2;
-    return dispatch_ax_f64(h, p.lx, a, true, s);
+    const int v = precision == SEM_FP64_NATIVE ? 0 : ax_variant_for(h, p.lx, false);
+    return dispatch_variant<double>(h, p.lx, a, true, v, s);
 }
 
 // Set kernel attributes and cache occupancies of the CG kernels of this
 // handle before any stream capture (those calls are kept out of captures).
 int prepare_cg_kernels(sem_handle* h) {
     for (const MeshPart& p : h->parts) {
-        AxParams<double> a = {};
-        a.dry = 1;
-        AxParams<float> b = {};
-        b.dry = 1;
-        int rc = dispatch_ax_f64(h, p.lx, a, true, 0);
-        if (!rc) rc = dispatch_ax_f64(h, p.lx, a, false, 0);
-        if (!rc) rc = dispatch_ax_f32(h, p.lx, b, true, 0);
-        if (!rc) rc = dispatch_ax_f32(h, p.lx, b, false, 0);
-        if (rc) return rc;
+        for (int fp32 = 0; fp32 < 2; fp32++)
+            for (int fused = 0; fused < 2; fused++) {
+                const int v = ax_variant_for(h, p.lx, fp32 != 0);
+                int rc;
+                if (fp32) {
+                    AxParams<float> a = {};
+                    a.dry = 1;
+                    a.variant = v;
+                    rc = v > 0 ? dispatch_ax_bulk_f32(h, p.lx, a, fused != 0, 0)
+                               : dispatch_ax_f32(h, p.lx, a, fused != 0, 0);
+                } else {
+                    AxParams<double> a = {};
+                    a.dry = 1;
+                    a.G = h->G64;
+                    if (v == kDfVariant) {
+                        rc = dispatch_variant<double>(h, p.lx, a, fused != 0, v, 0);
+                    } else {
+                        a.variant = v;
+                        rc = v > 0 ? dispatch_ax_bulk_f64(h, p.lx, a, fused != 0, 0)
+                                   : dispatch_ax_f64(h, p.lx, a, fused != 0, 0);
+                    }
+                    // the plain FP64 kernel also serves SEM_FP64_NATIVE
+                    if (!rc && v > 0) rc = dispatch_ax_f64(h, p.lx, a, fused != 0, 0);
+                }
+                if (rc) return rc;
+            }
     }
+    return SEM_OK;
+}
+
+// Autotuner: time every operator variant that fits (shared-slab staging and
+// the bulk-staged (elements per CTA, stages) configurations) on this handle's
+// own factors with the plain kernel, a few launches each after a warm-up, and
+// keep the fastest per order for the precision.  The fused CG kernel uses the
+// same choice.  Runs once per handle and precision, outside any capture.
+int autotune_ax(sem_handle* h, bool fp32, cudaStream_t s) {
+    int rc = ensure_workspace(h, fp32);
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    SEM_CUDA_TRY(cudaEventCreate(&e0));
+    SEM_CUDA_TRY(cudaEventCreate(&e1));
+    for (const MeshPart& p : h->parts) {
+        if (h->ax_variant[fp32][p.lx] >= 0) continue;
+        float best = 1e30f;
+        int best_v = 0;
+        for (int v = 0; v <= kDfVariant; v++) {
+            if (v > 0 && v < kDfVariant && !bulk_fits(p.lx, v, fp32)) continue;
+            if (v == kDfVariant && (fp32 || p.lx > 12)) continue;
+            int rc2;
+            auto run = [&](int dry) -> int {
+                if (fp32) {
+                    AxParams<float> a = {};
+                    a.u = h->ws.z32 + p.loc_off;
+                    a.w = h->ws.w32 + p.loc_off;
+                    a.G = h->G32 + 6 * p.loc_off;
+                    a.D = h->D32[p.lx];
+                    a.E = p.E;
+                    a.dry = dry;
+                    return dispatch_variant<float>(h, p.lx, a, false, v, s);
+                }
+                AxParams<double> a = {};
+                a.u = h->ws.z + p.loc_off;
+                a.w = h->ws.w + p.loc_off;
+                a.G = h->G64 + 6 * p.loc_off;
+                a.D = h->D64[p.lx];
+                a.E = p.E;
+                a.dry = dry;
+                return dispatch_variant<double>(h, p.lx, a, false, v, s);
+            };
+            rc2 = run(1);
+            if (rc2) {  // does not fit / cannot be resident: not a candidate
+                set_error("");
+                continue;
+            }
+            for (int w = 0; w < 2 && !rc2; w++) rc2 = run(0);
+            cudaEventRecord(e0, s);
+            for (int w = 0; w < 5 && !rc2; w++) rc2 = run(0);
+            cudaEventRecord(e1, s);
+            if (rc2) break;
+            SEM_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_v = v;
+            }
+        }
+        h->ax_variant[fp32][p.lx] = best_v;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     return SEM_OK;
 }
 
@@ -111,8 +239,6 @@ int launch_mass32(sem_handle* h, const float* u, float* w, cudaStream_t s) {
 }  // namespace sem
 
 using namespace sem;
-
-static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 extern "C" {
 

@@ -32,7 +32,9 @@ struct AxParams {
     CGState* st;
     double* partials;
     unsigned int* counter;
-    int dry;  // 1: only prepare the kernel (attributes, occupancy); no launch
+    int* err;     // set to 1 when a bounded wait of a staged kernel expires
+    int dry;      // 1: only prepare the kernel (attributes, occupancy); no launch
+    int variant;  // 0: shared-slab kernel; 1..kBulkVariants: bulk-staged (EPC, stages)
 };
 
 template <typename T, int LX>
@@ -243,6 +245,22 @@ inline int dispatch_ax(sem_handle* h, int lx, const AxParams<T>& a, cudaStream_t
     }
 }
 
+
+// Bulk-staged variants (sem_ax_bulk.cuh): variant v = 1..kBulkVariants uses
+// (elements per CTA, stages) = kBulkCfg[v - 1]; only even lx in {4,6,8,10,12}.
+constexpr int kBulkVariants = kBulkVariantsMax;
+constexpr int kBulkCfg[kBulkVariants][2] = {{1, 3}, {2, 2}, {2, 3}, {4, 2}};
+int dispatch_ax_bulk_f64(sem_handle* h, int lx, const AxParams<double>& a, bool fused, cudaStream_t s);
+int dispatch_ax_bulk_f32(sem_handle* h, int lx, const AxParams<float>& a, bool fused, cudaStream_t s);
+inline bool bulk_supported(int lx) { return lx == 4 || lx == 6 || lx == 8 || lx == 10 || lx == 12; }
+// Shared memory of the fused (larger) bulk kernel of variant v fits in a CTA.
+inline bool bulk_fits(int lx, int v, bool fp32) {
+    if (v < 1 || v > kBulkVariants || !bulk_supported(lx)) return false;
+    const size_t epc = kBulkCfg[v - 1][0], nst = kBulkCfg[v - 1][1];
+    const size_t n3 = (size_t)lx * lx * lx, el = fp32 ? 4 : 8;
+    const size_t bytes = el * ((size_t)lx * (lx + 1) + 3 * epc * n3 + nst * epc * n3 * 8) + 16 * nst + 64;
+    return bytes <= 227 * 1024 && epc * lx * lx <= 1024;
+}
 
 // per-precision entry points (sem_ax_f64.cu, sem_ax_f32.cu)
 int dispatch_ax_f64(sem_handle* h, int lx, const AxParams<double>& a, bool fused, cudaStream_t s);

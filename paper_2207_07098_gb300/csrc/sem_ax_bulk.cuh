@@ -1,0 +1,276 @@
+// Local operator kernels with bulk-copy staging: each CTA walks its element
+// groups through a ring of NST shared-memory stages.  One elected thread
+// fills a stage with cp.async.bulk copies (the group's u, or z and p, and its
+// six factor blocks, each one contiguous run of global memory) that signal an
+// mbarrier; the CTA computes group g while the copies of the next NST-1
+// groups are in flight, and refills the stage as soon as phase 1 has consumed
+// it.  The arithmetic is that of ax_group (sem_ax.cuh): same contractions,
+// same order.  Only for even lx (element blocks are multiples of 16 bytes).
+#pragma once
+
+#include "sem_ax.cuh"
+
+namespace sem {
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of `bar` for at most ~`budget` clock cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long budget) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > budget) return false;
+    return true;
+}
+
+constexpr long long kWaitBudget = 4000000000LL;  // about two seconds at 2 GHz
+
+template <typename T, int LX, int EPC, int NST, bool FUSED>
+struct BulkCfg {
+    static constexpr int N2 = LX * LX, N3 = LX * LX * LX, DP = LX + 1;
+    static constexpr int USED = EPC * N2;
+    static constexpr int THREADS = ((USED + 31) / 32) * 32;
+    static constexpr int IN = FUSED ? 2 : 1;                   // u, or z and p
+    static constexpr size_t STAGE = (size_t)EPC * N3 * (IN + 6);  // elements of T per stage
+    static constexpr size_t WORK = (size_t)LX * DP + 3 * (size_t)EPC * N3;
+    static constexpr size_t BYTES = sizeof(T) * (WORK + NST * STAGE) + 16 * NST + 64;
+    static_assert(LX % 2 == 0, "bulk staging needs even lx");
+};
+
+template <typename T, int LX, int EPC, int NST, bool FUSED>
+__global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
+    ax_bulk_kernel(AxParams<T> a) {
+    using C = BulkCfg<T, LX, EPC, NST, FUSED>;
+    constexpr int N2 = C::N2, N3 = C::N3, DP = C::DP;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    T* sD = reinterpret_cast<T*>(smem_raw);
+    T* su = sD + ((LX * DP + 3) & ~3);  // 16-byte aligned
+    T* sr = su + EPC * N3;
+    T* ss = sr + EPC * N3;
+    T* stage0 = ss + EPC * N3;          // EPC*N3*sizeof(T) is a multiple of 16 for even LX
+    uint64_t* bars = reinterpret_cast<uint64_t*>(stage0 + NST * C::STAGE);
+    __shared__ int abort_flag;
+
+    double beta = 0.0;
+    bool first = false;
+    if (FUSED) {
+        if (a.st->done) return;  // uniform over the grid
+        beta = cg_beta(a.st);
+        first = (a.st->iter == 0);
+    }
+    const T tbeta = (T)beta;
+    const int64_t ngroups = (a.E + EPC - 1) / EPC;
+    const int tid = threadIdx.x;
+    const int el = tid / N2;
+    const int ij = tid - el * N2;
+    const int i = ij % LX, j = ij / LX;
+    const bool active = el < EPC;
+    const int so = (active ? el : 0) * N3;
+
+    // stage s of group g: [in0 | in1 | G], each in element order
+    auto issue = [&](int s, int64_t g) {
+        const int64_t e0 = g * EPC;
+        const int cnt = (int)(a.E - e0 < EPC ? a.E - e0 : EPC);
+        T* st = stage0 + s * C::STAGE;
+        const uint32_t bin = (uint32_t)(cnt * N3 * sizeof(T));
+        const uint32_t bG = 6u * bin;
+        mbar_expect_tx(&bars[s], (uint32_t)C::IN * bin + bG);
+        if (FUSED) {
+            bulk_load(st, a.z + e0 * N3, bin, &bars[s]);
+            bulk_load(st + EPC * N3, a.p + e0 * N3, bin, &bars[s]);
+        } else {
+            bulk_load(st, a.u + e0 * N3, bin, &bars[s]);
+        }
+        bulk_load(st + C::IN * EPC * N3, a.G + e0 * 6 * N3, bG, &bars[s]);
+    };
+
+    if (tid == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < NST; s++) mbar_init(&bars[s], 1);
+        mbar_fence_init();
+    }
+    for (int t = tid; t < LX * LX; t += blockDim.x) sD[(t / LX) * DP + (t % LX)] = a.D[t];
+    __syncthreads();
+    if (tid == 0)
+        for (int s = 0; s < NST; s++) {
+            const int64_t g = blockIdx.x + (int64_t)s * gridDim.x;
+            if (g < ngroups) issue(s, g);
+        }
+
+    double pap = 0.0;
+    int64_t it = 0;
+    for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x, it++) {
+        const int s = (int)(it % NST);
+        const uint32_t parity = (uint32_t)((it / NST) & 1);
+        if (!mbar_wait_bounded(&bars[s], parity, kWaitBudget)) abort_flag = 1;
+        __syncthreads();
+        if (abort_flag) break;
+        const T* st = stage0 + s * C::STAGE;
+        const int64_t e = g * EPC + el;
+        const bool valid = active && e < a.E;
+        const int64_t base = e * N3 + ij;
+        // phase 0: this thread's column of u (or z + beta p)
+        T ucol[LX];
+#pragma unroll
+        for (int k = 0; k < LX; k++) {
+            T v = st[so + k * N2 + ij];
+            if (FUSED) {
+                const T pp = first ? T(0) : st[EPC * N3 + so + k * N2 + ij];
+                v = fma(tbeta, pp, v);
+                if (valid) a.p[base + k * N2] = v;
+            }
+            ucol[k] = v;
+            if (active) su[so + k * N2 + ij] = v;
+        }
+        __syncthreads();
+        // phase 1: derivatives and weighting by the factors of the stage
+        const T* Gs = st + C::IN * EPC * N3 + (active ? el : 0) * 6 * N3 + ij;
+        T wt[LX];
+#pragma unroll
+        for (int k = 0; k < LX; k++) {
+            T ur = T(0), us = T(0), ut = T(0);
+#pragma unroll
+            for (int l = 0; l < LX; l++) {
+                ur = fma(sD[i * DP + l], su[so + k * N2 + j * LX + l], ur);
+                us = fma(sD[j * DP + l], su[so + k * N2 + l * LX + i], us);
+                ut = fma(sD[k * DP + l], ucol[l], ut);
+            }
+            const T g11 = Gs[0 * N3 + k * N2], g12 = Gs[1 * N3 + k * N2], g13 = Gs[2 * N3 + k * N2];
+            const T g22 = Gs[3 * N3 + k * N2], g23 = Gs[4 * N3 + k * N2], g33 = Gs[5 * N3 + k * N2];
+            const T wr = fma(g11, ur, fma(g12, us, g13 * ut));
+            const T ws = fma(g12, ur, fma(g22, us, g23 * ut));
+            wt[k] = fma(g13, ur, fma(g23, us, g33 * ut));
+            if (active) {
+                sr[so + k * N2 + ij] = wr;
+                ss[so + k * N2 + ij] = ws;
+            }
+        }
+        __syncthreads();
+        // the stage is consumed: refill it with the group NST rounds ahead
+        if (tid == 0) {
+            const int64_t gn = g + (int64_t)NST * gridDim.x;
+            if (gn < ngroups) issue(s, gn);
+        }
+        // phase 2: transposed contractions
+        T pw = T(0);
+#pragma unroll
+        for (int k = 0; k < LX; k++) {
+            T acc = T(0);
+#pragma unroll
+            for (int l = 0; l < LX; l++) {
+                acc = fma(sD[l * DP + i], sr[so + k * N2 + j * LX + l], acc);
+                acc = fma(sD[l * DP + j], ss[so + k * N2 + l * LX + i], acc);
+                acc = fma(sD[l * DP + k], wt[l], acc);
+            }
+            if (valid) {
+                st_stream(a.w + base + k * N2, acc);
+                if (FUSED) pw = fma(ucol[k], acc, pw);
+            }
+        }
+        if (FUSED) pap += (double)pw;
+        __syncthreads();
+    }
+    if (abort_flag) {
+        // a copy never completed: report, let the other copies land, return
+        if (tid == 0) {
+            atomicExch(a.err, 1);
+            for (int s = 0; s < NST; s++) {
+                const int64_t ahead = it + s;
+                const int ss_ = (int)(ahead % NST);
+                mbar_wait_bounded(&bars[ss_], (uint32_t)((ahead / NST) & 1), kWaitBudget / 4);
+            }
+        }
+        return;
+    }
+    if (FUSED) {
+        double v[1] = {pap};
+        CGState* stt = a.st;
+        grid_sum_finalize<1>(v, a.partials, a.counter, [&](double (&acc)[1]) { cg_set_alpha(stt, acc[0]); });
+    }
+}
+
+template <typename T, int LX, int EPC, int NST, bool FUSED>
+inline int launch_ax_bulk_t(sem_handle* h, const AxParams<T>& a, cudaStream_t s) {
+    using C = BulkCfg<T, LX, EPC, NST, FUSED>;
+    if constexpr (C::BYTES > 227 * 1024) {
+        return fail(SEM_EINVAL, "bulk variant does not fit in shared memory");
+    } else {
+        static int per_sm = -1;
+        if (per_sm < 0) {
+            cudaFuncSetAttribute(ax_bulk_kernel<T, LX, EPC, NST, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)C::BYTES);
+            int nb = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ax_bulk_kernel<T, LX, EPC, NST, FUSED>, C::THREADS,
+                                                          C::BYTES);
+            per_sm = nb;
+        }
+        if (per_sm <= 0) return fail(SEM_EINVAL, "bulk variant cannot be resident");
+        if (a.dry) return SEM_OK;
+        const int64_t ngroups = (a.E + EPC - 1) / EPC;
+        int64_t grid = std::min<int64_t>(ngroups, (int64_t)h->sm_count * per_sm);
+        grid = std::max<int64_t>(1, std::min<int64_t>(grid, kMaxPartials));
+        ax_bulk_kernel<T, LX, EPC, NST, FUSED><<<(int)grid, C::THREADS, C::BYTES, s>>>(a);
+        SEM_LAUNCH_CHECK("ax_bulk_kernel");
+        h->launches++;
+        return SEM_OK;
+    }
+}
+
+template <typename T, int LX, bool FUSED>
+inline int dispatch_bulk_cfg(sem_handle* h, const AxParams<T>& a, cudaStream_t s) {
+    switch (a.variant) {
+        case 1: return launch_ax_bulk_t<T, LX, kBulkCfg[0][0], kBulkCfg[0][1], FUSED>(h, a, s);
+        case 2: return launch_ax_bulk_t<T, LX, kBulkCfg[1][0], kBulkCfg[1][1], FUSED>(h, a, s);
+        case 3: return launch_ax_bulk_t<T, LX, kBulkCfg[2][0], kBulkCfg[2][1], FUSED>(h, a, s);
+        case 4: return launch_ax_bulk_t<T, LX, kBulkCfg[3][0], kBulkCfg[3][1], FUSED>(h, a, s);
+        default: return fail(SEM_EINVAL, "unknown operator variant");
+    }
+}
+
+template <typename T, bool FUSED>
+inline int dispatch_ax_bulk(sem_handle* h, int lx, const AxParams<T>& a, cudaStream_t s) {
+    switch (lx) {
+        case 4: return dispatch_bulk_cfg<T, 4, FUSED>(h, a, s);
+        case 6: return dispatch_bulk_cfg<T, 6, FUSED>(h, a, s);
+        case 8: return dispatch_bulk_cfg<T, 8, FUSED>(h, a, s);
+        case 10: return dispatch_bulk_cfg<T, 10, FUSED>(h, a, s);
+        case 12: return dispatch_bulk_cfg<T, 12, FUSED>(h, a, s);
+        default: return fail(SEM_EINVAL, "bulk staging needs lx in {4, 6, 8, 10, 12}");
+    }
+}
+
+}  // namespace sem

@@ -1,0 +1,263 @@
+// FP64-accurate local operator on the FP32 pipe ("double-float" arithmetic).
+//
+// On GB300 the FP64 pipe runs at 1/64 of the FP32 rate, so an FP64 ax_helm
+// with ~57 FP64 FMAs per point is limited to ~10% of HBM bandwidth.  This
+// kernel keeps FP64 accuracy (relative error ~2^-44 per operation, far below
+// the 1e-12 parity bar) with pairs of floats x = hi + lo:
+//   * exact products with an FMA (p = a*b, e = fma(a, b, -p): p + e = a*b),
+//   * sums of the high parts with Knuth's TwoSum (s + err = a + b exactly),
+//   * the low-order cross terms (a_hi b_lo + a_lo b_hi) in plain FP32,
+// applied to the same contractions and the same G weighting as ax_group.
+// The factors are stored pre-split (12 float planes per element: the six hi
+// planes then the six lo planes, the same 48 bytes per point as FP64); D is
+// split once per CTA; u (double) is split with integer operations (no FP64
+// conversion), and each output is rebuilt as double(hi) + double(lo).
+#pragma once
+
+#include "sem_ax.cuh"
+
+namespace sem {
+
+struct dfl {
+    float h, l;
+};
+
+// hi/lo split of a double with integer operations: hi = the double truncated
+// to 24 significant bits, lo = the next 24 bits rounded to float.  Exact to
+// ~2^-48 relative for |x| in [2^-90, 2^127]; smaller magnitudes become 0.
+__device__ __forceinline__ dfl split_double(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
+    const unsigned ed = (hi32 >> 20) & 0x7ffu;  // biased FP64 exponent
+    const unsigned sign = hi32 & 0x80000000u;
+    // top 23 mantissa bits, exponent rebiased 1023 -> 127 (low 8 bits of
+    // ed - 896 = low 8 bits of ed with bit 7 flipped)
+    const unsigned t = __funnelshift_l(lo32, hi32, 3);
+    const unsigned hb = ((t & 0x7fffffffu) ^ 0x40000000u) | sign;
+    // remaining 29 mantissa bits, scaled by 2^(ed - 1075)
+    const unsigned rem = lo32 & 0x1fffffffu;
+    const float lo_mag = __uint2float_rn(rem) * __uint_as_float((ed - 948u) << 23);
+    const bool ok = ed > 948u && ed < 1151u;
+    dfl r;
+    r.h = ok ? __uint_as_float(hb) : 0.0f;
+    r.l = ok ? __uint_as_float(__float_as_uint(lo_mag) | sign) : 0.0f;
+    return r;
+}
+
+__device__ __forceinline__ double join(dfl a) { return (double)a.h + (double)a.l; }
+
+// acc += a * b with a, b pairs; (S, E) is an unnormalised running pair.
+__device__ __forceinline__ void df_mac(float& S, float& E, float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    const float s = S + p;
+    const float bb = s - S;
+    const float err = (S - (s - bb)) + (p - bb);
+    S = s;
+    E += err + e;
+}
+
+__device__ __forceinline__ dfl df_norm(float S, float E) {
+    dfl r;
+    r.h = S + E;
+    r.l = E - (r.h - S);
+    return r;
+}
+
+template <int LX>
+struct DfCfg {
+    static constexpr int N2 = LX * LX, N3 = LX * LX * LX, DP = LX + 1;
+    static constexpr int EPC = (256 / N2) > 0 ? (256 / N2) : 1;
+    static constexpr int USED = EPC * N2;
+    static constexpr int THREADS = ((USED + 31) / 32) * 32;
+    // floats: D hi/lo (padded rows), then u, wr, ws hi and lo per element slot
+    static constexpr size_t FLOATS = 2 * (size_t)LX * DP + 6 * (size_t)EPC * N3;
+};
+
+// Gs: [E][12][lx^3] floats (hi planes 0..5, lo planes 6..11); D2: [2][lx][lx]
+// (hi then lo).  Same parameters as AxParams<double> otherwise.
+struct DfParams {
+    const double* u;
+    const double* z;
+    double* p;
+    double* w;
+    const float* G2;
+    const float* D2;
+    int64_t E;
+    CGState* st;
+    double* partials;
+    unsigned int* counter;
+    int dry;
+};
+
+template <int LX, bool FUSED>
+__global__ void __launch_bounds__(DfCfg<LX>::THREADS) ax_df_kernel(DfParams a) {
+    using C = DfCfg<LX>;
+    constexpr int N2 = C::N2, N3 = C::N3, EPC = C::EPC, DP = C::DP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* sDh = reinterpret_cast<float*>(smem_raw);
+    float* sDl = sDh + LX * DP;
+    float* suh = sDl + LX * DP;
+    float* sul = suh + EPC * N3;
+    float* srh = sul + EPC * N3;
+    float* srl = srh + EPC * N3;
+    float* ssh = srl + EPC * N3;
+    float* ssl = ssh + EPC * N3;
+
+    double beta = 0.0;
+    bool first = false;
+    if (FUSED) {
+        if (a.st->done) return;
+        beta = cg_beta(a.st);
+        first = (a.st->iter == 0);
+    }
+    for (int t = threadIdx.x; t < LX * LX; t += blockDim.x) {
+        sDh[(t / LX) * DP + (t % LX)] = a.D2[t];
+        sDl[(t / LX) * DP + (t % LX)] = a.D2[LX * LX + t];
+    }
+    const AxThread<LX> th;
+    const int so = th.so, ij = th.ij, i = th.i, j = th.j;
+    const int64_t ngroups = (a.E + EPC - 1) / EPC;
+    double pap = 0.0;
+    __syncthreads();
+    for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
+        const int64_t e = g * EPC + th.el;
+        const bool valid = th.active && e < a.E;
+        const int64_t base = e * N3 + ij;
+        double ud[LX];
+#pragma unroll
+        for (int k = 0; k < LX; k++) ud[k] = valid ? ld_stream((FUSED ? a.z : a.u) + base + k * N2) : 0.0;
+        if (FUSED) {
+            double pold[LX];
+#pragma unroll
+            for (int k = 0; k < LX; k++) pold[k] = (valid && !first) ? a.p[base + k * N2] : 0.0;
+#pragma unroll
+            for (int k = 0; k < LX; k++) {
+                ud[k] = fma(beta, pold[k], ud[k]);
+                if (valid) a.p[base + k * N2] = ud[k];
+            }
+        }
+        float uh[LX], ul[LX];
+#pragma unroll
+        for (int k = 0; k < LX; k++) {
+            const dfl v = split_double(ud[k]);
+            uh[k] = v.h;
+            ul[k] = v.l;
+            if (th.active) {
+                suh[so + k * N2 + ij] = v.h;
+                sul[so + k * N2 + ij] = v.l;
+            }
+        }
+        __syncthreads();
+        const float* Ge = a.G2 + e * 12 * N3 + ij;
+        float wth[LX], wtl[LX];
+#pragma unroll
+        for (int k = 0; k < LX; k++) {
+            float rS = 0.f, rE = 0.f, sS = 0.f, sE = 0.f, tS = 0.f, tE = 0.f;
+#pragma unroll
+            for (int l = 0; l < LX; l++) {
+                const int qr = so + k * N2 + j * LX + l, qs = so + k * N2 + l * LX + i;
+                df_mac(rS, rE, sDh[i * DP + l], sDl[i * DP + l], suh[qr], sul[qr]);
+                df_mac(sS, sE, sDh[j * DP + l], sDl[j * DP + l], suh[qs], sul[qs]);
+                df_mac(tS, tE, sDh[k * DP + l], sDl[k * DP + l], uh[l], ul[l]);
+            }
+            const dfl ur = df_norm(rS, rE), us = df_norm(sS, sE), ut = df_norm(tS, tE);
+            float gh[6], gl[6];
+#pragma unroll
+            for (int c = 0; c < 6; c++) {
+                gh[c] = valid ? ld_stream(Ge + c * N3 + k * N2) : 0.f;
+                gl[c] = valid ? ld_stream(Ge + (6 + c) * N3 + k * N2) : 0.f;
+            }
+            float aS = 0.f, aE = 0.f, bS = 0.f, bE = 0.f, cS = 0.f, cE = 0.f;
+            // (wr, ws, wt) = G (ur, us, ut), G = [[11 12 13] [12 22 23] [13 23 33]]
+            df_mac(aS, aE, gh[0], gl[0], ur.h, ur.l);
+            df_mac(aS, aE, gh[1], gl[1], us.h, us.l);
+            df_mac(aS, aE, gh[2], gl[2], ut.h, ut.l);
+            df_mac(bS, bE, gh[1], gl[1], ur.h, ur.l);
+            df_mac(bS, bE, gh[3], gl[3], us.h, us.l);
+            df_mac(bS, bE, gh[4], gl[4], ut.h, ut.l);
+            df_mac(cS, cE, gh[2], gl[2], ur.h, ur.l);
+            df_mac(cS, cE, gh[4], gl[4], us.h, us.l);
+            df_mac(cS, cE, gh[5], gl[5], ut.h, ut.l);
+            const dfl wr = df_norm(aS, aE), ws = df_norm(bS, bE), wt = df_norm(cS, cE);
+            wth[k] = wt.h;
+            wtl[k] = wt.l;
+            if (th.active) {
+                srh[so + k * N2 + ij] = wr.h;
+                srl[so + k * N2 + ij] = wr.l;
+                ssh[so + k * N2 + ij] = ws.h;
+                ssl[so + k * N2 + ij] = ws.l;
+            }
+        }
+        __syncthreads();
+        double pw = 0.0;
+#pragma unroll
+        for (int k = 0; k < LX; k++) {
+            float S = 0.f, E = 0.f;
+#pragma unroll
+            for (int l = 0; l < LX; l++) {
+                const int qr = so + k * N2 + j * LX + l, qs = so + k * N2 + l * LX + i;
+                df_mac(S, E, sDh[l * DP + i], sDl[l * DP + i], srh[qr], srl[qr]);
+                df_mac(S, E, sDh[l * DP + j], sDl[l * DP + j], ssh[qs], ssl[qs]);
+                df_mac(S, E, sDh[l * DP + k], sDl[l * DP + k], wth[l], wtl[l]);
+            }
+            const double wv = join(df_norm(S, E));
+            if (valid) {
+                st_stream(a.w + base + k * N2, wv);
+                if (FUSED) pw = fma(ud[k], wv, pw);
+            }
+        }
+        if (FUSED) pap += pw;
+        __syncthreads();
+    }
+    if (FUSED) {
+        double v[1] = {pap};
+        CGState* st = a.st;
+        grid_sum_finalize<1>(v, a.partials, a.counter, [&](double (&acc)[1]) { cg_set_alpha(st, acc[0]); });
+    }
+}
+
+template <int LX, bool FUSED>
+inline int launch_ax_df_t(sem_handle* h, const DfParams& a, cudaStream_t s) {
+    using C = DfCfg<LX>;
+    constexpr size_t smem = C::FLOATS * sizeof(float);
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        cudaFuncSetAttribute(ax_df_kernel<LX, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ax_df_kernel<LX, FUSED>, C::THREADS, smem);
+        per_sm = nb > 0 ? nb : 1;
+    }
+    if (a.dry) return SEM_OK;
+    const int64_t ngroups = (a.E + C::EPC - 1) / C::EPC;
+    int64_t grid = std::min<int64_t>(ngroups, (int64_t)h->sm_count * per_sm);
+    grid = std::max<int64_t>(1, std::min<int64_t>(grid, kMaxPartials));
+    ax_df_kernel<LX, FUSED><<<(int)grid, C::THREADS, smem, s>>>(a);
+    SEM_LAUNCH_CHECK("ax_df_kernel");
+    h->launches++;
+    return SEM_OK;
+}
+
+template <bool FUSED>
+inline int dispatch_ax_df(sem_handle* h, int lx, const DfParams& a, cudaStream_t s) {
+    switch (lx) {
+        case 2: return launch_ax_df_t<2, FUSED>(h, a, s);
+        case 3: return launch_ax_df_t<3, FUSED>(h, a, s);
+        case 4: return launch_ax_df_t<4, FUSED>(h, a, s);
+        case 5: return launch_ax_df_t<5, FUSED>(h, a, s);
+        case 6: return launch_ax_df_t<6, FUSED>(h, a, s);
+        case 7: return launch_ax_df_t<7, FUSED>(h, a, s);
+        case 8: return launch_ax_df_t<8, FUSED>(h, a, s);
+        case 9: return launch_ax_df_t<9, FUSED>(h, a, s);
+        case 10: return launch_ax_df_t<10, FUSED>(h, a, s);
+        case 11: return launch_ax_df_t<11, FUSED>(h, a, s);
+        case 12: return launch_ax_df_t<12, FUSED>(h, a, s);
+        default: return fail(SEM_EINVAL, "FP32-pair operator supports lx <= 12");
+    }
+}
+
+int dispatch_ax_df_entry(sem_handle* h, int lx, const DfParams& a, bool fused, cudaStream_t s);
+
+}  // namespace sem

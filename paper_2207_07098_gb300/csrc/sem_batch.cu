@@ -93,7 +93,8 @@ __global__ void __launch_bounds__(256) upd_batch_kernel(T* x, const T* p, T* r, 
 template <typename T>
 __global__ void __launch_bounds__(256) init_batch_kernel(const T* b, const T* r, T* z, const T* minv,
                                                           const uint8_t* mult, CGState* st_base, TileList tl,
-                                                          const int* act, double tol, int max_iter) {
+                                                          const int* act, double tol, const double* tol_per_solve,
+                                                          int max_iter) {
     __shared__ double inv[256];
     __shared__ double red[96];
     __shared__ int is_last;
@@ -122,6 +123,7 @@ __global__ void __launch_bounds__(256) init_batch_kernel(const T* b, const T* r,
             v[2] = fma(bv * bv, iv, v[2]);
         }
         if (tile_finalize<3>(tl, t, s, v, acc, red, &is_last)) {
+            if (tol_per_solve) tol = tol_per_solve[s];
             st->rho = acc[0];
             st->rho_old = 1.0;
             st->rr = acc[1];
@@ -259,7 +261,8 @@ static int build_plan(sem_handle* h) {
         (rc = dalloc(h, &bp.tsolve, tsol.size())) || (rc = dalloc(h, &bp.stfirst, ns)) ||
         (rc = dalloc(h, &bp.stcount, ns)) || (rc = dalloc(h, &bp.gpart, (size_t)bp.ngroups)) ||
         (rc = dalloc(h, &bp.tpart, (size_t)bp.ntiles * 3)) || (rc = dalloc(h, &bp.scount, ns)) ||
-        (rc = dalloc(h, &bp.rrbb, (size_t)2 * ns)) || (rc = dalloc(h, &bp.act, ns)))
+        (rc = dalloc(h, &bp.rrbb, (size_t)2 * ns)) || (rc = dalloc(h, &bp.act, ns)) ||
+        (rc = dalloc(h, &bp.itol, ns)))
         return rc;
     SEM_CUDA_TRY(cudaMemcpy(bp.sgfirst, sgfirst.data(), ns * sizeof(int), cudaMemcpyHostToDevice));
     SEM_CUDA_TRY(cudaMemcpy(bp.sgcount, sgcount.data(), ns * sizeof(int), cudaMemcpyHostToDevice));
@@ -499,7 +502,7 @@ static int solve_batch(sem_handle* h, double* x_user, const double* b_user, cons
     if ((rc = batch_true_residual(h, s))) return rc;
     if (o.mode == SEM_MODE_FP64) {
         init_batch_kernel<double><<<grid_tiles(h), 256, 0, s>>>(h->ws.b, h->ws.r, h->ws.z, h->minv64, h->mult, h->state,
-                                                                 tiles(h), nullptr, o.tol, o.max_iter);
+                                                                 tiles(h), nullptr, o.tol, nullptr, o.max_iter);
         SEM_LAUNCH_CHECK("init_batch_kernel");
         h->launches++;
         if ((rc = batch_loop(h, false, h->state, o, s, hs, &ax_sum, &ax_n))) return rc;
@@ -511,6 +514,7 @@ static int solve_batch(sem_handle* h, double* x_user, const double* b_user, cons
     } else {
         std::vector<double> prev(ns, INFINITY);
         std::vector<int> act(ns, 0), fin(ns, 0);
+        std::vector<double> itol(ns, o.inner_tol);
         if ((rc = read_rrbb())) return rc;
         CGState* inner = h->state + ns;
         for (int round = 0;; round++) {
@@ -524,14 +528,16 @@ static int solve_batch(sem_handle* h, double* x_user, const double* b_user, cons
                 else if (!std::isfinite(rel)) { status[q] = SEM_EBREAKDOWN; fin[q] = 1; }
                 else if (outer[q] >= o.max_outer) { status[q] = SEM_ENOTCONV; fin[q] = 1; }
                 else if (outer[q] > 0 && rel > 0.5 * prev[q]) { status[q] = SEM_ESTAGNATE; fin[q] = 1; }
-                else { act[q] = 1; prev[q] = rel; nact++; }
+                else { act[q] = 1; prev[q] = rel; itol[q] = inner_tolerance(o, rel); nact++; }
             }
             if (nact == 0) break;
             SEM_CUDA_TRY(cudaMemcpyAsync(bp.act, act.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
+            SEM_CUDA_TRY(cudaMemcpyAsync(bp.itol, itol.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, s));
             prepare_batch_kernel<<<grid_tiles(h), 256, 0, s>>>(h->ws.r, h->ws.b32, h->ws.r32, h->ws.d32, tiles(h),
                                                                bp.act, bp.rrbb);
             init_batch_kernel<float><<<grid_tiles(h), 256, 0, s>>>(h->ws.b32, h->ws.r32, h->ws.z32, h->minv32, h->mult,
-                                                                    inner, tiles(h), bp.act, o.inner_tol, o.max_iter);
+                                                                    inner, tiles(h), bp.act, o.inner_tol, bp.itol,
+                                                                    o.max_iter);
             SEM_LAUNCH_CHECK("batch refinement prepare");
             h->launches += 2;
             if ((rc = batch_loop(h, true, inner, o, s, hs, &ax_sum, &ax_n))) return rc;

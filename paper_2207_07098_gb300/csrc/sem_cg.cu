@@ -10,6 +10,7 @@
 // Each launch returns at once when the solve is already done, so a graph of
 // several iterations can run past convergence without changing the result;
 // the host reads the state between graph launches.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -223,7 +224,8 @@ static int launch_iteration(sem_handle* h, int precision, cudaStream_t s) {
 
 static int get_graph(sem_handle* h, int precision, int chunk, cudaGraphExec_t* out) {
     GraphCache& g = h->graph;
-    if (g.exec && g.key_prec == precision && g.key_chunk == chunk) {
+    const int variant = precision == SEM_FP64_NATIVE ? 0 : ax_variant_for(h, h->parts[0].lx, precision == SEM_FP32);
+    if (g.exec && g.key_prec == precision && g.key_chunk == chunk && g.key_variant == variant) {
         *out = g.exec;
         return SEM_OK;
     }
@@ -264,6 +266,7 @@ static int get_graph(sem_handle* h, int precision, int chunk, cudaGraphExec_t* o
     }
     g.key_prec = precision;
     g.key_chunk = chunk;
+    g.key_variant = variant;
     *out = g.exec;
     return SEM_OK;
 }
@@ -325,6 +328,15 @@ static int true_residual(sem_handle* h, const double* x, const double* b, double
     return SEM_OK;
 }
 
+// Relative tolerance of one inner FP32 solve: opts.inner_tol, relaxed when
+// the outer residual `rel` is already close to the target so the last step
+// only removes the remaining factor rel / tol (with margin), never looser
+// than 0.1 so each refinement step still cuts the residual by ten.
+double inner_tolerance(const sem_solve_opts& o, double rel) {
+    const double need = 0.3 * o.tol / rel;
+    return std::min(0.1, std::max(o.inner_tol, need));
+}
+
 static bool is_host_ptr(const void* p) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -338,6 +350,11 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
                         sem_solve_stats* stats, cudaStream_t s) {
     int rc = ensure_workspace(h, o.mode == SEM_MODE_MIXED_IR);
     if (rc) return rc;
+    if (o.autotune) {
+        if (o.mode == SEM_MODE_MIXED_IR && (rc = autotune_ax(h, true, s))) return rc;
+        if ((o.mode == SEM_MODE_MIXED_IR || o.precision != SEM_FP64_NATIVE) && (rc = autotune_ax(h, false, s)))
+            return rc;
+    }
     const int64_t n = h->n_local;
     const size_t bytes = sizeof(double) * n;
     const bool xh = is_host_ptr(x_user), bh = is_host_ptr(b_user);
@@ -384,8 +401,8 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
             ir_prepare_kernel<<<grid_for(h, n, 256, 8), 256, 0, s>>>(h->ws.r, rrbb, h->ws.b32, h->ws.r32,
                                                                      h->ws.d32, n);
             cg_init_kernel<float><<<grid_for(h, n, 256, 4), 256, 0, s>>>(
-                h->ws.b32, h->ws.r32, h->ws.z32, h->minv32, h->mult, n, o.inner_tol, o.max_iter, h->state + 1,
-                h->partials, h->counters + 5);
+                h->ws.b32, h->ws.r32, h->ws.z32, h->minv32, h->mult, n, inner_tolerance(o, rel), o.max_iter,
+                h->state + 1, h->partials, h->counters + 5);
             SEM_LAUNCH_CHECK("ir prepare");
             h->launches += 2;
             if ((rc = run_cg_loop(h, SEM_FP32, o, 1, s, &hs, &tm))) return rc;
@@ -409,8 +426,17 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
     cudaEventElapsedTime(&ms, ev0, ev1);
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
+    int err_word = 0;
+    SEM_CUDA_TRY(cudaMemcpy(&err_word, device_error_word(h), sizeof(int), cudaMemcpyDeviceToHost));
+    if (err_word) {
+        cudaMemset(device_error_word(h), 0, sizeof(int));
+        cudaMemset(h->counters, 0, 16 * sizeof(unsigned));
+        return fail(SEM_ETIMEOUT, "a staged operator kernel gave up waiting for its bulk copies");
+    }
     st.relres = hb[1] > 0 ? std::sqrt(hb[0] / hb[1]) : 0.0;
     st.time_ms = ms;
+    st.ax_variant = o.mode == SEM_MODE_MIXED_IR ? ax_variant_for(h, h->parts[0].lx, true)
+                    : (o.precision == SEM_FP64_NATIVE ? 0 : ax_variant_for(h, h->parts[0].lx, false));
     st.status = status;
     st.kernel_launches = h->launches - launches0;
     st.ax_samples = tm.samples;

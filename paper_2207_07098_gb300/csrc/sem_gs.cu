@@ -4,45 +4,69 @@
 // QQ^T is deterministic and atomic-free: every node with several local copies
 // is one segment whose copies are listed in ascending local index; one thread
 // sums the segment in that order and writes the sum back to every copy.
+// Segments of 2, 4 and 8 copies (faces, edges, vertices of a hex mesh) carry
+// their indices as int2 / int4 vectors, so one thread issues its index loads
+// and value loads without a dependent offset lookup.
 #include "sem_device.cuh"
 #include "sem_internal.h"
 
 namespace sem {
 
+// One launch covers, in this order: free segments of 2, 4 and 8 copies
+// (index vectors), free segments of other sizes (CSR), then either the zeroing
+// of every Dirichlet copy (apply_mask) or the sums over Dirichlet segments.
+// Copies are always summed left to right in ascending local index.
 template <typename T>
-__global__ void __launch_bounds__(256) gs_kernel(T* __restrict__ u, const int* __restrict__ seg_off,
-                                                 const int* __restrict__ seg_idx, int64_t nseg_free,
-                                                 int64_t nseg, const int* __restrict__ zero_idx,
-                                                 int64_t nzero, int apply_mask) {
-    const int64_t total = nseg + (apply_mask ? nzero : 0);
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+__global__ void __launch_bounds__(256) gs_kernel(T* __restrict__ u, GSLists g, int apply_mask) {
+    const int64_t n1 = g.npair, n2 = n1 + g.nquad, n3 = n2 + g.noct, n4 = n3 + g.noth;
+    const int64_t n5 = n4 + (apply_mask ? g.nzero : g.ndir);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n5;
          t += (int64_t)gridDim.x * blockDim.x) {
-        if (t < nseg) {
-            const int a = seg_off[t], b = seg_off[t + 1];
-            if (apply_mask && t >= nseg_free) {
-                for (int c = a; c < b; c++) u[seg_idx[c]] = T(0);
-            } else {
-                T s = u[seg_idx[a]];
-                for (int c = a + 1; c < b; c++) s += u[seg_idx[c]];
-                for (int c = a; c < b; c++) u[seg_idx[c]] = s;
-            }
+        if (t < n1) {
+            const int2 q = g.pairs[t];
+            const T s = u[q.x] + u[q.y];
+            u[q.x] = s;
+            u[q.y] = s;
+        } else if (t < n2) {
+            const int4 q = g.quads[t - n1];
+            const T a = u[q.x], b = u[q.y], c = u[q.z], d = u[q.w];
+            const T s = ((a + b) + c) + d;
+            u[q.x] = s;
+            u[q.y] = s;
+            u[q.z] = s;
+            u[q.w] = s;
+        } else if (t < n3) {
+            const int4 q0 = g.octs[2 * (t - n2)], q1 = g.octs[2 * (t - n2) + 1];
+            const T a0 = u[q0.x], a1 = u[q0.y], a2 = u[q0.z], a3 = u[q0.w];
+            const T a4 = u[q1.x], a5 = u[q1.y], a6 = u[q1.z], a7 = u[q1.w];
+            const T s = ((((((a0 + a1) + a2) + a3) + a4) + a5) + a6) + a7;
+            u[q0.x] = s; u[q0.y] = s; u[q0.z] = s; u[q0.w] = s;
+            u[q1.x] = s; u[q1.y] = s; u[q1.z] = s; u[q1.w] = s;
+        } else if (t < n4) {
+            const int a = g.oth_off[t - n3], b = g.oth_off[t - n3 + 1];
+            T s = u[g.oth_idx[a]];
+            for (int c = a + 1; c < b; c++) s += u[g.oth_idx[c]];
+            for (int c = a; c < b; c++) u[g.oth_idx[c]] = s;
+        } else if (apply_mask) {
+            u[g.zero_idx[t - n4]] = T(0);
         } else {
-            u[zero_idx[t - nseg]] = T(0);
+            const int a = g.dir_off[t - n4], b = g.dir_off[t - n4 + 1];
+            T s = u[g.dir_idx[a]];
+            for (int c = a + 1; c < b; c++) s += u[g.dir_idx[c]];
+            for (int c = a; c < b; c++) u[g.dir_idx[c]] = s;
         }
     }
 }
 
 int launch_gs(sem_handle* h, void* u, bool fp32, bool apply_mask, cudaStream_t s) {
     const GSLists& g = h->gs;
-    const int64_t total = g.nseg + (apply_mask ? g.nzero : 0);
+    const int64_t total = g.npair + g.nquad + g.noct + g.noth + (apply_mask ? g.nzero : g.ndir);
     if (total == 0) return SEM_OK;
     const int grid = grid_for(h, total, 256, 8);
     if (fp32)
-        gs_kernel<float><<<grid, 256, 0, s>>>((float*)u, g.seg_off, g.seg_idx, g.nseg_free, g.nseg,
-                                              g.zero_idx, g.nzero, apply_mask ? 1 : 0);
+        gs_kernel<float><<<grid, 256, 0, s>>>((float*)u, g, apply_mask ? 1 : 0);
     else
-        gs_kernel<double><<<grid, 256, 0, s>>>((double*)u, g.seg_off, g.seg_idx, g.nseg_free, g.nseg,
-                                               g.zero_idx, g.nzero, apply_mask ? 1 : 0);
+        gs_kernel<double><<<grid, 256, 0, s>>>((double*)u, g, apply_mask ? 1 : 0);
     SEM_LAUNCH_CHECK("gs_kernel");
     h->launches++;
     return SEM_OK;

@@ -15,6 +15,8 @@ namespace sem {
 constexpr int kMaxLx = 16;
 constexpr int kReduceThreads = 256;
 constexpr int kMaxPartials = 4096;  // upper bound on CTAs of a reducing launch
+constexpr int kBulkVariantsMax = 4;  // operator variants 1..4 are bulk-staged
+constexpr int kDfVariant = 5;        // FP64 data, FP32-pair arithmetic (FP64 precisions only)
 
 // ---------------------------------------------------------------------------
 // errors
@@ -66,18 +68,23 @@ struct MeshPart {
     int64_t n_free = 0;
 };
 
-// Gather-scatter lists: every node with >= 2 copies is one segment
-// (local indices ascending).  Segments of free nodes come first, then those of
-// Dirichlet nodes; `zero` lists Dirichlet nodes with a single copy.
+// Gather-scatter lists.  Every node with >= 2 copies is one segment whose
+// local indices are listed in ascending order.  Segments of free nodes are
+// split by size (2, 4, 8 copies: index vectors; any other count: CSR) and
+// ordered by their first local index; segments of Dirichlet nodes are kept as
+// CSR (they are only summed when the mask is not applied); `zero` lists every
+// local copy of every Dirichlet node.
 struct GSLists {
-    int* seg_off = nullptr;   // [nseg + 1]
-    int* seg_idx = nullptr;   // [n_shared]
-    int* zero_idx = nullptr;  // [nzero]
-    int* seg_solve = nullptr; // batch: solve of each segment (unused for one mesh)
-    int64_t nseg_free = 0;
-    int64_t nseg = 0;
-    int64_t n_shared = 0;
-    int64_t nzero = 0;
+    int2* pairs = nullptr;
+    int4* quads = nullptr;
+    int4* octs = nullptr;      // two int4 per segment
+    int* oth_off = nullptr;    // [noth + 1]
+    int* oth_idx = nullptr;
+    int* dir_off = nullptr;    // [ndir + 1]
+    int* dir_idx = nullptr;
+    int* zero_idx = nullptr;   // [nzero]
+    int64_t npair = 0, nquad = 0, noct = 0, noth = 0, ndir = 0, nzero = 0;
+    int64_t n_shared = 0;      // local points in segments
 };
 
 struct Workspace {
@@ -129,6 +136,7 @@ struct BatchPlan {
     unsigned int* scount = nullptr;  // [nsolve] per-solve ticket counters
     double* rrbb = nullptr;   // [nsolve * 2]
     int* act = nullptr;       // [nsolve] solves taking part in an inner solve
+    double* itol = nullptr;   // [nsolve] inner relative tolerance of each active solve
     bool ready = false;
 };
 
@@ -138,6 +146,7 @@ struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     int key_prec = -1;
     int key_chunk = 0;
+    int key_variant = -1;
     const void* key_ptr = nullptr;
 };
 
@@ -156,9 +165,11 @@ struct sem_handle {
     // basis per lx (index lx): D in FP64 and FP32
     double* D64[sem::kMaxLx + 1] = {};
     float* D32[sem::kMaxLx + 1] = {};
+    float* D2[sem::kMaxLx + 1] = {};   // [2][lx][lx]: hi and lo floats of D
     // set-up data
     double* G64 = nullptr;     // [E][6][lx^3], h1 folded in
     float* G32 = nullptr;
+    float* G2 = nullptr;       // [E][12][lx^3]: hi planes then lo planes of G64 (FP32-pair kernel)
     double* B64 = nullptr;     // [n_local] mass
     double* minv64 = nullptr;  // [n_local]
     float* minv32 = nullptr;
@@ -177,6 +188,7 @@ struct sem_handle {
     cudaStream_t capture_stream = nullptr;
     cudaEvent_t ax_ev[2] = {nullptr, nullptr};  // bracket the first K-A of each graph
     int64_t launches = 0;                        // kernels launched by this handle
+    int ax_variant[2][sem::kMaxLx + 1];          // tuned operator variant per [fp32][lx], -1 = not tuned
     size_t device_bytes = 0;
 };
 
@@ -217,5 +229,9 @@ int launch_residual(sem_handle* h, const double* b, const double* ax, double* r,
                     double* rr_out, cudaStream_t s);  // r = b - ax, rr_out[0] = <r,r>
 int grid_for(sem_handle* h, int64_t work_items, int threads, int per_sm);
 int prepare_cg_kernels(sem_handle* h);
+int autotune_ax(sem_handle* h, bool fp32, cudaStream_t s);
+int ax_variant_for(const sem_handle* h, int lx, bool fp32);
+int* device_error_word(sem_handle* h);
+double inner_tolerance(const sem_solve_opts& o, double rel);
 
 }  // namespace sem

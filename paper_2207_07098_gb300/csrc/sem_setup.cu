@@ -193,6 +193,21 @@ __global__ void jacobi_invert_kernel(const double* d, const uint8_t* mask, int64
     }
 }
 
+// G2[e][c][q] = hi(G[e][c][q]), G2[e][6 + c][q] = lo = float(G - hi)
+__global__ void split_factors_kernel(const double* G, float* G2, int64_t nelem_planes, int n3) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nelem_planes * n3;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t ec = t / n3;  // element * 6 + c
+        const int q = (int)(t - ec * n3);
+        const int64_t e = ec / 6;
+        const int c = (int)(ec - e * 6);
+        const double v = G[t];
+        const float hi = (float)v;
+        G2[(e * 12 + c) * n3 + q] = hi;
+        G2[(e * 12 + 6 + c) * n3 + q] = (float)(v - (double)hi);
+    }
+}
+
 __global__ void to_float_kernel(const double* a, float* b, int64_t n) {
     for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < n;
          L += (int64_t)gridDim.x * blockDim.x)
@@ -235,7 +250,6 @@ static void radix_sort_pairs(std::vector<uint64_t>& key, std::vector<int32_t>& v
 // by loc_off).  Returns SEM_OK or SEM_EINVAL.
 struct HostGS {
     std::vector<int32_t> free_off, free_idx, dir_off, dir_idx, zero;
-    std::vector<int32_t> free_solve, dir_solve;
     std::vector<uint8_t> mult;
 };
 
@@ -268,9 +282,7 @@ static int build_gs_part(const MeshPart& part, int solve, const int64_t* gid, co
         if (cnt >= 2) {
             auto& off = m0 ? out.free_off : out.dir_off;
             auto& idx = m0 ? out.free_idx : out.dir_idx;
-            auto& sol = m0 ? out.free_solve : out.dir_solve;
             off.push_back((int32_t)idx.size());
-            sol.push_back(solve);
             for (int64_t c = a; c < b; c++) idx.push_back((int32_t)(part.loc_off + val[c]));
         } else if (!m0) {
             out.zero.push_back((int32_t)(part.loc_off + val[a]));
@@ -287,18 +299,19 @@ static void free_handle(sem_handle* h) {
     for (int l = 0; l <= kMaxLx; l++) {
         cudaFree(h->D64[l]);
         cudaFree(h->D32[l]);
+        cudaFree(h->D2[l]);
     }
     cudaFree(h->G64);
     cudaFree(h->G32);
+    cudaFree(h->G2);
     cudaFree(h->B64);
     cudaFree(h->minv64);
     cudaFree(h->minv32);
     cudaFree(h->mult);
     cudaFree(h->mask);
-    cudaFree(h->gs.seg_off);
-    cudaFree(h->gs.seg_idx);
-    cudaFree(h->gs.zero_idx);
-    cudaFree(h->gs.seg_solve);
+    GSLists& gl = h->gs;
+    cudaFree(gl.pairs); cudaFree(gl.quads); cudaFree(gl.octs); cudaFree(gl.oth_off); cudaFree(gl.oth_idx);
+    cudaFree(gl.dir_off); cudaFree(gl.dir_idx); cudaFree(gl.zero_idx);
     cudaFree(h->partials);
     cudaFree(h->counters);
     cudaFree(h->state);
@@ -313,7 +326,7 @@ static void free_handle(sem_handle* h) {
     }
     cudaFree(bp.sgfirst); cudaFree(bp.sgcount); cudaFree(bp.tloc); cudaFree(bp.tlen); cudaFree(bp.tsolve);
     cudaFree(bp.stfirst); cudaFree(bp.stcount); cudaFree(bp.gpart); cudaFree(bp.tpart); cudaFree(bp.scount);
-    cudaFree(bp.rrbb); cudaFree(bp.act);
+    cudaFree(bp.rrbb); cudaFree(bp.act); cudaFree(bp.itol);
     if (h->graph.exec) cudaGraphExecDestroy(h->graph.exec);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     for (auto& ev : h->ax_ev)
@@ -349,7 +362,7 @@ static bool host_pointer(const void* p) {
     return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
 }
 
-static int setup_common(sem_handle** out, int nsolve, const sem_mesh_desc* meshes, cudaStream_t s) {
+static int setup_common(sem_handle** out, int nsolve, const sem_mesh_desc* meshes, int flags, cudaStream_t s) {
     *out = nullptr;
     if (nsolve < 1 || !meshes) return fail(SEM_EINVAL, "nsolve must be >= 1");
     int64_t n_local = 0, E = 0;
@@ -366,7 +379,11 @@ static int setup_common(sem_handle** out, int nsolve, const sem_mesh_desc* meshe
     }
     if (n_local >= ((int64_t)1 << 31) - 64)
         return fail(SEM_EINVAL, "n_local must be below 2^31 (32-bit local indices)");
+    const int forced = (flags & 0xF) - 1;  // pinned operator variant, -1 = autotune
+    if (forced > kDfVariant) return fail(SEM_EINVAL, "operator variant out of range");
     sem_handle* h = new sem_handle();
+    for (auto& row : h->ax_variant)
+        for (int& v : row) v = forced;
     int rc = SEM_OK;
     auto bail = [&](int code) {
         free_handle(h);
@@ -406,24 +423,60 @@ static int setup_common(sem_handle** out, int nsolve, const sem_mesh_desc* meshe
         h->n_free += p.n_free;
     }
     GSLists& g = h->gs;
-    g.nseg_free = (int64_t)hg.free_off.size();
-    g.nseg = g.nseg_free + (int64_t)hg.dir_off.size();
-    g.n_shared = (int64_t)(hg.free_idx.size() + hg.dir_idx.size());
-    g.nzero = (int64_t)hg.zero.size();
-    std::vector<int32_t> off(g.nseg + 1), idx(g.n_shared), sol(g.nseg);
+    // free segments by size class, each class ordered by first local index
+    std::vector<int2> pairs;
+    std::vector<int4> quads, octs;
+    std::vector<int32_t> oth_off, oth_idx, dir_off, dir_idx, zero;
     {
-        int64_t c = 0;
-        for (size_t q = 0; q < hg.free_off.size(); q++) { off[c] = hg.free_off[q]; sol[c] = hg.free_solve[q]; c++; }
-        const int32_t base = (int32_t)hg.free_idx.size();
-        for (size_t q = 0; q < hg.dir_off.size(); q++) { off[c] = base + hg.dir_off[q]; sol[c] = hg.dir_solve[q]; c++; }
-        off[g.nseg] = (int32_t)g.n_shared;
-        std::copy(hg.free_idx.begin(), hg.free_idx.end(), idx.begin());
-        std::copy(hg.dir_idx.begin(), hg.dir_idx.end(), idx.begin() + base);
+        const int64_t nf = (int64_t)hg.free_off.size();
+        std::vector<std::pair<int32_t, int64_t>> order(nf);
+        for (int64_t q = 0; q < nf; q++) order[q] = {hg.free_idx[hg.free_off[q]], q};
+        std::sort(order.begin(), order.end());
+        for (auto& o : order) {
+            const int64_t q = o.second;
+            const int32_t a = hg.free_off[q];
+            const int32_t b = q + 1 < nf ? hg.free_off[q + 1] : (int32_t)hg.free_idx.size();
+            const int32_t* ix = hg.free_idx.data() + a;
+            const int c = b - a;
+            if (c == 2) {
+                pairs.push_back(make_int2(ix[0], ix[1]));
+            } else if (c == 4) {
+                quads.push_back(make_int4(ix[0], ix[1], ix[2], ix[3]));
+            } else if (c == 8) {
+                octs.push_back(make_int4(ix[0], ix[1], ix[2], ix[3]));
+                octs.push_back(make_int4(ix[4], ix[5], ix[6], ix[7]));
+            } else {
+                oth_off.push_back((int32_t)oth_idx.size());
+                oth_idx.insert(oth_idx.end(), ix, ix + c);
+            }
+        }
+        oth_off.push_back((int32_t)oth_idx.size());
+        const int64_t nd = (int64_t)hg.dir_off.size();
+        for (int64_t q = 0; q < nd; q++) {
+            const int32_t a = hg.dir_off[q];
+            const int32_t b = q + 1 < nd ? hg.dir_off[q + 1] : (int32_t)hg.dir_idx.size();
+            dir_off.push_back((int32_t)dir_idx.size());
+            dir_idx.insert(dir_idx.end(), hg.dir_idx.begin() + a, hg.dir_idx.begin() + b);
+        }
+        dir_off.push_back((int32_t)dir_idx.size());
+        zero = hg.zero;
+        zero.insert(zero.end(), hg.dir_idx.begin(), hg.dir_idx.end());
+        std::sort(zero.begin(), zero.end());
     }
-    if ((rc = dalloc(h, &g.seg_off, off.size())) || (rc = dalloc(h, &g.seg_idx, idx.size() + 1)) ||
-        (rc = dalloc(h, &g.zero_idx, hg.zero.size() + 1)) || (rc = dalloc(h, &g.seg_solve, sol.size() + 1)) ||
+    g.npair = (int64_t)pairs.size();
+    g.nquad = (int64_t)quads.size();
+    g.noct = (int64_t)octs.size() / 2;
+    g.noth = (int64_t)oth_off.size() - 1;
+    g.ndir = (int64_t)dir_off.size() - 1;
+    g.nzero = (int64_t)zero.size();
+    g.n_shared = (int64_t)(hg.free_idx.size() + hg.dir_idx.size());
+    if ((rc = dalloc(h, &g.pairs, pairs.size() + 1)) || (rc = dalloc(h, &g.quads, quads.size() + 1)) ||
+        (rc = dalloc(h, &g.octs, octs.size() + 2)) || (rc = dalloc(h, &g.oth_off, oth_off.size())) ||
+        (rc = dalloc(h, &g.oth_idx, oth_idx.size() + 1)) || (rc = dalloc(h, &g.dir_off, dir_off.size())) ||
+        (rc = dalloc(h, &g.dir_idx, dir_idx.size() + 1)) || (rc = dalloc(h, &g.zero_idx, zero.size() + 1)) ||
         (rc = dalloc(h, &h->mult, n_local)) || (rc = dalloc(h, &h->mask, n_local)) ||
         (rc = dalloc(h, &h->G64, (size_t)6 * n_local)) || (rc = dalloc(h, &h->G32, (size_t)6 * n_local)) ||
+        (rc = dalloc(h, &h->G2, (size_t)12 * n_local)) ||
         (rc = dalloc(h, &h->B64, n_local)) || (rc = dalloc(h, &h->minv64, n_local)) ||
         (rc = dalloc(h, &h->minv32, n_local)) || (rc = dalloc(h, &h->partials, (size_t)kMaxPartials * 4)) ||
         (rc = dalloc(h, &h->counters, 16)) || (rc = dalloc(h, &h->state, (size_t)2 * nsolve + 2)) ||
@@ -438,26 +491,37 @@ static int setup_common(sem_handle** out, int nsolve, const sem_mesh_desc* meshe
             if (e_ != cudaSuccess) return bail(cuda_fail(e_, "upload"));                  \
         }                                                                                 \
     } while (0)
-    UP(g.seg_off, off.data(), off.size() * 4);
-    UP(g.seg_idx, idx.data(), idx.size() * 4);
-    UP(g.zero_idx, hg.zero.data(), hg.zero.size() * 4);
-    UP(g.seg_solve, sol.data(), sol.size() * 4);
+    UP(g.pairs, pairs.data(), pairs.size() * sizeof(int2));
+    UP(g.quads, quads.data(), quads.size() * sizeof(int4));
+    UP(g.octs, octs.data(), octs.size() * sizeof(int4));
+    UP(g.oth_off, oth_off.data(), oth_off.size() * 4);
+    UP(g.oth_idx, oth_idx.data(), oth_idx.size() * 4);
+    UP(g.dir_off, dir_off.data(), dir_off.size() * 4);
+    UP(g.dir_idx, dir_idx.data(), dir_idx.size() * 4);
+    UP(g.zero_idx, zero.data(), zero.size() * 4);
     UP(h->mult, hg.mult.data(), (size_t)n_local);
     UP(h->mask, mask_all.data(), (size_t)n_local);
-    if (cudaMemsetAsync(h->counters, 0, 16 * sizeof(unsigned), s) != cudaSuccess)
+    if (cudaMemsetAsync(h->counters, 0, 16 * sizeof(unsigned), s) != cudaSuccess ||
+        cudaMemsetAsync(h->scratch, 0, 64 * sizeof(double), s) != cudaSuccess)
         return bail(fail(SEM_ECUDA, "memset"));
     // basis per order
     for (int q = 0; q < nsolve; q++) {
         const int lx = h->parts[q].lx;
         if (h->D64[lx]) continue;
         double Dh[kMaxLx * kMaxLx];
-        float Df[kMaxLx * kMaxLx];
+        float Df[kMaxLx * kMaxLx], D2[2 * kMaxLx * kMaxLx];
         gll_basis(lx, nullptr, nullptr, Dh);
-        for (int t = 0; t < lx * lx; t++) Df[t] = (float)Dh[t];
-        if ((rc = dalloc(h, &h->D64[lx], (size_t)lx * lx)) || (rc = dalloc(h, &h->D32[lx], (size_t)lx * lx)))
+        for (int t = 0; t < lx * lx; t++) {
+            Df[t] = (float)Dh[t];
+            D2[t] = Df[t];
+            D2[lx * lx + t] = (float)(Dh[t] - (double)Df[t]);
+        }
+        if ((rc = dalloc(h, &h->D64[lx], (size_t)lx * lx)) || (rc = dalloc(h, &h->D32[lx], (size_t)lx * lx)) ||
+            (rc = dalloc(h, &h->D2[lx], (size_t)2 * lx * lx)))
             return bail(rc);
         UP(h->D64[lx], Dh, sizeof(double) * lx * lx);
         UP(h->D32[lx], Df, sizeof(float) * lx * lx);
+        UP(h->D2[lx], D2, sizeof(float) * 2 * lx * lx);
     }
     // geometry, mass, Jacobi diagonal: one part at a time through a staging buffer
     int64_t maxn = 0;
@@ -514,6 +578,11 @@ static int setup_common(sem_handle** out, int nsolve, const sem_mesh_desc* meshe
         jacobi_invert_kernel<<<grid_for(h, n_local, 256, 8), 256, 0, s>>>(dd, h->mask, n_local, h->minv64,
                                                                            h->minv32);
         to_float_kernel<<<grid_for(h, 6 * n_local, 256, 8), 256, 0, s>>>(h->G64, h->G32, 6 * n_local);
+        for (const MeshPart& p : h->parts) {
+            const int n3 = p.lx * p.lx * p.lx;
+            split_factors_kernel<<<grid_for(h, 6 * p.n_local, 256, 8), 256, 0, s>>>(
+                h->G64 + 6 * p.loc_off, h->G2 + 12 * p.loc_off, (int64_t)6 * p.E, n3);
+        }
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) rc = cuda_fail(e, "jacobi set-up");
     }
@@ -542,6 +611,7 @@ SEM_API void sem_solve_opts_default(sem_solve_opts* o) {
     o->precision = SEM_FP64;
     o->use_graph = 1;
     o->graph_chunk = 32;
+    o->autotune = 1;
 }
 
 SEM_API int sem_gll(int lx, double* xi, double* rho, double* D) {
@@ -553,7 +623,6 @@ SEM_API int sem_gll(int lx, double* xi, double* rho, double* D) {
 SEM_API int sem_setup(sem_handle** h, int E, int lx, const double* coords, const int64_t* gid,
                       const uint8_t* mask, const double* h1, int flags, cudaStream_t stream) {
     if (!h) return fail(SEM_EINVAL, "null handle pointer");
-    (void)flags;
     sem_mesh_desc m;
     m.E = E;
     m.lx = lx;
@@ -561,14 +630,13 @@ SEM_API int sem_setup(sem_handle** h, int E, int lx, const double* coords, const
     m.gid = gid;
     m.mask = mask;
     m.h1 = h1;
-    return setup_common(h, 1, &m, stream);
+    return setup_common(h, 1, &m, flags, stream);
 }
 
 SEM_API int sem_setup_batch(sem_handle** h, int nsolve, const sem_mesh_desc* meshes, int flags,
                             cudaStream_t stream) {
     if (!h) return fail(SEM_EINVAL, "null handle pointer");
-    (void)flags;
-    return setup_common(h, nsolve, meshes, stream);
+    return setup_common(h, nsolve, meshes, flags, stream);
 }
 
 SEM_API int sem_destroy(sem_handle* h) {

@@ -26,9 +26,9 @@ def host(t_):
 class Handle:
     """A libsem handle for one workloads.Mesh (destroyed with the object)."""
 
-    def __init__(self, mesh, h1=None):
+    def __init__(self, mesh, h1=None, flags=0):
         self.mesh = mesh
-        self.h = S.sem_setup(mesh.E, mesh.lx, mesh.coords, mesh.gid, mesh.mask, h1)
+        self.h = S.sem_setup(mesh.E, mesh.lx, mesh.coords, mesh.gid, mesh.mask, h1, flags)
         self.info = S.sem_get_info(self.h)
         self.n = self.info["n_local"]
 

@@ -124,6 +124,52 @@ def test_mass_and_dot(kind, dims, N):
     assert abs(d - P.dot(a, b)) <= 1e-13 * np.sum(np.abs(a * b) / P.mult())
 
 
+BULK_CASES = [("jitter", (3, 3, 2), 3), ("deformed", (5, 3, 2), 5), ("jitter", (3, 3, 3), 7),
+              ("deformed", (5, 4, 3), 7), ("deformed", (2, 3, 2), 9), ("deformed", (2, 2, 1), 11)]
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
+@pytest.mark.parametrize("kind,dims,N", BULK_CASES)
+def test_ax_bulk_staged_variants(variant, kind, dims, N):
+    """Bulk-copy staged kernels: same arithmetic in the same order as the
+    shared-slab kernel, so FP64 and FP32 results are bit-identical to it."""
+    m, h1 = _case(kind, dims, N)
+    P = oracle.Problem(m, h1)
+    H0 = Handle(m, h1, flags=S.SEM_FLAG_VARIANT(0))
+    Hv = Handle(m, h1, flags=S.SEM_FLAG_VARIANT(variant))
+    u = W.random_local_field(m, 21)
+    w64 = Hv.ax(u, S.SEM_FP64, assemble=0)
+    e2, einf = rel_err(w64, P.ax_local(u))
+    assert e2 <= TOL_AX64 and einf <= TOL_AX64, (e2, einf)
+    assert np.array_equal(w64, H0.ax(u, S.SEM_FP64, assemble=0))
+    u32 = u.astype(np.float32)
+    assert np.array_equal(Hv.ax(u32, S.SEM_FP32, assemble=0), H0.ax(u32, S.SEM_FP32, assemble=0))
+    uc = W.random_local_field(m, 22, continuous=True)
+    e2, einf = rel_err(Hv.ax(uc, S.SEM_FP64, assemble=1), P.ax(uc))
+    assert e2 <= TOL_AX64 and einf <= TOL_AX64, (e2, einf)
+
+
+DF_CASES = [("affine", (1, 1, 1), 1), ("jitter", (3, 3, 2), 3), ("deformed", (5, 3, 2), 4), ("jitter", (3, 3, 3), 7),
+            ("deformed", (5, 4, 3), 7), ("annulus", (8, 3, 2), 7), ("jitter", (2, 2, 3), 9), ("deformed", (2, 2, 1), 11)]
+
+
+@pytest.mark.parametrize("kind,dims,N", DF_CASES)
+def test_ax_fp32_pair_variant(kind, dims, N):
+    """FP64 data with FP32-pair arithmetic (variant 5): FP64 parity bar."""
+    m, h1 = _case(kind, dims, N)
+    P = oracle.Problem(m, h1)
+    H = Handle(m, h1, flags=S.SEM_FLAG_VARIANT(5))
+    u = W.random_local_field(m, 23)
+    e2, einf = rel_err(H.ax(u, S.SEM_FP64, assemble=0), P.ax_local(u))
+    assert e2 <= TOL_AX64 and einf <= TOL_AX64, (e2, einf)
+    uc = W.random_local_field(m, 24, continuous=True)
+    e2, einf = rel_err(H.ax(uc, S.SEM_FP64, assemble=1), P.ax(uc))
+    assert e2 <= TOL_AX64 and einf <= TOL_AX64, (e2, einf)
+    # the native FP64 kernel is still reachable on the same handle
+    e2, _ = rel_err(H.ax(u, S.SEM_FP64_NATIVE, assemble=0), P.ax_local(u))
+    assert e2 <= TOL_AX64
+
+
 def test_ax_deterministic():
     m, h1 = _case("jitter", (4, 3, 3), 7)
     H = Handle(m, h1)

@@ -66,6 +66,30 @@ def test_mixed_ir(case, inner_tol):
     assert rel_err(x, x64)[0] <= 1e-7
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+def test_solves_with_each_operator_variant(variant):
+    m, h1, P, b = _deformed_case(5, 7)
+    H = Handle(m, h1, flags=S.SEM_FLAG_VARIANT(variant))
+    for mode in (S.SEM_MODE_FP64, S.SEM_MODE_MIXED_IR):
+        x, st = H.solve(b, mode=mode, tol=TOL)
+        assert st["status"] == S.SEM_OK and st["relres"] <= TOL, st
+        # a pinned bulk variant too large for FP64 shared memory falls back to 0;
+        # the FP32-pair variant 5 exists for FP64 data only
+        if mode == S.SEM_MODE_FP64:
+            assert st["ax_variant"] in (variant, 0)
+        else:
+            assert st["ax_variant"] == (variant if variant <= 4 else 0)
+        assert _oracle_relres(P, x, b) <= 1.05 * TOL
+
+
+def test_autotuned_solve_reports_variant():
+    m, h1, P, b = _deformed_case(6, 7)
+    H = Handle(m, h1)
+    x, st = H.solve(b, mode=S.SEM_MODE_MIXED_IR, tol=TOL)
+    assert st["status"] == S.SEM_OK and 0 <= st["ax_variant"] <= 4
+    assert _oracle_relres(P, x, b) <= 1.05 * TOL
+
+
 def test_solve_bit_reproducible_and_graph_equivalent():
     m, h1, P, b = _deformed_case(4, 5)
     H = Handle(m, h1)
