@@ -52,6 +52,8 @@ def _args():
     ap.add_argument("--no-extras", action="store_true", help="skip the comparison solves and ax-only bench")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--suite", action="store_true",
+                    help="also measure the cube (FP64 and mixed), the 256-member batch and the annulus")
     return ap.parse_args()
 
 
@@ -290,6 +292,7 @@ def run_ours(args):
     cfgs = {1: (1, 3), 2: (2, 2), 3: (2, 3), 4: (4, 2)}
     kname = (f"ax_kernel<{tname},{m.lx},true>" if variant == 0 else
              f"ax_df_kernel<{m.lx},true>" if variant == 5 else
+             f"ax_dfl_kernel<{m.lx},true>" if variant == 6 else
              f"ax_bulk_kernel<{tname},{m.lx},{cfgs[variant][0]},{cfgs[variant][1]},true>")
     traffic = _traffic_for(kname, f"deformed_cube_{args.n}^3_N{args.order}")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -360,7 +363,7 @@ def _extras(S, torch, h, m, bd, n, args, peak, stats, ms_timed):
     ex["ax_helm_only"] = axr
     # every operator variant (pinned at set-up), plain ax_helm, both precisions
     var = {}
-    for v in range(6):
+    for v in range(7):
         hv = S.sem_setup(m.E, m.lx, m.coords, m.gid, m.mask, None, S.SEM_FLAG_VARIANT(v))
         row = {}
         for name, prec, dt, bpp in (("fp64", S.SEM_FP64, torch.float64, 64), ("fp32", S.SEM_FP32, torch.float32, 32)):
@@ -383,10 +386,143 @@ def _extras(S, torch, h, m, bd, n, args, peak, stats, ms_timed):
     return ex
 
 
+def _timed_solve(S, torch, h, b_dev, n, opts, reps=3):
+    """Best-of-reps solve time (CUDA events inside the library) and its stats."""
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    S.sem_cg_solve(h, x, b_dev, opts)
+    best = None
+    for _ in range(reps):
+        x.zero_()
+        st = S.sem_cg_solve(h, x, b_dev, opts)
+        if best is None or st["time_ms"] < best["time_ms"]:
+            best = st
+    return x, best
+
+
+def _solve_report(st, n_local, n_free):
+    t = st["time_ms"] * 1e-3
+    return {"time_ms": st["time_ms"], "iterations": st["iterations"], "outer": st["outer_iterations"],
+            "relres": st["relres"], "status": st["status"], "gdof_s_local": n_local * st["iterations"] / t / 1e9,
+            "gdof_s_unique_free": n_free * st["iterations"] / t / 1e9, "cg_iter_s": st["iterations"] / t,
+            "ax_variant": st["ax_variant"]}
+
+
+def run_suite(args):
+    """The other synthetic workloads: unit cube 4^3, N=7 (FP64 and mixed,
+    error vs the exact solution and, in the CPU-baseline leg, vs the oracle),
+    the 256-member batch (FP64 and mixed), and the rotor-like annulus (FP64 vs
+    mixed, ax_helm timings).  Prints one JSON line."""
+    import torch
+    import paper_2207_07098_gb300 as S
+    S.load()
+    out = {"suite": "sem_poisson", "data": "synthetic"}
+    modes = (("fp64", {"mode": S.SEM_MODE_FP64, "tol": 1e-10}),
+             ("mixed", {"mode": S.SEM_MODE_MIXED_IR, "tol": 1e-10, "inner_tol": 1e-5}))
+    # --- cube, manufactured solution
+    m, f = W.cube_sines(4, 7)
+    h = S.sem_setup(m.E, m.lx, m.coords, m.gid, m.mask, None)
+    info = S.sem_get_info(h)
+    fd = torch.from_numpy(f).cuda()
+    bd = torch.empty_like(fd)
+    S.sem_mass(h, bd, fd, S.SEM_FP64, 1)
+    exact = W.exact_sines(m)
+    cube = {"workload": "cube 4^3 hex, N=7, f = 3 pi^2 sin sin sin, h1 = 1", "n_local": m.n_local,
+            "n_unique_free": info["n_free"]}
+    xs = {}
+    for name, o in modes:
+        x, st = _timed_solve(S, torch, h, bd, m.n_local, o)
+        xs[name] = x.cpu().numpy()
+        r = _solve_report(st, m.n_local, info["n_free"])
+        r["max_error_vs_exact"] = float(np.max(np.abs(xs[name] - exact)))
+        cube[name] = r
+    d = xs["mixed"] - xs["fp64"]
+    cube["mixed_vs_fp64_gpu_rel_l2"] = float(np.linalg.norm(d) / np.linalg.norm(xs["fp64"]))
+    cube["speedup_mixed_vs_fp64"] = cube["fp64"]["time_ms"] / cube["mixed"]["time_ms"]
+    # CPU-baseline leg: the oracle's own solve (timed) and the GPU error against it
+    import oracle
+    P = oracle.Problem(m)
+    bo = P.mass(f, assemble=True)
+    t0 = time.perf_counter()
+    xo, oi = P.pcg(bo, tol=1e-10)
+    dt = time.perf_counter() - t0
+    cube["cpu_baseline"] = {"value": m.n_local * oi["iters"] / dt / 1e9, "unit": UNIT, "cores": oracle.threads(),
+                            "kind": "oracle", "sample": f"full FP64 PCG solve ({oi['iters']} iterations, {dt:.2f} s)",
+                            "iterations": oi["iters"]}
+    for name in xs:
+        cube[name]["rel_l2_error_vs_oracle"] = float(np.linalg.norm(xs[name] - xo) / np.linalg.norm(xo))
+    S.sem_destroy(h)
+    out["cube_4^3_N7"] = cube
+    # --- batch of 256 independent boxes
+    t0 = time.perf_counter()
+    members = [W.batch_member_case(p) for p in W.batch_params()]
+    gen_s = time.perf_counter() - t0
+    hb = S.sem_setup_batch([(mm.E, mm.lx, mm.coords, mm.gid, mm.mask, None) for mm, _ in members])
+    binfo = S.sem_get_info(hb)
+    bcat = torch.from_numpy(np.concatenate([bb for _, bb in members])).cuda()
+    nb = len(members)
+    batch = {"workload": "256 boxes, nx,ny,nz ~ U{2..16}, N ~ U{5,7,9}, amp ~ U(0,0.08), random RHS (seed 4)",
+             "n_local": binfo["n_local"], "elements": binfo["E"], "generation_s": gen_s}
+    for name, o in modes:
+        x = torch.zeros_like(bcat)
+        S.sem_cg_solve_batch(hb, x, bcat, nb, o)
+        x.zero_()
+        sts = S.sem_cg_solve_batch(hb, x, bcat, nb, o)
+        t = sts[0]["time_ms"] * 1e-3
+        dofit = sum(mm.n_local * st["iterations"] for (mm, _), st in zip(members, sts))
+        its = [st["iterations"] for st in sts]
+        batch[name] = {"time_ms": sts[0]["time_ms"], "gdof_s_local": dofit / t / 1e9,
+                       "cg_iter_s_summed_over_solves": sum(its) / t, "iterations_max": max(its),
+                       "iterations_mean": float(np.mean(its)), "all_converged": all(st["status"] == 0 for st in sts),
+                       "relres_max": max(st["relres"] for st in sts), "launches": sts[0]["kernel_launches"]}
+    batch["speedup_mixed_vs_fp64"] = batch["fp64"]["time_ms"] / batch["mixed"]["time_ms"]
+    S.sem_destroy(hb)
+    del bcat, members
+    torch.cuda.empty_cache()
+    out["batch_256"] = batch
+    # --- annulus
+    t0 = time.perf_counter()
+    m, f = W.annulus_case()
+    gen_s = time.perf_counter() - t0
+    h = S.sem_setup(m.E, m.lx, m.coords, m.gid, m.mask, None)
+    info = S.sem_get_info(h)
+    fd = torch.from_numpy(f).cuda()
+    bd = torch.empty_like(fd)
+    S.sem_mass(h, bd, fd, S.SEM_FP64, 1)
+    ann = {"workload": "O-grid annulus r in [0.5, 8], 64x32x24 elements (ratio 1.1), N=7, periodic span 4, "
+                       "Fourier RHS |k| <= 4 (seed 5)", "n_local": m.n_local, "n_unique_free": info["n_free"],
+           "generation_s": gen_s}
+    for name, o in modes:
+        _, st = _timed_solve(S, torch, h, bd, m.n_local, o, reps=2)
+        ann[name] = _solve_report(st, m.n_local, info["n_free"])
+    ann["speedup_mixed_vs_fp64"] = ann["fp64"]["time_ms"] / ann["mixed"]["time_ms"]
+    peak, _ = _peaks()
+    stream = torch.cuda.current_stream()
+    for name, prec, dt_, bpp in (("ax_fp64", S.SEM_FP64, torch.float64, 64), ("ax_fp32", S.SEM_FP32, torch.float32, 32)):
+        u = torch.randn(m.n_local, dtype=dt_, device="cuda")
+        w = torch.empty_like(u)
+        for _ in range(3):
+            S.sem_ax(h, w, u, prec, 0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(10):
+            S.sem_ax(h, w, u, prec, 0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 10
+        ann[name] = {"ms": t, "gb_s": bpp * m.n_local / (t * 1e-3) / 1e9,
+                     "frac_hbm": bpp * m.n_local / (t * 1e-3) / 1e9 / peak}
+    S.sem_destroy(h)
+    out["annulus_64x32x24_N7"] = ann
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.suite:
+        run_suite(args)
     else:
         run_ours(args)
 

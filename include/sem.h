@@ -114,7 +114,9 @@ typedef struct sem_solve_stats {
     int ax_samples;           /* number of such samples */
     int ax_variant;           /* operator kernel used by the CG loop: 0 = shared-slab staging,
                                  1..4 = bulk-copy staging (elements per CTA, stages) =
-                                 (1,3), (2,2), (2,3), (4,2) */
+                                 (1,3), (2,2), (2,3), (4,2), lx in {4,6,8,10,12};
+                                 5 = FP64 data in FP32-pair arithmetic (lx <= 12);
+                                 6 = as 5 with even/odd line transforms (even lx <= 12) */
 } sem_solve_stats;
 
 /* Mesh of one member of a batch (host pointers; see sem_setup). */
@@ -127,7 +129,7 @@ typedef struct sem_mesh_desc {
     const double* h1;       /* [E lx^3] or NULL for h1 = 1 */
 } sem_mesh_desc;
 
-/* Set-up flag: pin operator kernel variant v (0..4) for every precision. */
+/* Set-up flag: pin operator kernel variant v (0..6) for every precision. */
 #define SEM_FLAG_VARIANT(v) ((int)(((v) + 1) & 0xF))
 
 /* Fill *opts with the defaults listed above. */
@@ -150,9 +152,8 @@ SEM_API int sem_gll(int lx, double* xi, double* rho, double* D);
  *   mask    HOST [E lx^3] 0 on homogeneous Dirichlet nodes, 1 elsewhere
  *   h1      HOST [E lx^3] coefficient at every node, or NULL for h1 = 1
  *   flags   0, or SEM_FLAG_VARIANT(v) to pin the operator kernel variant v
- *           (0 = shared-slab staging, 1..4 = bulk-copy staging, see
- *           sem_solve_stats.ax_variant) instead of autotuning it; variants
- *           1..4 apply to lx in {4, 6, 8, 10, 12} and fall back to 0 elsewhere
+ *           (see sem_solve_stats.ax_variant) instead of autotuning it;
+ *           variants a kernel does not cover fall back to 0
  * Computes on the device the geometric factors G_st = rho rho rho J
  * sum_l dr_s/dx_l dr_t/dx_l (h1 folded in), the mass B = rho rho rho J and
  * the Jacobi diagonal, and on the host the gather-scatter lists.

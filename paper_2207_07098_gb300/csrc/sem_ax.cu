@@ -22,6 +22,7 @@ int* device_error_word(sem_handle* h) { return reinterpret_cast<int*>(h->scratch
 int ax_variant_for(const sem_handle* h, int lx, bool fp32) {
     const int v = h->ax_variant[fp32 ? 1 : 0][lx];
     if (v == kDfVariant) return (!fp32 && lx <= 12) ? v : 0;
+    if (v == kDflVariant) return (!fp32 && bulk_supported(lx)) ? v : 0;
     return (v > 0 && bulk_fits(lx, v, fp32)) ? v : 0;
 }
 
@@ -45,8 +46,23 @@ static int dispatch_variant(sem_handle* h, int lx, AxParams<T> a, bool fused, in
             d.dry = a.dry;
             return dispatch_ax_df_entry(h, lx, d, fused, s);
         }
+        if (variant == kDflVariant && bulk_supported(lx)) {
+            DflParams d = {};
+            d.u = a.u;
+            d.z = a.z;
+            d.p = a.p;
+            d.w = a.w;
+            d.G2 = h->G2 + (a.G - h->G64) * 2;
+            d.coef = h->DL[lx];
+            d.E = a.E;
+            d.st = a.st;
+            d.partials = a.partials;
+            d.counter = a.counter;
+            d.dry = a.dry;
+            return dispatch_ax_dfl_entry(h, lx, d, fused, s);
+        }
     }
-    if (variant == kDfVariant) variant = 0;
+    if (variant == kDfVariant || variant == kDflVariant) variant = 0;
     a.variant = variant;
     a.err = device_error_word(h);
     const bool bulk_ok = variant > 0 && bulk_fits(lx, variant, sizeof(T) == 4) && aligned16(a.w) &&
@@ -135,7 +151,7 @@ int prepare_cg_kernels(sem_handle* h) {
                     AxParams<double> a = {};
                     a.dry = 1;
                     a.G = h->G64;
-                    if (v == kDfVariant) {
+                    if (v == kDfVariant || v == kDflVariant) {
                         rc = dispatch_variant<double>(h, p.lx, a, fused != 0, v, 0);
                     } else {
                         a.variant = v;
@@ -166,9 +182,10 @@ int autotune_ax(sem_handle* h, bool fp32, cudaStream_t s) {
         if (h->ax_variant[fp32][p.lx] >= 0) continue;
         float best = 1e30f;
         int best_v = 0;
-        for (int v = 0; v <= kDfVariant; v++) {
+        for (int v = 0; v <= kDflVariant; v++) {
             if (v > 0 && v < kDfVariant && !bulk_fits(p.lx, v, fp32)) continue;
             if (v == kDfVariant && (fp32 || p.lx > 12)) continue;
+            if (v == kDflVariant && (fp32 || !bulk_supported(p.lx))) continue;
             int rc2;
             auto run = [&](int dry) -> int {
                 if (fp32) {

@@ -7,4 +7,8 @@ int dispatch_ax_df_entry(sem_handle* h, int lx, const DfParams& a, bool fused, c
     return fused ? dispatch_ax_df<true>(h, lx, a, s) : dispatch_ax_df<false>(h, lx, a, s);
 }
 
+int dispatch_ax_dfl_entry(sem_handle* h, int lx, const DflParams& a, bool fused, cudaStream_t s) {
+    return fused ? dispatch_ax_dfl<true>(h, lx, a, s) : dispatch_ax_dfl<false>(h, lx, a, s);
+}
+
 }  // namespace sem

@@ -260,4 +260,305 @@ inline int dispatch_ax_df(sem_handle* h, int lx, const DfParams& a, cudaStream_t
 
 int dispatch_ax_df_entry(sem_handle* h, int lx, const DfParams& a, bool fused, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// Line-transform form of the FP32-pair operator (even lx).  D and D^T are
+// centro-antisymmetric (M_{N-i,N-l} = -M_il), so with the even and odd parts
+// e_m = x_m + x_{N-m}, o_m = x_m - x_{N-m} of a line x (m < lx/2):
+//   y_i     = sum_m A_im o_m + sum_m B_im e_m,
+//   y_{N-i} = sum_m A_im o_m - sum_m B_im e_m,
+// with A_im = (M_im - M_{i,N-m}) / 2, B_im = (M_im + M_{i,N-m}) / 2:
+// (lx/2)^2 * 2 products per line instead of lx^2.  A thread owns one line
+// in each direction: r-lines (k, j), s-lines (k, i), t-lines (j, i).
+// ---------------------------------------------------------------------------
+
+// a + b (sign +1) or a - b (sign -1) of unnormalised pairs, unnormalised result
+__device__ __forceinline__ void pair_addsub(float ah, float al, float bh, float bl, float sign, float& h, float& l) {
+    const float b = sign * bh;
+    const float s = ah + b;
+    const float bb = s - ah;
+    const float err = (ah - (s - bb)) + (b - bb);
+    h = s;
+    l = err + (al + sign * bl);
+}
+
+template <int LX>
+struct DflCfg {
+    static constexpr int P = LX / 2;
+    static constexpr int N2 = LX * LX, N3 = LX * LX * LX;
+    static constexpr int LXP = LX + 1;           // padded row
+    static constexpr int N2P = LX * LXP + 1;     // padded plane
+    static constexpr int SLOT = LX * N2P;        // floats per element per array
+    static constexpr int EPC = (256 / N2) > 0 ? (256 / N2) : 1;
+    static constexpr int USED = EPC * N2;
+    static constexpr int THREADS = ((USED + 31) / 32) * 32;
+    // coefficient tables: [fwd/bwd][A/B][hi/lo][P][P]
+    static constexpr int COEF = 2 * 2 * 2 * P * P;
+    static constexpr size_t FLOATS = (size_t)COEF + 8 * (size_t)EPC * SLOT;
+    static __host__ __device__ constexpr int at(int k, int j, int i) { return k * N2P + j * LXP + i; }
+};
+
+// One line: x at xs[0], xs[st], ..., y written to ys[0], ys[st], ... (both
+// hi and lo arrays); coefficient tables A, B (hi, lo) of size P x P.
+template <int LX>
+__device__ __forceinline__ void df_line(const float* xh, const float* xl, int xst, float* yh, float* yl, int yst,
+                                        const float* Ah, const float* Al, const float* Bh, const float* Bl) {
+    constexpr int P = LX / 2, N = LX - 1;
+    float eh[P], el[P], oh[P], ol[P];
+#pragma unroll
+    for (int m = 0; m < P; m++) {
+        const float ah = xh[m * xst], al = xl[m * xst], bh = xh[(N - m) * xst], bl = xl[(N - m) * xst];
+        pair_addsub(ah, al, bh, bl, 1.0f, eh[m], el[m]);
+        pair_addsub(ah, al, bh, bl, -1.0f, oh[m], ol[m]);
+    }
+#pragma unroll
+    for (int i = 0; i < P; i++) {
+        float sS = 0.f, sE = 0.f, tS = 0.f, tE = 0.f;
+#pragma unroll
+        for (int m = 0; m < P; m++) {
+            df_mac(sS, sE, Ah[i * P + m], Al[i * P + m], oh[m], ol[m]);
+            df_mac(tS, tE, Bh[i * P + m], Bl[i * P + m], eh[m], el[m]);
+        }
+        float h, l;
+        pair_addsub(sS, sE, tS, tE, 1.0f, h, l);
+        dfl y = df_norm(h, l);
+        yh[i * yst] = y.h;
+        yl[i * yst] = y.l;
+        pair_addsub(sS, sE, tS, tE, -1.0f, h, l);
+        y = df_norm(h, l);
+        yh[(N - i) * yst] = y.h;
+        yl[(N - i) * yst] = y.l;
+    }
+}
+
+// Same, accumulating into y (y += M x).
+template <int LX>
+__device__ __forceinline__ void df_line_acc(const float* xh, const float* xl, int xst, float* yh, float* yl, int yst,
+                                            const float* Ah, const float* Al, const float* Bh, const float* Bl) {
+    constexpr int P = LX / 2, N = LX - 1;
+    float eh[P], el[P], oh[P], ol[P];
+#pragma unroll
+    for (int m = 0; m < P; m++) {
+        const float ah = xh[m * xst], al = xl[m * xst], bh = xh[(N - m) * xst], bl = xl[(N - m) * xst];
+        pair_addsub(ah, al, bh, bl, 1.0f, eh[m], el[m]);
+        pair_addsub(ah, al, bh, bl, -1.0f, oh[m], ol[m]);
+    }
+#pragma unroll
+    for (int i = 0; i < P; i++) {
+        float sS = 0.f, sE = 0.f, tS = 0.f, tE = 0.f;
+#pragma unroll
+        for (int m = 0; m < P; m++) {
+            df_mac(sS, sE, Ah[i * P + m], Al[i * P + m], oh[m], ol[m]);
+            df_mac(tS, tE, Bh[i * P + m], Bl[i * P + m], eh[m], el[m]);
+        }
+        float h, l, h2, l2;
+        pair_addsub(sS, sE, tS, tE, 1.0f, h, l);
+        pair_addsub(yh[i * yst], yl[i * yst], h, l, 1.0f, h2, l2);
+        dfl y = df_norm(h2, l2);
+        yh[i * yst] = y.h;
+        yl[i * yst] = y.l;
+        pair_addsub(sS, sE, tS, tE, -1.0f, h, l);
+        pair_addsub(yh[(N - i) * yst], yl[(N - i) * yst], h, l, 1.0f, h2, l2);
+        y = df_norm(h2, l2);
+        yh[(N - i) * yst] = y.h;
+        yl[(N - i) * yst] = y.l;
+    }
+}
+
+// coefficient tables (host-built, float pairs): cf[((dir * 2 + ab) * 2 + hl) * P*P + i*P + m],
+// dir 0 = D (forward), 1 = D^T (backward); ab 0 = A (odd part), 1 = B (even part)
+struct DflParams {
+    const double* u;
+    const double* z;
+    double* p;
+    double* w;
+    const float* G2;
+    const float* coef;
+    int64_t E;
+    CGState* st;
+    double* partials;
+    unsigned int* counter;
+    int dry;
+};
+
+template <int LX, bool FUSED>
+__global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a) {
+    using C = DflCfg<LX>;
+    constexpr int P = C::P, N2 = C::N2, N3 = C::N3, EPC = C::EPC, SLOT = C::SLOT, PP = P * P;
+    constexpr int N2P = C::N2P, LXP = C::LXP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* cf = reinterpret_cast<float*>(smem_raw);
+    float* arr = cf + C::COEF;  // 8 arrays x EPC slots: uh ul | rh rl | sh sl | th tl
+    double beta = 0.0;
+    bool first = false;
+    if (FUSED) {
+        if (a.st->done) return;
+        beta = cg_beta(a.st);
+        first = (a.st->iter == 0);
+    }
+    for (int t = threadIdx.x; t < C::COEF; t += blockDim.x) cf[t] = a.coef[t];
+    const int tid = threadIdx.x;
+    const int el = tid / N2;
+    const int t2 = tid - el * N2;          // column (i, j) in phase 0, line id in the transforms
+    const int lo_ = t2 % LX, hi_ = t2 / LX;  // i / j of the column; also the line coordinates
+    const bool active = el < EPC;
+    const int slot = (active ? el : 0) * SLOT;
+    float* uh = arr + 0 * EPC * SLOT + slot;
+    float* ul = arr + 1 * EPC * SLOT + slot;
+    float* rh = arr + 2 * EPC * SLOT + slot;
+    float* rl = arr + 3 * EPC * SLOT + slot;
+    float* sh = arr + 4 * EPC * SLOT + slot;
+    float* sl = arr + 5 * EPC * SLOT + slot;
+    float* th = arr + 6 * EPC * SLOT + slot;
+    float* tl = arr + 7 * EPC * SLOT + slot;
+    const float* fAh = cf + 0 * PP;
+    const float* fAl = cf + 1 * PP;
+    const float* fBh = cf + 2 * PP;
+    const float* fBl = cf + 3 * PP;
+    const float* bAh = cf + 4 * PP;
+    const float* bAl = cf + 5 * PP;
+    const float* bBh = cf + 6 * PP;
+    const float* bBl = cf + 7 * PP;
+    const int64_t ngroups = (a.E + EPC - 1) / EPC;
+    double pap = 0.0;
+    __syncthreads();
+    for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
+        const int64_t e = g * EPC + el;
+        const bool valid = active && e < a.E;
+        const int64_t base = e * N3 + t2;  // column (i = lo_, j = hi_)
+        // phase 0: column of u (or z + beta p), split into pairs
+        double ud[LX];
+#pragma unroll
+        for (int k = 0; k < LX; k++) ud[k] = valid ? ld_stream((FUSED ? a.z : a.u) + base + k * N2) : 0.0;
+        if (FUSED) {
+            double pold[LX];
+#pragma unroll
+            for (int k = 0; k < LX; k++) pold[k] = (valid && !first) ? a.p[base + k * N2] : 0.0;
+#pragma unroll
+            for (int k = 0; k < LX; k++) {
+                ud[k] = fma(beta, pold[k], ud[k]);
+                if (valid) a.p[base + k * N2] = ud[k];
+            }
+        }
+        if (active) {
+#pragma unroll
+            for (int k = 0; k < LX; k++) {
+                const dfl v = split_double(ud[k]);
+                uh[C::at(k, hi_, lo_)] = v.h;
+                ul[C::at(k, hi_, lo_)] = v.l;
+            }
+        }
+        __syncthreads();
+        // phase 1: derivative lines ur (along i), us (along j), ut (along k)
+        if (active) {
+            df_line<LX>(uh + C::at(hi_, lo_, 0), ul + C::at(hi_, lo_, 0), 1, rh + C::at(hi_, lo_, 0),
+                        rl + C::at(hi_, lo_, 0), 1, fAh, fAl, fBh, fBl);  // r-line (k=hi_, j=lo_)
+            df_line<LX>(uh + C::at(hi_, 0, lo_), ul + C::at(hi_, 0, lo_), LXP, sh + C::at(hi_, 0, lo_),
+                        sl + C::at(hi_, 0, lo_), LXP, fAh, fAl, fBh, fBl);  // s-line (k=hi_, i=lo_)
+            df_line<LX>(uh + C::at(0, hi_, lo_), ul + C::at(0, hi_, lo_), N2P, th + C::at(0, hi_, lo_),
+                        tl + C::at(0, hi_, lo_), N2P, fAh, fAl, fBh, fBl);  // t-line (j=hi_, i=lo_)
+        }
+        __syncthreads();
+        // phase 2: (wr, ws, wt) = G (ur, us, ut) at the column's points
+        const float* Ge = a.G2 + e * 12 * N3 + t2;
+        if (active) {
+#pragma unroll
+            for (int k = 0; k < LX; k++) {
+                const int q = C::at(k, hi_, lo_);
+                float gh[6], gl[6];
+#pragma unroll
+                for (int c = 0; c < 6; c++) {
+                    gh[c] = valid ? ld_stream(Ge + c * N3 + k * N2) : 0.f;
+                    gl[c] = valid ? ld_stream(Ge + (6 + c) * N3 + k * N2) : 0.f;
+                }
+                const float urh = rh[q], url = rl[q], ush = sh[q], usl = sl[q], uth = th[q], utl = tl[q];
+                float aS = 0.f, aE = 0.f, bS = 0.f, bE = 0.f, cS = 0.f, cE = 0.f;
+                df_mac(aS, aE, gh[0], gl[0], urh, url);
+                df_mac(aS, aE, gh[1], gl[1], ush, usl);
+                df_mac(aS, aE, gh[2], gl[2], uth, utl);
+                df_mac(bS, bE, gh[1], gl[1], urh, url);
+                df_mac(bS, bE, gh[3], gl[3], ush, usl);
+                df_mac(bS, bE, gh[4], gl[4], uth, utl);
+                df_mac(cS, cE, gh[2], gl[2], urh, url);
+                df_mac(cS, cE, gh[4], gl[4], ush, usl);
+                df_mac(cS, cE, gh[5], gl[5], uth, utl);
+                dfl v = df_norm(aS, aE);
+                rh[q] = v.h;
+                rl[q] = v.l;
+                v = df_norm(bS, bE);
+                sh[q] = v.h;
+                sl[q] = v.l;
+                v = df_norm(cS, cE);
+                th[q] = v.h;
+                tl[q] = v.l;
+            }
+        }
+        __syncthreads();
+        // phase 3: w = D^T-lines of wr (into the u arrays), then += those of ws
+        if (active)
+            df_line<LX>(rh + C::at(hi_, lo_, 0), rl + C::at(hi_, lo_, 0), 1, uh + C::at(hi_, lo_, 0),
+                        ul + C::at(hi_, lo_, 0), 1, bAh, bAl, bBh, bBl);
+        __syncthreads();
+        if (active)
+            df_line_acc<LX>(sh + C::at(hi_, 0, lo_), sl + C::at(hi_, 0, lo_), LXP, uh + C::at(hi_, 0, lo_),
+                            ul + C::at(hi_, 0, lo_), LXP, bAh, bAl, bBh, bBl);
+        __syncthreads();
+        // phase 4: += D^T-lines of wt along k; the t-line is this thread's column
+        if (active)
+            df_line_acc<LX>(th + C::at(0, hi_, lo_), tl + C::at(0, hi_, lo_), N2P, uh + C::at(0, hi_, lo_),
+                            ul + C::at(0, hi_, lo_), N2P, bAh, bAl, bBh, bBl);
+        double pw = 0.0;
+        if (valid) {
+#pragma unroll
+            for (int k = 0; k < LX; k++) {
+                const int q = C::at(k, hi_, lo_);
+                const double wv = (double)uh[q] + (double)ul[q];
+                st_stream(a.w + base + k * N2, wv);
+                if (FUSED) pw = fma(ud[k], wv, pw);
+            }
+        }
+        if (FUSED) pap += pw;
+        __syncthreads();
+    }
+    if (FUSED) {
+        double v[1] = {pap};
+        CGState* st = a.st;
+        grid_sum_finalize<1>(v, a.partials, a.counter, [&](double (&acc)[1]) { cg_set_alpha(st, acc[0]); });
+    }
+}
+
+template <int LX, bool FUSED>
+inline int launch_ax_dfl_t(sem_handle* h, const DflParams& a, cudaStream_t s) {
+    using C = DflCfg<LX>;
+    constexpr size_t smem = C::FLOATS * sizeof(float);
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        cudaFuncSetAttribute(ax_dfl_kernel<LX, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ax_dfl_kernel<LX, FUSED>, C::THREADS, smem);
+        per_sm = nb > 0 ? nb : 1;
+    }
+    if (a.dry) return SEM_OK;
+    const int64_t ngroups = (a.E + C::EPC - 1) / C::EPC;
+    int64_t grid = std::min<int64_t>(ngroups, (int64_t)h->sm_count * per_sm);
+    grid = std::max<int64_t>(1, std::min<int64_t>(grid, kMaxPartials));
+    ax_dfl_kernel<LX, FUSED><<<(int)grid, C::THREADS, smem, s>>>(a);
+    SEM_LAUNCH_CHECK("ax_dfl_kernel");
+    h->launches++;
+    return SEM_OK;
+}
+
+template <bool FUSED>
+inline int dispatch_ax_dfl(sem_handle* h, int lx, const DflParams& a, cudaStream_t s) {
+    switch (lx) {
+        case 4: return launch_ax_dfl_t<4, FUSED>(h, a, s);
+        case 6: return launch_ax_dfl_t<6, FUSED>(h, a, s);
+        case 8: return launch_ax_dfl_t<8, FUSED>(h, a, s);
+        case 10: return launch_ax_dfl_t<10, FUSED>(h, a, s);
+        case 12: return launch_ax_dfl_t<12, FUSED>(h, a, s);
+        default: return fail(SEM_EINVAL, "line-transform FP32-pair operator needs lx in {4, 6, 8, 10, 12}");
+    }
+}
+
+int dispatch_ax_dfl_entry(sem_handle* h, int lx, const DflParams& a, bool fused, cudaStream_t s);
+
 }  // namespace sem

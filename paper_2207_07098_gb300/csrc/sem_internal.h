@@ -17,6 +17,7 @@ constexpr int kReduceThreads = 256;
 constexpr int kMaxPartials = 4096;  // upper bound on CTAs of a reducing launch
 constexpr int kBulkVariantsMax = 4;  // operator variants 1..4 are bulk-staged
 constexpr int kDfVariant = 5;        // FP64 data, FP32-pair arithmetic (FP64 precisions only)
+constexpr int kDflVariant = 6;       // same, line-transform form with even/odd splitting (even lx)
 
 // ---------------------------------------------------------------------------
 // errors
@@ -166,6 +167,7 @@ struct sem_handle {
     double* D64[sem::kMaxLx + 1] = {};
     float* D32[sem::kMaxLx + 1] = {};
     float* D2[sem::kMaxLx + 1] = {};   // [2][lx][lx]: hi and lo floats of D
+    float* DL[sem::kMaxLx + 1] = {};   // even/odd line coefficients of D and D^T (float pairs)
     // set-up data
     double* G64 = nullptr;     // [E][6][lx^3], h1 folded in
     float* G32 = nullptr;

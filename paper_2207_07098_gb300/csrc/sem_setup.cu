@@ -300,6 +300,7 @@ static void free_handle(sem_handle* h) {
         cudaFree(h->D64[l]);
         cudaFree(h->D32[l]);
         cudaFree(h->D2[l]);
+        cudaFree(h->DL[l]);
     }
     cudaFree(h->G64);
     cudaFree(h->G32);
@@ -380,7 +381,7 @@ static int setup_common(sem_handle** out, int nsolve, const sem_mesh_desc* meshe
     if (n_local >= ((int64_t)1 << 31) - 64)
         return fail(SEM_EINVAL, "n_local must be below 2^31 (32-bit local indices)");
     const int forced = (flags & 0xF) - 1;  // pinned operator variant, -1 = autotune
-    if (forced > kDfVariant) return fail(SEM_EINVAL, "operator variant out of range");
+    if (forced > kDflVariant) return fail(SEM_EINVAL, "operator variant out of range");
     sem_handle* h = new sem_handle();
     for (auto& row : h->ax_variant)
         for (int& v : row) v = forced;
@@ -522,6 +523,25 @@ static int setup_common(sem_handle** out, int nsolve, const sem_mesh_desc* meshe
         UP(h->D64[lx], Dh, sizeof(double) * lx * lx);
         UP(h->D32[lx], Df, sizeof(float) * lx * lx);
         UP(h->D2[lx], D2, sizeof(float) * 2 * lx * lx);
+        if (lx % 2 == 0) {
+            // even/odd line coefficients: [dir][A/B][hi/lo][P][P], dir 0 = D, 1 = D^T,
+            // A_im = (M_im - M_{i,N-m}) / 2, B_im = (M_im + M_{i,N-m}) / 2
+            const int P = lx / 2, N = lx - 1;
+            std::vector<float> cf(8 * P * P);
+            for (int dir = 0; dir < 2; dir++)
+                for (int i = 0; i < P; i++)
+                    for (int m = 0; m < P; m++) {
+                        auto M = [&](int r, int c) { return dir == 0 ? Dh[r * lx + c] : Dh[c * lx + r]; };
+                        const double A = 0.5 * (M(i, m) - M(i, N - m)), B = 0.5 * (M(i, m) + M(i, N - m));
+                        const float Ah = (float)A, Bh = (float)B;
+                        cf[((dir * 2 + 0) * 2 + 0) * P * P + i * P + m] = Ah;
+                        cf[((dir * 2 + 0) * 2 + 1) * P * P + i * P + m] = (float)(A - (double)Ah);
+                        cf[((dir * 2 + 1) * 2 + 0) * P * P + i * P + m] = Bh;
+                        cf[((dir * 2 + 1) * 2 + 1) * P * P + i * P + m] = (float)(B - (double)Bh);
+                    }
+            if ((rc = dalloc(h, &h->DL[lx], cf.size()))) return bail(rc);
+            UP(h->DL[lx], cf.data(), sizeof(float) * cf.size());
+        }
     }
     // geometry, mass, Jacobi diagonal: one part at a time through a staging buffer
     int64_t maxn = 0;

@@ -153,12 +153,15 @@ DF_CASES = [("affine", (1, 1, 1), 1), ("jitter", (3, 3, 2), 3), ("deformed", (5,
             ("deformed", (5, 4, 3), 7), ("annulus", (8, 3, 2), 7), ("jitter", (2, 2, 3), 9), ("deformed", (2, 2, 1), 11)]
 
 
+@pytest.mark.parametrize("variant", [5, 6])
 @pytest.mark.parametrize("kind,dims,N", DF_CASES)
-def test_ax_fp32_pair_variant(kind, dims, N):
-    """FP64 data with FP32-pair arithmetic (variant 5): FP64 parity bar."""
+def test_ax_fp32_pair_variant(variant, kind, dims, N):
+    """FP64 data with FP32-pair arithmetic (variant 5; variant 6 = line
+    transforms with even/odd splitting, even lx): FP64 parity bar.  Orders the
+    variant does not cover fall back to the native FP64 kernel."""
     m, h1 = _case(kind, dims, N)
     P = oracle.Problem(m, h1)
-    H = Handle(m, h1, flags=S.SEM_FLAG_VARIANT(5))
+    H = Handle(m, h1, flags=S.SEM_FLAG_VARIANT(variant))
     u = W.random_local_field(m, 23)
     e2, einf = rel_err(H.ax(u, S.SEM_FP64, assemble=0), P.ax_local(u))
     assert e2 <= TOL_AX64 and einf <= TOL_AX64, (e2, einf)

@@ -66,7 +66,7 @@ def test_mixed_ir(case, inner_tol):
     assert rel_err(x, x64)[0] <= 1e-7
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
 def test_solves_with_each_operator_variant(variant):
     m, h1, P, b = _deformed_case(5, 7)
     H = Handle(m, h1, flags=S.SEM_FLAG_VARIANT(variant))
