@@ -251,6 +251,8 @@ inline int dispatch_ax(sem_handle* h, int lx, const AxParams<T>& a, cudaStream_t
 constexpr int kBulkVariants = kBulkVariantsMax;
 constexpr int kBulkCfg[kBulkVariants][2] = {{1, 3}, {2, 2}, {2, 3}, {4, 2}};
 int dispatch_ax_bulk_f64(sem_handle* h, int lx, const AxParams<double>& a, bool fused, cudaStream_t s);
+int bulk_set_d_f64(const double* D, int lx);
+int bulk_set_d_f32(const float* D, int lx);
 int dispatch_ax_bulk_f32(sem_handle* h, int lx, const AxParams<float>& a, bool fused, cudaStream_t s);
 inline bool bulk_supported(int lx) { return lx == 4 || lx == 6 || lx == 8 || lx == 10 || lx == 12; }
 // Shared memory of the fused (larger) bulk kernel of variant v fits in a CTA.

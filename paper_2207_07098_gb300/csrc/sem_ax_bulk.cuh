@@ -59,6 +59,53 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 
 constexpr long long kWaitBudget = 4000000000LL;  // about two seconds at 2 GHz
 
+// D of every order in constant memory (one copy per translation unit, filled
+// at set-up): entries indexed with compile-time (k, l) become constant-bank
+// operands of the FMAs instead of shared-memory loads.
+static __constant__ float c_bulkD32[kMaxLx + 1][kMaxLx * kMaxLx];
+static __constant__ double c_bulkD64[kMaxLx + 1][kMaxLx * kMaxLx];
+
+template <typename T>
+__device__ __forceinline__ T bulk_d(int lx, int idx) {
+    if constexpr (sizeof(T) == 4)
+        return c_bulkD32[lx][idx];
+    else
+        return c_bulkD64[lx][idx];
+}
+
+// LX consecutive values of shared memory into registers with the widest
+// aligned vector loads (rows start on multiples of LX*sizeof(T) bytes).
+template <typename T, int LX>
+__device__ __forceinline__ void load_row(const T* p, T (&r)[LX]) {
+    if constexpr (sizeof(T) == 4 && LX % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < LX / 4; q++) {
+            const float4 v = reinterpret_cast<const float4*>(p)[q];
+            r[4 * q] = v.x;
+            r[4 * q + 1] = v.y;
+            r[4 * q + 2] = v.z;
+            r[4 * q + 3] = v.w;
+        }
+    } else if constexpr (sizeof(T) == 4 && LX % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < LX / 2; q++) {
+            const float2 v = reinterpret_cast<const float2*>(p)[q];
+            r[2 * q] = v.x;
+            r[2 * q + 1] = v.y;
+        }
+    } else if constexpr (sizeof(T) == 8 && LX % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < LX / 2; q++) {
+            const double2 v = reinterpret_cast<const double2*>(p)[q];
+            r[2 * q] = v.x;
+            r[2 * q + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < LX; q++) r[q] = p[q];
+    }
+}
+
 template <typename T, int LX, int EPC, int NST, bool FUSED>
 struct BulkCfg {
     static constexpr int N2 = LX * LX, N3 = LX * LX * LX, DP = LX + 1;
@@ -125,6 +172,15 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
     }
     for (int t = tid; t < LX * LX; t += blockDim.x) sD[(t / LX) * DP + (t % LX)] = a.D[t];
     __syncthreads();
+    // this thread's rows (r, s derivatives) and columns (transposed ones) of D
+    T Dri[LX], Drj[LX], Dci[LX], Dcj[LX];
+#pragma unroll
+    for (int l = 0; l < LX; l++) {
+        Dri[l] = sD[i * DP + l];
+        Drj[l] = sD[j * DP + l];
+        Dci[l] = sD[l * DP + i];
+        Dcj[l] = sD[l * DP + j];
+    }
     if (tid == 0)
         for (int s = 0; s < NST; s++) {
             const int64_t g = blockIdx.x + (int64_t)s * gridDim.x;
@@ -163,11 +219,13 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
 #pragma unroll
         for (int k = 0; k < LX; k++) {
             T ur = T(0), us = T(0), ut = T(0);
+            T row[LX];
+            load_row<T, LX>(su + so + k * N2 + j * LX, row);
 #pragma unroll
             for (int l = 0; l < LX; l++) {
-                ur = fma(sD[i * DP + l], su[so + k * N2 + j * LX + l], ur);
-                us = fma(sD[j * DP + l], su[so + k * N2 + l * LX + i], us);
-                ut = fma(sD[k * DP + l], ucol[l], ut);
+                ur = fma(Dri[l], row[l], ur);
+                us = fma(Drj[l], su[so + k * N2 + l * LX + i], us);
+                ut = fma(bulk_d<T>(LX, k * LX + l), ucol[l], ut);
             }
             const T g11 = Gs[0 * N3 + k * N2], g12 = Gs[1 * N3 + k * N2], g13 = Gs[2 * N3 + k * N2];
             const T g22 = Gs[3 * N3 + k * N2], g23 = Gs[4 * N3 + k * N2], g33 = Gs[5 * N3 + k * N2];
@@ -190,11 +248,13 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
 #pragma unroll
         for (int k = 0; k < LX; k++) {
             T acc = T(0);
+            T row[LX];
+            load_row<T, LX>(sr + so + k * N2 + j * LX, row);
 #pragma unroll
             for (int l = 0; l < LX; l++) {
-                acc = fma(sD[l * DP + i], sr[so + k * N2 + j * LX + l], acc);
-                acc = fma(sD[l * DP + j], ss[so + k * N2 + l * LX + i], acc);
-                acc = fma(sD[l * DP + k], wt[l], acc);
+                acc = fma(Dci[l], row[l], acc);
+                acc = fma(Dcj[l], ss[so + k * N2 + l * LX + i], acc);
+                acc = fma(bulk_d<T>(LX, l * LX + k), wt[l], acc);
             }
             if (valid) {
                 st_stream(a.w + base + k * N2, acc);
@@ -221,6 +281,17 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
         CGState* stt = a.st;
         grid_sum_finalize<1>(v, a.partials, a.counter, [&](double (&acc)[1]) { cg_set_alpha(stt, acc[0]); });
     }
+}
+
+// Fill this translation unit's constant copy of D for order lx.
+template <typename T>
+inline int bulk_set_d(const T* D, int lx) {
+    cudaError_t e;
+    if constexpr (sizeof(T) == 4)
+        e = cudaMemcpyToSymbol(c_bulkD32, D, sizeof(T) * lx * lx, sizeof(T) * (size_t)lx * kMaxLx * kMaxLx);
+    else
+        e = cudaMemcpyToSymbol(c_bulkD64, D, sizeof(T) * lx * lx, sizeof(T) * (size_t)lx * kMaxLx * kMaxLx);
+    return e == cudaSuccess ? SEM_OK : cuda_fail(e, "cudaMemcpyToSymbol(D)");
 }
 
 template <typename T, int LX, int EPC, int NST, bool FUSED>

@@ -11,4 +11,8 @@ int dispatch_ax_dfl_entry(sem_handle* h, int lx, const DflParams& a, bool fused,
     return fused ? dispatch_ax_dfl<true>(h, lx, a, s) : dispatch_ax_dfl<false>(h, lx, a, s);
 }
 
+int dispatch_ax_dfl_pair_entry(sem_handle* h, int lx, const DflParams& a, cudaStream_t s) {
+    return dispatch_ax_dfl_pair(h, lx, a, s);
+}
+
 }  // namespace sem

@@ -285,8 +285,11 @@ template <int LX>
 struct DflCfg {
     static constexpr int P = LX / 2;
     static constexpr int N2 = LX * LX, N3 = LX * LX * LX;
-    static constexpr int LXP = LX + 1;           // padded row
-    static constexpr int N2P = LX * LXP + 1;     // padded plane
+    // padded row and plane strides, chosen (by an offline search over the
+    // column, r-, s- and t-line access patterns of a warp) so that no access
+    // has more than a 2-way shared-memory bank conflict
+    static constexpr int LXP = LX == 4 ? 5 : LX == 6 ? 7 : LX == 8 ? 9 : LX == 10 ? 11 : LX == 12 ? 17 : LX + 1;
+    static constexpr int N2P = LX == 4 ? 20 : LX == 6 ? 42 : LX == 8 ? 72 : LX == 10 ? 111 : LX == 12 ? 204 : LX * LXP + 1;
     static constexpr int SLOT = LX * N2P;        // floats per element per array
     static constexpr int EPC = (256 / N2) > 0 ? (256 / N2) : 1;
     static constexpr int USED = EPC * N2;
@@ -371,6 +374,13 @@ struct DflParams {
     const double* z;
     double* p;
     double* w;
+    // pair form of the CG vectors (fused kernel with PAIR): hi and lo planes
+    const float* zh;
+    const float* zl;
+    float* ph;
+    float* pl;
+    float* wh;
+    float* wl;
     const float* G2;
     const float* coef;
     int64_t E;
@@ -380,8 +390,9 @@ struct DflParams {
     int dry;
 };
 
-template <int LX, bool FUSED>
+template <int LX, bool FUSED, bool PAIR = false>
 __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a) {
+    static_assert(!PAIR || FUSED, "the pair form exists for the fused CG kernel only");
     using C = DflCfg<LX>;
     constexpr int P = C::P, N2 = C::N2, N3 = C::N3, EPC = C::EPC, SLOT = C::SLOT, PP = P * P;
     constexpr int N2P = C::N2P, LXP = C::LXP;
@@ -427,6 +438,35 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
         const int64_t base = e * N3 + t2;  // column (i = lo_, j = hi_)
         // phase 0: column of u (or z + beta p), split into pairs
         double ud[LX];
+        float cuh[LX], cul[LX];  // the column of u as pairs (PAIR form)
+        if (PAIR) {
+            dfl b2;
+            b2.h = (float)beta;
+            b2.l = (float)(beta - (double)b2.h);
+#pragma unroll
+            for (int k = 0; k < LX; k++) {
+                float S = valid ? ld_stream(a.zh + base + k * N2) : 0.f;
+                float Ee = valid ? ld_stream(a.zl + base + k * N2) : 0.f;
+                if (valid && !first) df_mac(S, Ee, b2.h, b2.l, a.ph[base + k * N2], a.pl[base + k * N2]);
+                const dfl v = df_norm(S, Ee);
+                cuh[k] = v.h;
+                cul[k] = v.l;
+            }
+            if (valid) {
+#pragma unroll
+                for (int k = 0; k < LX; k++) {
+                    a.ph[base + k * N2] = cuh[k];
+                    a.pl[base + k * N2] = cul[k];
+                }
+            }
+            if (active) {
+#pragma unroll
+                for (int k = 0; k < LX; k++) {
+                    uh[C::at(k, hi_, lo_)] = cuh[k];
+                    ul[C::at(k, hi_, lo_)] = cul[k];
+                }
+            }
+        } else {
 #pragma unroll
         for (int k = 0; k < LX; k++) ud[k] = valid ? ld_stream((FUSED ? a.z : a.u) + base + k * N2) : 0.0;
         if (FUSED) {
@@ -446,6 +486,7 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
                 uh[C::at(k, hi_, lo_)] = v.h;
                 ul[C::at(k, hi_, lo_)] = v.l;
             }
+        }
         }
         __syncthreads();
         // phase 1: derivative lines ur (along i), us (along j), ut (along k)
@@ -507,7 +548,20 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
             df_line_acc<LX>(th + C::at(0, hi_, lo_), tl + C::at(0, hi_, lo_), N2P, uh + C::at(0, hi_, lo_),
                             ul + C::at(0, hi_, lo_), N2P, bAh, bAl, bBh, bBl);
         double pw = 0.0;
-        if (valid) {
+        if (PAIR) {
+            float S = 0.f, Ee = 0.f;
+            if (valid) {
+#pragma unroll
+                for (int k = 0; k < LX; k++) {
+                    const int q = C::at(k, hi_, lo_);
+                    const float wvh = uh[q], wvl = ul[q];
+                    st_stream(a.wh + base + k * N2, wvh);
+                    st_stream(a.wl + base + k * N2, wvl);
+                    df_mac(S, Ee, cuh[k], cul[k], wvh, wvl);
+                }
+            }
+            pw = (double)S + (double)Ee;
+        } else if (valid) {
 #pragma unroll
             for (int k = 0; k < LX; k++) {
                 const int q = C::at(k, hi_, lo_);
@@ -526,22 +580,22 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
     }
 }
 
-template <int LX, bool FUSED>
+template <int LX, bool FUSED, bool PAIR = false>
 inline int launch_ax_dfl_t(sem_handle* h, const DflParams& a, cudaStream_t s) {
     using C = DflCfg<LX>;
     constexpr size_t smem = C::FLOATS * sizeof(float);
     static int per_sm = -1;
     if (per_sm < 0) {
-        cudaFuncSetAttribute(ax_dfl_kernel<LX, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(ax_dfl_kernel<LX, FUSED, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int nb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ax_dfl_kernel<LX, FUSED>, C::THREADS, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ax_dfl_kernel<LX, FUSED, PAIR>, C::THREADS, smem);
         per_sm = nb > 0 ? nb : 1;
     }
     if (a.dry) return SEM_OK;
     const int64_t ngroups = (a.E + C::EPC - 1) / C::EPC;
     int64_t grid = std::min<int64_t>(ngroups, (int64_t)h->sm_count * per_sm);
     grid = std::max<int64_t>(1, std::min<int64_t>(grid, kMaxPartials));
-    ax_dfl_kernel<LX, FUSED><<<(int)grid, C::THREADS, smem, s>>>(a);
+    ax_dfl_kernel<LX, FUSED, PAIR><<<(int)grid, C::THREADS, smem, s>>>(a);
     SEM_LAUNCH_CHECK("ax_dfl_kernel");
     h->launches++;
     return SEM_OK;
@@ -559,6 +613,18 @@ inline int dispatch_ax_dfl(sem_handle* h, int lx, const DflParams& a, cudaStream
     }
 }
 
+inline int dispatch_ax_dfl_pair(sem_handle* h, int lx, const DflParams& a, cudaStream_t s) {
+    switch (lx) {
+        case 4: return launch_ax_dfl_t<4, true, true>(h, a, s);
+        case 6: return launch_ax_dfl_t<6, true, true>(h, a, s);
+        case 8: return launch_ax_dfl_t<8, true, true>(h, a, s);
+        case 10: return launch_ax_dfl_t<10, true, true>(h, a, s);
+        case 12: return launch_ax_dfl_t<12, true, true>(h, a, s);
+        default: return fail(SEM_EINVAL, "pair-form CG operator needs lx in {4, 6, 8, 10, 12}");
+    }
+}
+
 int dispatch_ax_dfl_entry(sem_handle* h, int lx, const DflParams& a, bool fused, cudaStream_t s);
+int dispatch_ax_dfl_pair_entry(sem_handle* h, int lx, const DflParams& a, cudaStream_t s);
 
 }  // namespace sem

@@ -501,16 +501,37 @@ static int solve_batch(sem_handle* h, double* x_user, const double* b_user, cons
     };
     if ((rc = batch_true_residual(h, s))) return rc;
     if (o.mode == SEM_MODE_FP64) {
-        init_batch_kernel<double><<<grid_tiles(h), 256, 0, s>>>(h->ws.b, h->ws.r, h->ws.z, h->minv64, h->mult, h->state,
-                                                                 tiles(h), nullptr, o.tol, nullptr, o.max_iter);
-        SEM_LAUNCH_CHECK("init_batch_kernel");
-        h->launches++;
-        if ((rc = batch_loop(h, false, h->state, o, s, hs, &ax_sum, &ax_n))) return rc;
-        for (int q = 0; q < ns; q++) {
-            status[q] = hs[q].status;
-            iters[q] = hs[q].iter;
+        // CG with residual replacement per solve (see the single-mesh solver)
+        std::vector<int> act(ns, 1);
+        for (int restart = 0;; restart++) {
+            if (restart > 0) {
+                if ((rc = batch_true_residual(h, s)) || (rc = read_rrbb())) return rc;
+                int nact = 0;
+                for (int q = 0; q < ns; q++) {
+                    const double bb = rrbb[2 * q + 1];
+                    const double rel = bb > 0 ? std::sqrt(rrbb[2 * q] / bb) : 0.0;
+                    act[q] = (status[q] == SEM_OK && rel > o.tol && iters[q] < o.max_iter && restart <= 4) ? 1 : 0;
+                    nact += act[q];
+                }
+                if (nact == 0) break;
+                SEM_CUDA_TRY(cudaMemcpyAsync(bp.act, act.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
+                init_batch_kernel<double><<<grid_tiles(h), 256, 0, s>>>(h->ws.b, h->ws.r, h->ws.z, h->minv64, h->mult,
+                                                                         h->state, tiles(h), bp.act, o.tol, nullptr,
+                                                                         o.max_iter);
+            } else {
+                init_batch_kernel<double><<<grid_tiles(h), 256, 0, s>>>(h->ws.b, h->ws.r, h->ws.z, h->minv64, h->mult,
+                                                                         h->state, tiles(h), nullptr, o.tol, nullptr,
+                                                                         o.max_iter);
+            }
+            SEM_LAUNCH_CHECK("init_batch_kernel");
+            h->launches++;
+            if ((rc = batch_loop(h, false, h->state, o, s, hs, &ax_sum, &ax_n))) return rc;
+            for (int q = 0; q < ns; q++)
+                if (act[q]) {
+                    status[q] = hs[q].status;
+                    iters[q] += hs[q].iter;
+                }
         }
-        if ((rc = batch_true_residual(h, s)) || (rc = read_rrbb())) return rc;
     } else {
         std::vector<double> prev(ns, INFINITY);
         std::vector<int> act(ns, 0), fin(ns, 0);

@@ -71,7 +71,19 @@ __global__ void __launch_bounds__(256) cg_update_kernel(UpdParams<T> a) {
     __shared__ T inv[256];
     for (int m = threadIdx.x; m < 256; m += blockDim.x) inv[m] = m ? (T)(1.0 / m) : T(0);
     __syncthreads();
-    double rz = 0.0, rr = 0.0;
+    // per-thread partial sums in T with Kahan compensation, converted to FP64
+    // once per thread (FP64 accumulation across threads and CTAs)
+    T rzs = T(0), rzc = T(0), rrs = T(0), rrc = T(0);
+    auto kahan = [](T& sum, T& c, T v) {
+        if constexpr (sizeof(T) == 8) {
+            sum += v;  // FP64: plain accumulation (the FP64 pipe is the bottleneck)
+        } else {
+            const T y = v - c;
+            const T t = sum + y;
+            c = (t - sum) - y;
+            sum = t;
+        }
+    };
     const int64_t nv = a.n / W;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv; q += (int64_t)gridDim.x * blockDim.x) {
         V x = reinterpret_cast<const V*>(a.x)[q];
@@ -94,9 +106,10 @@ __global__ void __launch_bounds__(256) cg_update_kernel(UpdParams<T> a) {
         reinterpret_cast<V*>(a.x)[q] = x;
         reinterpret_cast<V*>(a.r)[q] = r;
         reinterpret_cast<V*>(a.z)[q] = z;
-        rz += (double)lrz;
-        rr += (double)lrr;
+        kahan(rzs, rzc, lrz);
+        kahan(rrs, rrc, lrr);
     }
+    double rz = (double)rzs - (double)rzc, rr = (double)rrs - (double)rrc;
     if (blockIdx.x == 0) {  // scalar tail
         for (int64_t L = nv * W + threadIdx.x; L < a.n; L += blockDim.x) {
             T x = a.x[L], r = a.r[L], z;
@@ -214,7 +227,22 @@ int launch_cg_update(sem_handle* h, int precision, cudaStream_t s) {
     return SEM_OK;
 }
 
+static int launch_ka(sem_handle* h, int precision, cudaStream_t s) {
+    return precision == kPairPrec ? launch_pair_ka(h, s) : launch_cg_pupdate_ax(h, precision, s);
+}
+
+static int launch_kb_kc(sem_handle* h, int precision, cudaStream_t s) {
+    if (precision == kPairPrec) return launch_pair_rest(h, s);
+    int rc = launch_gs(h, precision == SEM_FP32 ? (void*)h->ws.w32 : (void*)h->ws.w, precision == SEM_FP32, true, s);
+    if (!rc) rc = launch_cg_update(h, precision, s);
+    return rc;
+}
+
 static int launch_iteration(sem_handle* h, int precision, cudaStream_t s) {
+    if (precision == kPairPrec) {
+        int rc = launch_ka(h, precision, s);
+        return rc ? rc : launch_kb_kc(h, precision, s);
+    }
     int rc = launch_cg_pupdate_ax(h, precision, s);
     if (!rc) rc = launch_gs(h, precision == SEM_FP32 ? (void*)h->ws.w32 : (void*)h->ws.w, precision == SEM_FP32,
                             true, s);
@@ -225,6 +253,7 @@ static int launch_iteration(sem_handle* h, int precision, cudaStream_t s) {
 static int get_graph(sem_handle* h, int precision, int chunk, cudaGraphExec_t* out) {
     GraphCache& g = h->graph;
     const int variant = precision == SEM_FP64_NATIVE ? 0 : ax_variant_for(h, h->parts[0].lx, precision == SEM_FP32);
+    // (the pair-form loop has its own precision code and always the line kernel)
     if (g.exec && g.key_prec == precision && g.key_chunk == chunk && g.key_variant == variant) {
         *out = g.exec;
         return SEM_OK;
@@ -235,6 +264,7 @@ static int get_graph(sem_handle* h, int precision, int chunk, cudaGraphExec_t* o
     }
     if (!h->capture_stream) SEM_CUDA_TRY(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
     int prc = prepare_cg_kernels(h);
+    if (!prc && precision == kPairPrec) prc = prepare_pair_kernels(h);
     if (prc) return prc;
     for (auto& ev : h->ax_ev)
         if (!ev) SEM_CUDA_TRY(cudaEventCreate(&ev));
@@ -244,11 +274,9 @@ static int get_graph(sem_handle* h, int precision, int chunk, cudaGraphExec_t* o
     int rc = SEM_OK;
     for (int it = 0; it < chunk && rc == SEM_OK; it++) {
         if (it == 0 && cudaEventRecordWithFlags(h->ax_ev[0], cs, cudaEventRecordExternal) != cudaSuccess) rc = fail(SEM_ECUDA, "event record");
-        if (!rc) rc = launch_cg_pupdate_ax(h, precision, cs);
+        if (!rc) rc = launch_ka(h, precision, cs);
         if (it == 0 && !rc && cudaEventRecordWithFlags(h->ax_ev[1], cs, cudaEventRecordExternal) != cudaSuccess) rc = fail(SEM_ECUDA, "event record");
-        if (!rc) rc = launch_gs(h, precision == SEM_FP32 ? (void*)h->ws.w32 : (void*)h->ws.w, precision == SEM_FP32,
-                                true, cs);
-        if (!rc) rc = launch_cg_update(h, precision, cs);
+        if (!rc) rc = launch_kb_kc(h, precision, cs);
     }
     h->launches = launches_before;
     cudaGraph_t graph = nullptr;
@@ -371,17 +399,41 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
     CGState hs;
     int status = SEM_OK;
     if (o.mode == SEM_MODE_FP64) {
+        // CG with residual replacement: when the recursive residual says
+        // "converged" but the true residual ||b - A x|| is still above tol
+        // (rounding drift), CG restarts from the true residual, up to four times.
         const int prec = o.precision == SEM_FP64_NATIVE ? SEM_FP64_NATIVE : SEM_FP64;
-        if ((rc = true_residual(h, h->ws.x, h->ws.b, rrbb, s))) return rc;
-        cg_init_kernel<double><<<grid_for(h, n, 256, 4), 256, 0, s>>>(
-            h->ws.b, h->ws.r, h->ws.z, h->minv64, h->mult, n, o.tol, o.max_iter, h->state, h->partials,
-            h->counters + 5);
-        SEM_LAUNCH_CHECK("cg_init_kernel");
-        h->launches++;
-        if ((rc = run_cg_loop(h, prec, o, 0, s, &hs, &tm))) return rc;
-        st.iterations = hs.iter;
-        st.relres_recursive = hs.bb > 0 ? std::sqrt(hs.rr / hs.bb) : 0.0;
-        status = hs.status;
+        // with the line-transform FP32-pair operator, the CG vectors live as float pairs
+        const bool pair = prec == SEM_FP64 && pair_cg_available(h);
+        if (pair && (rc = ensure_pair_workspace(h))) return rc;
+        int used = 0;
+        for (int restart = 0;; restart++) {
+            if (pair && restart > 0 && (rc = launch_pair_join_x(h, s))) return rc;
+            if ((rc = true_residual(h, h->ws.x, h->ws.b, rrbb, s))) return rc;
+            if (restart > 0) {
+                double hb[2];
+                SEM_CUDA_TRY(cudaMemcpyAsync(hb, rrbb, sizeof(hb), cudaMemcpyDeviceToHost, s));
+                SEM_CUDA_TRY(cudaStreamSynchronize(s));
+                const double rel = hb[1] > 0 ? std::sqrt(hb[0] / hb[1]) : 0.0;
+                if (rel <= o.tol || status != SEM_OK || restart > 4 || used >= o.max_iter) break;
+            }
+            if (pair) {
+                if ((rc = launch_pair_split_x(h, s)) || (rc = launch_pair_init(h, o.tol, o.max_iter - used, s)))
+                    return rc;
+            } else {
+                cg_init_kernel<double><<<grid_for(h, n, 256, 4), 256, 0, s>>>(
+                    h->ws.b, h->ws.r, h->ws.z, h->minv64, h->mult, n, o.tol, o.max_iter - used, h->state,
+                    h->partials, h->counters + 5);
+                SEM_LAUNCH_CHECK("cg_init_kernel");
+                h->launches++;
+            }
+            if ((rc = run_cg_loop(h, pair ? kPairPrec : prec, o, 0, s, &hs, &tm))) return rc;
+            if (pair && (rc = launch_pair_join_x(h, s))) return rc;
+            used += hs.iter;
+            st.relres_recursive = hs.bb > 0 ? std::sqrt(hs.rr / hs.bb) : 0.0;
+            status = hs.status;
+        }
+        st.iterations = used;
     } else {
         // FP64 refinement around an FP32 inner CG
         double prev = INFINITY;

@@ -1,0 +1,255 @@
+// FP64-mode CG with the vectors stored as float pairs (x = hi + lo, two float
+// planes, the same 8 bytes per point as a double).  On GB300 the FP64 pipe
+// (1/64 of the FP32 rate) bounds the plain FP64 vector update at ~7 FP64
+// operations per point; in pair form the update, the gather-scatter sums and
+// the operator run on the FP32 pipe with error-free transformations (products
+// by FMA, sums by TwoSum), ~2^-44 relative per operation.  Doubles appear only
+// at the solve boundaries (split of x0 and of the true residual, join of the
+// solution) and in the scalar reductions, which are accumulated in FP64.
+#include <algorithm>
+
+#include "sem_ax_df.cuh"
+#include "sem_internal.h"
+
+namespace sem {
+
+__device__ __forceinline__ void split_accurate(double x, float& h, float& l) {
+    h = (float)x;
+    l = (float)(x - (double)h);
+}
+
+__global__ void split_pairs_kernel(const double* __restrict__ x, float* __restrict__ h, float* __restrict__ l,
+                                   int64_t n) {
+    for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < n; L += (int64_t)gridDim.x * blockDim.x)
+        split_accurate(x[L], h[L], l[L]);
+}
+
+__global__ void join_pairs_kernel(const float* __restrict__ h, const float* __restrict__ l, double* __restrict__ x,
+                                  int64_t n) {
+    for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < n; L += (int64_t)gridDim.x * blockDim.x)
+        x[L] = (double)h[L] + (double)l[L];
+}
+
+// CG start from the true residual r (double): r and z = Minv r stored as
+// pairs; rho = <r,z>, rr = <r,r>, bb = <b,b> in FP64.
+__global__ void __launch_bounds__(256) init_pair_kernel(const double* __restrict__ b, const double* __restrict__ r,
+                                                        const double* __restrict__ minv, const uint8_t* __restrict__ mult,
+                                                        float* rh, float* rl, float* zh, float* zl, int64_t n,
+                                                        double tol, int max_iter, CGState* st, double* partials,
+                                                        unsigned int* counter) {
+    __shared__ double inv[256];
+    for (int m = threadIdx.x; m < 256; m += blockDim.x) inv[m] = m ? 1.0 / m : 0.0;
+    __syncthreads();
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < n; L += (int64_t)gridDim.x * blockDim.x) {
+        const double rv = r[L], zv = minv[L] * rv, bv = b[L], iv = inv[mult[L]];
+        split_accurate(rv, rh[L], rl[L]);
+        split_accurate(zv, zh[L], zl[L]);
+        v[0] = fma(rv * zv, iv, v[0]);
+        v[1] = fma(rv * rv, iv, v[1]);
+        v[2] = fma(bv * bv, iv, v[2]);
+    }
+    grid_sum_finalize<3>(v, partials, counter, [&](double (&acc)[3]) {
+        st->rho = acc[0];
+        st->rho_old = 1.0;
+        st->rr = acc[1];
+        st->bb = acc[2];
+        st->tol2 = tol * tol * acc[2];
+        st->alpha = 0.0;
+        st->pap = 0.0;
+        st->iter = 0;
+        st->max_iter = max_iter;
+        const bool conv = (acc[2] == 0.0 || acc[1] <= st->tol2);
+        st->done = (conv || max_iter <= 0) ? 1 : 0;
+        st->status = (conv || max_iter > 0) ? SEM_OK : SEM_ENOTCONV;
+    });
+}
+
+struct PairVecs {
+    float *xh, *xl, *ph, *pl, *rh, *rl, *wh, *wl, *zh, *zl;
+    const float *mh, *ml;  // Minv pairs
+    const uint8_t* mult;
+    int64_t n;
+    CGState* st;
+    double* partials;
+    unsigned int* counter;
+};
+
+// K-C in pair form: x += alpha p; r -= alpha w; z = Minv r; <r,z>, <r,r>.
+__global__ void __launch_bounds__(256) cg_update_pair_kernel(PairVecs a) {
+    if (a.st->done) return;
+    dfl al;
+    split_accurate(a.st->alpha, al.h, al.l);
+    __shared__ float inv[256];
+    for (int m = threadIdx.x; m < 256; m += blockDim.x) inv[m] = m ? 1.0f / (float)m : 0.0f;
+    __syncthreads();
+    float zS = 0.f, zE = 0.f, rS = 0.f, rE = 0.f;
+    for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < a.n; L += (int64_t)gridDim.x * blockDim.x) {
+        float S = a.xh[L], E = a.xl[L];
+        df_mac(S, E, al.h, al.l, ld_stream(a.ph + L), ld_stream(a.pl + L));
+        const dfl x = df_norm(S, E);
+        S = a.rh[L];
+        E = a.rl[L];
+        df_mac(S, E, -al.h, -al.l, ld_stream(a.wh + L), ld_stream(a.wl + L));
+        const dfl r = df_norm(S, E);
+        const float mh = ld_stream(a.mh + L), ml = ld_stream(a.ml + L);
+        float zs = 0.f, ze = 0.f;
+        df_mac(zs, ze, mh, ml, r.h, r.l);
+        const dfl z = df_norm(zs, ze);
+        a.xh[L] = x.h;
+        a.xl[L] = x.l;
+        a.rh[L] = r.h;
+        a.rl[L] = r.l;
+        a.zh[L] = z.h;
+        a.zl[L] = z.l;
+        const float iv = inv[a.mult[L]];
+        df_mac(zS, zE, r.h * iv, r.l * iv, z.h, z.l);
+        df_mac(rS, rE, r.h * iv, r.l * iv, r.h, r.l);
+    }
+    double v[2] = {(double)zS + (double)zE, (double)rS + (double)rE};
+    CGState* st = a.st;
+    grid_sum_finalize<2>(v, a.partials, a.counter, [&](double (&acc)[2]) { cg_set_rho(st, acc[0], acc[1]); });
+}
+
+// QQ^T + mask on pairs: copies summed in ascending local index with TwoSum.
+__device__ __forceinline__ void pair_accumulate(float& S, float& E, float h, float l) {
+    const float s = S + h;
+    const float bb = s - S;
+    const float err = (S - (s - bb)) + (h - bb);
+    S = s;
+    E += err + l;
+}
+
+__device__ __forceinline__ void seg_pair(float* uh, float* ul, const int* idx, int c) {
+    float S = uh[idx[0]], E = ul[idx[0]];
+    for (int q = 1; q < c; q++) pair_accumulate(S, E, uh[idx[q]], ul[idx[q]]);
+    const dfl v = df_norm(S, E);
+    for (int q = 0; q < c; q++) {
+        uh[idx[q]] = v.h;
+        ul[idx[q]] = v.l;
+    }
+}
+
+__global__ void __launch_bounds__(256) gs_pair_kernel(float* __restrict__ uh, float* __restrict__ ul, GSLists g) {
+    const int64_t n1 = g.npair, n2 = n1 + g.nquad, n3 = n2 + g.noct, n4 = n3 + g.noth, n5 = n4 + g.nzero;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n5; t += (int64_t)gridDim.x * blockDim.x) {
+        if (t < n1) {
+            const int2 q = g.pairs[t];
+            const int ix[2] = {q.x, q.y};
+            seg_pair(uh, ul, ix, 2);
+        } else if (t < n2) {
+            const int4 q = g.quads[t - n1];
+            const int ix[4] = {q.x, q.y, q.z, q.w};
+            seg_pair(uh, ul, ix, 4);
+        } else if (t < n3) {
+            const int4 q0 = g.octs[2 * (t - n2)], q1 = g.octs[2 * (t - n2) + 1];
+            const int ix[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+            seg_pair(uh, ul, ix, 8);
+        } else if (t < n4) {
+            const int a = g.oth_off[t - n3], b = g.oth_off[t - n3 + 1];
+            seg_pair(uh, ul, g.oth_idx + a, b - a);
+        } else {
+            const int L = g.zero_idx[t - n4];
+            uh[L] = 0.0f;
+            ul[L] = 0.0f;
+        }
+    }
+}
+
+__global__ void split_minv_kernel(const double* minv, float* mh, float* ml, int64_t n) {
+    for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < n; L += (int64_t)gridDim.x * blockDim.x)
+        split_accurate(minv[L], mh[L], ml[L]);
+}
+
+// ---------------------------------------------------------------------------
+
+bool pair_cg_available(const sem_handle* h) {
+    return h->nsolve == 1 && ax_variant_for(h, h->parts[0].lx, false) == kDflVariant;
+}
+
+int ensure_pair_workspace(sem_handle* h) {
+    if (h->ws.pv[0]) return SEM_OK;
+    const size_t n = (size_t)h->n_local;
+    for (int q = 0; q < 12; q++) {
+        int rc = dalloc(h, &h->ws.pv[q], n);
+        if (rc) return rc;
+    }
+    split_minv_kernel<<<grid_for(h, h->n_local, 256, 8), 256>>>(h->minv64, h->ws.pv[10], h->ws.pv[11], h->n_local);
+    SEM_LAUNCH_CHECK("split_minv_kernel");
+    SEM_CUDA_TRY(cudaDeviceSynchronize());
+    return SEM_OK;
+}
+
+static PairVecs pair_vecs(sem_handle* h) {
+    float** v = h->ws.pv;
+    return PairVecs{v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], v[8], v[9], v[10], v[11],
+                    h->mult, h->n_local, h->state, h->partials, h->counters + 3};
+}
+
+int launch_pair_split_x(sem_handle* h, cudaStream_t s) {
+    split_pairs_kernel<<<grid_for(h, h->n_local, 256, 8), 256, 0, s>>>(h->ws.x, h->ws.pv[0], h->ws.pv[1], h->n_local);
+    SEM_LAUNCH_CHECK("split_pairs_kernel");
+    h->launches++;
+    return SEM_OK;
+}
+
+int launch_pair_join_x(sem_handle* h, cudaStream_t s) {
+    join_pairs_kernel<<<grid_for(h, h->n_local, 256, 8), 256, 0, s>>>(h->ws.pv[0], h->ws.pv[1], h->ws.x, h->n_local);
+    SEM_LAUNCH_CHECK("join_pairs_kernel");
+    h->launches++;
+    return SEM_OK;
+}
+
+int launch_pair_init(sem_handle* h, double tol, int max_iter, cudaStream_t s) {
+    float** v = h->ws.pv;
+    init_pair_kernel<<<grid_for(h, h->n_local, 256, 4), 256, 0, s>>>(h->ws.b, h->ws.r, h->minv64, h->mult, v[4], v[5],
+                                                                     v[8], v[9], h->n_local, tol, max_iter, h->state,
+                                                                     h->partials, h->counters + 5);
+    SEM_LAUNCH_CHECK("init_pair_kernel");
+    h->launches++;
+    return SEM_OK;
+}
+
+// One CG iteration in pair form: K-A (line-transform operator, pair I/O),
+// then K-B (pair gather-scatter + mask) and K-C (pair update).
+int launch_pair_ka(sem_handle* h, cudaStream_t s) {
+    const MeshPart& p = h->parts[0];
+    float** v = h->ws.pv;
+    DflParams d = {};
+    d.zh = v[8];
+    d.zl = v[9];
+    d.ph = v[2];
+    d.pl = v[3];
+    d.wh = v[6];
+    d.wl = v[7];
+    d.G2 = h->G2;
+    d.coef = h->DL[p.lx];
+    d.E = p.E;
+    d.st = h->state;
+    d.partials = h->partials;
+    d.counter = h->counters + 2;
+    return dispatch_ax_dfl_pair_entry(h, p.lx, d, s);
+}
+
+int launch_pair_rest(sem_handle* h, cudaStream_t s) {
+    float** v = h->ws.pv;
+    const GSLists& g = h->gs;
+    const int64_t total = g.npair + g.nquad + g.noct + g.noth + g.nzero;
+    if (total > 0) {
+        gs_pair_kernel<<<grid_for(h, total, 256, 8), 256, 0, s>>>(v[6], v[7], g);
+        SEM_LAUNCH_CHECK("gs_pair_kernel");
+        h->launches++;
+    }
+    cg_update_pair_kernel<<<grid_for(h, h->n_local, 256, 4), 256, 0, s>>>(pair_vecs(h));
+    SEM_LAUNCH_CHECK("cg_update_pair_kernel");
+    h->launches++;
+    return SEM_OK;
+}
+
+int prepare_pair_kernels(sem_handle* h) {
+    DflParams d = {};
+    d.dry = 1;
+    return dispatch_ax_dfl_pair_entry(h, h->parts[0].lx, d, 0);
+}
+
+}  // namespace sem

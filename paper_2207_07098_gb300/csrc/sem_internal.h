@@ -103,6 +103,8 @@ struct Workspace {
     float* w32 = nullptr;
     float* d32 = nullptr;
     float* b32 = nullptr;
+    // FP64 mode in pair form: x, p, r, w, z (hi, lo planes each), Minv (hi, lo)
+    float* pv[12] = {};
     bool have64 = false, have32 = false;
 };
 
@@ -231,6 +233,16 @@ int launch_residual(sem_handle* h, const double* b, const double* ax, double* r,
                     double* rr_out, cudaStream_t s);  // r = b - ax, rr_out[0] = <r,r>
 int grid_for(sem_handle* h, int64_t work_items, int threads, int per_sm);
 int prepare_cg_kernels(sem_handle* h);
+// FP64 CG with float-pair vectors (sem_cg_pair.cu)
+constexpr int kPairPrec = 100;  // "precision" code of the pair-form CG loop
+bool pair_cg_available(const sem_handle* h);
+int ensure_pair_workspace(sem_handle* h);
+int launch_pair_split_x(sem_handle* h, cudaStream_t s);
+int launch_pair_join_x(sem_handle* h, cudaStream_t s);
+int launch_pair_init(sem_handle* h, double tol, int max_iter, cudaStream_t s);
+int launch_pair_ka(sem_handle* h, cudaStream_t s);
+int launch_pair_rest(sem_handle* h, cudaStream_t s);
+int prepare_pair_kernels(sem_handle* h);
 int autotune_ax(sem_handle* h, bool fp32, cudaStream_t s);
 int ax_variant_for(const sem_handle* h, int lx, bool fp32);
 int* device_error_word(sem_handle* h);

@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "sem_ax.cuh"
 #include "sem_device.cuh"
 #include "sem_internal.h"
 
@@ -321,6 +322,7 @@ static void free_handle(sem_handle* h) {
     Workspace& w = h->ws;
     cudaFree(w.r); cudaFree(w.p); cudaFree(w.z); cudaFree(w.w); cudaFree(w.x); cudaFree(w.b);
     cudaFree(w.r32); cudaFree(w.p32); cudaFree(w.z32); cudaFree(w.w32); cudaFree(w.d32); cudaFree(w.b32);
+    for (float* pv : w.pv) cudaFree(pv);
     BatchPlan& bp = h->batch;
     for (auto& g : bp.lxg) {
         cudaFree(g.loc); cudaFree(g.cnt); cudaFree(g.solve);
@@ -522,6 +524,7 @@ static int setup_common(sem_handle** out, int nsolve, const sem_mesh_desc* meshe
             return bail(rc);
         UP(h->D64[lx], Dh, sizeof(double) * lx * lx);
         UP(h->D32[lx], Df, sizeof(float) * lx * lx);
+        if ((rc = bulk_set_d_f64(Dh, lx)) || (rc = bulk_set_d_f32(Df, lx))) return bail(rc);
         UP(h->D2[lx], D2, sizeof(float) * 2 * lx * lx);
         if (lx % 2 == 0) {
             // even/odd line coefficients: [dir][A/B][hi/lo][P][P], dir 0 = D, 1 = D^T,
