@@ -15,4 +15,8 @@ int dispatch_ax_dfl_pair_entry(sem_handle* h, int lx, const DflParams& a, cudaSt
     return dispatch_ax_dfl_pair(h, lx, a, s);
 }
 
+int dispatch_ax_dfl_batch_entry(sem_handle* h, int lx, const DflParams& a, bool fused, cudaStream_t s) {
+    return fused ? dispatch_ax_dfl_batch<true>(h, lx, a, s) : dispatch_ax_dfl_batch<false>(h, lx, a, s);
+}
+
 }  // namespace sem

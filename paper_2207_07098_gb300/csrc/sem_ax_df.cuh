@@ -388,11 +388,23 @@ struct DflParams {
     double* partials;
     unsigned int* counter;
     int dry;
+    // batched form: element-group list of one order, per-solve states and
+    // partials (see BatchAxParams)
+    const int64_t* loc;
+    const int* cnt;
+    const int* solve;
+    int64_t ngroups;
+    int64_t goff;
+    const int* sgfirst;
+    const int* sgcount;
+    double* gpart;
+    unsigned int* scount;
 };
 
-template <int LX, bool FUSED, bool PAIR = false>
+template <int LX, bool FUSED, bool PAIR = false, bool BATCH = false>
 __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a) {
     static_assert(!PAIR || FUSED, "the pair form exists for the fused CG kernel only");
+    static_assert(!(PAIR && BATCH), "no pair form for batches");
     using C = DflCfg<LX>;
     constexpr int P = C::P, N2 = C::N2, N3 = C::N3, EPC = C::EPC, SLOT = C::SLOT, PP = P * P;
     constexpr int N2P = C::N2P, LXP = C::LXP;
@@ -401,11 +413,13 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
     float* arr = cf + C::COEF;  // 8 arrays x EPC slots: uh ul | rh rl | sh sl | th tl
     double beta = 0.0;
     bool first = false;
-    if (FUSED) {
+    if (FUSED && !BATCH) {
         if (a.st->done) return;
         beta = cg_beta(a.st);
         first = (a.st->iter == 0);
     }
+    __shared__ double red[32];
+    __shared__ int is_last;
     for (int t = threadIdx.x; t < C::COEF; t += blockDim.x) cf[t] = a.coef[t];
     const int tid = threadIdx.x;
     const int el = tid / N2;
@@ -429,13 +443,30 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
     const float* bAl = cf + 5 * PP;
     const float* bBh = cf + 6 * PP;
     const float* bBl = cf + 7 * PP;
-    const int64_t ngroups = (a.E + EPC - 1) / EPC;
+    const int64_t ngroups = BATCH ? a.ngroups : (a.E + EPC - 1) / EPC;
     double pap = 0.0;
     __syncthreads();
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
-        const int64_t e = g * EPC + el;
-        const bool valid = active && e < a.E;
-        const int64_t base = e * N3 + t2;  // column (i = lo_, j = hi_)
+        int64_t eoff;  // local index of this thread's element
+        bool valid;
+        int sol = 0;
+        if (BATCH) {
+            sol = a.solve[g];
+            if (FUSED) {
+                const CGState* stg = a.st + sol;
+                // no write to this solve's state can happen before all its groups are done
+                if (stg->done) continue;
+                beta = cg_beta(stg);
+                first = (stg->iter == 0);
+            }
+            eoff = a.loc[g] + (int64_t)el * N3;
+            valid = active && el < a.cnt[g];
+        } else {
+            const int64_t e = g * EPC + el;
+            eoff = e * N3;
+            valid = active && e < a.E;
+        }
+        const int64_t base = eoff + t2;  // column (i = lo_, j = hi_)
         // phase 0: column of u (or z + beta p), split into pairs
         double ud[LX];
         float cuh[LX], cul[LX];  // the column of u as pairs (PAIR form)
@@ -500,7 +531,7 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
         }
         __syncthreads();
         // phase 2: (wr, ws, wt) = G (ur, us, ut) at the column's points
-        const float* Ge = a.G2 + e * 12 * N3 + t2;
+        const float* Ge = a.G2 + 12 * eoff + t2;
         if (active) {
 #pragma unroll
             for (int k = 0; k < LX; k++) {
@@ -570,10 +601,32 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
                 if (FUSED) pw = fma(ud[k], wv, pw);
             }
         }
-        if (FUSED) pap += pw;
+        if (FUSED && BATCH) {
+            double v[1] = {pw};
+            block_sum<1>(v, red);
+            if (threadIdx.x == 0) {
+                a.gpart[a.goff + g] = v[0];
+                __threadfence();
+                is_last = (atomicAdd(&a.scount[sol], 1u) == (unsigned)a.sgcount[sol] - 1u) ? 1 : 0;
+            }
+            __syncthreads();
+            if (is_last) {
+                __threadfence();
+                const int f = a.sgfirst[sol], c = a.sgcount[sol];
+                double acc[1] = {0.0};
+                for (int q = threadIdx.x; q < c; q += blockDim.x) acc[0] += __ldcg(&a.gpart[f + q]);
+                block_sum<1>(acc, red);
+                if (threadIdx.x == 0) {
+                    cg_set_alpha(a.st + sol, acc[0]);
+                    a.scount[sol] = 0u;
+                }
+            }
+        } else if (FUSED) {
+            pap += pw;
+        }
         __syncthreads();
     }
-    if (FUSED) {
+    if (FUSED && !BATCH) {
         double v[1] = {pap};
         CGState* st = a.st;
         grid_sum_finalize<1>(v, a.partials, a.counter, [&](double (&acc)[1]) { cg_set_alpha(st, acc[0]); });
@@ -612,6 +665,40 @@ inline int dispatch_ax_dfl(sem_handle* h, int lx, const DflParams& a, cudaStream
         default: return fail(SEM_EINVAL, "line-transform FP32-pair operator needs lx in {4, 6, 8, 10, 12}");
     }
 }
+
+template <int LX, bool FUSED>
+inline int launch_ax_dfl_batch_t(sem_handle* h, const DflParams& a, cudaStream_t s) {
+    using C = DflCfg<LX>;
+    constexpr size_t smem = C::FLOATS * sizeof(float);
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        cudaFuncSetAttribute(ax_dfl_kernel<LX, FUSED, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ax_dfl_kernel<LX, FUSED, false, true>, C::THREADS, smem);
+        per_sm = nb > 0 ? nb : 1;
+    }
+    if (a.dry || a.ngroups == 0) return SEM_OK;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(a.ngroups, (int64_t)h->sm_count * per_sm));
+    ax_dfl_kernel<LX, FUSED, false, true><<<(int)grid, C::THREADS, smem, s>>>(a);
+    SEM_LAUNCH_CHECK("ax_dfl_kernel (batched)");
+    h->launches++;
+    return SEM_OK;
+}
+
+template <bool FUSED>
+inline int dispatch_ax_dfl_batch(sem_handle* h, int lx, const DflParams& a, cudaStream_t s) {
+    switch (lx) {
+        case 4: return launch_ax_dfl_batch_t<4, FUSED>(h, a, s);
+        case 6: return launch_ax_dfl_batch_t<6, FUSED>(h, a, s);
+        case 8: return launch_ax_dfl_batch_t<8, FUSED>(h, a, s);
+        case 10: return launch_ax_dfl_batch_t<10, FUSED>(h, a, s);
+        case 12: return launch_ax_dfl_batch_t<12, FUSED>(h, a, s);
+        default: return fail(SEM_EINVAL, "batched line-transform operator needs lx in {4, 6, 8, 10, 12}");
+    }
+}
+
+int dispatch_ax_dfl_batch_entry(sem_handle* h, int lx, const DflParams& a, bool fused, cudaStream_t s);
 
 inline int dispatch_ax_dfl_pair(sem_handle* h, int lx, const DflParams& a, cudaStream_t s) {
     switch (lx) {

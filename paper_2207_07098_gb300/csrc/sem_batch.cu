@@ -10,6 +10,7 @@
 #include <cmath>
 #include <vector>
 
+#include "sem_ax_df.cuh"
 #include "sem_batch.cuh"
 #include "sem_internal.h"
 
@@ -283,6 +284,13 @@ static TileList tiles(sem_handle* h) {
 
 static int grid_tiles(sem_handle* h) { return grid_for(h, h->batch.ntiles * 256, 256, 8); }
 
+// FP64 batches use the FP32-pair line-transform operator for the orders it
+// covers unless a native variant (0..4) was pinned at set-up.
+static bool batch_uses_pair_arith(const sem_handle* h, int lx) {
+    const int v = h->ax_variant[0][lx];
+    return (lx % 2 == 0 && lx >= 4 && lx <= 12) && (v < 0 || v >= kDfVariant);
+}
+
 // K-A over every order present: fused (CG state slot base `st`) or plain.
 static int batch_ax(sem_handle* h, bool fp32, bool fused, const void* u, CGState* st, cudaStream_t s) {
     BatchPlan& bp = h->batch;
@@ -299,6 +307,17 @@ static int batch_ax(sem_handle* h, bool fp32, bool fused, const void* u, CGState
             a.loc = g.loc; a.cnt = g.cnt; a.solve = g.solve; a.ngroups = g.ngroups; a.goff = g.goff;
             a.st = st; a.sgfirst = bp.sgfirst; a.sgcount = bp.sgcount; a.gpart = bp.gpart; a.scount = bp.scount;
             rc = dispatch_ax_batch_f32(h, g.lx, a, fused, s);
+        } else if (batch_uses_pair_arith(h, g.lx)) {
+            DflParams d = {};
+            d.u = (const double*)u;
+            d.z = h->ws.z;
+            d.p = h->ws.p;
+            d.w = h->ws.w;
+            d.G2 = h->G2;
+            d.coef = h->DL[g.lx];
+            d.loc = g.loc; d.cnt = g.cnt; d.solve = g.solve; d.ngroups = g.ngroups; d.goff = g.goff;
+            d.st = st; d.sgfirst = bp.sgfirst; d.sgcount = bp.sgcount; d.gpart = bp.gpart; d.scount = bp.scount;
+            rc = dispatch_ax_dfl_batch_entry(h, g.lx, d, fused, s);
         } else {
             BatchAxParams<double> a = {};
             a.u = (const double*)u;
@@ -324,6 +343,12 @@ static int prepare_batch_kernels(sem_handle* h) {
         b.dry = 1;
         int rc = dispatch_ax_batch_f64(h, g.lx, a, true, 0);
         if (!rc) rc = dispatch_ax_batch_f64(h, g.lx, a, false, 0);
+        if (!rc && batch_uses_pair_arith(h, g.lx)) {
+            DflParams d = {};
+            d.dry = 1;
+            rc = dispatch_ax_dfl_batch_entry(h, g.lx, d, true, 0);
+            if (!rc) rc = dispatch_ax_dfl_batch_entry(h, g.lx, d, false, 0);
+        }
         if (!rc) rc = dispatch_ax_batch_f32(h, g.lx, b, true, 0);
         if (!rc) rc = dispatch_ax_batch_f32(h, g.lx, b, false, 0);
         if (rc) return rc;

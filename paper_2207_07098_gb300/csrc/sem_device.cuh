@@ -14,6 +14,16 @@ template <typename T>
 __device__ __forceinline__ T ld_stream(const T* p) { return __ldcs(p); }
 template <typename T>
 __device__ __forceinline__ void st_stream(T* p, T v) { __stcs(p, v); }
+// Output of an operator launch: inside the CG loop (KEEP) the next launch
+// reads it at once, so it is stored with the default policy and can stay in
+// L2; a plain operator application streams it out (evict-first).
+template <bool KEEP, typename T>
+__device__ __forceinline__ void st_keep(T* p, T v) {
+    if (KEEP)
+        *p = v;
+    else
+        __stcs(p, v);
+}
 
 // Sum of NV values over the block (blockDim.x a multiple of 32, <= 1024).
 // Fixed shuffle/tree order: bit-reproducible for a fixed block size.  The
