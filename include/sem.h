@@ -132,6 +132,12 @@ typedef struct sem_mesh_desc {
 /* Set-up flag: pin operator kernel variant v (0..6) for every precision. */
 #define SEM_FLAG_VARIANT(v) ((int)(((v) + 1) & 0xF))
 
+/* Set-up flag for testing failure detection: the bulk-staged operator kernels
+ * announce 16 bytes more than they copy, so no stage ever completes; their
+ * bounded waits (shortened to ~50 ms) expire, the kernels record the failure
+ * and return, and the solve reports SEM_ETIMEOUT.  No fault, no hang. */
+#define SEM_FLAG_TEST_STALL 0x100
+
 /* Fill *opts with the defaults listed above. */
 SEM_API void sem_solve_opts_default(sem_solve_opts* opts);
 

@@ -20,6 +20,9 @@ SEM_FP64, SEM_FP32, SEM_FP64_NATIVE = 0, 1, 2
 SEM_MODE_FP64, SEM_MODE_MIXED_IR = 0, 1
 
 
+SEM_FLAG_TEST_STALL = 0x100
+
+
 def SEM_FLAG_VARIANT(v: int) -> int:
     """Set-up flag pinning operator kernel variant v (0..4), as in sem.h."""
     return (v + 1) & 0xF

@@ -65,6 +65,8 @@ static int dispatch_variant(sem_handle* h, int lx, AxParams<T> a, bool fused, in
     if (variant == kDfVariant || variant == kDflVariant) variant = 0;
     a.variant = variant;
     a.err = device_error_word(h);
+    a.wait_budget = h->test_stall ? 100000000LL : 4000000000LL;  // ~50 ms / ~2 s at 2 GHz
+    a.tx_extra = h->test_stall ? 16u : 0u;
     const bool bulk_ok = variant > 0 && bulk_fits(lx, variant, sizeof(T) == 4) && aligned16(a.w) &&
                          (fused ? (aligned16(a.z) && aligned16(a.p)) : aligned16(a.u)) && aligned16(a.G);
     if (!bulk_ok) a.variant = 0;

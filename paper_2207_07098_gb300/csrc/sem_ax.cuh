@@ -35,6 +35,8 @@ struct AxParams {
     int* err;     // set to 1 when a bounded wait of a staged kernel expires
     int dry;      // 1: only prepare the kernel (attributes, occupancy); no launch
     int variant;  // 0: shared-slab kernel; 1..kBulkVariants: bulk-staged (EPC, stages)
+    long long wait_budget;  // clock cycles a staged kernel waits for a stage
+    unsigned tx_extra;      // bytes announced beyond the copies (test of the bounded wait)
 };
 
 template <typename T, int LX>
@@ -162,7 +164,7 @@ __device__ __forceinline__ T ax_group(const AxSmem<T, LX>& sm, const AxThread<LX
             acc = fma(sD[l * DP + k], wt[l], acc);
         }
         if (valid) {
-            st_stream(w + base + k * N2, acc);
+            st_keep<FUSED>(w + base + k * N2, acc);
             if (FUSED) pw = fma(ucol[k], acc, pw);
         }
     }

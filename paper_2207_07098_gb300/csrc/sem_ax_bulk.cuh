@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
         T* st = stage0 + s * C::STAGE;
         const uint32_t bin = (uint32_t)(cnt * N3 * sizeof(T));
         const uint32_t bG = 6u * bin;
-        mbar_expect_tx(&bars[s], (uint32_t)C::IN * bin + bG);
+        mbar_expect_tx(&bars[s], (uint32_t)C::IN * bin + bG + a.tx_extra);
         if (FUSED) {
             bulk_load(st, a.z + e0 * N3, bin, &bars[s]);
             bulk_load(st + EPC * N3, a.p + e0 * N3, bin, &bars[s]);
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x, it++) {
         const int s = (int)(it % NST);
         const uint32_t parity = (uint32_t)((it / NST) & 1);
-        if (!mbar_wait_bounded(&bars[s], parity, kWaitBudget)) abort_flag = 1;
+        if (!mbar_wait_bounded(&bars[s], parity, a.wait_budget)) abort_flag = 1;
         __syncthreads();
         if (abort_flag) break;
         const T* st = stage0 + s * C::STAGE;
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
                 acc = fma(bulk_d<T>(LX, l * LX + k), wt[l], acc);
             }
             if (valid) {
-                st_stream(a.w + base + k * N2, acc);
+                st_keep<FUSED>(a.w + base + k * N2, acc);
                 if (FUSED) pw = fma(ucol[k], acc, pw);
             }
         }
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
             for (int s = 0; s < NST; s++) {
                 const int64_t ahead = it + s;
                 const int ss_ = (int)(ahead % NST);
-                mbar_wait_bounded(&bars[ss_], (uint32_t)((ahead / NST) & 1), kWaitBudget / 4);
+                mbar_wait_bounded(&bars[ss_], (uint32_t)((ahead / NST) & 1), a.wait_budget / 4);
             }
         }
         return;

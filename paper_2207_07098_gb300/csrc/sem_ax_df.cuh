@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(DfCfg<LX>::THREADS) ax_df_kernel(DfParams a) {
             }
             const double wv = join(df_norm(S, E));
             if (valid) {
-                st_stream(a.w + base + k * N2, wv);
+                st_keep<FUSED>(a.w + base + k * N2, wv);
                 if (FUSED) pw = fma(ud[k], wv, pw);
             }
         }
@@ -586,8 +586,8 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
                 for (int k = 0; k < LX; k++) {
                     const int q = C::at(k, hi_, lo_);
                     const float wvh = uh[q], wvl = ul[q];
-                    st_stream(a.wh + base + k * N2, wvh);
-                    st_stream(a.wl + base + k * N2, wvl);
+                    st_keep<true>(a.wh + base + k * N2, wvh);
+                    st_keep<true>(a.wl + base + k * N2, wvl);
                     df_mac(S, Ee, cuh[k], cul[k], wvh, wvl);
                 }
             }
@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
             for (int k = 0; k < LX; k++) {
                 const int q = C::at(k, hi_, lo_);
                 const double wv = (double)uh[q] + (double)ul[q];
-                st_stream(a.w + base + k * N2, wv);
+                st_keep<FUSED>(a.w + base + k * N2, wv);
                 if (FUSED) pw = fma(ud[k], wv, pw);
             }
         }

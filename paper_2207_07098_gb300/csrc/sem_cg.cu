@@ -330,6 +330,15 @@ static int run_cg_loop(sem_handle* h, int precision, const sem_solve_opts& o, in
         }
         SEM_CUDA_TRY(cudaMemcpyAsync(out, h->state + slot, sizeof(CGState), cudaMemcpyDeviceToHost, s));
         SEM_CUDA_TRY(cudaStreamSynchronize(s));
+        int err_word = 0;
+        SEM_CUDA_TRY(cudaMemcpy(&err_word, device_error_word(h), sizeof(int), cudaMemcpyDeviceToHost));
+        if (err_word) {
+            // a staged kernel gave up waiting: its CTAs skipped the reductions, so
+            // the counters are reset and the solve ends with SEM_ETIMEOUT
+            cudaMemset(device_error_word(h), 0, sizeof(int));
+            cudaMemset(h->counters, 0, 16 * sizeof(unsigned));
+            return fail(SEM_ETIMEOUT, "a staged operator kernel gave up waiting for its bulk copies");
+        }
         if (exec && tm) {
             float ms = 0.0f;
             if (cudaEventElapsedTime(&ms, h->ax_ev[0], h->ax_ev[1]) == cudaSuccess) {

@@ -7,6 +7,8 @@
 // Segments of 2, 4 and 8 copies (faces, edges, vertices of a hex mesh) carry
 // their indices as int2 / int4 vectors, so one thread issues its index loads
 // and value loads without a dependent offset lookup.
+#include <algorithm>
+
 #include "sem_device.cuh"
 #include "sem_internal.h"
 
@@ -15,45 +17,89 @@ namespace sem {
 // One launch covers, in this order: free segments of 2, 4 and 8 copies
 // (index vectors), free segments of other sizes (CSR), then either the zeroing
 // of every Dirichlet copy (apply_mask) or the sums over Dirichlet segments.
-// Copies are always summed left to right in ascending local index.
+// Copies are always summed left to right in ascending local index.  The loads
+// are latency-bound (scattered 4- or 8-byte accesses), so each thread issues
+// the index and value loads of U segments before it sums and stores any.
+template <typename T, int U>
+__device__ __forceinline__ void gs_pairs(T* __restrict__ u, const int2* __restrict__ idx, int64_t n, int64_t t0,
+                                         int64_t stride) {
+    for (int64_t t = t0; t < n; t += stride * U) {
+        int2 q[U];
+        T a[U], b[U];
+#pragma unroll
+        for (int k = 0; k < U; k++) q[k] = (t + k * stride < n) ? idx[t + k * stride] : make_int2(-1, -1);
+#pragma unroll
+        for (int k = 0; k < U; k++)
+            if (q[k].x >= 0) {
+                a[k] = u[q[k].x];
+                b[k] = u[q[k].y];
+            }
+#pragma unroll
+        for (int k = 0; k < U; k++)
+            if (q[k].x >= 0) {
+                const T sum = a[k] + b[k];
+                u[q[k].x] = sum;
+                u[q[k].y] = sum;
+            }
+    }
+}
+
+template <typename T, int U>
+__device__ __forceinline__ void gs_quads(T* __restrict__ u, const int4* __restrict__ idx, int64_t n, int64_t t0,
+                                         int64_t stride) {
+    for (int64_t t = t0; t < n; t += stride * U) {
+        int4 q[U];
+        T a[U][4];
+#pragma unroll
+        for (int k = 0; k < U; k++) q[k] = (t + k * stride < n) ? idx[t + k * stride] : make_int4(-1, -1, -1, -1);
+#pragma unroll
+        for (int k = 0; k < U; k++)
+            if (q[k].x >= 0) {
+                a[k][0] = u[q[k].x];
+                a[k][1] = u[q[k].y];
+                a[k][2] = u[q[k].z];
+                a[k][3] = u[q[k].w];
+            }
+#pragma unroll
+        for (int k = 0; k < U; k++)
+            if (q[k].x >= 0) {
+                const T sum = ((a[k][0] + a[k][1]) + a[k][2]) + a[k][3];
+                u[q[k].x] = sum;
+                u[q[k].y] = sum;
+                u[q[k].z] = sum;
+                u[q[k].w] = sum;
+            }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) gs_kernel(T* __restrict__ u, GSLists g, int apply_mask) {
-    const int64_t n1 = g.npair, n2 = n1 + g.nquad, n3 = n2 + g.noct, n4 = n3 + g.noth;
-    const int64_t n5 = n4 + (apply_mask ? g.nzero : g.ndir);
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n5;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        if (t < n1) {
-            const int2 q = g.pairs[t];
-            const T s = u[q.x] + u[q.y];
-            u[q.x] = s;
-            u[q.y] = s;
-        } else if (t < n2) {
-            const int4 q = g.quads[t - n1];
-            const T a = u[q.x], b = u[q.y], c = u[q.z], d = u[q.w];
-            const T s = ((a + b) + c) + d;
-            u[q.x] = s;
-            u[q.y] = s;
-            u[q.z] = s;
-            u[q.w] = s;
-        } else if (t < n3) {
-            const int4 q0 = g.octs[2 * (t - n2)], q1 = g.octs[2 * (t - n2) + 1];
-            const T a0 = u[q0.x], a1 = u[q0.y], a2 = u[q0.z], a3 = u[q0.w];
-            const T a4 = u[q1.x], a5 = u[q1.y], a6 = u[q1.z], a7 = u[q1.w];
-            const T s = ((((((a0 + a1) + a2) + a3) + a4) + a5) + a6) + a7;
-            u[q0.x] = s; u[q0.y] = s; u[q0.z] = s; u[q0.w] = s;
-            u[q1.x] = s; u[q1.y] = s; u[q1.z] = s; u[q1.w] = s;
-        } else if (t < n4) {
-            const int a = g.oth_off[t - n3], b = g.oth_off[t - n3 + 1];
-            T s = u[g.oth_idx[a]];
-            for (int c = a + 1; c < b; c++) s += u[g.oth_idx[c]];
-            for (int c = a; c < b; c++) u[g.oth_idx[c]] = s;
-        } else if (apply_mask) {
-            u[g.zero_idx[t - n4]] = T(0);
-        } else {
-            const int a = g.dir_off[t - n4], b = g.dir_off[t - n4 + 1];
-            T s = u[g.dir_idx[a]];
-            for (int c = a + 1; c < b; c++) s += u[g.dir_idx[c]];
-            for (int c = a; c < b; c++) u[g.dir_idx[c]] = s;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    gs_pairs<T, 4>(u, g.pairs, g.npair, t0, stride);
+    gs_quads<T, 2>(u, g.quads, g.nquad, t0, stride);
+    for (int64_t t = t0; t < g.noct; t += stride) {
+        const int4 q0 = g.octs[2 * t], q1 = g.octs[2 * t + 1];
+        const T a0 = u[q0.x], a1 = u[q0.y], a2 = u[q0.z], a3 = u[q0.w];
+        const T a4 = u[q1.x], a5 = u[q1.y], a6 = u[q1.z], a7 = u[q1.w];
+        const T sum = ((((((a0 + a1) + a2) + a3) + a4) + a5) + a6) + a7;
+        u[q0.x] = sum; u[q0.y] = sum; u[q0.z] = sum; u[q0.w] = sum;
+        u[q1.x] = sum; u[q1.y] = sum; u[q1.z] = sum; u[q1.w] = sum;
+    }
+    for (int64_t t = t0; t < g.noth; t += stride) {
+        const int a = g.oth_off[t], b = g.oth_off[t + 1];
+        T sum = u[g.oth_idx[a]];
+        for (int c = a + 1; c < b; c++) sum += u[g.oth_idx[c]];
+        for (int c = a; c < b; c++) u[g.oth_idx[c]] = sum;
+    }
+    if (apply_mask) {
+        for (int64_t t = t0; t < g.nzero; t += stride) u[g.zero_idx[t]] = T(0);
+    } else {
+        for (int64_t t = t0; t < g.ndir; t += stride) {
+            const int a = g.dir_off[t], b = g.dir_off[t + 1];
+            T sum = u[g.dir_idx[a]];
+            for (int c = a + 1; c < b; c++) sum += u[g.dir_idx[c]];
+            for (int c = a; c < b; c++) u[g.dir_idx[c]] = sum;
         }
     }
 }
@@ -62,7 +108,8 @@ int launch_gs(sem_handle* h, void* u, bool fp32, bool apply_mask, cudaStream_t s
     const GSLists& g = h->gs;
     const int64_t total = g.npair + g.nquad + g.noct + g.noth + (apply_mask ? g.nzero : g.ndir);
     if (total == 0) return SEM_OK;
-    const int grid = grid_for(h, total, 256, 8);
+    const int64_t widest = std::max({g.npair / 4, g.nquad / 2, g.noct, g.noth, g.nzero, g.ndir, (int64_t)1});
+    const int grid = grid_for(h, widest, 256, 8);
     if (fp32)
         gs_kernel<float><<<grid, 256, 0, s>>>((float*)u, g, apply_mask ? 1 : 0);
     else

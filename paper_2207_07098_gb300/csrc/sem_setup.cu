@@ -387,6 +387,7 @@ static int setup_common(sem_handle** out, int nsolve, const sem_mesh_desc* meshe
     sem_handle* h = new sem_handle();
     for (auto& row : h->ax_variant)
         for (int& v : row) v = forced;
+    h->test_stall = (flags & SEM_FLAG_TEST_STALL) ? 1 : 0;
     int rc = SEM_OK;
     auto bail = [&](int code) {
         free_handle(h);

@@ -167,3 +167,32 @@ def test_full_size_solve_true_residual():
     assert st["status"] == S.SEM_OK and st["relres"] <= TOL, st
     P = oracle.Problem(m, h1)
     assert _oracle_relres(P, x, b) <= 1.05 * TOL
+
+
+def test_bounded_wait_expiry_reports_timeout_and_context_survives():
+    """Failure detection without a fault: with SEM_FLAG_TEST_STALL the staged
+    operator kernels announce more bytes than they copy, so their bounded
+    mbarrier waits expire (~50 ms); the kernels record the failure and
+    return, and the solve reports SEM_ETIMEOUT.  The context stays usable."""
+    m, h1, P, b = _deformed_case(3, 7)
+    H = Handle(m, h1, flags=S.SEM_FLAG_VARIANT(2) | S.SEM_FLAG_TEST_STALL)
+    for mode in (S.SEM_MODE_MIXED_IR, S.SEM_MODE_FP64):
+        with pytest.raises(S.SemError) as ei:
+            H.solve(b, mode=mode, tol=TOL, graph_chunk=2)
+        assert ei.value.status == S.SEM_ETIMEOUT
+    H.close()
+    H2 = Handle(m, h1, flags=S.SEM_FLAG_VARIANT(2))
+    x, st = H2.solve(b, tol=TOL)
+    assert st["status"] == S.SEM_OK and _oracle_relres(P, x, b) <= 1.05 * TOL
+
+
+def test_non_finite_rhs_reports_breakdown():
+    m, h1, P, b = _deformed_case(2, 5)
+    H = Handle(m, h1)
+    bad = b.copy()
+    bad[np.flatnonzero(m.mask)[3]] = np.nan
+    for mode in (S.SEM_MODE_FP64, S.SEM_MODE_MIXED_IR):
+        x, st = H.solve(bad, mode=mode, tol=TOL, max_iter=50)
+        assert st["status"] in (S.SEM_EBREAKDOWN, S.SEM_ENOTCONV, S.SEM_ESTAGNATE), st
+    x, st = H.solve(b, tol=TOL)
+    assert st["status"] == S.SEM_OK
