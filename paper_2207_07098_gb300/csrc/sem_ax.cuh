@@ -37,6 +37,17 @@ struct AxParams {
     int variant;  // 0: shared-slab kernel; 1..kBulkVariants: bulk-staged (EPC, stages)
     long long wait_budget;  // clock cycles a staged kernel waits for a stage
     unsigned tx_extra;      // bytes announced beyond the copies (test of the bounded wait)
+    // batched form (bulk kernel): element-group list of one order, per-solve
+    // CG states (st is the base) and partials
+    const int64_t* loc;
+    const int* cnt;
+    const int* solve;
+    int64_t ngroups;
+    int64_t goff;
+    const int* sgfirst;
+    const int* sgcount;
+    double* gpart;
+    unsigned int* scount;
 };
 
 template <typename T, int LX>
@@ -255,6 +266,7 @@ constexpr int kBulkCfg[kBulkVariants][2] = {{1, 3}, {2, 2}, {2, 3}, {4, 2}};
 int dispatch_ax_bulk_f64(sem_handle* h, int lx, const AxParams<double>& a, bool fused, cudaStream_t s);
 int bulk_set_d_f64(const double* D, int lx);
 int bulk_set_d_f32(const float* D, int lx);
+int dispatch_ax_bulk_batch_f32(sem_handle* h, int lx, const AxParams<float>& a, bool fused, cudaStream_t s);
 int dispatch_ax_bulk_f32(sem_handle* h, int lx, const AxParams<float>& a, bool fused, cudaStream_t s);
 inline bool bulk_supported(int lx) { return lx == 4 || lx == 6 || lx == 8 || lx == 10 || lx == 12; }
 // Shared memory of the fused (larger) bulk kernel of variant v fits in a CTA.

@@ -118,7 +118,7 @@ struct BulkCfg {
     static_assert(LX % 2 == 0, "bulk staging needs even lx");
 };
 
-template <typename T, int LX, int EPC, int NST, bool FUSED>
+template <typename T, int LX, int EPC, int NST, bool FUSED, bool BATCH = false>
 __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
     ax_bulk_kernel(AxParams<T> a) {
     using C = BulkCfg<T, LX, EPC, NST, FUSED>;
@@ -134,13 +134,15 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
 
     double beta = 0.0;
     bool first = false;
-    if (FUSED) {
+    if (FUSED && !BATCH) {
         if (a.st->done) return;  // uniform over the grid
         beta = cg_beta(a.st);
         first = (a.st->iter == 0);
     }
-    const T tbeta = (T)beta;
-    const int64_t ngroups = (a.E + EPC - 1) / EPC;
+    T tbeta = (T)beta;
+    const int64_t ngroups = BATCH ? a.ngroups : (a.E + EPC - 1) / EPC;
+    __shared__ double red[32];
+    __shared__ int is_last;
     const int tid = threadIdx.x;
     const int el = tid / N2;
     const int ij = tid - el * N2;
@@ -149,20 +151,25 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
     const int so = (active ? el : 0) * N3;
 
     // stage s of group g: [in0 | in1 | G], each in element order
+    // local index of the first element of group g, and its element count
+    auto group_off = [&](int64_t g) -> int64_t { return BATCH ? a.loc[g] : g * EPC * N3; };
+    auto group_cnt = [&](int64_t g) -> int {
+        return BATCH ? a.cnt[g] : (int)(a.E - g * EPC < EPC ? a.E - g * EPC : EPC);
+    };
     auto issue = [&](int s, int64_t g) {
-        const int64_t e0 = g * EPC;
-        const int cnt = (int)(a.E - e0 < EPC ? a.E - e0 : EPC);
+        const int64_t off = group_off(g);
+        const int cnt = group_cnt(g);
         T* st = stage0 + s * C::STAGE;
         const uint32_t bin = (uint32_t)(cnt * N3 * sizeof(T));
         const uint32_t bG = 6u * bin;
         mbar_expect_tx(&bars[s], (uint32_t)C::IN * bin + bG + a.tx_extra);
         if (FUSED) {
-            bulk_load(st, a.z + e0 * N3, bin, &bars[s]);
-            bulk_load(st + EPC * N3, a.p + e0 * N3, bin, &bars[s]);
+            bulk_load(st, a.z + off, bin, &bars[s]);
+            bulk_load(st + EPC * N3, a.p + off, bin, &bars[s]);
         } else {
-            bulk_load(st, a.u + e0 * N3, bin, &bars[s]);
+            bulk_load(st, a.u + off, bin, &bars[s]);
         }
-        bulk_load(st + C::IN * EPC * N3, a.G + e0 * 6 * N3, bG, &bars[s]);
+        bulk_load(st + C::IN * EPC * N3, a.G + 6 * off, bG, &bars[s]);
     };
 
     if (tid == 0) {
@@ -195,10 +202,25 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
         if (!mbar_wait_bounded(&bars[s], parity, a.wait_budget)) abort_flag = 1;
         __syncthreads();
         if (abort_flag) break;
+        int sol = 0;
+        if (BATCH && FUSED) {
+            sol = a.solve[g];
+            const CGState* stg = a.st + sol;
+            if (stg->done) {  // converged solve: drop the stage, keep the ring going
+                __syncthreads();
+                if (tid == 0) {
+                    const int64_t gn = g + (int64_t)NST * gridDim.x;
+                    if (gn < ngroups) issue(s, gn);
+                }
+                continue;
+            }
+            beta = cg_beta(stg);
+            first = (stg->iter == 0);
+            tbeta = (T)beta;
+        }
         const T* st = stage0 + s * C::STAGE;
-        const int64_t e = g * EPC + el;
-        const bool valid = active && e < a.E;
-        const int64_t base = e * N3 + ij;
+        const bool valid = active && el < group_cnt(g);
+        const int64_t base = group_off(g) + (int64_t)(active ? el : 0) * N3 + ij;
         // phase 0: this thread's column of u (or z + beta p)
         T ucol[LX];
 #pragma unroll
@@ -261,7 +283,29 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
                 if (FUSED) pw = fma(ucol[k], acc, pw);
             }
         }
-        if (FUSED) pap += (double)pw;
+        if (FUSED && BATCH) {
+            double v[1] = {(double)pw};
+            block_sum<1>(v, red);
+            if (tid == 0) {
+                a.gpart[a.goff + g] = v[0];
+                __threadfence();
+                is_last = (atomicAdd(&a.scount[sol], 1u) == (unsigned)a.sgcount[sol] - 1u) ? 1 : 0;
+            }
+            __syncthreads();
+            if (is_last) {
+                __threadfence();
+                const int f = a.sgfirst[sol], c = a.sgcount[sol];
+                double acc[1] = {0.0};
+                for (int q = tid; q < c; q += blockDim.x) acc[0] += __ldcg(&a.gpart[f + q]);
+                block_sum<1>(acc, red);
+                if (tid == 0) {
+                    cg_set_alpha(a.st + sol, acc[0]);
+                    a.scount[sol] = 0u;
+                }
+            }
+        } else if (FUSED) {
+            pap += (double)pw;
+        }
         __syncthreads();
     }
     if (abort_flag) {
@@ -276,7 +320,7 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
         }
         return;
     }
-    if (FUSED) {
+    if (FUSED && !BATCH) {
         double v[1] = {pap};
         CGState* stt = a.st;
         grid_sum_finalize<1>(v, a.partials, a.counter, [&](double (&acc)[1]) { cg_set_alpha(stt, acc[0]); });
@@ -318,6 +362,55 @@ inline int launch_ax_bulk_t(sem_handle* h, const AxParams<T>& a, cudaStream_t s)
         SEM_LAUNCH_CHECK("ax_bulk_kernel");
         h->launches++;
         return SEM_OK;
+    }
+}
+
+// Batched form: one persistent launch over the element-group list of one order.
+template <typename T, int LX, int EPC, int NST, bool FUSED>
+inline int launch_ax_bulk_batch_t(sem_handle* h, const AxParams<T>& a, cudaStream_t s) {
+    using C = BulkCfg<T, LX, EPC, NST, FUSED>;
+    if constexpr (C::BYTES > 227 * 1024) {
+        return fail(SEM_EINVAL, "bulk variant does not fit in shared memory");
+    } else {
+        static int per_sm = -1;
+        if (per_sm < 0) {
+            cudaFuncSetAttribute(ax_bulk_kernel<T, LX, EPC, NST, FUSED, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES);
+            int nb = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ax_bulk_kernel<T, LX, EPC, NST, FUSED, true>,
+                                                          C::THREADS, C::BYTES);
+            per_sm = nb;
+        }
+        if (per_sm <= 0) return fail(SEM_EINVAL, "bulk variant cannot be resident");
+        if (a.dry || a.ngroups == 0) return SEM_OK;
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(a.ngroups, (int64_t)h->sm_count * per_sm));
+        ax_bulk_kernel<T, LX, EPC, NST, FUSED, true><<<(int)grid, C::THREADS, C::BYTES, s>>>(a);
+        SEM_LAUNCH_CHECK("ax_bulk_kernel (batched)");
+        h->launches++;
+        return SEM_OK;
+    }
+}
+
+template <typename T, int LX, bool FUSED>
+inline int dispatch_bulk_batch_cfg(sem_handle* h, const AxParams<T>& a, cudaStream_t s) {
+    switch (a.variant) {
+        case 1: return launch_ax_bulk_batch_t<T, LX, kBulkCfg[0][0], kBulkCfg[0][1], FUSED>(h, a, s);
+        case 2: return launch_ax_bulk_batch_t<T, LX, kBulkCfg[1][0], kBulkCfg[1][1], FUSED>(h, a, s);
+        case 3: return launch_ax_bulk_batch_t<T, LX, kBulkCfg[2][0], kBulkCfg[2][1], FUSED>(h, a, s);
+        case 4: return launch_ax_bulk_batch_t<T, LX, kBulkCfg[3][0], kBulkCfg[3][1], FUSED>(h, a, s);
+        default: return fail(SEM_EINVAL, "unknown operator variant");
+    }
+}
+
+template <typename T, bool FUSED>
+inline int dispatch_ax_bulk_batch(sem_handle* h, int lx, const AxParams<T>& a, cudaStream_t s) {
+    switch (lx) {
+        case 4: return dispatch_bulk_batch_cfg<T, 4, FUSED>(h, a, s);
+        case 6: return dispatch_bulk_batch_cfg<T, 6, FUSED>(h, a, s);
+        case 8: return dispatch_bulk_batch_cfg<T, 8, FUSED>(h, a, s);
+        case 10: return dispatch_bulk_batch_cfg<T, 10, FUSED>(h, a, s);
+        case 12: return dispatch_bulk_batch_cfg<T, 12, FUSED>(h, a, s);
+        default: return fail(SEM_EINVAL, "bulk staging needs lx in {4, 6, 8, 10, 12}");
     }
 }
 

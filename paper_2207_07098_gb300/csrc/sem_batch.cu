@@ -203,23 +203,25 @@ __global__ void correct_batch_kernel(double* x, const float* d32, TileList tl, c
 
 static int epc_of(int lx) { return std::max(1, 256 / (lx * lx)); }
 
-static int build_plan(sem_handle* h) {
-    BatchPlan& bp = h->batch;
-    if (bp.ready) return SEM_OK;
+static int batch_bulk_variant(const sem_handle* h, int lx);
+
+// Cuts every solve of order lx into groups of at most epc_for(lx) elements
+// (epc 0: no groups of that order), one list per order present, numbered
+// globally; fills the per-solve first group and group count on the device.
+template <typename EpcFor>
+static int build_group_lists(sem_handle* h, const std::vector<int>& lxs, EpcFor epc_for,
+                             std::vector<LxGroups>& lists, int64_t* total, int** d_first,
+                             int** d_count, double** d_part) {
     const int ns = h->nsolve;
-    std::vector<int> lxs;
-    for (auto& p : h->parts) lxs.push_back(p.lx);
-    std::sort(lxs.begin(), lxs.end());
-    lxs.erase(std::unique(lxs.begin(), lxs.end()), lxs.end());
-    std::vector<int> sgfirst(ns), sgcount(ns);
+    std::vector<int> sgfirst(ns, 0), sgcount(ns, 0);
     int64_t goff = 0;
     int rc;
     for (int lx : lxs) {
-        const int epc = epc_of(lx);
+        const int epc = epc_for(lx);
         const int64_t n3 = (int64_t)lx * lx * lx;
         std::vector<int64_t> loc;
         std::vector<int> cnt, sol;
-        for (int q = 0; q < ns; q++) {
+        for (int q = 0; q < ns && epc > 0; q++) {
             const MeshPart& p = h->parts[q];
             if (p.lx != lx) continue;
             sgfirst[q] = (int)(goff + (int64_t)loc.size());
@@ -234,16 +236,44 @@ static int build_plan(sem_handle* h) {
         g.lx = lx;
         g.ngroups = (int64_t)loc.size();
         g.goff = goff;
-        if ((rc = dalloc(h, &g.loc, loc.size())) || (rc = dalloc(h, &g.cnt, cnt.size())) ||
-            (rc = dalloc(h, &g.solve, sol.size())))
+        lists.push_back(g);
+        LxGroups& gl = lists.back();
+        if ((rc = dalloc(h, &gl.loc, loc.size())) || (rc = dalloc(h, &gl.cnt, cnt.size())) ||
+            (rc = dalloc(h, &gl.solve, sol.size())))
             return rc;
-        SEM_CUDA_TRY(cudaMemcpy(g.loc, loc.data(), loc.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
-        SEM_CUDA_TRY(cudaMemcpy(g.cnt, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice));
-        SEM_CUDA_TRY(cudaMemcpy(g.solve, sol.data(), sol.size() * sizeof(int), cudaMemcpyHostToDevice));
+        if (!loc.empty()) {
+            SEM_CUDA_TRY(cudaMemcpy(gl.loc, loc.data(), loc.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+            SEM_CUDA_TRY(cudaMemcpy(gl.cnt, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice));
+            SEM_CUDA_TRY(cudaMemcpy(gl.solve, sol.data(), sol.size() * sizeof(int), cudaMemcpyHostToDevice));
+        }
         goff += g.ngroups;
-        bp.lxg.push_back(g);
     }
-    bp.ngroups = goff;
+    *total = goff;
+    if ((rc = dalloc(h, d_first, ns)) || (rc = dalloc(h, d_count, ns)) || (rc = dalloc(h, d_part, (size_t)goff)))
+        return rc;
+    SEM_CUDA_TRY(cudaMemcpy(*d_first, sgfirst.data(), ns * sizeof(int), cudaMemcpyHostToDevice));
+    SEM_CUDA_TRY(cudaMemcpy(*d_count, sgcount.data(), ns * sizeof(int), cudaMemcpyHostToDevice));
+    return SEM_OK;
+}
+
+static int build_plan(sem_handle* h) {
+    BatchPlan& bp = h->batch;
+    if (bp.ready) return SEM_OK;
+    const int ns = h->nsolve;
+    std::vector<int> lxs;
+    for (auto& p : h->parts) lxs.push_back(p.lx);
+    std::sort(lxs.begin(), lxs.end());
+    lxs.erase(std::unique(lxs.begin(), lxs.end()), lxs.end());
+    int rc = build_group_lists(h, lxs, epc_of, bp.lxg, &bp.ngroups, &bp.sgfirst, &bp.sgcount, &bp.gpart);
+    if (!rc)
+        rc = build_group_lists(
+            h, lxs,
+            [&](int lx) {
+                const int v = batch_bulk_variant(h, lx);
+                return v > 0 ? kBulkCfg[v - 1][0] : 0;
+            },
+            bp.blxg, &bp.bngroups, &bp.bsgfirst, &bp.bsgcount, &bp.bgpart);
+    if (rc) return rc;
     std::vector<int64_t> tloc;
     std::vector<int> tlen, tsol, stfirst(ns), stcount(ns);
     for (int q = 0; q < ns; q++) {
@@ -257,16 +287,12 @@ static int build_plan(sem_handle* h) {
         stcount[q] = (int)tloc.size() - stfirst[q];
     }
     bp.ntiles = (int64_t)tloc.size();
-    if ((rc = dalloc(h, &bp.sgfirst, ns)) || (rc = dalloc(h, &bp.sgcount, ns)) ||
-        (rc = dalloc(h, &bp.tloc, tloc.size())) || (rc = dalloc(h, &bp.tlen, tlen.size())) ||
+    if ((rc = dalloc(h, &bp.tloc, tloc.size())) || (rc = dalloc(h, &bp.tlen, tlen.size())) ||
         (rc = dalloc(h, &bp.tsolve, tsol.size())) || (rc = dalloc(h, &bp.stfirst, ns)) ||
-        (rc = dalloc(h, &bp.stcount, ns)) || (rc = dalloc(h, &bp.gpart, (size_t)bp.ngroups)) ||
-        (rc = dalloc(h, &bp.tpart, (size_t)bp.ntiles * 3)) || (rc = dalloc(h, &bp.scount, ns)) ||
+        (rc = dalloc(h, &bp.stcount, ns)) || (rc = dalloc(h, &bp.tpart, (size_t)bp.ntiles * 3)) || (rc = dalloc(h, &bp.scount, ns)) ||
         (rc = dalloc(h, &bp.rrbb, (size_t)2 * ns)) || (rc = dalloc(h, &bp.act, ns)) ||
         (rc = dalloc(h, &bp.itol, ns)))
         return rc;
-    SEM_CUDA_TRY(cudaMemcpy(bp.sgfirst, sgfirst.data(), ns * sizeof(int), cudaMemcpyHostToDevice));
-    SEM_CUDA_TRY(cudaMemcpy(bp.sgcount, sgcount.data(), ns * sizeof(int), cudaMemcpyHostToDevice));
     SEM_CUDA_TRY(cudaMemcpy(bp.tloc, tloc.data(), tloc.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
     SEM_CUDA_TRY(cudaMemcpy(bp.tlen, tlen.data(), tlen.size() * sizeof(int), cudaMemcpyHostToDevice));
     SEM_CUDA_TRY(cudaMemcpy(bp.tsolve, tsol.data(), tsol.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -291,12 +317,45 @@ static bool batch_uses_pair_arith(const sem_handle* h, int lx) {
     return (lx % 2 == 0 && lx >= 4 && lx <= 12) && (v < 0 || v >= kDfVariant);
 }
 
+// FP32 batches use the bulk-staged operator for order lx (the variant pinned
+// at set-up, else (2 elements, 2 stages), else (1, 3)) when it fits and every
+// solve of that order starts on a 16-byte boundary (bulk copies need it; the
+// elements of an even order keep it).
+static int batch_bulk_variant(const sem_handle* h, int lx) {
+    for (const MeshPart& p : h->parts)
+        if (p.lx == lx && (p.loc_off % 4) != 0) return 0;
+    const int pinned = h->ax_variant[1][lx];
+    if (pinned == 0) return 0;
+    if (pinned > 0 && pinned <= kBulkVariantsMax && bulk_fits(lx, pinned, true)) return pinned;
+    if (bulk_fits(lx, 2, true)) return 2;
+    if (bulk_fits(lx, 1, true)) return 1;
+    return 0;
+}
+
 // K-A over every order present: fused (CG state slot base `st`) or plain.
 static int batch_ax(sem_handle* h, bool fp32, bool fused, const void* u, CGState* st, cudaStream_t s) {
     BatchPlan& bp = h->batch;
-    for (const LxGroups& g : bp.lxg) {
+    for (size_t li = 0; li < bp.lxg.size(); li++) {
+        const LxGroups& g = bp.lxg[li];
         int rc;
-        if (fp32) {
+        const int bv = batch_bulk_variant(h, g.lx);
+        if (fp32 && bv > 0) {
+            const LxGroups& gb = bp.blxg[li];
+            AxParams<float> a = {};
+            a.u = (const float*)u;
+            a.z = h->ws.z32;
+            a.p = h->ws.p32;
+            a.w = h->ws.w32;
+            a.G = h->G32;
+            a.D = h->D32[g.lx];
+            a.variant = bv;
+            a.err = device_error_word(h);
+            a.wait_budget = h->test_stall ? 100000000LL : 4000000000LL;
+            a.tx_extra = h->test_stall ? 16u : 0u;
+            a.loc = gb.loc; a.cnt = gb.cnt; a.solve = gb.solve; a.ngroups = gb.ngroups; a.goff = gb.goff;
+            a.st = st; a.sgfirst = bp.bsgfirst; a.sgcount = bp.bsgcount; a.gpart = bp.bgpart; a.scount = bp.scount;
+            rc = dispatch_ax_bulk_batch_f32(h, g.lx, a, fused, s);
+        } else if (fp32) {
             BatchAxParams<float> a = {};
             a.u = (const float*)u;
             a.z = h->ws.z32;
@@ -343,6 +402,13 @@ static int prepare_batch_kernels(sem_handle* h) {
         b.dry = 1;
         int rc = dispatch_ax_batch_f64(h, g.lx, a, true, 0);
         if (!rc) rc = dispatch_ax_batch_f64(h, g.lx, a, false, 0);
+        if (!rc && batch_bulk_variant(h, g.lx) > 0) {
+            AxParams<float> c = {};
+            c.dry = 1;
+            c.variant = batch_bulk_variant(h, g.lx);
+            rc = dispatch_ax_bulk_batch_f32(h, g.lx, c, true, 0);
+            if (!rc) rc = dispatch_ax_bulk_batch_f32(h, g.lx, c, false, 0);
+        }
         if (!rc && batch_uses_pair_arith(h, g.lx)) {
             DflParams d = {};
             d.dry = 1;
@@ -534,7 +600,7 @@ static int solve_batch(sem_handle* h, double* x_user, const double* b_user, cons
                 int nact = 0;
                 for (int q = 0; q < ns; q++) {
                     const double bb = rrbb[2 * q + 1];
-                    const double rel = bb > 0 ? std::sqrt(rrbb[2 * q] / bb) : 0.0;
+                    const double rel = relative_residual(rrbb[2 * q], bb);
                     act[q] = (status[q] == SEM_OK && rel > o.tol && iters[q] < o.max_iter && restart <= 4) ? 1 : 0;
                     nact += act[q];
                 }
@@ -569,9 +635,9 @@ static int solve_batch(sem_handle* h, double* x_user, const double* b_user, cons
                 act[q] = 0;
                 if (fin[q]) continue;
                 const double bb = rrbb[2 * q + 1];
-                const double rel = bb > 0 ? std::sqrt(rrbb[2 * q] / bb) : 0.0;
-                if (bb == 0.0 || rel <= o.tol) { status[q] = SEM_OK; fin[q] = 1; }
-                else if (!std::isfinite(rel)) { status[q] = SEM_EBREAKDOWN; fin[q] = 1; }
+                const double rel = relative_residual(rrbb[2 * q], bb);
+                if (!std::isfinite(rel)) { status[q] = SEM_EBREAKDOWN; fin[q] = 1; }
+                else if (bb == 0.0 || rel <= o.tol) { status[q] = SEM_OK; fin[q] = 1; }
                 else if (outer[q] >= o.max_outer) { status[q] = SEM_ENOTCONV; fin[q] = 1; }
                 else if (outer[q] > 0 && rel > 0.5 * prev[q]) { status[q] = SEM_ESTAGNATE; fin[q] = 1; }
                 else { act[q] = 1; prev[q] = rel; itol[q] = inner_tolerance(o, rel); nact++; }
@@ -615,7 +681,7 @@ static int solve_batch(sem_handle* h, double* x_user, const double* b_user, cons
             st.iterations = iters[q];
             st.outer_iterations = o.mode == SEM_MODE_MIXED_IR ? outer[q] : 0;
             const double bb = rrbb[2 * q + 1];
-            st.relres = bb > 0 ? std::sqrt(rrbb[2 * q] / bb) : 0.0;
+            st.relres = relative_residual(rrbb[2 * q], bb);
             st.relres_recursive = o.mode == SEM_MODE_FP64 && hs[q].bb > 0 ? std::sqrt(hs[q].rr / hs[q].bb) : st.relres;
             st.time_ms = ms;
             st.kernel_launches = h->launches - launches0;

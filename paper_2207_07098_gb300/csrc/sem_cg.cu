@@ -423,7 +423,7 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
                 double hb[2];
                 SEM_CUDA_TRY(cudaMemcpyAsync(hb, rrbb, sizeof(hb), cudaMemcpyDeviceToHost, s));
                 SEM_CUDA_TRY(cudaStreamSynchronize(s));
-                const double rel = hb[1] > 0 ? std::sqrt(hb[0] / hb[1]) : 0.0;
+                const double rel = relative_residual(hb[0], hb[1]);
                 if (rel <= o.tol || status != SEM_OK || restart > 4 || used >= o.max_iter) break;
             }
             if (pair) {
@@ -452,10 +452,10 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
             double hb[2];
             SEM_CUDA_TRY(cudaMemcpyAsync(hb, rrbb, sizeof(hb), cudaMemcpyDeviceToHost, s));
             SEM_CUDA_TRY(cudaStreamSynchronize(s));
-            const double rel = hb[1] > 0 ? std::sqrt(hb[0] / hb[1]) : 0.0;
+            const double rel = relative_residual(hb[0], hb[1]);
             st.relres_recursive = rel;
-            if (hb[1] == 0.0 || rel <= o.tol) { status = SEM_OK; break; }
             if (!std::isfinite(rel)) { status = SEM_EBREAKDOWN; break; }
+            if (hb[1] == 0.0 || rel <= o.tol) { status = SEM_OK; break; }
             if (outer >= o.max_outer) { status = SEM_ENOTCONV; break; }
             if (outer > 0 && rel > 0.5 * prev) { status = SEM_ESTAGNATE; break; }
             prev = rel;
@@ -494,7 +494,7 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
         cudaMemset(h->counters, 0, 16 * sizeof(unsigned));
         return fail(SEM_ETIMEOUT, "a staged operator kernel gave up waiting for its bulk copies");
     }
-    st.relres = hb[1] > 0 ? std::sqrt(hb[0] / hb[1]) : 0.0;
+    st.relres = relative_residual(hb[0], hb[1]);
     st.time_ms = ms;
     st.ax_variant = o.mode == SEM_MODE_MIXED_IR ? ax_variant_for(h, h->parts[0].lx, true)
                     : (o.precision == SEM_FP64_NATIVE ? 0 : ax_variant_for(h, h->parts[0].lx, false));

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -140,10 +141,24 @@ struct BatchPlan {
     double* rrbb = nullptr;   // [nsolve * 2]
     int* act = nullptr;       // [nsolve] solves taking part in an inner solve
     double* itol = nullptr;   // [nsolve] inner relative tolerance of each active solve
+    // second group lists, cut to the element count of the FP32 bulk-staged
+    // operator (blxg[i] has the order of lxg[i]; no groups where it is unused)
+    std::vector<LxGroups> blxg;
+    int64_t bngroups = 0;
+    int* bsgfirst = nullptr;  // [nsolve]
+    int* bsgcount = nullptr;  // [nsolve]
+    double* bgpart = nullptr; // [bngroups]
     bool ready = false;
 };
 
 constexpr int kTile = 4096;
+
+// sqrt(rr / bb) of a true residual: NaN when either norm is not finite (a
+// non-finite right-hand side or iterate), 0 for a zero right-hand side.
+inline double relative_residual(double rr, double bb) {
+    if (!std::isfinite(rr) || !std::isfinite(bb)) return NAN;
+    return bb > 0 ? std::sqrt(rr / bb) : 0.0;
+}
 
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;

@@ -327,6 +327,10 @@ static void free_handle(sem_handle* h) {
     for (auto& g : bp.lxg) {
         cudaFree(g.loc); cudaFree(g.cnt); cudaFree(g.solve);
     }
+    for (auto& g : bp.blxg) {
+        cudaFree(g.loc); cudaFree(g.cnt); cudaFree(g.solve);
+    }
+    cudaFree(bp.bsgfirst); cudaFree(bp.bsgcount); cudaFree(bp.bgpart);
     cudaFree(bp.sgfirst); cudaFree(bp.sgcount); cudaFree(bp.tloc); cudaFree(bp.tlen); cudaFree(bp.tsolve);
     cudaFree(bp.stfirst); cudaFree(bp.stcount); cudaFree(bp.gpart); cudaFree(bp.tpart); cudaFree(bp.scount);
     cudaFree(bp.rrbb); cudaFree(bp.act); cudaFree(bp.itol);

@@ -140,3 +140,62 @@ def test_batch_256_member_workload_sampled():
     finally:
         S.sem_destroy(h)
         torch.cuda.empty_cache()
+
+
+def _even_members(seed, count, orders=(3, 5, 7, 9, 11)):
+    rng = np.random.default_rng(seed)
+    out = []
+    for q in range(count):
+        nx, ny, nz = (int(v) for v in rng.integers(1, 5, size=3))
+        N = int(rng.choice(np.asarray(orders)))
+        m = W.box_mesh(nx, ny, nz, N, amp=float(rng.uniform(0.0, 0.08)))
+        h1 = W.h1_wavy(m) if q % 2 else None
+        out.append((m, h1, W.random_global_rhs(m, 300 + q)))
+    return out
+
+
+@pytest.mark.parametrize("flags", [0, S.SEM_FLAG_VARIANT(1), S.SEM_FLAG_VARIANT(4)])
+def test_batch_even_orders_bulk_operator(flags):
+    """Every order even (lx 4..12): the FP32 inner solves run the bulk-staged
+    batched operator (default (2, 2), or the pinned variant where it fits);
+    the mixed solve reaches 1e-10 by the oracle's residual and agrees with the
+    slab operator (variant 0) to solver accuracy."""
+    members = _even_members(11, 7)
+    h = _setup_flags(members, flags)
+    h0 = _setup_flags(members, S.SEM_FLAG_VARIANT(0))
+    try:
+        xs, st = _solve(h, members, mode=S.SEM_MODE_MIXED_IR)
+        x0, s0 = _solve(h0, members, mode=S.SEM_MODE_MIXED_IR)
+        xr, _ = _solve(h, members, mode=S.SEM_MODE_MIXED_IR)
+        for q, (m, h1, b) in enumerate(members):
+            assert st[q]["status"] == S.SEM_OK and st[q]["relres"] <= TOL, (q, st[q])
+            assert np.array_equal(xs[q], xr[q]), q
+            P = oracle.Problem(m, h1)
+            assert _oracle_relres(P, xs[q], b) <= 1.05 * TOL, q
+            assert rel_err(xs[q], x0[q])[0] <= 1e-7, q
+    finally:
+        S.sem_destroy(h)
+        S.sem_destroy(h0)
+
+
+def test_batch_misaligned_even_order_falls_back():
+    """A solve of odd lx (lx = 3, 27 nodes per element) ahead of even-order
+    solves shifts their first local index off a 16-byte boundary; those orders
+    take the slab operator and the mixed solve still converges."""
+    m3 = W.box_mesh(1, 1, 3, 2, amp=0.05)
+    members = [(m3, None, W.random_global_rhs(m3, 299))] + _even_members(13, 4)
+    h = _setup(members)
+    try:
+        off = S.sem_get_offsets(h, len(members))
+        assert any(o % 4 for o in off[1:-1])
+        xs, st = _solve(h, members, mode=S.SEM_MODE_MIXED_IR)
+        for q, (m, h1, b) in enumerate(members):
+            assert st[q]["status"] == S.SEM_OK, (q, st[q])
+            P = oracle.Problem(m, h1)
+            assert _oracle_relres(P, xs[q], b) <= 1.05 * TOL, q
+    finally:
+        S.sem_destroy(h)
+
+
+def _setup_flags(members, flags):
+    return S.sem_setup_batch([(m.E, m.lx, m.coords, m.gid, m.mask, h1) for m, h1, _ in members], flags)
