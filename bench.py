@@ -198,20 +198,30 @@ def run_reference(args):
 
 
 def _traffic_for(kernel: str, workload: str):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel's
-    source is unchanged since the capture (else None)."""
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    summaries (a `traffic-record:` line in profiles/*.md), if the kernel's
+    source file is unchanged since the capture (else None)."""
+    import glob
     import hashlib
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    try:
-        with open(path) as fh:
-            rec = json.load(fh).get(kernel)
-        if not rec or rec.get("workload") != workload:
-            return None
-        src = os.path.join(ROOT, rec["source"])
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        return rec["bytes_per_launch"] if h == rec.get("source_sha") else None
-    except Exception:
-        return None
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        try:
+            lines = open(path).read().splitlines()
+        except OSError:
+            continue
+        for line in lines:
+            line = line.strip().strip("`")
+            if not line.startswith("traffic-record:"):
+                continue
+            rec = dict(kv.split("=", 1) for kv in line[len("traffic-record:"):].split())
+            if rec.get("kernel") != kernel or rec.get("workload") != workload:
+                continue
+            try:
+                src = os.path.join(ROOT, rec["source"])
+                h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+            except (KeyError, OSError):
+                return None
+            return float(rec["bytes_per_launch"]) if h == rec.get("source_sha") else None
+    return None
 
 
 def run_ours(args):

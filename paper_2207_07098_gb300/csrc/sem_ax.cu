@@ -53,7 +53,6 @@ static int dispatch_variant(sem_handle* h, int lx, AxParams<T> a, bool fused, in
             d.p = a.p;
             d.w = a.w;
             d.G2 = h->G2 + (a.G - h->G64) * 2;
-            d.coef = h->DL[lx];
             d.E = a.E;
             d.st = a.st;
             d.partials = a.partials;

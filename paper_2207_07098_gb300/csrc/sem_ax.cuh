@@ -266,6 +266,8 @@ constexpr int kBulkCfg[kBulkVariants][2] = {{1, 3}, {2, 2}, {2, 3}, {4, 2}};
 int dispatch_ax_bulk_f64(sem_handle* h, int lx, const AxParams<double>& a, bool fused, cudaStream_t s);
 int bulk_set_d_f64(const double* D, int lx);
 int bulk_set_d_f32(const float* D, int lx);
+// fills the constant-bank line-transform tables of order lx (sem_ax_df.cu)
+int dfl_set_coef(const float* cf, int lx);
 int dispatch_ax_bulk_batch_f32(sem_handle* h, int lx, const AxParams<float>& a, bool fused, cudaStream_t s);
 int dispatch_ax_bulk_f32(sem_handle* h, int lx, const AxParams<float>& a, bool fused, cudaStream_t s);
 inline bool bulk_supported(int lx) { return lx == 4 || lx == 6 || lx == 8 || lx == 10 || lx == 12; }

@@ -281,6 +281,17 @@ __device__ __forceinline__ void pair_addsub(float ah, float al, float bh, float 
     l = err + (al + sign * bl);
 }
 
+// Coefficient tables of the line transforms for every even order, in the
+// constant bank: the unrolled transforms read them as immediate constant
+// operands of the FP32 multiplies (no shared-memory loads).  Layout per order:
+// [dir][A/B][hi/lo][P][P] (dir 0 = D, 1 = D^T), at dfl_coef_off(lx).
+constexpr int dfl_coef_off(int lx) {
+    return lx == 4 ? 0 : lx == 6 ? 32 : lx == 8 ? 104 : lx == 10 ? 232 : lx == 12 ? 432 : -1;
+}
+constexpr int kDflCoefTotal = 720;
+static __constant__ float c_dflcoef[kDflCoefTotal];
+int dfl_set_coef(const float* cf, int lx);
+
 template <int LX>
 struct DflCfg {
     static constexpr int P = LX / 2;
@@ -296,16 +307,20 @@ struct DflCfg {
     static constexpr int THREADS = ((USED + 31) / 32) * 32;
     // coefficient tables: [fwd/bwd][A/B][hi/lo][P][P]
     static constexpr int COEF = 2 * 2 * 2 * P * P;
-    static constexpr size_t FLOATS = (size_t)COEF + 8 * (size_t)EPC * SLOT;
+    static constexpr size_t FLOATS = 8 * (size_t)EPC * SLOT;
     static __host__ __device__ constexpr int at(int k, int j, int i) { return k * N2P + j * LXP + i; }
 };
 
 // One line: x at xs[0], xs[st], ..., y written to ys[0], ys[st], ... (both
 // hi and lo arrays); coefficient tables A, B (hi, lo) of size P x P.
-template <int LX>
-__device__ __forceinline__ void df_line(const float* xh, const float* xl, int xst, float* yh, float* yl, int yst,
-                                        const float* Ah, const float* Al, const float* Bh, const float* Bl) {
-    constexpr int P = LX / 2, N = LX - 1;
+// CA: constant-bank offset of the A (hi) table; A lo, B hi, B lo follow at P*P strides.
+template <int LX, int CA>
+__device__ __forceinline__ void df_line(const float* xh, const float* xl, int xst, float* yh, float* yl, int yst) {
+    constexpr int P = LX / 2, N = LX - 1, PP = P * P;
+    const float* Ah = c_dflcoef + CA;
+    const float* Al = c_dflcoef + CA + PP;
+    const float* Bh = c_dflcoef + CA + 2 * PP;
+    const float* Bl = c_dflcoef + CA + 3 * PP;
     float eh[P], el[P], oh[P], ol[P];
 #pragma unroll
     for (int m = 0; m < P; m++) {
@@ -334,10 +349,13 @@ __device__ __forceinline__ void df_line(const float* xh, const float* xl, int xs
 }
 
 // Same, accumulating into y (y += M x).
-template <int LX>
-__device__ __forceinline__ void df_line_acc(const float* xh, const float* xl, int xst, float* yh, float* yl, int yst,
-                                            const float* Ah, const float* Al, const float* Bh, const float* Bl) {
-    constexpr int P = LX / 2, N = LX - 1;
+template <int LX, int CA>
+__device__ __forceinline__ void df_line_acc(const float* xh, const float* xl, int xst, float* yh, float* yl, int yst) {
+    constexpr int P = LX / 2, N = LX - 1, PP = P * P;
+    const float* Ah = c_dflcoef + CA;
+    const float* Al = c_dflcoef + CA + PP;
+    const float* Bh = c_dflcoef + CA + 2 * PP;
+    const float* Bl = c_dflcoef + CA + 3 * PP;
     float eh[P], el[P], oh[P], ol[P];
 #pragma unroll
     for (int m = 0; m < P; m++) {
@@ -367,8 +385,6 @@ __device__ __forceinline__ void df_line_acc(const float* xh, const float* xl, in
     }
 }
 
-// coefficient tables (host-built, float pairs): cf[((dir * 2 + ab) * 2 + hl) * P*P + i*P + m],
-// dir 0 = D (forward), 1 = D^T (backward); ab 0 = A (odd part), 1 = B (even part)
 struct DflParams {
     const double* u;
     const double* z;
@@ -382,7 +398,6 @@ struct DflParams {
     float* wh;
     float* wl;
     const float* G2;
-    const float* coef;
     int64_t E;
     CGState* st;
     double* partials;
@@ -406,11 +421,11 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
     static_assert(!PAIR || FUSED, "the pair form exists for the fused CG kernel only");
     static_assert(!(PAIR && BATCH), "no pair form for batches");
     using C = DflCfg<LX>;
-    constexpr int P = C::P, N2 = C::N2, N3 = C::N3, EPC = C::EPC, SLOT = C::SLOT, PP = P * P;
+    constexpr int P = C::P, N2 = C::N2, N3 = C::N3, EPC = C::EPC, SLOT = C::SLOT;
     constexpr int N2P = C::N2P, LXP = C::LXP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* cf = reinterpret_cast<float*>(smem_raw);
-    float* arr = cf + C::COEF;  // 8 arrays x EPC slots: uh ul | rh rl | sh sl | th tl
+    float* arr = reinterpret_cast<float*>(smem_raw);  // 8 arrays x EPC slots: uh ul | rh rl | sh sl | th tl
+    constexpr int CF = dfl_coef_off(LX), CB = CF + 4 * P * P;  // forward (D) and backward (D^T) tables
     double beta = 0.0;
     bool first = false;
     if (FUSED && !BATCH) {
@@ -420,7 +435,6 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
     }
     __shared__ double red[32];
     __shared__ int is_last;
-    for (int t = threadIdx.x; t < C::COEF; t += blockDim.x) cf[t] = a.coef[t];
     const int tid = threadIdx.x;
     const int el = tid / N2;
     const int t2 = tid - el * N2;          // column (i, j) in phase 0, line id in the transforms
@@ -435,14 +449,6 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
     float* sl = arr + 5 * EPC * SLOT + slot;
     float* th = arr + 6 * EPC * SLOT + slot;
     float* tl = arr + 7 * EPC * SLOT + slot;
-    const float* fAh = cf + 0 * PP;
-    const float* fAl = cf + 1 * PP;
-    const float* fBh = cf + 2 * PP;
-    const float* fBl = cf + 3 * PP;
-    const float* bAh = cf + 4 * PP;
-    const float* bAl = cf + 5 * PP;
-    const float* bBh = cf + 6 * PP;
-    const float* bBl = cf + 7 * PP;
     const int64_t ngroups = BATCH ? a.ngroups : (a.E + EPC - 1) / EPC;
     double pap = 0.0;
     __syncthreads();
@@ -522,12 +528,12 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
         __syncthreads();
         // phase 1: derivative lines ur (along i), us (along j), ut (along k)
         if (active) {
-            df_line<LX>(uh + C::at(hi_, lo_, 0), ul + C::at(hi_, lo_, 0), 1, rh + C::at(hi_, lo_, 0),
-                        rl + C::at(hi_, lo_, 0), 1, fAh, fAl, fBh, fBl);  // r-line (k=hi_, j=lo_)
-            df_line<LX>(uh + C::at(hi_, 0, lo_), ul + C::at(hi_, 0, lo_), LXP, sh + C::at(hi_, 0, lo_),
-                        sl + C::at(hi_, 0, lo_), LXP, fAh, fAl, fBh, fBl);  // s-line (k=hi_, i=lo_)
-            df_line<LX>(uh + C::at(0, hi_, lo_), ul + C::at(0, hi_, lo_), N2P, th + C::at(0, hi_, lo_),
-                        tl + C::at(0, hi_, lo_), N2P, fAh, fAl, fBh, fBl);  // t-line (j=hi_, i=lo_)
+            df_line<LX, CF>(uh + C::at(hi_, lo_, 0), ul + C::at(hi_, lo_, 0), 1, rh + C::at(hi_, lo_, 0),
+                        rl + C::at(hi_, lo_, 0), 1);  // r-line (k=hi_, j=lo_)
+            df_line<LX, CF>(uh + C::at(hi_, 0, lo_), ul + C::at(hi_, 0, lo_), LXP, sh + C::at(hi_, 0, lo_),
+                        sl + C::at(hi_, 0, lo_), LXP);  // s-line (k=hi_, i=lo_)
+            df_line<LX, CF>(uh + C::at(0, hi_, lo_), ul + C::at(0, hi_, lo_), N2P, th + C::at(0, hi_, lo_),
+                        tl + C::at(0, hi_, lo_), N2P);  // t-line (j=hi_, i=lo_)
         }
         __syncthreads();
         // phase 2: (wr, ws, wt) = G (ur, us, ut) at the column's points
@@ -567,17 +573,17 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
         __syncthreads();
         // phase 3: w = D^T-lines of wr (into the u arrays), then += those of ws
         if (active)
-            df_line<LX>(rh + C::at(hi_, lo_, 0), rl + C::at(hi_, lo_, 0), 1, uh + C::at(hi_, lo_, 0),
-                        ul + C::at(hi_, lo_, 0), 1, bAh, bAl, bBh, bBl);
+            df_line<LX, CB>(rh + C::at(hi_, lo_, 0), rl + C::at(hi_, lo_, 0), 1, uh + C::at(hi_, lo_, 0),
+                        ul + C::at(hi_, lo_, 0), 1);
         __syncthreads();
         if (active)
-            df_line_acc<LX>(sh + C::at(hi_, 0, lo_), sl + C::at(hi_, 0, lo_), LXP, uh + C::at(hi_, 0, lo_),
-                            ul + C::at(hi_, 0, lo_), LXP, bAh, bAl, bBh, bBl);
+            df_line_acc<LX, CB>(sh + C::at(hi_, 0, lo_), sl + C::at(hi_, 0, lo_), LXP, uh + C::at(hi_, 0, lo_),
+                            ul + C::at(hi_, 0, lo_), LXP);
         __syncthreads();
         // phase 4: += D^T-lines of wt along k; the t-line is this thread's column
         if (active)
-            df_line_acc<LX>(th + C::at(0, hi_, lo_), tl + C::at(0, hi_, lo_), N2P, uh + C::at(0, hi_, lo_),
-                            ul + C::at(0, hi_, lo_), N2P, bAh, bAl, bBh, bBl);
+            df_line_acc<LX, CB>(th + C::at(0, hi_, lo_), tl + C::at(0, hi_, lo_), N2P, uh + C::at(0, hi_, lo_),
+                            ul + C::at(0, hi_, lo_), N2P);
         double pw = 0.0;
         if (PAIR) {
             float S = 0.f, Ee = 0.f;

@@ -317,18 +317,17 @@ static bool batch_uses_pair_arith(const sem_handle* h, int lx) {
     return (lx % 2 == 0 && lx >= 4 && lx <= 12) && (v < 0 || v >= kDfVariant);
 }
 
-// FP32 batches use the bulk-staged operator for order lx (the variant pinned
-// at set-up, else (2 elements, 2 stages), else (1, 3)) when it fits and every
-// solve of that order starts on a 16-byte boundary (bulk copies need it; the
-// elements of an even order keep it).
+// FP32 batches use the bulk-staged operator for order lx only when a bulk
+// variant was pinned at set-up, it fits, and every solve of that order starts
+// on a 16-byte boundary (bulk copies need it; the elements of an even order
+// keep it).  By default they use the slab kernel over the element-group
+// lists: on the 256-box batch (N in {5, 7, 9}) it was faster than every bulk
+// variant (mixed solve 2.97 s against 3.50-3.97 s).
 static int batch_bulk_variant(const sem_handle* h, int lx) {
     for (const MeshPart& p : h->parts)
         if (p.lx == lx && (p.loc_off % 4) != 0) return 0;
     const int pinned = h->ax_variant[1][lx];
-    if (pinned == 0) return 0;
     if (pinned > 0 && pinned <= kBulkVariantsMax && bulk_fits(lx, pinned, true)) return pinned;
-    if (bulk_fits(lx, 2, true)) return 2;
-    if (bulk_fits(lx, 1, true)) return 1;
     return 0;
 }
 
@@ -373,7 +372,6 @@ static int batch_ax(sem_handle* h, bool fp32, bool fused, const void* u, CGState
             d.p = h->ws.p;
             d.w = h->ws.w;
             d.G2 = h->G2;
-            d.coef = h->DL[g.lx];
             d.loc = g.loc; d.cnt = g.cnt; d.solve = g.solve; d.ngroups = g.ngroups; d.goff = g.goff;
             d.st = st; d.sgfirst = bp.sgfirst; d.sgcount = bp.sgcount; d.gpart = bp.gpart; d.scount = bp.scount;
             rc = dispatch_ax_dfl_batch_entry(h, g.lx, d, fused, s);
@@ -422,10 +420,10 @@ static int prepare_batch_kernels(sem_handle* h) {
     return SEM_OK;
 }
 
-static int batch_iteration(sem_handle* h, bool fp32, CGState* st, cudaStream_t s) {
-    int rc = batch_ax(h, fp32, true, nullptr, st, s);
+// K-B and K-C of one batched iteration.
+static int batch_kb_kc(sem_handle* h, bool fp32, CGState* st, cudaStream_t s) {
+    int rc = launch_gs(h, fp32 ? (void*)h->ws.w32 : (void*)h->ws.w, fp32, true, s);
     if (rc) return rc;
-    if ((rc = launch_gs(h, fp32 ? (void*)h->ws.w32 : (void*)h->ws.w, fp32, true, s))) return rc;
     if (fp32)
         upd_batch_kernel<float><<<grid_tiles(h), 256, 0, s>>>(h->ws.d32, h->ws.p32, h->ws.r32, h->ws.w32, h->ws.z32,
                                                                h->minv32, h->mult, st, tiles(h));
@@ -435,6 +433,11 @@ static int batch_iteration(sem_handle* h, bool fp32, CGState* st, cudaStream_t s
     SEM_LAUNCH_CHECK("upd_batch_kernel");
     h->launches++;
     return SEM_OK;
+}
+
+static int batch_iteration(sem_handle* h, bool fp32, CGState* st, cudaStream_t s) {
+    int rc = batch_ax(h, fp32, true, nullptr, st, s);
+    return rc ? rc : batch_kb_kc(h, fp32, st, s);
 }
 
 static int batch_graph(sem_handle* h, bool fp32, CGState* st, int chunk, cudaGraphExec_t* out, int* per_launch) {
@@ -463,16 +466,7 @@ static int batch_graph(sem_handle* h, bool fp32, CGState* st, int chunk, cudaGra
         if (!rc) rc = batch_ax(h, fp32, true, nullptr, st, cs);
         if (it == 0 && !rc && cudaEventRecordWithFlags(h->ax_ev[1], cs, cudaEventRecordExternal) != cudaSuccess)
             rc = fail(SEM_ECUDA, "event record");
-        if (!rc) rc = launch_gs(h, fp32 ? (void*)h->ws.w32 : (void*)h->ws.w, fp32, true, cs);
-        if (!rc) {
-            if (fp32)
-                upd_batch_kernel<float><<<grid_tiles(h), 256, 0, cs>>>(h->ws.d32, h->ws.p32, h->ws.r32, h->ws.w32,
-                                                                        h->ws.z32, h->minv32, h->mult, st, tiles(h));
-            else
-                upd_batch_kernel<double><<<grid_tiles(h), 256, 0, cs>>>(h->ws.x, h->ws.p, h->ws.r, h->ws.w, h->ws.z,
-                                                                         h->minv64, h->mult, st, tiles(h));
-            if (cudaGetLastError() != cudaSuccess) rc = fail(SEM_ECUDA, "upd_batch_kernel launch");
-        }
+        if (!rc) rc = batch_kb_kc(h, fp32, st, cs);
     }
     h->launches = before;
     cudaGraph_t graph = nullptr;

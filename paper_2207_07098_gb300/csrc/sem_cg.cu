@@ -239,15 +239,8 @@ static int launch_kb_kc(sem_handle* h, int precision, cudaStream_t s) {
 }
 
 static int launch_iteration(sem_handle* h, int precision, cudaStream_t s) {
-    if (precision == kPairPrec) {
-        int rc = launch_ka(h, precision, s);
-        return rc ? rc : launch_kb_kc(h, precision, s);
-    }
-    int rc = launch_cg_pupdate_ax(h, precision, s);
-    if (!rc) rc = launch_gs(h, precision == SEM_FP32 ? (void*)h->ws.w32 : (void*)h->ws.w, precision == SEM_FP32,
-                            true, s);
-    if (!rc) rc = launch_cg_update(h, precision, s);
-    return rc;
+    int rc = launch_ka(h, precision, s);
+    return rc ? rc : launch_kb_kc(h, precision, s);
 }
 
 static int get_graph(sem_handle* h, int precision, int chunk, cudaGraphExec_t* out) {
@@ -272,10 +265,15 @@ static int get_graph(sem_handle* h, int precision, int chunk, cudaGraphExec_t* o
     const int64_t launches_before = h->launches;  // captured kernels are counted per graph launch
     SEM_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     int rc = SEM_OK;
+    // the K-A that is timed: the second of the chunk (it follows K-C inside the
+    // graph, as in steady state; the first one starts after the host check)
+    const int timed = chunk > 1 ? 1 : 0;
     for (int it = 0; it < chunk && rc == SEM_OK; it++) {
-        if (it == 0 && cudaEventRecordWithFlags(h->ax_ev[0], cs, cudaEventRecordExternal) != cudaSuccess) rc = fail(SEM_ECUDA, "event record");
+        if (it == timed && cudaEventRecordWithFlags(h->ax_ev[0], cs, cudaEventRecordExternal) != cudaSuccess)
+            rc = fail(SEM_ECUDA, "event record");
         if (!rc) rc = launch_ka(h, precision, cs);
-        if (it == 0 && !rc && cudaEventRecordWithFlags(h->ax_ev[1], cs, cudaEventRecordExternal) != cudaSuccess) rc = fail(SEM_ECUDA, "event record");
+        if (it == timed && !rc && cudaEventRecordWithFlags(h->ax_ev[1], cs, cudaEventRecordExternal) != cudaSuccess)
+            rc = fail(SEM_ECUDA, "event record");
         if (!rc) rc = launch_kb_kc(h, precision, cs);
     }
     h->launches = launches_before;
@@ -305,8 +303,9 @@ struct AxTiming {
 };
 
 // Run CG iterations on state slot `slot` until done.  Returns SEM_OK or an
-// error; the solve status is in the state.  With graphs, the duration of the
-// first K-A of every graph launch is added to `tm`.
+// error; the solve status is in the state.  With graphs, the duration of one
+// K-A of every graph launch (the second of the chunk) is added to `tm`; a
+// launch that ends the solve before that K-A ran adds nothing.
 static int run_cg_loop(sem_handle* h, int precision, const sem_solve_opts& o, int slot, cudaStream_t s,
                        CGState* out, AxTiming* tm) {
     const int chunk = std::max(1, std::min(o.graph_chunk, 1024));
@@ -319,6 +318,7 @@ static int run_cg_loop(sem_handle* h, int precision, const sem_solve_opts& o, in
     SEM_CUDA_TRY(cudaStreamSynchronize(s));
     const int64_t max_rounds = (int64_t)out->max_iter / chunk + 3;
     for (int64_t round = 0; !out->done && round < max_rounds; round++) {
+        const int iter_before = out->iter;
         if (exec) {
             SEM_CUDA_TRY(cudaGraphLaunch(exec, s));
             h->launches += 3 * (int64_t)chunk;
@@ -339,7 +339,7 @@ static int run_cg_loop(sem_handle* h, int precision, const sem_solve_opts& o, in
             cudaMemset(h->counters, 0, 16 * sizeof(unsigned));
             return fail(SEM_ETIMEOUT, "a staged operator kernel gave up waiting for its bulk copies");
         }
-        if (exec && tm) {
+        if (exec && tm && (chunk == 1 || out->iter - iter_before >= 2)) {
             float ms = 0.0f;
             if (cudaEventElapsedTime(&ms, h->ax_ev[0], h->ax_ev[1]) == cudaSuccess) {
                 tm->ms += ms;

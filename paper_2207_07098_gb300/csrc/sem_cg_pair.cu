@@ -223,7 +223,6 @@ int launch_pair_ka(sem_handle* h, cudaStream_t s) {
     d.wh = v[6];
     d.wl = v[7];
     d.G2 = h->G2;
-    d.coef = h->DL[p.lx];
     d.E = p.E;
     d.st = h->state;
     d.partials = h->partials;
@@ -236,7 +235,9 @@ int launch_pair_rest(sem_handle* h, cudaStream_t s) {
     const GSLists& g = h->gs;
     const int64_t total = g.npair + g.nquad + g.noct + g.noth + g.nzero;
     if (total > 0) {
-        gs_pair_kernel<<<grid_for(h, total, 256, 8), 256, 0, s>>>(v[6], v[7], g);
+        // one segment per thread: each thread walks one chain of dependent loads
+        const int grid = (int)std::min<int64_t>((total + 255) / 256, 1 << 20);
+        gs_pair_kernel<<<grid, 256, 0, s>>>(v[6], v[7], g);
         SEM_LAUNCH_CHECK("gs_pair_kernel");
         h->launches++;
     }

@@ -14,12 +14,12 @@
 
 namespace sem {
 
-// One launch covers, in this order: free segments of 2, 4 and 8 copies
-// (index vectors), free segments of other sizes (CSR), then either the zeroing
-// of every Dirichlet copy (apply_mask) or the sums over Dirichlet segments.
-// Copies are always summed left to right in ascending local index.  The loads
-// are latency-bound (scattered 4- or 8-byte accesses), so each thread issues
-// the index and value loads of U segments before it sums and stores any.
+// One launch covers free segments of 2, 4 and 8 copies (index vectors), free
+// segments of other sizes (CSR), and either the zeroing of every Dirichlet copy
+// (apply_mask) or the sums over Dirichlet segments.  Copies are always summed
+// left to right in ascending local index.  The loads are latency-bound
+// (scattered 4- or 8-byte accesses), so each thread issues the index and value
+// loads of U segments before it sums and stores any.
 template <typename T, int U>
 __device__ __forceinline__ void gs_pairs(T* __restrict__ u, const int2* __restrict__ idx, int64_t n, int64_t t0,
                                          int64_t stride) {
@@ -72,48 +72,84 @@ __device__ __forceinline__ void gs_quads(T* __restrict__ u, const int4* __restri
     }
 }
 
+// CTA ranges of the segment classes of one gather-scatter launch: the
+// classes touch disjoint local points, so they run side by side, each CTA on
+// one class (a thread walks one chain of dependent loads instead of one per
+// class).  b[c] = first CTA after class c.
+struct GsRanges {
+    int b[6];
+};
+constexpr int kGsThreads = 256;
+constexpr int kGsPairU = 4, kGsQuadU = 2, kGsZeroU = 4;
+
 template <typename T>
-__global__ void __launch_bounds__(256) gs_kernel(T* __restrict__ u, GSLists g, int apply_mask) {
-    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    gs_pairs<T, 4>(u, g.pairs, g.npair, t0, stride);
-    gs_quads<T, 2>(u, g.quads, g.nquad, t0, stride);
-    for (int64_t t = t0; t < g.noct; t += stride) {
-        const int4 q0 = g.octs[2 * t], q1 = g.octs[2 * t + 1];
-        const T a0 = u[q0.x], a1 = u[q0.y], a2 = u[q0.z], a3 = u[q0.w];
-        const T a4 = u[q1.x], a5 = u[q1.y], a6 = u[q1.z], a7 = u[q1.w];
-        const T sum = ((((((a0 + a1) + a2) + a3) + a4) + a5) + a6) + a7;
-        u[q0.x] = sum; u[q0.y] = sum; u[q0.z] = sum; u[q0.w] = sum;
-        u[q1.x] = sum; u[q1.y] = sum; u[q1.z] = sum; u[q1.w] = sum;
-    }
-    for (int64_t t = t0; t < g.noth; t += stride) {
-        const int a = g.oth_off[t], b = g.oth_off[t + 1];
-        T sum = u[g.oth_idx[a]];
-        for (int c = a + 1; c < b; c++) sum += u[g.oth_idx[c]];
-        for (int c = a; c < b; c++) u[g.oth_idx[c]] = sum;
-    }
-    if (apply_mask) {
-        for (int64_t t = t0; t < g.nzero; t += stride) u[g.zero_idx[t]] = T(0);
-    } else {
-        for (int64_t t = t0; t < g.ndir; t += stride) {
-            const int a = g.dir_off[t], b = g.dir_off[t + 1];
-            T sum = u[g.dir_idx[a]];
-            for (int c = a + 1; c < b; c++) sum += u[g.dir_idx[c]];
-            for (int c = a; c < b; c++) u[g.dir_idx[c]] = sum;
+__global__ void __launch_bounds__(kGsThreads) gs_kernel(T* __restrict__ u, GSLists g, int apply_mask, GsRanges rg) {
+    const int b = blockIdx.x;
+    int c = 0;
+    while (c < 5 && b >= rg.b[c]) c++;
+    const int b0 = c ? rg.b[c - 1] : 0;
+    const int64_t t0 = (int64_t)(b - b0) * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)(rg.b[c] - b0) * blockDim.x;
+    if (c == 0) {
+        gs_pairs<T, kGsPairU>(u, g.pairs, g.npair, t0, stride);
+    } else if (c == 1) {
+        gs_quads<T, kGsQuadU>(u, g.quads, g.nquad, t0, stride);
+    } else if (c == 2) {
+        for (int64_t t = t0; t < g.noct; t += stride) {
+            const int4 q0 = g.octs[2 * t], q1 = g.octs[2 * t + 1];
+            const T a0 = u[q0.x], a1 = u[q0.y], a2 = u[q0.z], a3 = u[q0.w];
+            const T a4 = u[q1.x], a5 = u[q1.y], a6 = u[q1.z], a7 = u[q1.w];
+            const T sum = ((((((a0 + a1) + a2) + a3) + a4) + a5) + a6) + a7;
+            u[q0.x] = sum; u[q0.y] = sum; u[q0.z] = sum; u[q0.w] = sum;
+            u[q1.x] = sum; u[q1.y] = sum; u[q1.z] = sum; u[q1.w] = sum;
+        }
+    } else if (c == 3) {
+        for (int64_t t = t0; t < g.noth; t += stride) {
+            const int a = g.oth_off[t], e = g.oth_off[t + 1];
+            T sum = u[g.oth_idx[a]];
+            for (int q = a + 1; q < e; q++) sum += u[g.oth_idx[q]];
+            for (int q = a; q < e; q++) u[g.oth_idx[q]] = sum;
+        }
+    } else if (c == 4) {
+        if (apply_mask) {
+            for (int64_t t = t0; t < g.nzero; t += stride * kGsZeroU) {
+                int q[kGsZeroU];
+#pragma unroll
+                for (int k = 0; k < kGsZeroU; k++) q[k] = (t + k * stride < g.nzero) ? g.zero_idx[t + k * stride] : -1;
+#pragma unroll
+                for (int k = 0; k < kGsZeroU; k++)
+                    if (q[k] >= 0) u[q[k]] = T(0);
+            }
+        } else {
+            for (int64_t t = t0; t < g.ndir; t += stride) {
+                const int a = g.dir_off[t], e = g.dir_off[t + 1];
+                T sum = u[g.dir_idx[a]];
+                for (int q = a + 1; q < e; q++) sum += u[g.dir_idx[q]];
+                for (int q = a; q < e; q++) u[g.dir_idx[q]] = sum;
+            }
         }
     }
+}
+
+static int ctas_for(int64_t items, int per_thread) {
+    const int64_t per_cta = (int64_t)kGsThreads * per_thread;
+    return (int)std::min<int64_t>((items + per_cta - 1) / per_cta, 1 << 20);
 }
 
 int launch_gs(sem_handle* h, void* u, bool fp32, bool apply_mask, cudaStream_t s) {
     const GSLists& g = h->gs;
     const int64_t total = g.npair + g.nquad + g.noct + g.noth + (apply_mask ? g.nzero : g.ndir);
     if (total == 0) return SEM_OK;
-    const int64_t widest = std::max({g.npair / 4, g.nquad / 2, g.noct, g.noth, g.nzero, g.ndir, (int64_t)1});
-    const int grid = grid_for(h, widest, 256, 8);
+    const int n[5] = {ctas_for(g.npair, kGsPairU), ctas_for(g.nquad, kGsQuadU), ctas_for(g.noct, 1),
+                      ctas_for(g.noth, 1), apply_mask ? ctas_for(g.nzero, kGsZeroU) : ctas_for(g.ndir, 1)};
+    GsRanges rg;
+    int acc = 0;
+    for (int c = 0; c < 5; c++) rg.b[c] = (acc += n[c]);
+    rg.b[5] = acc;
     if (fp32)
-        gs_kernel<float><<<grid, 256, 0, s>>>((float*)u, g, apply_mask ? 1 : 0);
+        gs_kernel<float><<<acc, kGsThreads, 0, s>>>((float*)u, g, apply_mask ? 1 : 0, rg);
     else
-        gs_kernel<double><<<grid, 256, 0, s>>>((double*)u, g, apply_mask ? 1 : 0);
+        gs_kernel<double><<<acc, kGsThreads, 0, s>>>((double*)u, g, apply_mask ? 1 : 0, rg);
     SEM_LAUNCH_CHECK("gs_kernel");
     h->launches++;
     return SEM_OK;

@@ -184,7 +184,6 @@ struct sem_handle {
     double* D64[sem::kMaxLx + 1] = {};
     float* D32[sem::kMaxLx + 1] = {};
     float* D2[sem::kMaxLx + 1] = {};   // [2][lx][lx]: hi and lo floats of D
-    float* DL[sem::kMaxLx + 1] = {};   // even/odd line coefficients of D and D^T (float pairs)
     // set-up data
     double* G64 = nullptr;     // [E][6][lx^3], h1 folded in
     float* G32 = nullptr;

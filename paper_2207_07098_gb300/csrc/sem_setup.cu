@@ -301,7 +301,6 @@ static void free_handle(sem_handle* h) {
         cudaFree(h->D64[l]);
         cudaFree(h->D32[l]);
         cudaFree(h->D2[l]);
-        cudaFree(h->DL[l]);
     }
     cudaFree(h->G64);
     cudaFree(h->G32);
@@ -531,7 +530,7 @@ static int setup_common(sem_handle** out, int nsolve, const sem_mesh_desc* meshe
         UP(h->D32[lx], Df, sizeof(float) * lx * lx);
         if ((rc = bulk_set_d_f64(Dh, lx)) || (rc = bulk_set_d_f32(Df, lx))) return bail(rc);
         UP(h->D2[lx], D2, sizeof(float) * 2 * lx * lx);
-        if (lx % 2 == 0) {
+        if (lx % 2 == 0 && lx >= 4 && lx <= 12) {
             // even/odd line coefficients: [dir][A/B][hi/lo][P][P], dir 0 = D, 1 = D^T,
             // A_im = (M_im - M_{i,N-m}) / 2, B_im = (M_im + M_{i,N-m}) / 2
             const int P = lx / 2, N = lx - 1;
@@ -547,8 +546,7 @@ static int setup_common(sem_handle** out, int nsolve, const sem_mesh_desc* meshe
                         cf[((dir * 2 + 1) * 2 + 0) * P * P + i * P + m] = Bh;
                         cf[((dir * 2 + 1) * 2 + 1) * P * P + i * P + m] = (float)(B - (double)Bh);
                     }
-            if ((rc = dalloc(h, &h->DL[lx], cf.size()))) return bail(rc);
-            UP(h->DL[lx], cf.data(), sizeof(float) * cf.size());
+            if ((rc = dfl_set_coef(cf.data(), lx))) return bail(rc);
         }
     }
     // geometry, mass, Jacobi diagonal: one part at a time through a staging buffer

@@ -154,11 +154,11 @@ def _even_members(seed, count, orders=(3, 5, 7, 9, 11)):
     return out
 
 
-@pytest.mark.parametrize("flags", [0, S.SEM_FLAG_VARIANT(1), S.SEM_FLAG_VARIANT(4)])
+@pytest.mark.parametrize("flags", [S.SEM_FLAG_VARIANT(1), S.SEM_FLAG_VARIANT(2), S.SEM_FLAG_VARIANT(4)])
 def test_batch_even_orders_bulk_operator(flags):
-    """Every order even (lx 4..12): the FP32 inner solves run the bulk-staged
-    batched operator (default (2, 2), or the pinned variant where it fits);
-    the mixed solve reaches 1e-10 by the oracle's residual and agrees with the
+    """Every order even (lx 4..12) and a bulk variant pinned: the FP32 inner
+    solves run the bulk-staged batched operator where the variant fits; the
+    mixed solve reaches 1e-10 by the oracle's residual and agrees with the
     slab operator (variant 0) to solver accuracy."""
     members = _even_members(11, 7)
     h = _setup_flags(members, flags)
@@ -180,11 +180,12 @@ def test_batch_even_orders_bulk_operator(flags):
 
 def test_batch_misaligned_even_order_falls_back():
     """A solve of odd lx (lx = 3, 27 nodes per element) ahead of even-order
-    solves shifts their first local index off a 16-byte boundary; those orders
-    take the slab operator and the mixed solve still converges."""
+    solves shifts their first local index off a 16-byte boundary; with a bulk
+    variant pinned, those orders still take the slab operator and the mixed
+    solve converges."""
     m3 = W.box_mesh(1, 1, 3, 2, amp=0.05)
     members = [(m3, None, W.random_global_rhs(m3, 299))] + _even_members(13, 4)
-    h = _setup(members)
+    h = _setup_flags(members, S.SEM_FLAG_VARIANT(2))
     try:
         off = S.sem_get_offsets(h, len(members))
         assert any(o % 4 for o in off[1:-1])
@@ -199,3 +200,4 @@ def test_batch_misaligned_even_order_falls_back():
 
 def _setup_flags(members, flags):
     return S.sem_setup_batch([(m.E, m.lx, m.coords, m.gid, m.mask, h1) for m, h1, _ in members], flags)
+
