@@ -75,7 +75,32 @@ struct PairVecs {
     unsigned int* counter;
 };
 
+// One point of K-C in pair form (FP64-accurate on the FP32 pipe).
+__device__ __forceinline__ void upd_pair_point(float& xh, float& xl, float ph, float pl, float& rh, float& rl,
+                                               float wh, float wl, float mh, float ml, float& zh, float& zl,
+                                               float iv, dfl al, float& zS, float& zE, float& rS, float& rE) {
+    float S = xh, E = xl;
+    df_mac(S, E, al.h, al.l, ph, pl);
+    const dfl x = df_norm(S, E);
+    S = rh;
+    E = rl;
+    df_mac(S, E, -al.h, -al.l, wh, wl);
+    const dfl r = df_norm(S, E);
+    float zs = 0.f, ze = 0.f;
+    df_mac(zs, ze, mh, ml, r.h, r.l);
+    const dfl z = df_norm(zs, ze);
+    xh = x.h;
+    xl = x.l;
+    rh = r.h;
+    rl = r.l;
+    zh = z.h;
+    zl = z.l;
+    df_mac(zS, zE, r.h * iv, r.l * iv, z.h, z.l);
+    df_mac(rS, rE, r.h * iv, r.l * iv, r.h, r.l);
+}
+
 // K-C in pair form: x += alpha p; r -= alpha w; z = Minv r; <r,z>, <r,r>.
+// Four points per thread and step (16-byte loads and stores of every plane).
 __global__ void __launch_bounds__(256) cg_update_pair_kernel(PairVecs a) {
     if (a.st->done) return;
     dfl al;
@@ -84,27 +109,30 @@ __global__ void __launch_bounds__(256) cg_update_pair_kernel(PairVecs a) {
     for (int m = threadIdx.x; m < 256; m += blockDim.x) inv[m] = m ? 1.0f / (float)m : 0.0f;
     __syncthreads();
     float zS = 0.f, zE = 0.f, rS = 0.f, rE = 0.f;
-    for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < a.n; L += (int64_t)gridDim.x * blockDim.x) {
-        float S = a.xh[L], E = a.xl[L];
-        df_mac(S, E, al.h, al.l, ld_stream(a.ph + L), ld_stream(a.pl + L));
-        const dfl x = df_norm(S, E);
-        S = a.rh[L];
-        E = a.rl[L];
-        df_mac(S, E, -al.h, -al.l, ld_stream(a.wh + L), ld_stream(a.wl + L));
-        const dfl r = df_norm(S, E);
-        const float mh = ld_stream(a.mh + L), ml = ld_stream(a.ml + L);
-        float zs = 0.f, ze = 0.f;
-        df_mac(zs, ze, mh, ml, r.h, r.l);
-        const dfl z = df_norm(zs, ze);
-        a.xh[L] = x.h;
-        a.xl[L] = x.l;
-        a.rh[L] = r.h;
-        a.rl[L] = r.l;
-        a.zh[L] = z.h;
-        a.zl[L] = z.l;
-        const float iv = inv[a.mult[L]];
-        df_mac(zS, zE, r.h * iv, r.l * iv, z.h, z.l);
-        df_mac(rS, rE, r.h * iv, r.l * iv, r.h, r.l);
+    const int64_t nv = a.n / 4;
+    auto ld4 = [](const float* p, int64_t q) { return reinterpret_cast<const float4*>(p)[q]; };
+    auto ld4s = [](const float* p, int64_t q) { return ld_stream(reinterpret_cast<const float4*>(p) + q); };
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv; q += (int64_t)gridDim.x * blockDim.x) {
+        float4 xh = ld4(a.xh, q), xl = ld4(a.xl, q), rh = ld4(a.rh, q), rl = ld4(a.rl, q);
+        const float4 ph = ld4s(a.ph, q), pl = ld4s(a.pl, q), wh = ld4s(a.wh, q), wl = ld4s(a.wl, q);
+        const float4 mh = ld4s(a.mh, q), ml = ld4s(a.ml, q);
+        const uchar4 mu = reinterpret_cast<const uchar4*>(a.mult)[q];
+        float4 zh, zl;
+        upd_pair_point(xh.x, xl.x, ph.x, pl.x, rh.x, rl.x, wh.x, wl.x, mh.x, ml.x, zh.x, zl.x, inv[mu.x], al, zS, zE, rS, rE);
+        upd_pair_point(xh.y, xl.y, ph.y, pl.y, rh.y, rl.y, wh.y, wl.y, mh.y, ml.y, zh.y, zl.y, inv[mu.y], al, zS, zE, rS, rE);
+        upd_pair_point(xh.z, xl.z, ph.z, pl.z, rh.z, rl.z, wh.z, wl.z, mh.z, ml.z, zh.z, zl.z, inv[mu.z], al, zS, zE, rS, rE);
+        upd_pair_point(xh.w, xl.w, ph.w, pl.w, rh.w, rl.w, wh.w, wl.w, mh.w, ml.w, zh.w, zl.w, inv[mu.w], al, zS, zE, rS, rE);
+        reinterpret_cast<float4*>(a.xh)[q] = xh;
+        reinterpret_cast<float4*>(a.xl)[q] = xl;
+        reinterpret_cast<float4*>(a.rh)[q] = rh;
+        reinterpret_cast<float4*>(a.rl)[q] = rl;
+        reinterpret_cast<float4*>(a.zh)[q] = zh;
+        reinterpret_cast<float4*>(a.zl)[q] = zl;
+    }
+    if (blockIdx.x == 0) {  // scalar tail
+        for (int64_t L = nv * 4 + threadIdx.x; L < a.n; L += blockDim.x)
+            upd_pair_point(a.xh[L], a.xl[L], a.ph[L], a.pl[L], a.rh[L], a.rl[L], a.wh[L], a.wl[L], a.mh[L], a.ml[L],
+                           a.zh[L], a.zl[L], inv[a.mult[L]], al, zS, zE, rS, rE);
     }
     double v[2] = {(double)zS + (double)zE, (double)rS + (double)rE};
     CGState* st = a.st;
@@ -235,13 +263,11 @@ int launch_pair_rest(sem_handle* h, cudaStream_t s) {
     const GSLists& g = h->gs;
     const int64_t total = g.npair + g.nquad + g.noct + g.noth + g.nzero;
     if (total > 0) {
-        // one segment per thread: each thread walks one chain of dependent loads
-        const int grid = (int)std::min<int64_t>((total + 255) / 256, 1 << 20);
-        gs_pair_kernel<<<grid, 256, 0, s>>>(v[6], v[7], g);
+        gs_pair_kernel<<<grid_for(h, total, 256, 8), 256, 0, s>>>(v[6], v[7], g);
         SEM_LAUNCH_CHECK("gs_pair_kernel");
         h->launches++;
     }
-    cg_update_pair_kernel<<<grid_for(h, h->n_local, 256, 4), 256, 0, s>>>(pair_vecs(h));
+    cg_update_pair_kernel<<<grid_for(h, h->n_local / 4 + 1, 256, 4), 256, 0, s>>>(pair_vecs(h));
     SEM_LAUNCH_CHECK("cg_update_pair_kernel");
     h->launches++;
     return SEM_OK;
