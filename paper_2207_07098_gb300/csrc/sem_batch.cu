@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256) upd_batch_kernel(T* x, const T* p, T* r, 
         const T ta = (T)st->alpha;
         const int64_t l0 = tl.tloc[t], l1 = l0 + tl.tlen[t];
         T lrz = T(0), lrr = T(0);
-        for (int64_t L = l0 + threadIdx.x; L < l1; L += blockDim.x) {
+        auto point = [&](int64_t L) {
             const T xv = fma(ta, p[L], x[L]);
             const T rv = fma(-ta, w[L], r[L]);
             const T zv = minv[L] * rv;
@@ -82,7 +82,44 @@ __global__ void __launch_bounds__(256) upd_batch_kernel(T* x, const T* p, T* r, 
             const T iv = inv[mult[L]];
             lrz = fma(rv * zv, iv, lrz);
             lrr = fma(rv * rv, iv, lrr);
+        };
+        bool vec = false;
+        if constexpr (sizeof(T) == 4) {
+            vec = (l0 & 3) == 0;  // 16-byte aligned tile: four points per thread and step
+            const int64_t v0 = l0 / 4, v1 = vec ? l1 / 4 : v0;
+            for (int64_t q = v0 + threadIdx.x; q < v1; q += blockDim.x) {
+                float4 xv = reinterpret_cast<const float4*>(x)[q];
+                float4 rv = reinterpret_cast<const float4*>(r)[q];
+                const float4 pv = ld_stream(reinterpret_cast<const float4*>(p) + q);
+                const float4 wv = ld_stream(reinterpret_cast<const float4*>(w) + q);
+                const float4 mv = ld_stream(reinterpret_cast<const float4*>(minv) + q);
+                const uchar4 mu = reinterpret_cast<const uchar4*>(mult)[q];
+                float* xs = reinterpret_cast<float*>(&xv);
+                float* rs = reinterpret_cast<float*>(&rv);
+                const float* ps = reinterpret_cast<const float*>(&pv);
+                const float* ws = reinterpret_cast<const float*>(&wv);
+                const float* ms = reinterpret_cast<const float*>(&mv);
+                const unsigned char* us = reinterpret_cast<const unsigned char*>(&mu);
+                float4 zv;
+                float* zs = reinterpret_cast<float*>(&zv);
+#pragma unroll
+                for (int c = 0; c < 4; c++) {  // the arithmetic of point(), one point at a time
+                    xs[c] = fmaf(ta, ps[c], xs[c]);
+                    rs[c] = fmaf(-ta, ws[c], rs[c]);
+                    zs[c] = ms[c] * rs[c];
+                    const float iv = inv[us[c]];
+                    lrz = fmaf(rs[c] * zs[c], iv, lrz);
+                    lrr = fmaf(rs[c] * rs[c], iv, lrr);
+                }
+                reinterpret_cast<float4*>(x)[q] = xv;
+                reinterpret_cast<float4*>(r)[q] = rv;
+                reinterpret_cast<float4*>(z)[q] = zv;
+            }
+            if (vec)
+                for (int64_t L = v1 * 4 + threadIdx.x; L < l1; L += blockDim.x) point(L);  // ragged end
         }
+        if (!vec)
+            for (int64_t L = l0 + threadIdx.x; L < l1; L += blockDim.x) point(L);
         double v[2] = {(double)lrz, (double)lrr}, acc[2];
         if (tile_finalize<2>(tl, t, s, v, acc, red, &is_last)) cg_set_rho(st, acc[0], acc[1]);
         __syncthreads();
