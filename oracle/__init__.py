@@ -87,6 +87,7 @@ def configure(lib):
         getattr(lib, name).argtypes = [ctypes.c_void_p, _dp]
     lib.or_get_geom.argtypes = [ctypes.c_void_p, _dp, _dp]
     lib.or_ax_local.argtypes = [ctypes.c_void_p, _dp, _dp]
+    lib.or_ax_local_abs.argtypes = [ctypes.c_void_p, _dp, _dp]
     lib.or_ax.argtypes = [ctypes.c_void_p, _dp, _dp]
     lib.or_gs.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int]
     lib.or_mass.argtypes = [ctypes.c_void_p, _dp, _dp, ctypes.c_int]
@@ -185,6 +186,14 @@ class Problem:
         u = np.ascontiguousarray(u, dtype=np.float64)
         w = np.zeros(self.n)
         self.lib.or_ax_local(self.h, _d(u), _d(w))
+        return w
+
+    def ax_local_abs(self, u):
+        """|D^T| |h1 G| |D| |u| per element (magnitude of the terms of A_L u),
+        the scale of the rounding error of any evaluation of A_L u."""
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        w = np.zeros(self.n)
+        self.lib.or_ax_local_abs(self.h, _d(u), _d(w))
         return w
 
     def ax(self, u):

@@ -242,6 +242,67 @@ void or_ax_local(const or_problem* p, const double* u, double* w) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Magnitude of the terms of A^e u: the same three stages with |D|, |G|, |u| */
+/* (|D^T| |h1 G| |D| |u|).  An evaluation of A^e u in arithmetic of unit     */
+/* roundoff eps errs by at most about (number of sequential operations) x    */
+/* eps times this, pointwise (the running error bound of a sum of products). */
+/* Test infrastructure: it scales the parity tolerance of cancelling inputs. */
+/* ------------------------------------------------------------------------ */
+
+void or_ax_local_abs(const or_problem* p, const double* u, double* w) {
+    const int lx = p->lx;
+    const int n3 = lx * lx * lx;
+    const int64_t n = p->n;
+#pragma omp parallel
+    {
+        double* ur = (double*)malloc(sizeof(double) * n3);
+        double* us = (double*)malloc(sizeof(double) * n3);
+        double* ut = (double*)malloc(sizeof(double) * n3);
+#pragma omp for schedule(static)
+        for (int e = 0; e < p->E; e++) {
+            const int64_t o = (int64_t)e * n3;
+            const double* ue = u + o;
+            for (int k = 0; k < lx; k++)
+                for (int j = 0; j < lx; j++)
+                    for (int i = 0; i < lx; i++) {
+                        double a = 0.0, b = 0.0, c = 0.0;
+                        for (int l = 0; l < lx; l++) {
+                            a += fabs(p->D[i * lx + l]) * fabs(ue[k * lx * lx + j * lx + l]);
+                            b += fabs(p->D[j * lx + l]) * fabs(ue[k * lx * lx + l * lx + i]);
+                            c += fabs(p->D[k * lx + l]) * fabs(ue[l * lx * lx + j * lx + i]);
+                        }
+                        const int q = k * lx * lx + j * lx + i;
+                        ur[q] = a;
+                        us[q] = b;
+                        ut[q] = c;
+                    }
+            for (int q = 0; q < n3; q++) {
+                const int64_t L = o + q;
+                const double g11 = fabs(p->G[0 * n + L]), g12 = fabs(p->G[1 * n + L]), g13 = fabs(p->G[2 * n + L]);
+                const double g22 = fabs(p->G[3 * n + L]), g23 = fabs(p->G[4 * n + L]), g33 = fabs(p->G[5 * n + L]);
+                const double a = ur[q], b = us[q], c = ut[q];
+                const double h = fabs(p->h1[L]);
+                ur[q] = h * (g11 * a + g12 * b + g13 * c);
+                us[q] = h * (g12 * a + g22 * b + g23 * c);
+                ut[q] = h * (g13 * a + g23 * b + g33 * c);
+            }
+            for (int k = 0; k < lx; k++)
+                for (int j = 0; j < lx; j++)
+                    for (int i = 0; i < lx; i++) {
+                        double acc = 0.0;
+                        for (int l = 0; l < lx; l++) acc += fabs(p->D[l * lx + i]) * ur[k * lx * lx + j * lx + l];
+                        for (int l = 0; l < lx; l++) acc += fabs(p->D[l * lx + j]) * us[k * lx * lx + l * lx + i];
+                        for (int l = 0; l < lx; l++) acc += fabs(p->D[l * lx + k]) * ut[l * lx * lx + j * lx + i];
+                        w[o + k * lx * lx + j * lx + i] = acc;
+                    }
+        }
+        free(ur);
+        free(us);
+        free(ut);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* QQ^T: every copy of a node receives the sum over all its copies, summed   */
 /* in ascending local index (Sec. II-A, A = QQ^T A_L).                        */
 /* ------------------------------------------------------------------------ */

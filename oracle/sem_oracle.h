@@ -54,6 +54,8 @@ void or_get_dmat(const or_problem* p, double* D);
 
 /* w = A_L u (local, unassembled). */
 void or_ax_local(const or_problem* p, const double* u, double* w);
+/* |D^T| |h1 G| |D| |u| per element: the magnitude of the terms of A^e u. */
+void or_ax_local_abs(const or_problem* p, const double* u, double* w);
 /* u <- QQ^T u (sum over the copies of each node, in ascending local index);
  * then u <- mask * u if apply_mask. */
 void or_gs(const or_problem* p, double* u, int apply_mask);

@@ -92,6 +92,36 @@ def element_matrices(mesh, h1=None):
     return out, Bm
 
 
+def element_magnitude_matrices(mesh, h1=None):
+    """Dense sum_st |D_s|^T diag(|h1 G_st|) |D_t| per element: the magnitudes
+    of the terms of A^e u act on |u| through this nonnegative matrix."""
+    N = mesh.N
+    lx = mesh.lx
+    n3 = lx ** 3
+    _, rho, D = basis_data(N)
+    Ds_ = [np.abs(M) for M in derivative_matrices(D)]
+    Dsigned = derivative_matrices(D)
+    w3 = np.kron(rho, np.kron(rho, rho))
+    hh = np.ones(mesh.n_local) if h1 is None else np.asarray(h1)
+    out = np.zeros((mesh.E, n3, n3))
+    for e in range(mesh.E):
+        X = mesh.coords[:, e, :]
+        Jm = np.zeros((n3, 3, 3))
+        for m in range(3):
+            for s in range(3):
+                Jm[:, m, s] = Dsigned[s] @ X[m]
+        J = np.linalg.det(Jm)
+        inv = np.linalg.inv(Jm)
+        he = hh[e * n3:(e + 1) * n3]
+        A = np.zeros((n3, n3))
+        for s in range(3):
+            for t in range(3):
+                g = np.abs(w3 * J * np.einsum("ql,ql->q", inv[:, s, :], inv[:, t, :]) * he)
+                A += Ds_[s].T @ (g[:, None] * Ds_[t])
+        out[e] = A
+    return out
+
+
 def scatter_matrix(mesh):
     """Q (n_L x n_U) with Q[L, g] = 1 when local node L is a copy of global node g
     (global nodes numbered by ascending id).  Also returns the mask per global node."""

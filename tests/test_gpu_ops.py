@@ -173,6 +173,37 @@ def test_ax_fp32_pair_variant(variant, kind, dims, N):
     assert e2 <= TOL_AX64
 
 
+@pytest.mark.parametrize("field", ["smooth", "random"])
+@pytest.mark.parametrize("variant", [5, 6])
+def test_ax_fp64_pair_kernels_within_rounding_bound(variant, field):
+    """FP32-pair FP64 operators against the native FP64 kernel on the same
+    handle (same factors): every output within the running rounding bound of
+    the pair arithmetic, |w_pair - w_fp64| <= 64 (2^-48 + 2^-53) |D^T||h1 G||D||u|
+    (a float pair carries 48 of the 53 mantissa bits; ~36 sequential operations
+    per output; the magnitude operator comes from the oracle).  Against the
+    oracle, the native kernel holds the 1e-12 relative bar on both fields; a
+    smooth field (sums that cancel) takes the pair kernels to a few 1e-12."""
+    m, h1 = _case("deformed", (8, 8, 8), 7)
+    P = oracle.Problem(m, h1)
+    H = Handle(m, h1, flags=S.SEM_FLAG_VARIANT(variant))
+    u = W.forcing_sines(m) if field == "smooth" else W.random_local_field(m, 25, continuous=True)
+    mag = P.ax_local_abs(u)
+    # the pair format has a bounded exponent range (inputs below 2^-75 and lo
+    # parts below FP32's normal range are flushed), so values far below the
+    # operator's scale (the sin field is ~1e-47 at the corner x = y = z = 1) are
+    # held to an absolute floor 2^-20 of the largest magnitude instead
+    bound = 64.0 * (2.0 ** -48 + 2.0 ** -53) * (mag + 2.0 ** -20 * mag.max())
+    w_pair = H.ax(u, S.SEM_FP64, assemble=0)
+    w_fp64 = H.ax(u, S.SEM_FP64_NATIVE, assemble=0)
+    assert np.all(np.abs(w_pair - w_fp64) <= bound)
+    e2, einf = rel_err(H.ax(u, S.SEM_FP64_NATIVE, assemble=1), P.ax(u))
+    assert e2 <= TOL_AX64 and einf <= TOL_AX64, (e2, einf)
+    p2, pinf = rel_err(H.ax(u, S.SEM_FP64, assemble=1), P.ax(u))
+    print(f"{field}: native {e2:.2e} / {einf:.2e}, variant {variant} {p2:.2e} / {pinf:.2e} (2-norm / max)")
+    if field == "random":
+        assert p2 <= TOL_AX64 and pinf <= TOL_AX64, (p2, pinf)
+
+
 def test_ax_deterministic():
     m, h1 = _case("jitter", (4, 3, 3), 7)
     H = Handle(m, h1)

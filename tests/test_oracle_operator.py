@@ -191,6 +191,25 @@ def test_ax_symmetric_positive_definite():
         assert P.dot(u, P.ax(u)) > 0.0
 
 
+@pytest.mark.parametrize("dims,N,jitter", [((2, 1, 1), 3, False), ((2, 2, 1), 4, True)])
+def test_ax_magnitude_operator(dims, N, jitter):
+    """The oracle's |D^T| |h1 G| |D| |u| (the scale of rounding errors of any
+    evaluation of A_L u) equals the nonnegative dense matrix built from
+    Kronecker products of |D| and numpy Jacobians, bounds |A_L u| pointwise,
+    and is absolutely homogeneous."""
+    m = W.box_mesh(*dims, N, amp=0.05, jitter=0.25 / N ** 2 if jitter else 0.0, seed=3)
+    h1 = W.h1_wavy(m)
+    P = oracle.Problem(m, h1)
+    u = W.random_local_field(m, 41)
+    a = P.ax_local_abs(u)
+    M = dense_ref.element_magnitude_matrices(m, h1)
+    n3 = m.lx ** 3
+    ref = np.concatenate([M[e] @ np.abs(u[e * n3:(e + 1) * n3]) for e in range(m.E)])
+    assert np.max(np.abs(a - ref)) <= 1e-13 * np.max(ref)
+    assert np.all(a >= np.abs(P.ax_local(u)))
+    assert np.allclose(P.ax_local_abs(-3.0 * u), 3.0 * a, rtol=1e-15, atol=0)
+
+
 def test_mass_integrates_constant():
     m = W.box_mesh(2, 2, 2, 5, amp=0.05)
     P = oracle.Problem(m)
