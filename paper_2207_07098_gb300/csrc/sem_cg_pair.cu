@@ -158,26 +158,76 @@ __device__ __forceinline__ void seg_pair(float* uh, float* ul, const int* idx, i
     }
 }
 
-__global__ void __launch_bounds__(256) gs_pair_kernel(float* __restrict__ uh, float* __restrict__ ul, GSLists g) {
-    const int64_t n1 = g.npair, n2 = n1 + g.nquad, n3 = n2 + g.noct, n4 = n3 + g.noth, n5 = n4 + g.nzero;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n5; t += (int64_t)gridDim.x * blockDim.x) {
-        if (t < n1) {
-            const int2 q = g.pairs[t];
-            const int ix[2] = {q.x, q.y};
-            seg_pair(uh, ul, ix, 2);
-        } else if (t < n2) {
-            const int4 q = g.quads[t - n1];
+// Pairs of copies, U segments per thread: all index and value loads of the U
+// segments are issued before any sum is stored (the accesses are scattered
+// and latency-bound).
+template <int U>
+__device__ __forceinline__ void gs_pair_pairs(float* __restrict__ uh, float* __restrict__ ul, const int2* idx,
+                                              int64_t n, int64_t t0, int64_t stride) {
+    for (int64_t t = t0; t < n; t += stride * U) {
+        int2 q[U];
+        float ah[U], al[U], bh[U], bl[U];
+#pragma unroll
+        for (int k = 0; k < U; k++) q[k] = (t + k * stride < n) ? idx[t + k * stride] : make_int2(-1, -1);
+#pragma unroll
+        for (int k = 0; k < U; k++)
+            if (q[k].x >= 0) {
+                ah[k] = uh[q[k].x];
+                al[k] = ul[q[k].x];
+                bh[k] = uh[q[k].y];
+                bl[k] = ul[q[k].y];
+            }
+#pragma unroll
+        for (int k = 0; k < U; k++)
+            if (q[k].x >= 0) {
+                float S = ah[k], E = al[k];
+                pair_accumulate(S, E, bh[k], bl[k]);
+                const dfl v = df_norm(S, E);
+                uh[q[k].x] = v.h;
+                ul[q[k].x] = v.l;
+                uh[q[k].y] = v.h;
+                ul[q[k].y] = v.l;
+            }
+    }
+}
+
+// CTA ranges of the segment classes (as in the FP32 gather-scatter): pairs
+// (4 per thread), quads, octets, other sizes, Dirichlet zeroing.
+struct GsPairRanges {
+    int b[5];
+};
+constexpr int kGsPairU = 4;
+
+__global__ void __launch_bounds__(256) gs_pair_kernel(float* __restrict__ uh, float* __restrict__ ul, GSLists g,
+                                                      GsPairRanges rg) {
+    const int b = blockIdx.x;
+    int c = 0;
+    while (c < 4 && b >= rg.b[c]) c++;
+    const int b0 = c ? rg.b[c - 1] : 0;
+    const int64_t t0 = (int64_t)(b - b0) * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)(rg.b[c] - b0) * blockDim.x;
+    if (c == 0) {
+        gs_pair_pairs<kGsPairU>(uh, ul, g.pairs, g.npair, t0, stride);
+    } else if (c == 1) {
+        for (int64_t t = t0; t < g.nquad; t += stride) {
+            const int4 q = g.quads[t];
             const int ix[4] = {q.x, q.y, q.z, q.w};
             seg_pair(uh, ul, ix, 4);
-        } else if (t < n3) {
-            const int4 q0 = g.octs[2 * (t - n2)], q1 = g.octs[2 * (t - n2) + 1];
+        }
+    } else if (c == 2) {
+        for (int64_t t = t0; t < g.noct; t += stride) {
+            const int4 q0 = g.octs[2 * t], q1 = g.octs[2 * t + 1];
             const int ix[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
             seg_pair(uh, ul, ix, 8);
-        } else if (t < n4) {
-            const int a = g.oth_off[t - n3], b = g.oth_off[t - n3 + 1];
-            seg_pair(uh, ul, g.oth_idx + a, b - a);
-        } else {
-            const int L = g.zero_idx[t - n4];
+        }
+    } else if (c == 3) {
+        for (int64_t t = t0; t < g.noth; t += stride) {
+            const int a = g.oth_off[t], e = g.oth_off[t + 1];
+            seg_pair(uh, ul, g.oth_idx + a, e - a);
+        }
+    } else {
+        for (int64_t t = t0; t < g.nzero; t += stride) {
+            const int L = g.zero_idx[t];
             uh[L] = 0.0f;
             ul[L] = 0.0f;
         }
@@ -263,7 +313,16 @@ int launch_pair_rest(sem_handle* h, cudaStream_t s) {
     const GSLists& g = h->gs;
     const int64_t total = g.npair + g.nquad + g.noct + g.noth + g.nzero;
     if (total > 0) {
-        gs_pair_kernel<<<grid_for(h, total, 256, 8), 256, 0, s>>>(v[6], v[7], g);
+        auto ctas = [](int64_t items, int per_thread) {
+            const int64_t per = 256LL * per_thread;
+            return (int)std::min<int64_t>((items + per - 1) / per, 1 << 20);
+        };
+        GsPairRanges rg;
+        const int n[5] = {ctas(g.npair, kGsPairU), ctas(g.nquad, 1), ctas(g.noct, 1), ctas(g.noth, 1),
+                          ctas(g.nzero, 1)};
+        int acc = 0;
+        for (int c = 0; c < 5; c++) rg.b[c] = (acc += n[c]);
+        gs_pair_kernel<<<acc, 256, 0, s>>>(v[6], v[7], g, rg);
         SEM_LAUNCH_CHECK("gs_pair_kernel");
         h->launches++;
     }
