@@ -457,9 +457,71 @@ static int prepare_batch_kernels(sem_handle* h) {
     return SEM_OK;
 }
 
-// K-B and K-C of one batched iteration.
+// Solve of every gather-scatter segment (that of its first copy: segments
+// never span two meshes), for the gather-scatter that skips converged solves.
+// Built once per batch handle, before any graph capture.
+static int ensure_segment_solves(sem_handle* h) {
+    BatchPlan& bp = h->batch;
+    if (bp.sid_ready || h->nsolve > 65535) return SEM_OK;
+    const GSLists& g = h->gs;
+    std::vector<int64_t> starts;
+    for (const MeshPart& p : h->parts) starts.push_back(p.loc_off);
+    auto solve_of = [&](int64_t L) {
+        return (uint16_t)(std::upper_bound(starts.begin(), starts.end(), L) - starts.begin() - 1);
+    };
+    std::vector<uint16_t> sid[5];
+    {
+        std::vector<int2> v((size_t)g.npair);
+        if (g.npair) SEM_CUDA_TRY(cudaMemcpy(v.data(), g.pairs, sizeof(int2) * g.npair, cudaMemcpyDeviceToHost));
+        for (auto& q : v) sid[0].push_back(solve_of(q.x));
+    }
+    {
+        std::vector<int4> v((size_t)g.nquad);
+        if (g.nquad) SEM_CUDA_TRY(cudaMemcpy(v.data(), g.quads, sizeof(int4) * g.nquad, cudaMemcpyDeviceToHost));
+        for (auto& q : v) sid[1].push_back(solve_of(q.x));
+    }
+    {
+        std::vector<int4> v((size_t)(2 * g.noct));
+        if (g.noct) SEM_CUDA_TRY(cudaMemcpy(v.data(), g.octs, sizeof(int4) * 2 * g.noct, cudaMemcpyDeviceToHost));
+        for (int64_t t = 0; t < g.noct; t++) sid[2].push_back(solve_of(v[2 * t].x));
+    }
+    {
+        std::vector<int> off((size_t)g.noth + 1), idx;
+        if (g.noth) {
+            SEM_CUDA_TRY(cudaMemcpy(off.data(), g.oth_off, sizeof(int) * (g.noth + 1), cudaMemcpyDeviceToHost));
+            idx.resize((size_t)off[g.noth]);
+            SEM_CUDA_TRY(cudaMemcpy(idx.data(), g.oth_idx, sizeof(int) * idx.size(), cudaMemcpyDeviceToHost));
+        }
+        for (int64_t t = 0; t < g.noth; t++) sid[3].push_back(solve_of(idx[off[t]]));
+    }
+    {
+        std::vector<int> v((size_t)g.nzero);
+        if (g.nzero) SEM_CUDA_TRY(cudaMemcpy(v.data(), g.zero_idx, sizeof(int) * g.nzero, cudaMemcpyDeviceToHost));
+        for (int L : v) sid[4].push_back(solve_of(L));
+    }
+    for (int c = 0; c < 5; c++) {
+        int rc = dalloc(h, &bp.sid[c], sid[c].size());
+        if (rc) return rc;
+        if (!sid[c].empty())
+            SEM_CUDA_TRY(cudaMemcpy(bp.sid[c], sid[c].data(), sizeof(uint16_t) * sid[c].size(), cudaMemcpyHostToDevice));
+    }
+    bp.sid_ready = true;
+    return SEM_OK;
+}
+
+// K-B and K-C of one batched iteration (K-B leaves the segments of the
+// solves already done: their w is not used).
 static int batch_kb_kc(sem_handle* h, bool fp32, CGState* st, cudaStream_t s) {
-    int rc = launch_gs(h, fp32 ? (void*)h->ws.w32 : (void*)h->ws.w, fp32, true, s);
+    void* w = fp32 ? (void*)h->ws.w32 : (void*)h->ws.w;
+    int rc;
+    if (h->batch.sid_ready) {
+        GsSkip sk;
+        for (int c = 0; c < 5; c++) sk.sid[c] = h->batch.sid[c];
+        sk.st = st;
+        rc = launch_gs_skip(h, w, fp32, sk, s);
+    } else {
+        rc = launch_gs(h, w, fp32, true, s);
+    }
     if (rc) return rc;
     if (fp32)
         upd_batch_kernel<float><<<grid_tiles(h), 256, 0, s>>>(h->ws.d32, h->ws.p32, h->ws.r32, h->ws.w32, h->ws.z32,
@@ -491,6 +553,7 @@ static int batch_graph(sem_handle* h, bool fp32, CGState* st, int chunk, cudaGra
     }
     if (!h->capture_stream) SEM_CUDA_TRY(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
     int rc = prepare_batch_kernels(h);
+    if (!rc) rc = ensure_segment_solves(h);  // no allocation during capture
     if (rc) return rc;
     for (auto& ev : h->ax_ev)
         if (!ev) SEM_CUDA_TRY(cudaEventCreate(&ev));

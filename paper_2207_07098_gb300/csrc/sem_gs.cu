@@ -20,14 +20,20 @@ namespace sem {
 // left to right in ascending local index.  The loads are latency-bound
 // (scattered 4- or 8-byte accesses), so each thread issues the index and value
 // loads of U segments before it sums and stores any.
+// segment t of a class belongs to a solve that is done (batched, skipping)
+__device__ __forceinline__ bool seg_done(const uint16_t* sid, const CGState* st, int64_t t) {
+    return sid && st[sid[t]].done;
+}
+
 template <typename T, int U>
 __device__ __forceinline__ void gs_pairs(T* __restrict__ u, const int2* __restrict__ idx, int64_t n, int64_t t0,
-                                         int64_t stride) {
+                                         int64_t stride, const uint16_t* sid = nullptr, const CGState* st = nullptr) {
     for (int64_t t = t0; t < n; t += stride * U) {
         int2 q[U];
         T a[U], b[U];
 #pragma unroll
-        for (int k = 0; k < U; k++) q[k] = (t + k * stride < n) ? idx[t + k * stride] : make_int2(-1, -1);
+        for (int k = 0; k < U; k++)
+            q[k] = (t + k * stride < n && !seg_done(sid, st, t + k * stride)) ? idx[t + k * stride] : make_int2(-1, -1);
 #pragma unroll
         for (int k = 0; k < U; k++)
             if (q[k].x >= 0) {
@@ -46,12 +52,14 @@ __device__ __forceinline__ void gs_pairs(T* __restrict__ u, const int2* __restri
 
 template <typename T, int U>
 __device__ __forceinline__ void gs_quads(T* __restrict__ u, const int4* __restrict__ idx, int64_t n, int64_t t0,
-                                         int64_t stride) {
+                                         int64_t stride, const uint16_t* sid = nullptr, const CGState* st = nullptr) {
     for (int64_t t = t0; t < n; t += stride * U) {
         int4 q[U];
         T a[U][4];
 #pragma unroll
-        for (int k = 0; k < U; k++) q[k] = (t + k * stride < n) ? idx[t + k * stride] : make_int4(-1, -1, -1, -1);
+        for (int k = 0; k < U; k++)
+            q[k] = (t + k * stride < n && !seg_done(sid, st, t + k * stride)) ? idx[t + k * stride]
+                                                                               : make_int4(-1, -1, -1, -1);
 #pragma unroll
         for (int k = 0; k < U; k++)
             if (q[k].x >= 0) {
@@ -83,7 +91,8 @@ constexpr int kGsThreads = 256;
 constexpr int kGsPairU = 4, kGsQuadU = 2, kGsZeroU = 4;
 
 template <typename T>
-__global__ void __launch_bounds__(kGsThreads) gs_kernel(T* __restrict__ u, GSLists g, int apply_mask, GsRanges rg) {
+__global__ void __launch_bounds__(kGsThreads) gs_kernel(T* __restrict__ u, GSLists g, int apply_mask, GsRanges rg,
+                                                        GsSkip sk) {
     const int b = blockIdx.x;
     int c = 0;
     while (c < 5 && b >= rg.b[c]) c++;
@@ -91,11 +100,12 @@ __global__ void __launch_bounds__(kGsThreads) gs_kernel(T* __restrict__ u, GSLis
     const int64_t t0 = (int64_t)(b - b0) * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)(rg.b[c] - b0) * blockDim.x;
     if (c == 0) {
-        gs_pairs<T, kGsPairU>(u, g.pairs, g.npair, t0, stride);
+        gs_pairs<T, kGsPairU>(u, g.pairs, g.npair, t0, stride, sk.sid[0], sk.st);
     } else if (c == 1) {
-        gs_quads<T, kGsQuadU>(u, g.quads, g.nquad, t0, stride);
+        gs_quads<T, kGsQuadU>(u, g.quads, g.nquad, t0, stride, sk.sid[1], sk.st);
     } else if (c == 2) {
         for (int64_t t = t0; t < g.noct; t += stride) {
+            if (seg_done(sk.sid[2], sk.st, t)) continue;
             const int4 q0 = g.octs[2 * t], q1 = g.octs[2 * t + 1];
             const T a0 = u[q0.x], a1 = u[q0.y], a2 = u[q0.z], a3 = u[q0.w];
             const T a4 = u[q1.x], a5 = u[q1.y], a6 = u[q1.z], a7 = u[q1.w];
@@ -105,6 +115,7 @@ __global__ void __launch_bounds__(kGsThreads) gs_kernel(T* __restrict__ u, GSLis
         }
     } else if (c == 3) {
         for (int64_t t = t0; t < g.noth; t += stride) {
+            if (seg_done(sk.sid[3], sk.st, t)) continue;
             const int a = g.oth_off[t], e = g.oth_off[t + 1];
             T sum = u[g.oth_idx[a]];
             for (int q = a + 1; q < e; q++) sum += u[g.oth_idx[q]];
@@ -115,7 +126,10 @@ __global__ void __launch_bounds__(kGsThreads) gs_kernel(T* __restrict__ u, GSLis
             for (int64_t t = t0; t < g.nzero; t += stride * kGsZeroU) {
                 int q[kGsZeroU];
 #pragma unroll
-                for (int k = 0; k < kGsZeroU; k++) q[k] = (t + k * stride < g.nzero) ? g.zero_idx[t + k * stride] : -1;
+                for (int k = 0; k < kGsZeroU; k++)
+                    q[k] = (t + k * stride < g.nzero && !seg_done(sk.sid[4], sk.st, t + k * stride))
+                               ? g.zero_idx[t + k * stride]
+                               : -1;
 #pragma unroll
                 for (int k = 0; k < kGsZeroU; k++)
                     if (q[k] >= 0) u[q[k]] = T(0);
@@ -136,7 +150,7 @@ static int ctas_for(int64_t items, int per_thread) {
     return (int)std::min<int64_t>((items + per_cta - 1) / per_cta, 1 << 20);
 }
 
-int launch_gs(sem_handle* h, void* u, bool fp32, bool apply_mask, cudaStream_t s) {
+static int launch_gs_impl(sem_handle* h, void* u, bool fp32, bool apply_mask, const GsSkip& sk, cudaStream_t s) {
     const GSLists& g = h->gs;
     const int64_t total = g.npair + g.nquad + g.noct + g.noth + (apply_mask ? g.nzero : g.ndir);
     if (total == 0) return SEM_OK;
@@ -147,12 +161,20 @@ int launch_gs(sem_handle* h, void* u, bool fp32, bool apply_mask, cudaStream_t s
     for (int c = 0; c < 5; c++) rg.b[c] = (acc += n[c]);
     rg.b[5] = acc;
     if (fp32)
-        gs_kernel<float><<<acc, kGsThreads, 0, s>>>((float*)u, g, apply_mask ? 1 : 0, rg);
+        gs_kernel<float><<<acc, kGsThreads, 0, s>>>((float*)u, g, apply_mask ? 1 : 0, rg, sk);
     else
-        gs_kernel<double><<<acc, kGsThreads, 0, s>>>((double*)u, g, apply_mask ? 1 : 0, rg);
+        gs_kernel<double><<<acc, kGsThreads, 0, s>>>((double*)u, g, apply_mask ? 1 : 0, rg, sk);
     SEM_LAUNCH_CHECK("gs_kernel");
     h->launches++;
     return SEM_OK;
+}
+
+int launch_gs(sem_handle* h, void* u, bool fp32, bool apply_mask, cudaStream_t s) {
+    return launch_gs_impl(h, u, fp32, apply_mask, GsSkip{}, s);
+}
+
+int launch_gs_skip(sem_handle* h, void* u, bool fp32, const GsSkip& skip, cudaStream_t s) {
+    return launch_gs_impl(h, u, fp32, true, skip, s);
 }
 
 // <a, b> = sum_L a_L b_L / mult_L in FP64, fixed-order grid reduction.

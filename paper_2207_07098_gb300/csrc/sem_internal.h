@@ -76,6 +76,14 @@ struct MeshPart {
 // ordered by their first local index; segments of Dirichlet nodes are kept as
 // CSR (they are only summed when the mask is not applied); `zero` lists every
 // local copy of every Dirichlet node.
+// Per-segment solve of a batch (index into the CG states) for each segment
+// class; a gather-scatter given these and the states skips the segments of
+// converged solves.  sid == nullptr: no skipping.
+struct GsSkip {
+    const uint16_t* sid[5] = {};  // pairs, quads, octets, other sizes, Dirichlet zero list
+    const struct CGState* st = nullptr;
+};
+
 struct GSLists {
     int2* pairs = nullptr;
     int4* quads = nullptr;
@@ -148,6 +156,9 @@ struct BatchPlan {
     int* bsgfirst = nullptr;  // [nsolve]
     int* bsgcount = nullptr;  // [nsolve]
     double* bgpart = nullptr; // [bngroups]
+    // solve of every gather-scatter segment (batches of at most 65535 solves)
+    uint16_t* sid[5] = {};
+    bool sid_ready = false;
     bool ready = false;
 };
 
@@ -236,6 +247,8 @@ int ensure_workspace(sem_handle* h, bool fp32);
 int launch_ax_local(sem_handle* h, const void* u, void* w, int precision, cudaStream_t s);
 // gs (+ mask)
 int launch_gs(sem_handle* h, void* u, bool fp32, bool apply_mask, cudaStream_t s);
+// masked QQ^T of a batch that leaves the segments of solves already done
+int launch_gs_skip(sem_handle* h, void* u, bool fp32, const GsSkip& skip, cudaStream_t s);
 // w = B u
 int launch_mass(sem_handle* h, const double* u, double* w, cudaStream_t s);
 int launch_mass32(sem_handle* h, const float* u, float* w, cudaStream_t s);

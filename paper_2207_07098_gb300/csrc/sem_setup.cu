@@ -330,6 +330,7 @@ static void free_handle(sem_handle* h) {
         cudaFree(g.loc); cudaFree(g.cnt); cudaFree(g.solve);
     }
     cudaFree(bp.bsgfirst); cudaFree(bp.bsgcount); cudaFree(bp.bgpart);
+    for (auto* p : bp.sid) cudaFree(p);
     cudaFree(bp.sgfirst); cudaFree(bp.sgcount); cudaFree(bp.tloc); cudaFree(bp.tlen); cudaFree(bp.tsolve);
     cudaFree(bp.stfirst); cudaFree(bp.stcount); cudaFree(bp.gpart); cudaFree(bp.tpart); cudaFree(bp.scount);
     cudaFree(bp.rrbb); cudaFree(bp.act); cudaFree(bp.itol);
