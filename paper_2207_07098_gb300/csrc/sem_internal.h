@@ -215,7 +215,7 @@ struct sem_handle {
     sem::GraphCache graph;
     sem::BatchPlan batch;
     cudaStream_t capture_stream = nullptr;
-    cudaEvent_t ax_ev[2] = {nullptr, nullptr};  // bracket the first K-A of each graph
+    cudaEvent_t ax_ev[2] = {nullptr, nullptr};  // bracket one K-A per graph (single: 2nd, batch: 1st)
     int64_t launches = 0;                        // kernels launched by this handle
     int test_stall = 0;                          // SEM_FLAG_TEST_STALL: bulk copies never complete a stage
     int ax_variant[2][sem::kMaxLx + 1];          // tuned operator variant per [fp32][lx], -1 = not tuned
