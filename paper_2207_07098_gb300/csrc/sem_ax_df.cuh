@@ -525,6 +525,14 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
             }
         }
         }
+        // factors of the column's first point, requested now and used after phase 1
+        const float* Ge = a.G2 + 12 * eoff + t2;
+        float g0h[6], g0l[6];
+#pragma unroll
+        for (int c = 0; c < 6; c++) {
+            g0h[c] = (active && valid) ? ld_stream(Ge + c * N3) : 0.f;
+            g0l[c] = (active && valid) ? ld_stream(Ge + (6 + c) * N3) : 0.f;
+        }
         __syncthreads();
         // phase 1: derivative lines ur (along i), us (along j), ut (along k)
         if (active) {
@@ -536,17 +544,26 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
                         tl + C::at(0, hi_, lo_), N2P);  // t-line (j=hi_, i=lo_)
         }
         __syncthreads();
-        // phase 2: (wr, ws, wt) = G (ur, us, ut) at the column's points
-        const float* Ge = a.G2 + 12 * eoff + t2;
+        // phase 2: (wr, ws, wt) = G (ur, us, ut) at the column's points; the
+        // factors of point k + 1 are loaded while point k is computed (those of
+        // point 0 were requested before phase 1)
         if (active) {
+            float gh[6], gl[6];
+#pragma unroll
+            for (int c = 0; c < 6; c++) {
+                gh[c] = g0h[c];
+                gl[c] = g0l[c];
+            }
 #pragma unroll
             for (int k = 0; k < LX; k++) {
                 const int q = C::at(k, hi_, lo_);
-                float gh[6], gl[6];
+                float nh[6], nl[6];
+                if (k + 1 < LX) {
 #pragma unroll
-                for (int c = 0; c < 6; c++) {
-                    gh[c] = valid ? ld_stream(Ge + c * N3 + k * N2) : 0.f;
-                    gl[c] = valid ? ld_stream(Ge + (6 + c) * N3 + k * N2) : 0.f;
+                    for (int c = 0; c < 6; c++) {
+                        nh[c] = valid ? ld_stream(Ge + c * N3 + (k + 1) * N2) : 0.f;
+                        nl[c] = valid ? ld_stream(Ge + (6 + c) * N3 + (k + 1) * N2) : 0.f;
+                    }
                 }
                 const float urh = rh[q], url = rl[q], ush = sh[q], usl = sl[q], uth = th[q], utl = tl[q];
                 float aS = 0.f, aE = 0.f, bS = 0.f, bE = 0.f, cS = 0.f, cE = 0.f;
@@ -568,6 +585,13 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
                 v = df_norm(cS, cE);
                 th[q] = v.h;
                 tl[q] = v.l;
+                if (k + 1 < LX) {
+#pragma unroll
+                    for (int c = 0; c < 6; c++) {
+                        gh[c] = nh[c];
+                        gl[c] = nl[c];
+                    }
+                }
             }
         }
         __syncthreads();
