@@ -66,9 +66,11 @@ typedef enum sem_status {
 
 /* Arithmetic of one operator application or of the inner solve. */
 typedef enum sem_precision {
-    SEM_FP64 = 0,        /* double data, FP64-accurate arithmetic */
+    SEM_FP64 = 0,        /* double data, the fastest FP64-class operator: FP32-pair
+                            arithmetic (48-bit, unit roundoff 2^-48) where the autotuner
+                            or SEM_FLAG_VARIANT(5 or 6) picks it, else native FP64 */
     SEM_FP32 = 1,        /* float data, FP32 arithmetic and accumulation */
-    SEM_FP64_NATIVE = 2  /* double data, plain FP64 CUDA-core arithmetic */
+    SEM_FP64_NATIVE = 2  /* double data, plain FP64 CUDA-core arithmetic (2^-53) */
 } sem_precision;
 
 typedef enum sem_solve_mode {
