@@ -199,19 +199,31 @@ __global__ void __launch_bounds__(AxCfg<LX>::THREADS) ax_kernel(AxParams<T> a) {
     const AxThread<LX> th;
     const int64_t ngroups = (a.E + EPC - 1) / EPC;
     double pap = 0.0;
+    float paph = 0.f, papl = 0.f;  // FP32 kernels: <p, A p> as a float pair (no FP64 per group)
     const T tbeta = (T)beta;
     __syncthreads();
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
         const int64_t e = g * EPC + th.el;
         const bool valid = th.active && e < a.E;
         const T pw = ax_group<T, LX, FUSED>(sm, th, e, valid, a.u, a.z, a.p, a.w, a.G, tbeta, first);
-        if (FUSED) pap += (double)pw;
+        if (FUSED) {
+            if constexpr (sizeof(T) == 4)
+                fpair_add(paph, papl, pw);
+            else
+                pap += (double)pw;
+        }
         __syncthreads();
     }
     if (FUSED) {
-        double v[1] = {pap};
         CGState* st = a.st;
-        grid_sum_finalize<1>(v, a.partials, a.counter, [&](double (&acc)[1]) { cg_set_alpha(st, acc[0]); });
+        if constexpr (sizeof(T) == 4) {
+            float h[1] = {paph}, l[1] = {papl};
+            grid_sum_finalize_pair<1>(h, l, a.partials, a.counter,
+                                      [&](double (&acc)[1]) { cg_set_alpha(st, acc[0]); });
+        } else {
+            double v[1] = {pap};
+            grid_sum_finalize<1>(v, a.partials, a.counter, [&](double (&acc)[1]) { cg_set_alpha(st, acc[0]); });
+        }
     }
 }
 

@@ -195,6 +195,7 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
         }
 
     double pap = 0.0;
+    float paph = 0.f, papl = 0.f;  // FP32 kernels: <p, A p> as a float pair (no FP64 per group)
     int64_t it = 0;
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x, it++) {
         const int s = (int)(it % NST);
@@ -304,7 +305,10 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
                 }
             }
         } else if (FUSED) {
-            pap += (double)pw;
+            if constexpr (sizeof(T) == 4)
+                fpair_add(paph, papl, pw);
+            else
+                pap += (double)pw;
         }
         __syncthreads();
     }
@@ -321,9 +325,15 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
         return;
     }
     if (FUSED && !BATCH) {
-        double v[1] = {pap};
         CGState* stt = a.st;
-        grid_sum_finalize<1>(v, a.partials, a.counter, [&](double (&acc)[1]) { cg_set_alpha(stt, acc[0]); });
+        if constexpr (sizeof(T) == 4) {
+            float h[1] = {paph}, l[1] = {papl};
+            grid_sum_finalize_pair<1>(h, l, a.partials, a.counter,
+                                      [&](double (&acc)[1]) { cg_set_alpha(stt, acc[0]); });
+        } else {
+            double v[1] = {pap};
+            grid_sum_finalize<1>(v, a.partials, a.counter, [&](double (&acc)[1]) { cg_set_alpha(stt, acc[0]); });
+        }
     }
 }
 

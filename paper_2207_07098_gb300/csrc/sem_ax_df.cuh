@@ -451,6 +451,7 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
     float* tl = arr + 7 * EPC * SLOT + slot;
     const int64_t ngroups = BATCH ? a.ngroups : (a.E + EPC - 1) / EPC;
     double pap = 0.0;
+    float paph = 0.f, papl = 0.f;  // pair form: <p, A p> as a float pair (no FP64 per group)
     __syncthreads();
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
         int64_t eoff;  // local index of this thread's element
@@ -621,7 +622,8 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
                     df_mac(S, Ee, cuh[k], cul[k], wvh, wvl);
                 }
             }
-            pw = (double)S + (double)Ee;
+            if (!BATCH) fpair_add2(paph, papl, S, Ee);
+            else pw = (double)S + (double)Ee;
         } else if (valid) {
 #pragma unroll
             for (int k = 0; k < LX; k++) {
@@ -651,15 +653,21 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
                     a.scount[sol] = 0u;
                 }
             }
-        } else if (FUSED) {
+        } else if (FUSED && !PAIR) {
             pap += pw;
         }
         __syncthreads();
     }
     if (FUSED && !BATCH) {
-        double v[1] = {pap};
         CGState* st = a.st;
-        grid_sum_finalize<1>(v, a.partials, a.counter, [&](double (&acc)[1]) { cg_set_alpha(st, acc[0]); });
+        if constexpr (PAIR) {
+            float h[1] = {paph}, l[1] = {papl};
+            grid_sum_finalize_pair<1>(h, l, a.partials, a.counter,
+                                      [&](double (&acc)[1]) { cg_set_alpha(st, acc[0]); });
+        } else {
+            double v[1] = {pap};
+            grid_sum_finalize<1>(v, a.partials, a.counter, [&](double (&acc)[1]) { cg_set_alpha(st, acc[0]); });
+        }
     }
 }
 

@@ -109,22 +109,42 @@ __global__ void __launch_bounds__(256) cg_update_kernel(UpdParams<T> a) {
         kahan(rzs, rzc, lrz);
         kahan(rrs, rrc, lrr);
     }
-    double rz = (double)rzs - (double)rzc, rr = (double)rrs - (double)rrc;
-    if (blockIdx.x == 0) {  // scalar tail
-        for (int64_t L = nv * W + threadIdx.x; L < a.n; L += blockDim.x) {
-            T x = a.x[L], r = a.r[L], z;
-            T lrz = T(0), lrr = T(0);
-            upd_point<T>(x, a.p[L], r, a.w[L], z, a.minv[L], inv[a.mult[L]], ta, lrz, lrr);
-            a.x[L] = x;
-            a.r[L] = r;
-            a.z[L] = z;
-            rz += (double)lrz;
-            rr += (double)lrr;
+    if constexpr (sizeof(T) == 4) {
+        // float pairs (sum, -compensation) to the block sums: no FP64 per thread
+        float h[2] = {rzs, rrs}, l[2] = {-rzc, -rrc};
+        if (blockIdx.x == 0) {  // scalar tail
+            for (int64_t L = nv * W + threadIdx.x; L < a.n; L += blockDim.x) {
+                T x = a.x[L], r = a.r[L], z;
+                T lrz = T(0), lrr = T(0);
+                upd_point<T>(x, a.p[L], r, a.w[L], z, a.minv[L], inv[a.mult[L]], ta, lrz, lrr);
+                a.x[L] = x;
+                a.r[L] = r;
+                a.z[L] = z;
+                fpair_add(h[0], l[0], lrz);
+                fpair_add(h[1], l[1], lrr);
+            }
         }
+        CGState* st = a.st;
+        grid_sum_finalize_pair<2>(h, l, a.partials, a.counter,
+                                  [&](double (&acc)[2]) { cg_set_rho(st, acc[0], acc[1]); });
+    } else {
+        double rz = (double)rzs - (double)rzc, rr = (double)rrs - (double)rrc;
+        if (blockIdx.x == 0) {  // scalar tail
+            for (int64_t L = nv * W + threadIdx.x; L < a.n; L += blockDim.x) {
+                T x = a.x[L], r = a.r[L], z;
+                T lrz = T(0), lrr = T(0);
+                upd_point<T>(x, a.p[L], r, a.w[L], z, a.minv[L], inv[a.mult[L]], ta, lrz, lrr);
+                a.x[L] = x;
+                a.r[L] = r;
+                a.z[L] = z;
+                rz += (double)lrz;
+                rr += (double)lrr;
+            }
+        }
+        double v[2] = {rz, rr};
+        CGState* st = a.st;
+        grid_sum_finalize<2>(v, a.partials, a.counter, [&](double (&acc)[2]) { cg_set_rho(st, acc[0], acc[1]); });
     }
-    double v[2] = {rz, rr};
-    CGState* st = a.st;
-    grid_sum_finalize<2>(v, a.partials, a.counter, [&](double (&acc)[2]) { cg_set_rho(st, acc[0], acc[1]); });
 }
 
 // CG start: z = Minv r; rho = <r,z>, rr = <r,r>, bb = <b,b>; state reset.

@@ -134,9 +134,9 @@ __global__ void __launch_bounds__(256) cg_update_pair_kernel(PairVecs a) {
             upd_pair_point(a.xh[L], a.xl[L], a.ph[L], a.pl[L], a.rh[L], a.rl[L], a.wh[L], a.wl[L], a.mh[L], a.ml[L],
                            a.zh[L], a.zl[L], inv[a.mult[L]], al, zS, zE, rS, rE);
     }
-    double v[2] = {(double)zS + (double)zE, (double)rS + (double)rE};
+    float h[2] = {zS, rS}, l[2] = {zE, rE};  // float pairs to the block sums: no FP64 per thread
     CGState* st = a.st;
-    grid_sum_finalize<2>(v, a.partials, a.counter, [&](double (&acc)[2]) { cg_set_rho(st, acc[0], acc[1]); });
+    grid_sum_finalize_pair<2>(h, l, a.partials, a.counter, [&](double (&acc)[2]) { cg_set_rho(st, acc[0], acc[1]); });
 }
 
 // QQ^T + mask on pairs: copies summed in ascending local index with TwoSum.

@@ -86,6 +86,94 @@ __device__ __forceinline__ void grid_sum_finalize(double (&v)[NV], double* parti
     }
 }
 
+// Float-pair accumulation for the block and grid reductions of FP32 kernels:
+// the FP64 pipe of this GPU runs at 1/64 of the FP32 rate, so per-thread sums
+// stay in (hi, lo) float pairs (TwoSum of the high parts, low parts in FP32,
+// ~2^-48 relative) and only thread 0 of each block and the last block go to
+// FP64.
+__device__ __forceinline__ void fpair_add(float& h, float& l, float v) {
+    const float s = h + v;
+    const float bb = s - h;
+    l += (h - (s - bb)) + (v - bb);
+    h = s;
+}
+__device__ __forceinline__ void fpair_add2(float& h, float& l, float bh, float bl) {
+    const float s = h + bh;
+    const float bb = s - h;
+    l += ((h - (s - bb)) + (bh - bb)) + bl;
+    h = s;
+}
+
+// Sum of NV float pairs over the block (fixed shuffle/tree order); valid in
+// thread 0.  `red` holds 2 * NV * 32 floats of shared memory.
+template <int NV>
+__device__ __forceinline__ void block_sum_pair(float (&h)[NV], float (&l)[NV], float* red) {
+#pragma unroll
+    for (int q = 0; q < NV; q++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_down_sync(0xffffffffu, h[q], o);
+            const float ol = __shfl_down_sync(0xffffffffu, l[q], o);
+            fpair_add2(h[q], l[q], oh, ol);
+        }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; q++) {
+            red[q * 32 + wid] = h[q];
+            red[(NV + q) * 32 + wid] = l[q];
+        }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; q++) {
+            h[q] = lane < nw ? red[q * 32 + lane] : 0.f;
+            l[q] = lane < nw ? red[(NV + q) * 32 + lane] : 0.f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float oh = __shfl_down_sync(0xffffffffu, h[q], o);
+                const float ol = __shfl_down_sync(0xffffffffu, l[q], o);
+                fpair_add2(h[q], l[q], oh, ol);
+            }
+        }
+    }
+}
+
+// grid_sum_finalize for per-thread float pairs: the block sums become FP64
+// partials in thread 0; the last block adds them in FP64 in block order.
+template <int NV, typename Fin>
+__device__ __forceinline__ void grid_sum_finalize_pair(float (&h)[NV], float (&l)[NV], double* partials,
+                                                       unsigned int* counter, Fin fin) {
+    __shared__ float redf[2 * NV * 32];
+    __shared__ double red[NV * 32];
+    __shared__ int is_last;
+    block_sum_pair<NV>(h, l, redf);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; q++) partials[q * kMaxPartials + blockIdx.x] = (double)h[q] + (double)l[q];
+        __threadfence();
+        const unsigned int t = atomicAdd(counter, 1u);
+        is_last = (t == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (is_last) {
+        __threadfence();
+        double acc[NV];
+#pragma unroll
+        for (int q = 0; q < NV; q++) acc[q] = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+#pragma unroll
+            for (int q = 0; q < NV; q++) acc[q] += __ldcg(&partials[q * kMaxPartials + b]);
+        block_sum<NV>(acc, red);
+        if (threadIdx.x == 0) {
+            fin(acc);
+            *counter = 0u;
+        }
+    }
+}
+
 // CG scalar step after <p, A p> is known (Sec. II-B, P-CG).
 __device__ __forceinline__ void cg_set_alpha(CGState* st, double pap) {
     st->pap = pap;
