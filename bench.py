@@ -51,6 +51,8 @@ def _args():
     ap.add_argument("--order", type=int, default=7)
     ap.add_argument("--no-extras", action="store_true", help="skip the comparison solves and ax-only bench")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="pin the operator kernel variant (SEM_FLAG_VARIANT) instead of autotuning")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--suite", action="store_true",
                     help="also measure the cube (FP64 and mixed), the 256-member batch and the annulus")
@@ -239,7 +241,8 @@ def run_ours(args):
     n = m.n_local
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
-    h = S.sem_setup(m.E, m.lx, m.coords, m.gid, m.mask, h1)
+    h = S.sem_setup(m.E, m.lx, m.coords, m.gid, m.mask, h1,
+                    0 if args.variant is None else S.SEM_FLAG_VARIANT(args.variant))
     setup_s = time.perf_counter() - t0
     info = S.sem_get_info(h)
     bd = torch.from_numpy(b).cuda()
@@ -315,7 +318,8 @@ def run_ours(args):
            "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+f64" if args.solver == "mixed" else "f64", "data": "synthetic",
            "config": _config(args, m, {"inner_tol": 1e-5 if args.solver == "mixed" else None,
-                                       "n_unique_free": info["n_free"], "parallelism": f"replicas x{ws}"}),
+                                       "n_unique_free": info["n_free"], "parallelism": f"replicas x{ws}",
+                                       "operator_variant": "autotuned" if args.variant is None else args.variant}),
            "iterations_per_solve": iters / args.steps, "outer_per_solve": stats[-1]["outer_iterations"],
            "relres_max": worst, "gpu_launches": launches, "e2e": e2e, "roofline": roofline, "clocks": clk,
            "setup_s": setup_s}

@@ -188,11 +188,11 @@ __global__ void __launch_bounds__(AxCfg<LX>::THREADS) ax_kernel(AxParams<T> a) {
     constexpr int EPC = C::EPC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const AxSmem<T, LX> sm(smem_raw);
-    double beta = 0.0;
     bool first = false;
+    __shared__ T s_tbeta;  // beta, divided and converted once by thread 0 (GB300's FP64 pipe is slow)
     if (FUSED) {
         if (a.st->done) return;  // uniform over the grid
-        beta = cg_beta(a.st);
+        if (threadIdx.x == 0) s_tbeta = (T)cg_beta(a.st);
         first = (a.st->iter == 0);
     }
     ax_load_d<T, LX>(sm.sD, a.D);
@@ -200,8 +200,8 @@ __global__ void __launch_bounds__(AxCfg<LX>::THREADS) ax_kernel(AxParams<T> a) {
     const int64_t ngroups = (a.E + EPC - 1) / EPC;
     double pap = 0.0;
     float paph = 0.f, papl = 0.f;  // FP32 kernels: <p, A p> as a float pair (no FP64 per group)
-    const T tbeta = (T)beta;
     __syncthreads();
+    const T tbeta = FUSED ? s_tbeta : T(0);
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
         const int64_t e = g * EPC + th.el;
         const bool valid = th.active && e < a.E;

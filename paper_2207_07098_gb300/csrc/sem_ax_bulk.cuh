@@ -134,12 +134,13 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
 
     double beta = 0.0;
     bool first = false;
+    __shared__ T s_tbeta;  // beta, divided and converted once by thread 0 (GB300's FP64 pipe is slow)
     if (FUSED && !BATCH) {
         if (a.st->done) return;  // uniform over the grid
-        beta = cg_beta(a.st);
+        if (threadIdx.x == 0) s_tbeta = (T)cg_beta(a.st);
         first = (a.st->iter == 0);
     }
-    T tbeta = (T)beta;
+    T tbeta = T(0);
     const int64_t ngroups = BATCH ? a.ngroups : (a.E + EPC - 1) / EPC;
     __shared__ double red[32];
     __shared__ int is_last;
@@ -179,6 +180,7 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
     }
     for (int t = tid; t < LX * LX; t += blockDim.x) sD[(t / LX) * DP + (t % LX)] = a.D[t];
     __syncthreads();
+    if (FUSED && !BATCH) tbeta = s_tbeta;
     // this thread's rows (r, s derivatives) and columns (transposed ones) of D
     T Dri[LX], Drj[LX], Dci[LX], Dcj[LX];
 #pragma unroll

@@ -428,13 +428,21 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
     constexpr int CF = dfl_coef_off(LX), CB = CF + 4 * P * P;  // forward (D) and backward (D^T) tables
     double beta = 0.0;
     bool first = false;
-    if (FUSED && !BATCH) {
-        if (a.st->done) return;
-        beta = cg_beta(a.st);
-        first = (a.st->iter == 0);
-    }
     __shared__ double red[32];
     __shared__ int is_last;
+    __shared__ double sb_beta;
+    __shared__ int sb_done, sb_first;
+    __shared__ float sb_b2[2];  // beta as a float pair (pair form)
+    if (FUSED && !BATCH) {
+        if (a.st->done) return;
+        // beta divided (and split) once by thread 0: GB300's FP64 pipe is slow
+        if (threadIdx.x == 0) {
+            sb_beta = cg_beta(a.st);
+            sb_b2[0] = (float)sb_beta;
+            sb_b2[1] = (float)(sb_beta - (double)sb_b2[0]);
+        }
+        first = (a.st->iter == 0);
+    }
     const int tid = threadIdx.x;
     const int el = tid / N2;
     const int t2 = tid - el * N2;          // column (i, j) in phase 0, line id in the transforms
@@ -453,6 +461,12 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
     double pap = 0.0;
     float paph = 0.f, papl = 0.f;  // pair form: <p, A p> as a float pair (no FP64 per group)
     __syncthreads();
+    dfl b2 = {0.f, 0.f};
+    if (FUSED && !BATCH) {
+        beta = sb_beta;
+        b2.h = sb_b2[0];
+        b2.l = sb_b2[1];
+    }
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
         int64_t eoff;  // local index of this thread's element
         bool valid;
@@ -460,11 +474,21 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
         if (BATCH) {
             sol = a.solve[g];
             if (FUSED) {
-                const CGState* stg = a.st + sol;
-                // no write to this solve's state can happen before all its groups are done
-                if (stg->done) continue;
-                beta = cg_beta(stg);
-                first = (stg->iter == 0);
+                // the solve's scalars, read and divided once per group by thread 0
+                if (threadIdx.x == 0) {
+                    const CGState* stg = a.st + sol;
+                    // no write to this solve's state can happen before all its groups are done
+                    sb_done = stg->done;
+                    sb_beta = sb_done ? 0.0 : cg_beta(stg);
+                    sb_first = (stg->iter == 0);
+                }
+                __syncthreads();
+                if (sb_done) {
+                    __syncthreads();  // thread 0 rewrites the scalars next round
+                    continue;
+                }
+                beta = sb_beta;
+                first = sb_first != 0;
             }
             eoff = a.loc[g] + (int64_t)el * N3;
             valid = active && el < a.cnt[g];
@@ -478,9 +502,6 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
         double ud[LX];
         float cuh[LX], cul[LX];  // the column of u as pairs (PAIR form)
         if (PAIR) {
-            dfl b2;
-            b2.h = (float)beta;
-            b2.l = (float)(beta - (double)b2.h);
 #pragma unroll
             for (int k = 0; k < LX; k++) {
                 float S = valid ? ld_stream(a.zh + base + k * N2) : 0.f;

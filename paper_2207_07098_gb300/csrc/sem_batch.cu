@@ -30,9 +30,34 @@ struct TileList {
 // Per-tile partials -> per-solve sums in tile order, by the CTA that finishes
 // the solve's last tile.  Returns true in thread 0 of that CTA with sums in acc.
 template <int NV>
+__device__ __forceinline__ bool tile_finalize_sums(const TileList& tl, int64_t t, int s, double (&v)[NV],
+                                                   double (&acc)[NV], double* red, int* is_last);
+
+template <int NV>
 __device__ __forceinline__ bool tile_finalize(const TileList& tl, int64_t t, int s, double (&v)[NV],
                                               double (&acc)[NV], double* red, int* is_last) {
     block_sum<NV>(v, red);
+    return tile_finalize_sums<NV>(tl, t, s, v, acc, red, is_last);
+}
+
+// As tile_finalize for per-thread float pairs (FP32 kernels): the block sum
+// stays in FP32 pairs and only thread 0 converts it to FP64.
+template <int NV>
+__device__ __forceinline__ bool tile_finalize_pair(const TileList& tl, int64_t t, int s, float (&h)[NV],
+                                                   float (&l)[NV], double (&acc)[NV], double* red, float* redf,
+                                                   int* is_last) {
+    block_sum_pair<NV>(h, l, redf);
+    double v[NV];
+#pragma unroll
+    for (int q = 0; q < NV; q++) v[q] = threadIdx.x == 0 ? (double)h[q] + (double)l[q] : 0.0;
+    return tile_finalize_sums<NV>(tl, t, s, v, acc, red, is_last);
+}
+
+// thread 0 holds the tile's block sums in v: store them; the last tile of the
+// solve adds all of its tiles' sums in tile order (result in thread 0's acc)
+template <int NV>
+__device__ __forceinline__ bool tile_finalize_sums(const TileList& tl, int64_t t, int s, double (&v)[NV],
+                                                   double (&acc)[NV], double* red, int* is_last) {
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int q = 0; q < NV; q++) tl.tpart[t * 3 + q] = v[q];
@@ -62,8 +87,13 @@ __global__ void __launch_bounds__(256) upd_batch_kernel(T* x, const T* p, T* r, 
                                                          const uint8_t* mult, CGState* st_base, TileList tl) {
     __shared__ T inv[256];
     __shared__ double red[64];
+    __shared__ float redf[128];
     __shared__ int is_last;
-    for (int m = threadIdx.x; m < 256; m += blockDim.x) inv[m] = m ? (T)(1.0 / m) : T(0);
+    // 1/m per copy count; FP32 kernels divide in FP32 (the same correctly
+    // rounded values for m < 256; an FP64 division per thread would occupy
+    // GB300's slow FP64 pipe at every launch)
+    for (int m = threadIdx.x; m < 256; m += blockDim.x)
+        inv[m] = m ? (sizeof(T) == 4 ? (T)(1.0f / (float)m) : (T)(1.0 / m)) : T(0);
     __syncthreads();
     for (int64_t t = blockIdx.x; t < tl.ntiles; t += gridDim.x) {
         const int s = tl.tsolve[t];
@@ -120,8 +150,16 @@ __global__ void __launch_bounds__(256) upd_batch_kernel(T* x, const T* p, T* r, 
         }
         if (!vec)
             for (int64_t L = l0 + threadIdx.x; L < l1; L += blockDim.x) point(L);
-        double v[2] = {(double)lrz, (double)lrr}, acc[2];
-        if (tile_finalize<2>(tl, t, s, v, acc, red, &is_last)) cg_set_rho(st, acc[0], acc[1]);
+        double acc[2];
+        bool last;
+        if constexpr (sizeof(T) == 4) {
+            float h[2] = {lrz, lrr}, l[2] = {0.f, 0.f};
+            last = tile_finalize_pair<2>(tl, t, s, h, l, acc, red, redf, &is_last);
+        } else {
+            double v[2] = {(double)lrz, (double)lrr};
+            last = tile_finalize<2>(tl, t, s, v, acc, red, &is_last);
+        }
+        if (last) cg_set_rho(st, acc[0], acc[1]);
         __syncthreads();
     }
 }

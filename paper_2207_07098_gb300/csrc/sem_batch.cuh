@@ -36,29 +36,50 @@ __global__ void __launch_bounds__(AxCfg<LX>::THREADS) ax_batch_kernel(BatchAxPar
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const AxSmem<T, LX> sm(smem_raw);
     __shared__ double red[32];
+    __shared__ float redf[64];
     __shared__ int is_last;
+    // the solve's scalars, read and converted once per group by thread 0 (an
+    // FP64 division per thread would load GB300's slow FP64 pipe)
+    __shared__ T s_tbeta;
+    __shared__ int s_done, s_first;
     ax_load_d<T, LX>(sm.sD, a.D);
     const AxThread<LX> th;
     __syncthreads();
     for (int64_t g = blockIdx.x; g < a.ngroups; g += gridDim.x) {
         const int s = a.solve[g];
         CGState* st = a.st + s;
-        double beta = 0.0;
+        T tbeta = T(0);
         bool first = false;
         if (FUSED) {
-            // no write to this solve's state can happen before all its groups are done
-            if (st->done) continue;
-            beta = cg_beta(st);
-            first = (st->iter == 0);
+            if (threadIdx.x == 0) {
+                // no write to this solve's state can happen before all its groups are done
+                s_done = st->done;
+                s_tbeta = s_done ? T(0) : (T)cg_beta(st);
+                s_first = (st->iter == 0);
+            }
+            __syncthreads();
+            if (s_done) {
+                __syncthreads();  // thread 0 rewrites the scalars next round
+                continue;
+            }
+            tbeta = s_tbeta;
+            first = s_first != 0;
         }
         const int64_t loc = a.loc[g];
         const bool valid = th.active && th.el < a.cnt[g];
         const T pw = ax_group<T, LX, FUSED>(sm, th, th.el, valid, FUSED ? nullptr : a.u + loc,
                                             FUSED ? a.z + loc : nullptr, FUSED ? a.p + loc : nullptr,
-                                            a.w + loc, a.G + 6 * loc, (T)beta, first);
+                                            a.w + loc, a.G + 6 * loc, tbeta, first);
         if (FUSED) {
-            double v[1] = {(double)pw};
-            block_sum<1>(v, red);
+            double v[1] = {0.0};
+            if constexpr (sizeof(T) == 4) {  // float-pair block sum: FP64 only in thread 0
+                float ph[1] = {(float)pw}, pl[1] = {0.f};
+                block_sum_pair<1>(ph, pl, redf);
+                v[0] = (double)ph[0] + (double)pl[0];
+            } else {
+                v[0] = (double)pw;
+                block_sum<1>(v, red);
+            }
             if (threadIdx.x == 0) {
                 a.gpart[a.goff + g] = v[0];
                 __threadfence();

@@ -67,10 +67,16 @@ __global__ void __launch_bounds__(256) cg_update_kernel(UpdParams<T> a) {
     using M = typename VT::M;
     constexpr int W = VT::W;
     if (a.st->done) return;
-    const T ta = (T)a.st->alpha;
     __shared__ T inv[256];
-    for (int m = threadIdx.x; m < 256; m += blockDim.x) inv[m] = m ? (T)(1.0 / m) : T(0);
+    __shared__ T s_ta;  // alpha, converted once by thread 0
+    // 1/m per copy count; FP32 kernels divide in FP32 (the same correctly
+    // rounded values for m < 256; an FP64 division per thread would occupy
+    // GB300's slow FP64 pipe at every launch)
+    for (int m = threadIdx.x; m < 256; m += blockDim.x)
+        inv[m] = m ? (sizeof(T) == 4 ? (T)(1.0f / (float)m) : (T)(1.0 / m)) : T(0);
+    if (threadIdx.x == 0) s_ta = (T)a.st->alpha;
     __syncthreads();
+    const T ta = s_ta;
     // per-thread partial sums in T with Kahan compensation, converted to FP64
     // once per thread (FP64 accumulation across threads and CTAs)
     T rzs = T(0), rzc = T(0), rrs = T(0), rrc = T(0);

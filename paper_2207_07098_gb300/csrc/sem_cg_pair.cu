@@ -103,11 +103,14 @@ __device__ __forceinline__ void upd_pair_point(float& xh, float& xl, float ph, f
 // Four points per thread and step (16-byte loads and stores of every plane).
 __global__ void __launch_bounds__(256) cg_update_pair_kernel(PairVecs a) {
     if (a.st->done) return;
-    dfl al;
-    split_accurate(a.st->alpha, al.h, al.l);
     __shared__ float inv[256];
+    __shared__ float s_al[2];  // alpha as a float pair, split once by thread 0
     for (int m = threadIdx.x; m < 256; m += blockDim.x) inv[m] = m ? 1.0f / (float)m : 0.0f;
+    if (threadIdx.x == 0) split_accurate(a.st->alpha, s_al[0], s_al[1]);
     __syncthreads();
+    dfl al;
+    al.h = s_al[0];
+    al.l = s_al[1];
     float zS = 0.f, zE = 0.f, rS = 0.f, rE = 0.f;
     const int64_t nv = a.n / 4;
     auto ld4 = [](const float* p, int64_t q) { return reinterpret_cast<const float4*>(p)[q]; };
