@@ -95,11 +95,14 @@ __global__ void __launch_bounds__(256) upd_batch_kernel(T* x, const T* p, T* r, 
     for (int m = threadIdx.x; m < 256; m += blockDim.x)
         inv[m] = m ? (sizeof(T) == 4 ? (T)(1.0f / (float)m) : (T)(1.0 / m)) : T(0);
     __syncthreads();
+    __shared__ T s_ta;  // the solve's alpha, converted once per tile by thread 0
     for (int64_t t = blockIdx.x; t < tl.ntiles; t += gridDim.x) {
         const int s = tl.tsolve[t];
         CGState* st = st_base + s;
-        if (st->done) continue;
-        const T ta = (T)st->alpha;
+        if (st->done) continue;  // uniform over the CTA
+        if (threadIdx.x == 0) s_ta = (T)st->alpha;
+        __syncthreads();
+        const T ta = s_ta;
         const int64_t l0 = tl.tloc[t], l1 = l0 + tl.tlen[t];
         T lrz = T(0), lrr = T(0);
         auto point = [&](int64_t L) {
