@@ -44,7 +44,25 @@ __device__ __forceinline__ dfl split_double(double x) {
     return r;
 }
 
-__device__ __forceinline__ double join(dfl a) { return (double)a.h + (double)a.l; }
+// Exact float -> double by bit manipulation (integer pipe; a conversion
+// instruction would run on the FP64 pipe, 1/64 of the FP32 rate on GB300).
+// Zeros and subnormal floats give a signed zero, Inf/NaN stay Inf/NaN.
+__device__ __forceinline__ double float_to_double_bits(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned sign = b & 0x80000000u, e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+    unsigned hi, lo;
+    if (e == 0u) {
+        hi = sign;
+        lo = 0u;
+    } else {
+        hi = sign | ((e == 0xffu ? 0x7ffu : e + 896u) << 20) | (m >> 3);
+        lo = m << 29;
+    }
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// pair -> double: two exact conversions and one FP64 addition
+__device__ __forceinline__ double join(dfl a) { return float_to_double_bits(a.h) + float_to_double_bits(a.l); }
 
 // acc += a * b with a, b pairs; (S, E) is an unnormalised running pair.
 __device__ __forceinline__ void df_mac(float& S, float& E, float ah, float al, float bh, float bl) {
@@ -649,7 +667,7 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
 #pragma unroll
             for (int k = 0; k < LX; k++) {
                 const int q = C::at(k, hi_, lo_);
-                const double wv = (double)uh[q] + (double)ul[q];
+                const double wv = float_to_double_bits(uh[q]) + float_to_double_bits(ul[q]);
                 st_keep<FUSED>(a.w + base + k * N2, wv);
                 if (FUSED) pw = fma(ud[k], wv, pw);
             }
