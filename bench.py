@@ -282,6 +282,8 @@ def run_ours(args):
     xh = torch.zeros(n, dtype=torch.float64).pin_memory()
     bh = torch.from_numpy(b).pin_memory()
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     t0 = time.perf_counter()
     e_it = 0
     for _ in range(args.steps):
@@ -290,7 +292,10 @@ def run_ours(args):
         e_it += s["iterations"]
     torch.cuda.synchronize()
     e_dt = time.perf_counter() - t0
-    e2e = {"value": ws * n * e_it / e_dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * n,
+    if dist:
+        dist.barrier()
+    e_ms, e_units = combine_ranks(e_dt * 1e3, float(n * e_it), dist, "cuda")  # max time, summed work
+    e2e = {"value": e_units / (e_ms * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * n,
            "d2h_bytes_per_step": 8 * n}
 
     peak, peak_kind = _peaks()
