@@ -77,6 +77,15 @@ __device__ __forceinline__ void df_mac(float& S, float& E, float ah, float al, f
     E += err + e;
 }
 
+// (S, E) = a * b as an unnormalised pair: the first term of an accumulation
+// (the TwoSum of df_mac against a zero pair would be exact and is skipped)
+__device__ __forceinline__ void df_mul(float& S, float& E, float ah, float al, float bh, float bl) {
+    S = ah * bh;
+    float e = fmaf(ah, bh, -S);
+    e = fmaf(ah, bl, e);
+    E = fmaf(al, bh, e);
+}
+
 __device__ __forceinline__ dfl df_norm(float S, float E) {
     dfl r;
     r.h = S + E;
@@ -173,13 +182,19 @@ __global__ void __launch_bounds__(DfCfg<LX>::THREADS) ax_df_kernel(DfParams a) {
         float wth[LX], wtl[LX];
 #pragma unroll
         for (int k = 0; k < LX; k++) {
-            float rS = 0.f, rE = 0.f, sS = 0.f, sE = 0.f, tS = 0.f, tE = 0.f;
+            float rS, rE, sS, sE, tS, tE;
 #pragma unroll
             for (int l = 0; l < LX; l++) {
                 const int qr = so + k * N2 + j * LX + l, qs = so + k * N2 + l * LX + i;
-                df_mac(rS, rE, sDh[i * DP + l], sDl[i * DP + l], suh[qr], sul[qr]);
-                df_mac(sS, sE, sDh[j * DP + l], sDl[j * DP + l], suh[qs], sul[qs]);
-                df_mac(tS, tE, sDh[k * DP + l], sDl[k * DP + l], uh[l], ul[l]);
+                if (l == 0) {
+                    df_mul(rS, rE, sDh[i * DP], sDl[i * DP], suh[qr], sul[qr]);
+                    df_mul(sS, sE, sDh[j * DP], sDl[j * DP], suh[qs], sul[qs]);
+                    df_mul(tS, tE, sDh[k * DP], sDl[k * DP], uh[0], ul[0]);
+                } else {
+                    df_mac(rS, rE, sDh[i * DP + l], sDl[i * DP + l], suh[qr], sul[qr]);
+                    df_mac(sS, sE, sDh[j * DP + l], sDl[j * DP + l], suh[qs], sul[qs]);
+                    df_mac(tS, tE, sDh[k * DP + l], sDl[k * DP + l], uh[l], ul[l]);
+                }
             }
             const dfl ur = df_norm(rS, rE), us = df_norm(sS, sE), ut = df_norm(tS, tE);
             float gh[6], gl[6];
@@ -188,15 +203,15 @@ __global__ void __launch_bounds__(DfCfg<LX>::THREADS) ax_df_kernel(DfParams a) {
                 gh[c] = valid ? ld_stream(Ge + c * N3 + k * N2) : 0.f;
                 gl[c] = valid ? ld_stream(Ge + (6 + c) * N3 + k * N2) : 0.f;
             }
-            float aS = 0.f, aE = 0.f, bS = 0.f, bE = 0.f, cS = 0.f, cE = 0.f;
+            float aS, aE, bS, bE, cS, cE;
             // (wr, ws, wt) = G (ur, us, ut), G = [[11 12 13] [12 22 23] [13 23 33]]
-            df_mac(aS, aE, gh[0], gl[0], ur.h, ur.l);
+            df_mul(aS, aE, gh[0], gl[0], ur.h, ur.l);
             df_mac(aS, aE, gh[1], gl[1], us.h, us.l);
             df_mac(aS, aE, gh[2], gl[2], ut.h, ut.l);
-            df_mac(bS, bE, gh[1], gl[1], ur.h, ur.l);
+            df_mul(bS, bE, gh[1], gl[1], ur.h, ur.l);
             df_mac(bS, bE, gh[3], gl[3], us.h, us.l);
             df_mac(bS, bE, gh[4], gl[4], ut.h, ut.l);
-            df_mac(cS, cE, gh[2], gl[2], ur.h, ur.l);
+            df_mul(cS, cE, gh[2], gl[2], ur.h, ur.l);
             df_mac(cS, cE, gh[4], gl[4], us.h, us.l);
             df_mac(cS, cE, gh[5], gl[5], ut.h, ut.l);
             const dfl wr = df_norm(aS, aE), ws = df_norm(bS, bE), wt = df_norm(cS, cE);
@@ -217,7 +232,8 @@ __global__ void __launch_bounds__(DfCfg<LX>::THREADS) ax_df_kernel(DfParams a) {
 #pragma unroll
             for (int l = 0; l < LX; l++) {
                 const int qr = so + k * N2 + j * LX + l, qs = so + k * N2 + l * LX + i;
-                df_mac(S, E, sDh[l * DP + i], sDl[l * DP + i], srh[qr], srl[qr]);
+                if (l == 0) df_mul(S, E, sDh[i], sDl[i], srh[qr], srl[qr]);
+                else df_mac(S, E, sDh[l * DP + i], sDl[l * DP + i], srh[qr], srl[qr]);
                 df_mac(S, E, sDh[l * DP + j], sDl[l * DP + j], ssh[qs], ssl[qs]);
                 df_mac(S, E, sDh[l * DP + k], sDl[l * DP + k], wth[l], wtl[l]);
             }
@@ -348,9 +364,11 @@ __device__ __forceinline__ void df_line(const float* xh, const float* xl, int xs
     }
 #pragma unroll
     for (int i = 0; i < P; i++) {
-        float sS = 0.f, sE = 0.f, tS = 0.f, tE = 0.f;
+        float sS, sE, tS, tE;
+        df_mul(sS, sE, Ah[i * P], Al[i * P], oh[0], ol[0]);
+        df_mul(tS, tE, Bh[i * P], Bl[i * P], eh[0], el[0]);
 #pragma unroll
-        for (int m = 0; m < P; m++) {
+        for (int m = 1; m < P; m++) {
             df_mac(sS, sE, Ah[i * P + m], Al[i * P + m], oh[m], ol[m]);
             df_mac(tS, tE, Bh[i * P + m], Bl[i * P + m], eh[m], el[m]);
         }
@@ -383,9 +401,11 @@ __device__ __forceinline__ void df_line_acc(const float* xh, const float* xl, in
     }
 #pragma unroll
     for (int i = 0; i < P; i++) {
-        float sS = 0.f, sE = 0.f, tS = 0.f, tE = 0.f;
+        float sS, sE, tS, tE;
+        df_mul(sS, sE, Ah[i * P], Al[i * P], oh[0], ol[0]);
+        df_mul(tS, tE, Bh[i * P], Bl[i * P], eh[0], el[0]);
 #pragma unroll
-        for (int m = 0; m < P; m++) {
+        for (int m = 1; m < P; m++) {
             df_mac(sS, sE, Ah[i * P + m], Al[i * P + m], oh[m], ol[m]);
             df_mac(tS, tE, Bh[i * P + m], Bl[i * P + m], eh[m], el[m]);
         }
@@ -606,14 +626,14 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
                     }
                 }
                 const float urh = rh[q], url = rl[q], ush = sh[q], usl = sl[q], uth = th[q], utl = tl[q];
-                float aS = 0.f, aE = 0.f, bS = 0.f, bE = 0.f, cS = 0.f, cE = 0.f;
-                df_mac(aS, aE, gh[0], gl[0], urh, url);
+                float aS, aE, bS, bE, cS, cE;
+                df_mul(aS, aE, gh[0], gl[0], urh, url);
                 df_mac(aS, aE, gh[1], gl[1], ush, usl);
                 df_mac(aS, aE, gh[2], gl[2], uth, utl);
-                df_mac(bS, bE, gh[1], gl[1], urh, url);
+                df_mul(bS, bE, gh[1], gl[1], urh, url);
                 df_mac(bS, bE, gh[3], gl[3], ush, usl);
                 df_mac(bS, bE, gh[4], gl[4], uth, utl);
-                df_mac(cS, cE, gh[2], gl[2], urh, url);
+                df_mul(cS, cE, gh[2], gl[2], urh, url);
                 df_mac(cS, cE, gh[4], gl[4], ush, usl);
                 df_mac(cS, cE, gh[5], gl[5], uth, utl);
                 dfl v = df_norm(aS, aE);
@@ -658,7 +678,8 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
                     const float wvh = uh[q], wvl = ul[q];
                     st_keep<true>(a.wh + base + k * N2, wvh);
                     st_keep<true>(a.wl + base + k * N2, wvl);
-                    df_mac(S, Ee, cuh[k], cul[k], wvh, wvl);
+                    if (k == 0) df_mul(S, Ee, cuh[0], cul[0], wvh, wvl);
+                    else df_mac(S, Ee, cuh[k], cul[k], wvh, wvl);
                 }
             }
             if (!BATCH) fpair_add2(paph, papl, S, Ee);
