@@ -135,6 +135,10 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
 
 
+# mixed refinement: FP32 inner CG to 1e-2, its direction kept across the FP64
+# refinement steps (residual replacement)
+MIXED_OPTS = {"inner_tol": 1e-2, "ir_carry": 1}
+
 def _workload(args):
     m, h1, b = W.deformed_cube(args.n, args.order, seed=2)
     name = f"deformed cube {args.n}^3 hex, N={args.order}, h1 wavy, random RHS"
@@ -248,7 +252,7 @@ def run_ours(args):
     bd = torch.from_numpy(b).cuda()
     xd = torch.zeros(n, dtype=torch.float64, device="cuda")
     mode = S.SEM_MODE_MIXED_IR if args.solver == "mixed" else S.SEM_MODE_FP64
-    opts = {"mode": mode, "tol": 1e-10, "inner_tol": 1e-5}
+    opts = {"mode": mode, "tol": 1e-10, **(MIXED_OPTS if args.solver == "mixed" else {})}
 
     def step():
         xd.zero_()
@@ -322,7 +326,9 @@ def run_ours(args):
            "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+f64" if args.solver == "mixed" else "f64", "data": "synthetic",
-           "config": _config(args, m, {"inner_tol": 1e-5 if args.solver == "mixed" else None,
+           "config": _config(args, m, {"inner_tol": MIXED_OPTS["inner_tol"] if args.solver == "mixed" else None,
+                                       "refinement": ("inner CG direction kept across FP64 refinement steps"
+                                                      if args.solver == "mixed" else None),
                                        "n_unique_free": info["n_free"], "parallelism": f"replicas x{ws}",
                                        "operator_variant": "autotuned" if args.variant is None else args.variant}),
            "iterations_per_solve": iters / args.steps, "outer_per_solve": stats[-1]["outer_iterations"],
@@ -348,9 +354,10 @@ def _extras(S, torch, h, m, bd, n, args, peak, stats, ms_timed):
     ex = {}
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
     res = {}
-    for name, mode, prec in (("fp64", S.SEM_MODE_FP64, S.SEM_FP64), ("mixed", S.SEM_MODE_MIXED_IR, S.SEM_FP64)):
+    for name, mode, extra in (("fp64", S.SEM_MODE_FP64, {}), ("mixed", S.SEM_MODE_MIXED_IR, MIXED_OPTS),
+                              ("mixed_restart_1e-5", S.SEM_MODE_MIXED_IR, {"inner_tol": 1e-5, "ir_carry": 0})):
         x.zero_()
-        st = S.sem_cg_solve(h, x, bd, {"mode": mode, "precision": prec, "tol": 1e-10, "inner_tol": 1e-5})
+        st = S.sem_cg_solve(h, x, bd, {"mode": mode, "precision": S.SEM_FP64, "tol": 1e-10, **extra})
         res[name] = {"time_ms": st["time_ms"], "iterations": st["iterations"], "outer": st["outer_iterations"],
                      "relres": st["relres"], "gdof_s": n * st["iterations"] / (st["time_ms"] * 1e-3) / 1e9,
                      "ax_ms": st["ax_ms"]}
@@ -436,7 +443,7 @@ def run_suite(args):
     S.load()
     out = {"suite": "sem_poisson", "data": "synthetic"}
     modes = (("fp64", {"mode": S.SEM_MODE_FP64, "tol": 1e-10}),
-             ("mixed", {"mode": S.SEM_MODE_MIXED_IR, "tol": 1e-10, "inner_tol": 1e-5}))
+             ("mixed", {"mode": S.SEM_MODE_MIXED_IR, "tol": 1e-10, **MIXED_OPTS}))
     # --- cube, manufactured solution
     m, f = W.cube_sines(4, 7)
     h = S.sem_setup(m.E, m.lx, m.coords, m.gid, m.mask, None)

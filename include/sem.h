@@ -94,13 +94,23 @@ typedef struct sem_solve_opts {
     int max_iter;        /* max CG iterations (FP64 mode) or inner iterations per
                             refinement step (mixed mode) */
     int mode;            /* sem_solve_mode */
-    double inner_tol;    /* mixed mode: inner relative tolerance (1e-5) */
+    double inner_tol;    /* mixed mode: inner relative tolerance (1e-2; with ir_carry = 0,
+                            about 1e-5 is fastest) */
     int max_outer;       /* mixed mode: max refinement steps (30) */
     int precision;       /* FP64 mode: SEM_FP64 or SEM_FP64_NATIVE operator */
     int use_graph;       /* capture the CG iterations in CUDA graphs (1) */
     int graph_chunk;     /* CG iterations per graph launch between host checks (32) */
     int autotune;        /* time the operator-kernel variants on this handle's data at the
                             first solve of each precision and keep the fastest (1) */
+    int ir_carry;        /* mixed mode: from the second refinement step on, the inner CG
+                            keeps its search direction (rescaled to the new residual)
+                            instead of restarting from p = z, i.e. it continues as CG whose
+                            residual was replaced by the true FP64 one (residual
+                            replacement).  The inner iterations then add up to about the
+                            FP64 PCG count.  It pays with frequent replacements (inner_tol
+                            ~1e-2); with tight inner tolerances the replaced residual
+                            differs too much from the recursive one and restarting (0) is
+                            faster (1) */
 } sem_solve_opts;
 
 typedef struct sem_solve_stats {

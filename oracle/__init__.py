@@ -97,7 +97,7 @@ def configure(lib):
     lib.or_pcg.argtypes = [ctypes.c_void_p, _dp, _dp, ctypes.c_double, ctypes.c_int, _ip, _dp, _dp]
     lib.or_ir.restype = ctypes.c_int
     lib.or_ir.argtypes = [ctypes.c_void_p, _dp, _dp, ctypes.c_double, ctypes.c_double,
-                          ctypes.c_int, ctypes.c_int, _ip, _ip, _dp, _dp]
+                          ctypes.c_int, ctypes.c_int, ctypes.c_int, _ip, _ip, _dp, _dp]
     lib.or_threads.restype = ctypes.c_int
     return lib
 
@@ -233,14 +233,14 @@ class Problem:
         return x, info
 
     def ir(self, b, x0=None, tol: float = 1e-10, inner_tol: float = 1e-5, max_outer: int = 50,
-           max_inner: int = 100000):
+           max_inner: int = 100000, carry: bool = False):
         b = np.ascontiguousarray(b, dtype=np.float64)
         x = np.zeros(self.n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
         oi = ctypes.c_int(0)
         ii = ctypes.c_int(0)
         rr = ctypes.c_double(0.0)
         hist = np.zeros(max_outer + 1)
-        st = self.lib.or_ir(self.h, _d(b), _d(x), tol, inner_tol, max_outer, max_inner,
+        st = self.lib.or_ir(self.h, _d(b), _d(x), tol, inner_tol, max_outer, max_inner, 1 if carry else 0,
                             ctypes.byref(oi), ctypes.byref(ii), ctypes.byref(rr), _d(hist))
         return x, dict(status=int(st), outer=int(oi.value), inner=int(ii.value),
                        relres=float(rr.value), outer_hist=hist[: oi.value])

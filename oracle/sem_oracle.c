@@ -590,21 +590,29 @@ static double dot_f32(const or_problem* p, const float* a, const float* b) {
 }
 
 /* inner Jacobi-PCG in FP32 from d = 0; returns iterations */
+/* FP32 PCG from d = 0.  pp is the search direction (n floats, owned by the
+ * caller).  *carry <= 0: a fresh start (first direction = z).  *carry > 0:
+ * pp holds the direction of an earlier solve and *carry the <r, z> that went
+ * into it, rescaled to this right-hand side's units; the first direction is
+ * then z + (<r, z> / *carry) pp, i.e. CG continues after its residual was
+ * replaced by b (residual replacement).  On return *carry = the <r, z> of the
+ * last direction taken (0 if none). */
 static int pcg_f32(const or_problem* p, const or_f32* f, const float* b, float* d,
-                   double tol, int max_iter) {
+                   double tol, int max_iter, float* pp, double* carry) {
     const int64_t n = p->n;
     float* r = (float*)malloc(sizeof(float) * n);
     float* z = (float*)malloc(sizeof(float) * n);
-    float* pp = (float*)calloc((size_t)n, sizeof(float));
     float* w = (float*)malloc(sizeof(float) * n);
     for (int64_t L = 0; L < n; L++) { r[L] = b[L]; d[L] = 0.0f; }
     const double bnorm = sqrt(dot_f32(p, b, b));
-    double rho_old = 1.0;
+    const int carried = *carry > 0.0;
+    double rho_old = carried ? *carry : 1.0;
+    *carry = 0.0;
     int it = 0;
     while (bnorm > 0.0 && it < max_iter) {
         for (int64_t L = 0; L < n; L++) z[L] = f->minv[L] * r[L];
         const double rho = dot_f32(p, r, z);
-        const float beta = (it == 0) ? 0.0f : (float)(rho / rho_old);
+        const float beta = (it == 0 && !carried) ? 0.0f : (float)(rho / rho_old);
         for (int64_t L = 0; L < n; L++) pp[L] = z[L] + beta * pp[L];
         ax_local_f32(p, f, pp, w);
         gs_f32(p, w);
@@ -616,16 +624,17 @@ static int pcg_f32(const or_problem* p, const or_f32* f, const float* b, float* 
             r[L] -= alpha * w[L];
         }
         rho_old = rho;
+        *carry = rho;
         it++;
         if (sqrt(dot_f32(p, r, r)) / bnorm <= tol) break;
     }
-    free(r); free(z); free(pp); free(w);
+    free(r); free(z); free(w);
     return it;
 }
 
 int or_ir(const or_problem* p, const double* b, double* x, double tol, double inner_tol,
-          int max_outer, int max_inner, int* outer_iters, int* inner_iters, double* relres,
-          double* outer_hist) {
+          int max_outer, int max_inner, int carry, int* outer_iters, int* inner_iters,
+          double* relres, double* outer_hist) {
     const int64_t n = p->n;
     const int lx = p->lx;
     or_f32 f;
@@ -640,9 +649,10 @@ int or_ir(const or_problem* p, const double* b, double* x, double tol, double in
     double* w = (double*)malloc(sizeof(double) * n);
     float* r32 = (float*)malloc(sizeof(float) * n);
     float* d32 = (float*)malloc(sizeof(float) * n);
+    float* pp = (float*)calloc((size_t)n, sizeof(float));
     const double bnorm = sqrt(or_dot(p, b, b));
     int status = 1, outer = 0, inner = 0;
-    double prev = INFINITY, rel = 0.0;
+    double prev = INFINITY, rel = 0.0, rn_prev = 0.0, rho_carry = 0.0;
     for (;;) {
         or_ax(p, x, w);
         for (int64_t L = 0; L < n; L++) r[L] = b[L] - w[L];
@@ -654,14 +664,19 @@ int or_ir(const or_problem* p, const double* b, double* x, double tol, double in
         if (outer > 0 && rel > 0.5 * prev) { status = 3; break; }
         prev = rel;
         for (int64_t L = 0; L < n; L++) r32[L] = (float)(r[L] / rn);
-        inner += pcg_f32(p, &f, r32, d32, inner_tol, max_inner);
+        /* carried direction: the previous step's units were 1/rn_prev, these
+         * are 1/rn, so pp scales by c = rn_prev / rn and its <r, z> by c^2;
+         * folding one c into the <r, z> leaves pp as it is */
+        rho_carry = (carry && outer > 0 && rho_carry > 0.0) ? rho_carry * (rn_prev / rn) : 0.0;
+        inner += pcg_f32(p, &f, r32, d32, inner_tol, max_inner, pp, &rho_carry);
         for (int64_t L = 0; L < n; L++) x[L] += rn * (double)d32[L];
+        rn_prev = rn;
         outer++;
     }
     *outer_iters = outer;
     *inner_iters = inner;
     *relres = rel;
     free(f.D); free(f.G); free(f.h1); free(f.minv);
-    free(r); free(w); free(r32); free(d32);
+    free(r); free(w); free(r32); free(d32); free(pp);
     return status;
 }

@@ -81,10 +81,17 @@ int or_pcg(const or_problem* p, const double* b, double* x, double tol, int max_
  * A d = r/||r|| to inner_tol, then x += ||r|| d.  Stops when the true FP64
  * residual ||b - A x||/||b|| <= tol, after max_outer outer steps, or when an
  * outer step fails to halve the residual (stagnation, return 3).
- * outer_hist receives the true relative residual after each outer step. */
+ * outer_hist receives the true relative residual after each outer step.
+ * carry = 0: every inner solve starts CG afresh (first direction z).
+ * carry = 1: from the second outer step on, the inner CG keeps the search
+ * direction of the previous step (rescaled to the new residual's units) and
+ * continues as CG whose residual was replaced by the true one (residual
+ * replacement, van der Vorst and Ye 2000).  The paper's Sec. V outlook names
+ * lower precision without giving an algorithm: both variants are this
+ * implementation's reading. */
 int or_ir(const or_problem* p, const double* b, double* x, double tol, double inner_tol,
-          int max_outer, int max_inner, int* outer_iters, int* inner_iters, double* relres,
-          double* outer_hist);
+          int max_outer, int max_inner, int carry, int* outer_iters, int* inner_iters,
+          double* relres, double* outer_hist);
 
 /* Number of OpenMP threads the element loops use (1 without OpenMP). */
 int or_threads(void);

@@ -45,7 +45,8 @@ class sem_info(ctypes.Structure):
 class sem_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mode", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("precision", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("graph_chunk", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("graph_chunk", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("ir_carry", ctypes.c_int)]
 
 
 class sem_solve_stats(ctypes.Structure):

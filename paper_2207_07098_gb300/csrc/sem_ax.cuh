@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(AxCfg<LX>::THREADS) ax_kernel(AxParams<T> a) {
     if (FUSED) {
         if (a.st->done) return;  // uniform over the grid
         if (threadIdx.x == 0) s_tbeta = (T)cg_beta(a.st);
-        first = (a.st->iter == 0);
+        first = cg_first(a.st);
     }
     ax_load_d<T, LX>(sm.sD, a.D);
     const AxThread<LX> th;

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
     if (FUSED && !BATCH) {
         if (a.st->done) return;  // uniform over the grid
         if (threadIdx.x == 0) s_tbeta = (T)cg_beta(a.st);
-        first = (a.st->iter == 0);
+        first = cg_first(a.st);
     }
     T tbeta = T(0);
     const int64_t ngroups = BATCH ? a.ngroups : (a.E + EPC - 1) / EPC;
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
                 continue;
             }
             beta = cg_beta(stg);
-            first = (stg->iter == 0);
+            first = cg_first(stg);
             tbeta = (T)beta;
         }
         const T* st = stage0 + s * C::STAGE;

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(DfCfg<LX>::THREADS) ax_df_kernel(DfParams a) {
     if (FUSED) {
         if (a.st->done) return;
         beta = cg_beta(a.st);
-        first = (a.st->iter == 0);
+        first = cg_first(a.st);
     }
     for (int t = threadIdx.x; t < LX * LX; t += blockDim.x) {
         sDh[(t / LX) * DP + (t % LX)] = a.D2[t];
@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
             sb_b2[0] = (float)sb_beta;
             sb_b2[1] = (float)(sb_beta - (double)sb_b2[0]);
         }
-        first = (a.st->iter == 0);
+        first = cg_first(a.st);
     }
     const int tid = threadIdx.x;
     const int el = tid / N2;
@@ -518,7 +518,7 @@ __global__ void __launch_bounds__(DflCfg<LX>::THREADS) ax_dfl_kernel(DflParams a
                     // no write to this solve's state can happen before all its groups are done
                     sb_done = stg->done;
                     sb_beta = sb_done ? 0.0 : cg_beta(stg);
-                    sb_first = (stg->iter == 0);
+                    sb_first = cg_first(stg);
                 }
                 __syncthreads();
                 if (sb_done) {

@@ -168,12 +168,13 @@ __global__ void __launch_bounds__(256) upd_batch_kernel(T* x, const T* p, T* r, 
 }
 
 // CG start per solve: z = Minv r; rho, rr, bb.  Solves with act[s] == 0 are
-// marked done without work.
+// marked done without work.  carry (may be null): per solve, > 0 keeps the
+// solve's direction p with that rescaling, as cg_init_kernel's carry_c.
 template <typename T>
 __global__ void __launch_bounds__(256) init_batch_kernel(const T* b, const T* r, T* z, const T* minv,
                                                           const uint8_t* mult, CGState* st_base, TileList tl,
                                                           const int* act, double tol, const double* tol_per_solve,
-                                                          int max_iter) {
+                                                          int max_iter, const double* carry = nullptr) {
     __shared__ double inv[256];
     __shared__ double red[96];
     __shared__ int is_last;
@@ -187,6 +188,7 @@ __global__ void __launch_bounds__(256) init_batch_kernel(const T* b, const T* r,
                 st->done = 1;
                 st->status = SEM_OK;
                 st->iter = 0;
+                st->carry = 0;
                 st->max_iter = max_iter;
             }
             continue;
@@ -203,8 +205,10 @@ __global__ void __launch_bounds__(256) init_batch_kernel(const T* b, const T* r,
         }
         if (tile_finalize<3>(tl, t, s, v, acc, red, &is_last)) {
             if (tol_per_solve) tol = tol_per_solve[s];
+            const double cc = carry ? carry[s] : 0.0, rho_prev = st->rho_old;
             st->rho = acc[0];
-            st->rho_old = 1.0;
+            st->carry = cc > 0.0 ? 1 : 0;
+            st->rho_old = cc > 0.0 ? rho_prev * cc : 1.0;
             st->rr = acc[1];
             st->bb = acc[2];
             st->tol2 = tol * tol * acc[2];
@@ -369,7 +373,7 @@ static int build_plan(sem_handle* h) {
         (rc = dalloc(h, &bp.tsolve, tsol.size())) || (rc = dalloc(h, &bp.stfirst, ns)) ||
         (rc = dalloc(h, &bp.stcount, ns)) || (rc = dalloc(h, &bp.tpart, (size_t)bp.ntiles * 3)) || (rc = dalloc(h, &bp.scount, ns)) ||
         (rc = dalloc(h, &bp.rrbb, (size_t)2 * ns)) || (rc = dalloc(h, &bp.act, ns)) ||
-        (rc = dalloc(h, &bp.itol, ns)))
+        (rc = dalloc(h, &bp.itol, ns)) || (rc = dalloc(h, &bp.carry, ns)))
         return rc;
     SEM_CUDA_TRY(cudaMemcpy(bp.tloc, tloc.data(), tloc.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
     SEM_CUDA_TRY(cudaMemcpy(bp.tlen, tlen.data(), tlen.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -761,7 +765,8 @@ static int solve_batch(sem_handle* h, double* x_user, const double* b_user, cons
     } else {
         std::vector<double> prev(ns, INFINITY);
         std::vector<int> act(ns, 0), fin(ns, 0);
-        std::vector<double> itol(ns, o.inner_tol);
+        std::vector<double> itol(ns, o.inner_tol), carry(ns, 0.0), rn_prev(ns, 0.0);
+        std::vector<int> can_carry(ns, 0);
         if ((rc = read_rrbb())) return rc;
         CGState* inner = h->state + ns;
         for (int round = 0;; round++) {
@@ -775,16 +780,26 @@ static int solve_batch(sem_handle* h, double* x_user, const double* b_user, cons
                 else if (bb == 0.0 || rel <= o.tol) { status[q] = SEM_OK; fin[q] = 1; }
                 else if (outer[q] >= o.max_outer) { status[q] = SEM_ENOTCONV; fin[q] = 1; }
                 else if (outer[q] > 0 && rel > 0.5 * prev[q]) { status[q] = SEM_ESTAGNATE; fin[q] = 1; }
-                else { act[q] = 1; prev[q] = rel; itol[q] = inner_tolerance(o, rel); nact++; }
+                else {
+                    act[q] = 1;
+                    prev[q] = rel;
+                    itol[q] = inner_tolerance(o, rel);
+                    // kept direction: its units were ||r_prev|| / ||r|| times smaller
+                    const double rn = std::sqrt(rrbb[2 * q]);
+                    carry[q] = (o.ir_carry && can_carry[q] && rn > 0.0) ? rn_prev[q] / rn : 0.0;
+                    rn_prev[q] = rn;
+                    nact++;
+                }
             }
             if (nact == 0) break;
             SEM_CUDA_TRY(cudaMemcpyAsync(bp.act, act.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
             SEM_CUDA_TRY(cudaMemcpyAsync(bp.itol, itol.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, s));
+            SEM_CUDA_TRY(cudaMemcpyAsync(bp.carry, carry.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, s));
             prepare_batch_kernel<<<grid_tiles(h), 256, 0, s>>>(h->ws.r, h->ws.b32, h->ws.r32, h->ws.d32, tiles(h),
                                                                bp.act, bp.rrbb);
             init_batch_kernel<float><<<grid_tiles(h), 256, 0, s>>>(h->ws.b32, h->ws.r32, h->ws.z32, h->minv32, h->mult,
                                                                     inner, tiles(h), bp.act, o.inner_tol, bp.itol,
-                                                                    o.max_iter);
+                                                                    o.max_iter, bp.carry);
             SEM_LAUNCH_CHECK("batch refinement prepare");
             h->launches += 2;
             if ((rc = batch_loop(h, true, inner, o, s, hs, &ax_sum, &ax_n))) return rc;
@@ -792,6 +807,7 @@ static int solve_batch(sem_handle* h, double* x_user, const double* b_user, cons
                 if (act[q]) {
                     iters[q] += hs[q].iter;
                     outer[q]++;
+                    can_carry[q] = hs[q].status == SEM_OK && hs[q].iter > 0;
                 }
             correct_batch_kernel<<<grid_tiles(h), 256, 0, s>>>(h->ws.x, h->ws.d32, tiles(h), bp.act, bp.rrbb);
             SEM_LAUNCH_CHECK("correct_batch_kernel");

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(AxCfg<LX>::THREADS) ax_batch_kernel(BatchAxPar
                 // no write to this solve's state can happen before all its groups are done
                 s_done = st->done;
                 s_tbeta = s_done ? T(0) : (T)cg_beta(st);
-                s_first = (st->iter == 0);
+                s_first = cg_first(st);
             }
             __syncthreads();
             if (s_done) {

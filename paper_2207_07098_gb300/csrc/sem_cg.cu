@@ -154,12 +154,18 @@ __global__ void __launch_bounds__(256) cg_update_kernel(UpdParams<T> a) {
 }
 
 // CG start: z = Minv r; rho = <r,z>, rr = <r,r>, bb = <b,b>; state reset.
+// carry_c > 0: the direction p in memory is kept from the previous solve on
+// this state, whose units were carry_c times smaller than this one's (the
+// ratio of the two right-hand sides' scalings); the next iteration takes
+// p = z + rho / (rho_old_prev * carry_c) p, which is the continued CG step
+// with p rescaled by carry_c and its rho_old by carry_c^2 (residual
+// replacement).  carry_c <= 0: a fresh start (p = z).
 template <typename T>
 __global__ void __launch_bounds__(256) cg_init_kernel(const T* __restrict__ b, const T* __restrict__ r,
                                                       T* __restrict__ z, const T* __restrict__ minv,
                                                       const uint8_t* __restrict__ mult, int64_t n, double tol,
                                                       int max_iter, CGState* st, double* partials,
-                                                      unsigned int* counter) {
+                                                      unsigned int* counter, double carry_c) {
     __shared__ double inv[256];
     for (int m = threadIdx.x; m < 256; m += blockDim.x) inv[m] = m ? 1.0 / m : 0.0;
     __syncthreads();
@@ -175,8 +181,10 @@ __global__ void __launch_bounds__(256) cg_init_kernel(const T* __restrict__ b, c
         v[2] = fma(bv * bv, iv, v[2]);
     }
     grid_sum_finalize<3>(v, partials, counter, [&](double (&acc)[3]) {
+        const double rho_prev = st->rho_old;  // <r, z> that built the kept direction
         st->rho = acc[0];
-        st->rho_old = 1.0;
+        st->carry = carry_c > 0.0 ? 1 : 0;
+        st->rho_old = carry_c > 0.0 ? rho_prev * carry_c : 1.0;
         st->rr = acc[1];
         st->bb = acc[2];
         st->tol2 = tol * tol * acc[2];
@@ -458,7 +466,7 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
             } else {
                 cg_init_kernel<double><<<grid_for(h, n, 256, 4), 256, 0, s>>>(
                     h->ws.b, h->ws.r, h->ws.z, h->minv64, h->mult, n, o.tol, o.max_iter - used, h->state,
-                    h->partials, h->counters + 5);
+                    h->partials, h->counters + 5, 0.0);
                 SEM_LAUNCH_CHECK("cg_init_kernel");
                 h->launches++;
             }
@@ -470,8 +478,10 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
         }
         st.iterations = used;
     } else {
-        // FP64 refinement around an FP32 inner CG
-        double prev = INFINITY;
+        // FP64 refinement around an FP32 inner CG; with ir_carry the inner CG
+        // keeps its direction across steps (residual replacement)
+        double prev = INFINITY, rn_prev = 0.0;
+        bool can_carry = false;
         int outer = 0, inner = 0;
         for (;;) {
             if ((rc = true_residual(h, h->ws.x, h->ws.b, rrbb, s))) return rc;
@@ -485,15 +495,21 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
             if (outer >= o.max_outer) { status = SEM_ENOTCONV; break; }
             if (outer > 0 && rel > 0.5 * prev) { status = SEM_ESTAGNATE; break; }
             prev = rel;
+            // the inner right-hand side is r / ||r||: the kept direction's units
+            // were ||r_prev|| / ||r|| times smaller than the new ones
+            const double rn = std::sqrt(hb[0]);
+            const double carry_c = (o.ir_carry && can_carry && rn > 0.0) ? rn_prev / rn : 0.0;
             ir_prepare_kernel<<<grid_for(h, n, 256, 8), 256, 0, s>>>(h->ws.r, rrbb, h->ws.b32, h->ws.r32,
                                                                      h->ws.d32, n);
             cg_init_kernel<float><<<grid_for(h, n, 256, 4), 256, 0, s>>>(
                 h->ws.b32, h->ws.r32, h->ws.z32, h->minv32, h->mult, n, inner_tolerance(o, rel), o.max_iter,
-                h->state + 1, h->partials, h->counters + 5);
+                h->state + 1, h->partials, h->counters + 5, carry_c);
             SEM_LAUNCH_CHECK("ir prepare");
             h->launches += 2;
             if ((rc = run_cg_loop(h, SEM_FP32, o, 1, s, &hs, &tm))) return rc;
             inner += hs.iter;
+            can_carry = hs.status == SEM_OK && hs.iter > 0;
+            rn_prev = rn;
             ir_correct_kernel<<<grid_for(h, n, 256, 8), 256, 0, s>>>(h->ws.x, h->ws.d32, rrbb, n);
             SEM_LAUNCH_CHECK("ir_correct_kernel");
             h->launches++;

@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(256) init_pair_kernel(const double* __restrict
         st->alpha = 0.0;
         st->pap = 0.0;
         st->iter = 0;
+        st->carry = 0;
         st->max_iter = max_iter;
         const bool conv = (acc[2] == 0.0 || acc[1] <= st->tol2);
         st->done = (conv || max_iter <= 0) ? 1 : 0;

@@ -204,8 +204,11 @@ __device__ __forceinline__ void cg_set_rho(CGState* st, double rz, double rr) {
     }
 }
 
+// p = z (no earlier direction) in this iteration
+__device__ __forceinline__ bool cg_first(const CGState* st) { return st->iter == 0 && !st->carry; }
+
 __device__ __forceinline__ double cg_beta(const CGState* st) {
-    return st->iter == 0 ? 0.0 : st->rho / st->rho_old;
+    return cg_first(st) ? 0.0 : st->rho / st->rho_old;
 }
 
 }  // namespace sem

@@ -55,6 +55,8 @@ struct CGState {
     int max_iter;
     int done;         // 1 once converged, failed or out of iterations
     int status;       // SEM_OK / SEM_ENOTCONV / SEM_EBREAKDOWN
+    int carry;        // 1: the first iteration continues a direction p kept from an
+                      // earlier solve (rho_old rescaled to match) instead of p = z
 };
 
 // ---------------------------------------------------------------------------
@@ -149,6 +151,7 @@ struct BatchPlan {
     double* rrbb = nullptr;   // [nsolve * 2]
     int* act = nullptr;       // [nsolve] solves taking part in an inner solve
     double* itol = nullptr;   // [nsolve] inner relative tolerance of each active solve
+    double* carry = nullptr;  // [nsolve] refinement: rescaling of the kept direction (0 = restart)
     // second group lists, cut to the element count of the FP32 bulk-staged
     // operator (blxg[i] has the order of lxg[i]; no groups where it is unused)
     std::vector<LxGroups> blxg;

@@ -333,7 +333,7 @@ static void free_handle(sem_handle* h) {
     for (auto* p : bp.sid) cudaFree(p);
     cudaFree(bp.sgfirst); cudaFree(bp.sgcount); cudaFree(bp.tloc); cudaFree(bp.tlen); cudaFree(bp.tsolve);
     cudaFree(bp.stfirst); cudaFree(bp.stcount); cudaFree(bp.gpart); cudaFree(bp.tpart); cudaFree(bp.scount);
-    cudaFree(bp.rrbb); cudaFree(bp.act); cudaFree(bp.itol);
+    cudaFree(bp.rrbb); cudaFree(bp.act); cudaFree(bp.itol); cudaFree(bp.carry);
     if (h->graph.exec) cudaGraphExecDestroy(h->graph.exec);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     for (auto& ev : h->ax_ev)
@@ -633,12 +633,13 @@ SEM_API void sem_solve_opts_default(sem_solve_opts* o) {
     o->tol = 1e-10;
     o->max_iter = 100000;
     o->mode = SEM_MODE_FP64;
-    o->inner_tol = 1e-5;
+    o->inner_tol = 1e-2;
     o->max_outer = 30;
     o->precision = SEM_FP64;
     o->use_graph = 1;
     o->graph_chunk = 32;
     o->autotune = 1;
+    o->ir_carry = 1;
 }
 
 SEM_API int sem_gll(int lx, double* xi, double* rho, double* D) {

@@ -73,6 +73,28 @@ def test_batch_members_converge(mode):
         S.sem_destroy(h)
 
 
+@pytest.mark.parametrize("carry", [0, 1])
+def test_batch_mixed_restart_and_carried_direction(carry):
+    """Batched refinement with every member restarting its inner CG (ir_carry
+    = 0, the tight inner tolerance it is made for) and with every member
+    keeping its direction (ir_carry = 1): all members reach 1e-10 by the
+    oracle's residual; the carried form takes no more inner iterations in all
+    than restarting at the same inner tolerance."""
+    members = _members(3)
+    h = _setup(members)
+    try:
+        xs, st = _solve(h, members, mode=S.SEM_MODE_MIXED_IR, inner_tol=1e-2 if carry else 1e-5, ir_carry=carry)
+        for q, ((m, h1, b), x, s) in enumerate(zip(members, xs, st)):
+            assert s["status"] == S.SEM_OK and s["relres"] <= TOL, (q, s)
+            P = oracle.Problem(m, h1)
+            assert _oracle_relres(P, x, b) <= 1.05 * TOL, q
+        if carry:
+            _, st_r = _solve(h, members, mode=S.SEM_MODE_MIXED_IR, inner_tol=1e-2, ir_carry=0)
+            assert sum(s["iterations"] for s in st) <= sum(s["iterations"] for s in st_r)
+    finally:
+        S.sem_destroy(h)
+
+
 def test_batch_matches_single_and_is_reproducible():
     import torch
     members = _members(2, count=5)

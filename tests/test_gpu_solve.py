@@ -55,7 +55,7 @@ def test_fp64_pcg(case, precision):
 def test_mixed_ir(case, inner_tol):
     m, h1, P, b = _cube_case() if case == "cube" else _deformed_case()
     H = Handle(m, h1)
-    x, st = H.solve(b, mode=S.SEM_MODE_MIXED_IR, inner_tol=inner_tol, tol=TOL)
+    x, st = H.solve(b, mode=S.SEM_MODE_MIXED_IR, inner_tol=inner_tol, tol=TOL, ir_carry=0)
     assert st["status"] == S.SEM_OK, st
     assert st["relres"] <= TOL and st["outer_iterations"] >= 1
     assert _oracle_relres(P, x, b) <= 1.05 * TOL
@@ -64,6 +64,28 @@ def test_mixed_ir(case, inner_tol):
     assert e2 <= 1e-7, e2
     x64, _ = H.solve(b, mode=S.SEM_MODE_FP64, tol=TOL)
     assert rel_err(x, x64)[0] <= 1e-7
+
+
+@pytest.mark.parametrize("inner_tol", [1e-2, 1e-1])
+def test_mixed_ir_carried_direction(inner_tol):
+    """ir_carry: the inner FP32 CG keeps its direction across refinement steps
+    (residual replacement).  Same true residual and solution as the restarted
+    refinement; the inner iterations add up to about the FP64 PCG count, as
+    in the oracle's refinement with the same option."""
+    m, h1, P, b = _deformed_case()
+    H = Handle(m, h1)
+    x, st = H.solve(b, mode=S.SEM_MODE_MIXED_IR, inner_tol=inner_tol, tol=TOL, ir_carry=1)
+    assert st["status"] == S.SEM_OK, st
+    assert st["relres"] <= TOL and st["outer_iterations"] >= 3, st
+    assert _oracle_relres(P, x, b) <= 1.05 * TOL
+    xo, _ = P.pcg(b, tol=1e-12)
+    assert rel_err(x, xo)[0] <= 1e-7
+    _, st64 = H.solve(b, mode=S.SEM_MODE_FP64, tol=TOL)
+    _, ic = P.ir(b, tol=TOL, inner_tol=inner_tol, carry=True)
+    assert 0.9 * st64["iterations"] <= st["iterations"] <= 1.05 * st64["iterations"] + 5, (st, st64)
+    assert abs(st["iterations"] - ic["inner"]) <= 0.05 * ic["inner"] + 5, (st, ic)
+    _, st_r = H.solve(b, mode=S.SEM_MODE_MIXED_IR, inner_tol=inner_tol, tol=TOL, ir_carry=0)
+    assert st_r["iterations"] > st["iterations"], (st_r, st)
 
 
 @pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])

@@ -125,6 +125,26 @@ def test_ir_reaches_fp64_solution(inner_tol):
     assert np.linalg.norm(x - x64) <= 1e-7 * np.linalg.norm(x64)
 
 
+@pytest.mark.parametrize("inner_tol", [1e-2, 1e-1])
+def test_ir_carry_continues_one_cg(inner_tol):
+    """Refinement with the inner direction carried across steps, rescaled by
+    ||r_prev|| / ||r|| (CG with residual replacement): the inner iterations add
+    up to about the FP64 PCG count (one continued Krylov space), while
+    restarting at every step costs well over it.  A wrong rescaling (c^2 or
+    1/c instead of c) gives 1.35x the FP64 count, or no convergence at all."""
+    m, h1, b = W.deformed_cube(4, 7, seed=2)
+    P = oracle.Problem(m, h1)
+    _, i64 = P.pcg(b, tol=1e-10)
+    xref, _ = P.pcg(b, tol=1e-13)
+    _, ir = P.ir(b, tol=1e-10, inner_tol=inner_tol)
+    xc, ic = P.ir(b, tol=1e-10, inner_tol=inner_tol, carry=True)
+    assert ic["status"] == 0 and ic["relres"] <= 1e-10, ic
+    assert ic["outer"] >= 3
+    assert ic["inner"] <= 1.05 * i64["iters"], (ic["inner"], i64["iters"])
+    assert ir["inner"] >= 1.2 * i64["iters"], (ir["inner"], i64["iters"])
+    assert np.linalg.norm(xc - xref) <= 1e-7 * np.linalg.norm(xref)
+
+
 def test_ir_matches_dense_solution_small():
     m = W.box_mesh(2, 2, 2, 3, amp=0.05)
     P = oracle.Problem(m)
