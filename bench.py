@@ -135,8 +135,11 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
 
 
-# mixed refinement: FP32 inner CG to 1e-2, its direction kept across the FP64
-# refinement steps (residual replacement)
+# mixed refinement of the deformed-cube workload: FP32 inner CG to 1e-2 with its
+# direction kept across the FP64 refinement steps (residual replacement).  On
+# this workload it reaches 1e-10 14% sooner than the library's default
+# refinement (restarts, inner tolerance 1e-5, timed beside it in the extras);
+# on the ill-conditioned annulus restarting is the faster of the two.
 MIXED_OPTS = {"inner_tol": 1e-2, "ir_carry": 1}
 
 def _workload(args):
@@ -442,8 +445,10 @@ def run_suite(args):
     import paper_2207_07098_gb300 as S
     S.load()
     out = {"suite": "sem_poisson", "data": "synthetic"}
+    # mixed: the library's default refinement (restarts); mixed_carry: the kept direction
     modes = (("fp64", {"mode": S.SEM_MODE_FP64, "tol": 1e-10}),
-             ("mixed", {"mode": S.SEM_MODE_MIXED_IR, "tol": 1e-10, **MIXED_OPTS}))
+             ("mixed", {"mode": S.SEM_MODE_MIXED_IR, "tol": 1e-10}),
+             ("mixed_carry", {"mode": S.SEM_MODE_MIXED_IR, "tol": 1e-10, **MIXED_OPTS}))
     # --- cube, manufactured solution
     m, f = W.cube_sines(4, 7)
     h = S.sem_setup(m.E, m.lx, m.coords, m.gid, m.mask, None)
@@ -464,6 +469,7 @@ def run_suite(args):
     d = xs["mixed"] - xs["fp64"]
     cube["mixed_vs_fp64_gpu_rel_l2"] = float(np.linalg.norm(d) / np.linalg.norm(xs["fp64"]))
     cube["speedup_mixed_vs_fp64"] = cube["fp64"]["time_ms"] / cube["mixed"]["time_ms"]
+    cube["speedup_mixed_carry_vs_fp64"] = cube["fp64"]["time_ms"] / cube["mixed_carry"]["time_ms"]
     # CPU-baseline leg: the oracle's own solve (timed) and the GPU error against it
     import oracle
     P = oracle.Problem(m)
@@ -501,6 +507,7 @@ def run_suite(args):
                        "iterations_mean": float(np.mean(its)), "all_converged": all(st["status"] == 0 for st in sts),
                        "relres_max": max(st["relres"] for st in sts), "launches": sts[0]["kernel_launches"]}
     batch["speedup_mixed_vs_fp64"] = batch["fp64"]["time_ms"] / batch["mixed"]["time_ms"]
+    batch["speedup_mixed_carry_vs_fp64"] = batch["fp64"]["time_ms"] / batch["mixed_carry"]["time_ms"]
     S.sem_destroy(hb)
     del bcat, members
     torch.cuda.empty_cache()
@@ -521,6 +528,7 @@ def run_suite(args):
         _, st = _timed_solve(S, torch, h, bd, m.n_local, o, reps=2)
         ann[name] = _solve_report(st, m.n_local, info["n_free"])
     ann["speedup_mixed_vs_fp64"] = ann["fp64"]["time_ms"] / ann["mixed"]["time_ms"]
+    ann["speedup_mixed_carry_vs_fp64"] = ann["fp64"]["time_ms"] / ann["mixed_carry"]["time_ms"]
     peak, _ = _peaks()
     stream = torch.cuda.current_stream()
     for name, prec, dt_, bpp in (("ax_fp64", S.SEM_FP64, torch.float64, 64), ("ax_fp32", S.SEM_FP32, torch.float32, 32)):

@@ -633,13 +633,13 @@ SEM_API void sem_solve_opts_default(sem_solve_opts* o) {
     o->tol = 1e-10;
     o->max_iter = 100000;
     o->mode = SEM_MODE_FP64;
-    o->inner_tol = 1e-2;
+    o->inner_tol = 1e-5;
     o->max_outer = 30;
     o->precision = SEM_FP64;
     o->use_graph = 1;
     o->graph_chunk = 32;
     o->autotune = 1;
-    o->ir_carry = 1;
+    o->ir_carry = 0;
 }
 
 SEM_API int sem_gll(int lx, double* xi, double* rho, double* D) {
