@@ -46,6 +46,10 @@ MUTANTS = {
     "h1_at_wrong_point_in_jacobi": (
         "s += D[l * lx + i] * D[l * lx + i] * p->h1[La] * p->G[0 * n + La];",
         "s += D[l * lx + i] * D[l * lx + i] * p->h1[L0] * p->G[0 * n + La];"),
+    "ir_kept_direction_rescaled_by_c_squared": (
+        "rho_carry * (rn_prev / rn) : 0.0;", "rho_carry * (rn_prev / rn) * (rn_prev / rn) : 0.0;"),
+    "ir_kept_direction_rescaled_by_inverse": (
+        "rho_carry * (rn_prev / rn) : 0.0;", "rho_carry * (rn / rn_prev) : 0.0;"),
 }
 
 
@@ -98,6 +102,14 @@ def _battery() -> list[str]:
     xd = Q @ xg
     check("pcg_dense", info["status"] == 0 and np.linalg.norm(x - xd) < 1e-10 * np.linalg.norm(xd)
           and info["iters"] <= 2 * int(F.sum()))
+    # refinement with the inner direction kept: one continued CG, about the
+    # FP64 PCG iteration count (bounded so that a broken variant ends quickly)
+    mc, h1c, bc = W.deformed_cube(4, 7, seed=2)
+    Pc = oracle.Problem(mc, h1c)
+    _, i64 = Pc.pcg(bc, tol=1e-10, max_iter=1000)
+    _, ic = Pc.ir(bc, tol=1e-10, inner_tol=1e-2, carry=True, max_outer=12, max_inner=400)
+    check("ir_kept_direction", ic["status"] == 0 and ic["relres"] <= 1e-10
+          and ic["inner"] <= 1.05 * i64["iters"])
     return failed
 
 
