@@ -653,6 +653,7 @@ int or_ir(const or_problem* p, const double* b, double* x, double tol, double in
     const double bnorm = sqrt(or_dot(p, b, b));
     int status = 1, outer = 0, inner = 0;
     double prev = INFINITY, rel = 0.0, rn_prev = 0.0, rho_carry = 0.0;
+    int capped_last = 0;
     for (;;) {
         or_ax(p, x, w);
         for (int64_t L = 0; L < n; L++) r[L] = b[L] - w[L];
@@ -661,14 +662,19 @@ int or_ir(const or_problem* p, const double* b, double* x, double tol, double in
         if (outer > 0 && outer_hist) outer_hist[outer - 1] = rel;
         if (rel <= tol) { status = 0; break; }
         if (outer >= max_outer) { status = 1; break; }
-        if (outer > 0 && rel > 0.5 * prev) { status = 3; break; }
+        /* stagnation is judged only after an inner solve that reached its
+         * tolerance: one stopped by max_inner may leave a larger residual (CG
+         * does not shrink the residual norm monotonically) */
+        if (outer > 0 && rel > 0.5 * prev && !capped_last) { status = 3; break; }
         prev = rel;
         for (int64_t L = 0; L < n; L++) r32[L] = (float)(r[L] / rn);
         /* carried direction: the previous step's units were 1/rn_prev, these
          * are 1/rn, so pp scales by c = rn_prev / rn and its <r, z> by c^2;
          * folding one c into the <r, z> leaves pp as it is */
         rho_carry = (carry && outer > 0 && rho_carry > 0.0) ? rho_carry * (rn_prev / rn) : 0.0;
-        inner += pcg_f32(p, &f, r32, d32, inner_tol, max_inner, pp, &rho_carry);
+        const int it_step = pcg_f32(p, &f, r32, d32, inner_tol, max_inner, pp, &rho_carry);
+        inner += it_step;
+        capped_last = it_step >= max_inner;
         for (int64_t L = 0; L < n; L++) x[L] += rn * (double)d32[L];
         rn_prev = rn;
         outer++;

@@ -80,7 +80,8 @@ int or_pcg(const or_problem* p, const double* b, double* x, double tol, int max_
  * FP32 arithmetic (FP32 vectors, FP32 operator, FP64 dot products) on
  * A d = r/||r|| to inner_tol, then x += ||r|| d.  Stops when the true FP64
  * residual ||b - A x||/||b|| <= tol, after max_outer outer steps, or when an
- * outer step fails to halve the residual (stagnation, return 3).
+ * outer step whose inner solve reached inner_tol fails to halve the residual
+ * (stagnation, return 3); a step stopped by max_inner is not judged.
  * outer_hist receives the true relative residual after each outer step.
  * carry = 0: every inner solve starts CG afresh (first direction z).
  * carry = 1: from the second outer step on, the inner CG keeps the search

@@ -107,7 +107,7 @@ def _battery() -> list[str]:
     mc, h1c, bc = W.deformed_cube(4, 7, seed=2)
     Pc = oracle.Problem(mc, h1c)
     _, i64 = Pc.pcg(bc, tol=1e-10, max_iter=1000)
-    _, ic = Pc.ir(bc, tol=1e-10, inner_tol=1e-2, carry=True, max_outer=12, max_inner=400)
+    _, ic = Pc.ir(bc, tol=1e-10, inner_tol=1e-2, carry=True, max_outer=8, max_inner=400)
     check("ir_kept_direction", ic["status"] == 0 and ic["relres"] <= 1e-10
           and ic["inner"] <= 1.05 * i64["iters"])
     return failed

@@ -145,6 +145,24 @@ def test_ir_carry_continues_one_cg(inner_tol):
     assert np.linalg.norm(xc - xref) <= 1e-7 * np.linalg.norm(xref)
 
 
+def test_ir_kept_direction_with_capped_steps():
+    """Kept direction with every refinement step stopped after at most 100
+    inner iterations (a replacement at least every 100 iterations): on the
+    periodic annulus, where letting the FP32 CG run to 1e-3 between
+    replacements drifts too far, the capped form stays near the FP64 PCG
+    count.  The stagnation test skips capped steps (their residual can grow)."""
+    m, f = W.annulus_case(N=7, n_theta=16, n_r=8, n_z=6)
+    P = oracle.Problem(m)
+    b = P.mass(f, assemble=True)
+    xref, i64 = P.pcg(b, tol=1e-10)
+    _, iu = P.ir(b, tol=1e-10, inner_tol=1e-3, carry=True)
+    xc, ic = P.ir(b, tol=1e-10, inner_tol=1e-3, carry=True, max_inner=100, max_outer=60)
+    assert ic["status"] == 0 and ic["relres"] <= 1e-10, ic
+    assert ic["inner"] <= 1.25 * i64["iters"], (ic["inner"], i64["iters"])
+    assert ic["inner"] <= 0.85 * iu["inner"], (ic["inner"], iu["inner"])
+    assert np.linalg.norm(xc - xref) <= 1e-7 * np.linalg.norm(xref)
+
+
 def test_ir_matches_dense_solution_small():
     m = W.box_mesh(2, 2, 2, 3, amp=0.05)
     P = oracle.Problem(m)
