@@ -340,6 +340,17 @@ def run_ours(args):
 
     if rank == 0 and not args.no_extras:
         out["extras"] = _extras(S, torch, h, m, bd, n, args, peak, stats, ms)
+        sv = out["extras"]["solves_to_1e-10"]
+        # the FP64 arm the mixed solve is compared with, on the same GPU and mesh
+        out["fp64_arm"] = {
+            "fp64_native_time_ms": sv["fp64"]["time_ms"], "fp64_native_iterations": sv["fp64"]["iterations"],
+            "fp64_pair_time_ms": sv["fp64_pair"]["time_ms"], "fp64_pair_iterations": sv["fp64_pair"]["iterations"],
+            "mixed_time_ms": ms / args.steps,
+            "speedup_mixed_vs_fp64_native": sv["fp64"]["time_ms"] / (ms / args.steps),
+            "speedup_mixed_vs_fp64_pair": sv["fp64_pair"]["time_ms"] / (ms / args.steps),
+            "note": ("FP64 Jacobi-PCG to the same true 1e-10: native FP64 operator and vectors (SEM_FP64), and "
+                     "the FP32-pair operator and vectors (SEM_FP64_PAIR, 48-bit), both with the true residual "
+                     "recomputed by the native operator")}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, k, dt, thr, osetup = _oracle_sample(m, h1, b, args.cpu_seconds)
         out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
@@ -357,23 +368,30 @@ def _extras(S, torch, h, m, bd, n, args, peak, stats, ms_timed):
     ex = {}
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
     res = {}
-    for name, mode, extra in (("fp64", S.SEM_MODE_FP64, {}), ("mixed", S.SEM_MODE_MIXED_IR, MIXED_OPTS),
-                              ("mixed_restart_1e-5", S.SEM_MODE_MIXED_IR, {"inner_tol": 1e-5, "ir_carry": 0})):
+    for name, mode, prec, extra in (("fp64", S.SEM_MODE_FP64, S.SEM_FP64, {}),
+                                    ("fp64_pair", S.SEM_MODE_FP64, S.SEM_FP64_PAIR, {}),
+                                    ("mixed", S.SEM_MODE_MIXED_IR, S.SEM_FP64, MIXED_OPTS),
+                                    ("mixed_restart_1e-5", S.SEM_MODE_MIXED_IR, S.SEM_FP64,
+                                     {"inner_tol": 1e-5, "ir_carry": 0})):
         x.zero_()
-        st = S.sem_cg_solve(h, x, bd, {"mode": mode, "precision": S.SEM_FP64, "tol": 1e-10, **extra})
+        st = S.sem_cg_solve(h, x, bd, {"mode": mode, "precision": prec, "tol": 1e-10, **extra})
         res[name] = {"time_ms": st["time_ms"], "iterations": st["iterations"], "outer": st["outer_iterations"],
-                     "relres": st["relres"], "gdof_s": n * st["iterations"] / (st["time_ms"] * 1e-3) / 1e9,
-                     "ax_ms": st["ax_ms"]}
+                     "relres": st["relres"], "status": st["status"],
+                     "gdof_s": n * st["iterations"] / (st["time_ms"] * 1e-3) / 1e9, "ax_ms": st["ax_ms"],
+                     "ax_variant": st["ax_variant"]}
     res["speedup_mixed_vs_fp64"] = res["fp64"]["time_ms"] / res["mixed"]["time_ms"]
+    res["speedup_mixed_vs_fp64_pair"] = res["fp64_pair"]["time_ms"] / res["mixed"]["time_ms"]
     ex["solves_to_1e-10"] = res
-    x.zero_()
-    st = S.sem_cg_solve(h, x, bd, {"mode": S.SEM_MODE_FP64, "tol": 1e-30, "max_iter": 200})
-    ex["cg200_fp64"] = {"time_ms": st["time_ms"], "iterations": st["iterations"],
-                        "gdof_s": n * st["iterations"] / (st["time_ms"] * 1e-3) / 1e9}
+    for name, prec in (("cg200_fp64", S.SEM_FP64), ("cg200_fp64_pair", S.SEM_FP64_PAIR)):
+        x.zero_()
+        st = S.sem_cg_solve(h, x, bd, {"mode": S.SEM_MODE_FP64, "precision": prec, "tol": 1e-30, "max_iter": 200})
+        ex[name] = {"time_ms": st["time_ms"], "iterations": st["iterations"],
+                    "gdof_s": n * st["iterations"] / (st["time_ms"] * 1e-3) / 1e9}
     # ax_helm-only: plain local operator, back-to-back launches, CUDA events on the launching stream
     stream = torch.cuda.current_stream()
     axr = {}
-    for name, prec, dt, bpp in (("fp64", S.SEM_FP64, torch.float64, 64), ("fp32", S.SEM_FP32, torch.float32, 32)):
+    for name, prec, dt, bpp in (("fp64", S.SEM_FP64, torch.float64, 64), ("fp64_pair", S.SEM_FP64_PAIR, torch.float64, 64),
+                                ("fp32", S.SEM_FP32, torch.float32, 32)):
         u = torch.randn(n, dtype=dt, device="cuda")
         w = torch.empty_like(u)
         for _ in range(3):
@@ -389,13 +407,18 @@ def _extras(S, torch, h, m, bd, n, args, peak, stats, ms_timed):
         t = e0.elapsed_time(e1) / reps
         gbs = bpp * n / (t * 1e-3) / 1e9
         axr[name] = {"ms": t, "gb_s": gbs, "frac_hbm": gbs / peak, "bytes_per_point": bpp}
+    axr["accuracy"] = ("fp64: native FP64 arithmetic, 1e-12 of the oracle on every field tested; fp64_pair: "
+                       "FP32-pair arithmetic (unit roundoff 2^-48), 1e-12 on rough fields, a few 1e-12 on "
+                       "smooth cancelling ones")
     ex["ax_helm_only"] = axr
-    # every operator variant (pinned at set-up), plain ax_helm, both precisions
+    # every operator variant (pinned at set-up), plain ax_helm: 0..4 native FP64 and FP32, 5..6 FP32-pair
     var = {}
     for v in range(7):
         hv = S.sem_setup(m.E, m.lx, m.coords, m.gid, m.mask, None, S.SEM_FLAG_VARIANT(v))
         row = {}
-        for name, prec, dt, bpp in (("fp64", S.SEM_FP64, torch.float64, 64), ("fp32", S.SEM_FP32, torch.float32, 32)):
+        kinds = ((("fp64", S.SEM_FP64, torch.float64, 64), ("fp32", S.SEM_FP32, torch.float32, 32)) if v <= 4 else
+                 (("fp64_pair", S.SEM_FP64_PAIR, torch.float64, 64),))
+        for name, prec, dt, bpp in kinds:
             u = torch.randn(n, dtype=dt, device="cuda")
             w = torch.empty_like(u)
             for _ in range(3):
@@ -447,8 +470,10 @@ def run_suite(args):
     out = {"suite": "sem_poisson", "data": "synthetic"}
     # mixed: the library's default refinement (restarts); mixed_carry: the kept direction
     modes = (("fp64", {"mode": S.SEM_MODE_FP64, "tol": 1e-10}),
+             ("fp64_pair", {"mode": S.SEM_MODE_FP64, "precision": S.SEM_FP64_PAIR, "tol": 1e-10}),
              ("mixed", {"mode": S.SEM_MODE_MIXED_IR, "tol": 1e-10}),
-             ("mixed_carry", {"mode": S.SEM_MODE_MIXED_IR, "tol": 1e-10, **MIXED_OPTS}))
+             ("mixed_carry", {"mode": S.SEM_MODE_MIXED_IR, "tol": 1e-10, **MIXED_OPTS}),
+             ("mixed_carry_capped", {"mode": S.SEM_MODE_MIXED_IR, "tol": 1e-10, **MIXED_OPTS, "max_iter": 100}))
     # --- cube, manufactured solution
     m, f = W.cube_sines(4, 7)
     h = S.sem_setup(m.E, m.lx, m.coords, m.gid, m.mask, None)
@@ -469,7 +494,9 @@ def run_suite(args):
     d = xs["mixed"] - xs["fp64"]
     cube["mixed_vs_fp64_gpu_rel_l2"] = float(np.linalg.norm(d) / np.linalg.norm(xs["fp64"]))
     cube["speedup_mixed_vs_fp64"] = cube["fp64"]["time_ms"] / cube["mixed"]["time_ms"]
+    cube["speedup_mixed_vs_fp64_pair"] = cube["fp64_pair"]["time_ms"] / cube["mixed"]["time_ms"]
     cube["speedup_mixed_carry_vs_fp64"] = cube["fp64"]["time_ms"] / cube["mixed_carry"]["time_ms"]
+    cube["speedup_mixed_carry_capped_vs_fp64"] = cube["fp64"]["time_ms"] / cube["mixed_carry_capped"]["time_ms"]
     # CPU-baseline leg: the oracle's own solve (timed) and the GPU error against it
     import oracle
     P = oracle.Problem(m)
@@ -505,9 +532,13 @@ def run_suite(args):
         batch[name] = {"time_ms": sts[0]["time_ms"], "gdof_s_local": dofit / t / 1e9,
                        "cg_iter_s_summed_over_solves": sum(its) / t, "iterations_max": max(its),
                        "iterations_mean": float(np.mean(its)), "all_converged": all(st["status"] == 0 for st in sts),
-                       "relres_max": max(st["relres"] for st in sts), "launches": sts[0]["kernel_launches"]}
+                       "relres_max": max(st["relres"] for st in sts), "launches": sts[0]["kernel_launches"],
+                       "launches_per_iteration": sts[0]["launches_per_iteration"],
+                       "operator_variants": sorted({st["ax_variant"] for st in sts})}
     batch["speedup_mixed_vs_fp64"] = batch["fp64"]["time_ms"] / batch["mixed"]["time_ms"]
+    batch["speedup_mixed_vs_fp64_pair"] = batch["fp64_pair"]["time_ms"] / batch["mixed"]["time_ms"]
     batch["speedup_mixed_carry_vs_fp64"] = batch["fp64"]["time_ms"] / batch["mixed_carry"]["time_ms"]
+    batch["speedup_mixed_carry_capped_vs_fp64"] = batch["fp64"]["time_ms"] / batch["mixed_carry_capped"]["time_ms"]
     S.sem_destroy(hb)
     del bcat, members
     torch.cuda.empty_cache()
@@ -528,10 +559,14 @@ def run_suite(args):
         _, st = _timed_solve(S, torch, h, bd, m.n_local, o, reps=2)
         ann[name] = _solve_report(st, m.n_local, info["n_free"])
     ann["speedup_mixed_vs_fp64"] = ann["fp64"]["time_ms"] / ann["mixed"]["time_ms"]
+    ann["speedup_mixed_vs_fp64_pair"] = ann["fp64_pair"]["time_ms"] / ann["mixed"]["time_ms"]
     ann["speedup_mixed_carry_vs_fp64"] = ann["fp64"]["time_ms"] / ann["mixed_carry"]["time_ms"]
+    ann["speedup_mixed_carry_capped_vs_fp64"] = ann["fp64"]["time_ms"] / ann["mixed_carry_capped"]["time_ms"]
     peak, _ = _peaks()
     stream = torch.cuda.current_stream()
-    for name, prec, dt_, bpp in (("ax_fp64", S.SEM_FP64, torch.float64, 64), ("ax_fp32", S.SEM_FP32, torch.float32, 32)):
+    for name, prec, dt_, bpp in (("ax_fp64", S.SEM_FP64, torch.float64, 64),
+                                 ("ax_fp64_pair", S.SEM_FP64_PAIR, torch.float64, 64),
+                                 ("ax_fp32", S.SEM_FP32, torch.float32, 32)):
         u = torch.randn(m.n_local, dtype=dt_, device="cuda")
         w = torch.empty_like(u)
         for _ in range(3):

@@ -66,11 +66,22 @@ typedef enum sem_status {
 
 /* Arithmetic of one operator application or of the inner solve. */
 typedef enum sem_precision {
-    SEM_FP64 = 0,        /* double data, the fastest FP64-class operator: FP32-pair
-                            arithmetic (48-bit, unit roundoff 2^-48) where the autotuner
-                            or SEM_FLAG_VARIANT(5 or 6) picks it, else native FP64 */
+    SEM_FP64 = 0,        /* double data, FP64 arithmetic (unit roundoff 2^-53): the fastest of
+                            the native FP64 kernels (variants 0..4, autotuned per handle); holds
+                            the 1e-12 relative parity bar on every input tested, including
+                            smooth fields whose sums cancel */
     SEM_FP32 = 1,        /* float data, FP32 arithmetic and accumulation */
-    SEM_FP64_NATIVE = 2  /* double data, plain FP64 CUDA-core arithmetic (2^-53) */
+    SEM_FP64_NATIVE = 2, /* double data, the plain shared-slab FP64 kernel (variant 0) */
+    SEM_FP64_PAIR = 3    /* double data, FP32-pair ("double-float") arithmetic on the FP32 pipe:
+                            48 significant bits, unit roundoff 2^-48, about 4x the speed of
+                            SEM_FP64 on GB300 (whose FP64 pipe runs at 1/64 of the FP32 rate).
+                            Relative error vs exact FP64: ~1e-15..1e-14 on rough fields, up to
+                            a few 1e-12 where the element sums cancel (smooth fields), always
+                            within 64 * 2^-48 |D^T||h1 G||D||u| pointwise.  Range: inputs are
+                            split into two floats, so |u| below 2^-75 or at or above 2^128 (and
+                            Inf/NaN) is read as 0; the solver rescales x and b by a power of two
+                            to keep them inside it.  Variant 6 (line transforms, even lx <= 12)
+                            or 5 (lx <= 12); other orders fall back to SEM_FP64 */
 } sem_precision;
 
 typedef enum sem_solve_mode {
@@ -92,12 +103,19 @@ typedef struct sem_info {
 typedef struct sem_solve_opts {
     double tol;          /* relative residual ||b - A x|| / ||b|| to reach (1e-10) */
     int max_iter;        /* max CG iterations (FP64 mode) or inner iterations per
-                            refinement step (mixed mode) */
+                            refinement step (mixed mode).  In mixed mode a step that stops at
+                            this cap is not judged for stagnation, and with ir_carry its
+                            direction is kept: with ir_carry = 1, max_iter ~100-200 bounds the
+                            iterations between residual replacements (ill-conditioned
+                            problems) */
     int mode;            /* sem_solve_mode */
     double inner_tol;    /* mixed mode: inner relative tolerance (1e-5; with ir_carry = 1,
                             about 1e-2) */
-    int max_outer;       /* mixed mode: max refinement steps (30) */
-    int precision;       /* FP64 mode: SEM_FP64 or SEM_FP64_NATIVE operator */
+    int max_outer;       /* mixed mode: max refinement steps (100) */
+    int precision;       /* FP64 mode: operator of the CG iterations, SEM_FP64 (default),
+                            SEM_FP64_NATIVE or SEM_FP64_PAIR (with SEM_FP64_PAIR the CG vectors
+                            are float pairs too where variant 6 applies).  The true residual
+                            that decides convergence is always computed with SEM_FP64 */
     int use_graph;       /* capture the CG iterations in CUDA graphs (1) */
     int graph_chunk;     /* CG iterations per graph launch between host checks (32) */
     int autotune;        /* time the operator-kernel variants on this handle's data at the
@@ -115,13 +133,20 @@ typedef struct sem_solve_opts {
                             the 25 M-point periodic annulus, 24% slower) the replaced
                             residual differs too much from the recursive one and
                             restarting is faster, hence the default (0) */
+    int persistent;      /* run each CG loop as ONE persistent (cooperative) launch whose CTAs
+                            meet at bounded grid barriers, instead of graphs of three launches
+                            per iteration: -1 (default) below 2^20 local points, where launch
+                            latency dominates; 1 always; 0 never.  Single-mesh handles, lx <= 10,
+                            SEM_FP32 inner solves and SEM_FP64 / SEM_FP64_NATIVE (slab
+                            operator); not for SEM_FP64_PAIR */
 } sem_solve_opts;
 
 typedef struct sem_solve_stats {
     int status;               /* sem_status of this solve */
     int iterations;           /* CG iterations (all inner iterations in mixed mode) */
     int outer_iterations;     /* refinement steps (0 in FP64 mode) */
-    double relres;            /* TRUE residual ||b - A x|| / ||b||, recomputed in FP64 */
+    double relres;            /* TRUE residual ||b - A x|| / ||b||, recomputed with the
+                                 SEM_FP64 operator (native FP64 arithmetic) */
     double relres_recursive;  /* last recursive residual estimate of the CG loop */
     double time_ms;           /* device time of the solve (CUDA events) */
     int64_t kernel_launches;  /* kernels this solve launched (graph nodes included) */
@@ -132,7 +157,15 @@ typedef struct sem_solve_stats {
                                  1..4 = bulk-copy staging (elements per CTA, stages) =
                                  (1,3), (2,2), (2,3), (4,2), lx in {4,6,8,10,12};
                                  5 = FP64 data in FP32-pair arithmetic (lx <= 12);
-                                 6 = as 5 with even/odd line transforms (even lx <= 12) */
+                                 6 = as 5 with even/odd line transforms (even lx <= 12);
+                                 5 and 6 serve SEM_FP64_PAIR only;
+                                 7 (batches) = one slab launch over the element groups
+                                 of every order (orders up to lx = 10) */
+    int launches_per_iteration;  /* kernel launches of one CG iteration: 3 for one mesh
+                                 (operator, gather-scatter, update), 0 when the CG ran
+                                 as one persistent launch; for a batch the
+                                 operator launches (1 with variant 7, else one per
+                                 order) + 2 */
 } sem_solve_stats;
 
 /* Mesh of one member of a batch (host pointers; see sem_setup). */
@@ -145,13 +178,15 @@ typedef struct sem_mesh_desc {
     const double* h1;       /* [E lx^3] or NULL for h1 = 1 */
 } sem_mesh_desc;
 
-/* Set-up flag: pin operator kernel variant v (0..6) for every precision. */
+/* Set-up flag: pin operator kernel variant v: 0..4 for SEM_FP64 and SEM_FP32,
+ * 5 or 6 for SEM_FP64_PAIR (the other precisions stay autotuned). */
 #define SEM_FLAG_VARIANT(v) ((int)(((v) + 1) & 0xF))
 
 /* Set-up flag for testing failure detection: the bulk-staged operator kernels
- * announce 16 bytes more than they copy, so no stage ever completes; their
- * bounded waits (shortened to ~50 ms) expire, the kernels record the failure
- * and return, and the solve reports SEM_ETIMEOUT.  No fault, no hang. */
+ * announce 16 bytes more than they copy, so no stage ever completes, and the
+ * first CTA of the persistent CG kernel leaves before its first grid barrier;
+ * the bounded waits (shortened to ~50 ms) expire, the kernels record the
+ * failure and return, and the solve reports SEM_ETIMEOUT.  No fault, no hang. */
 #define SEM_FLAG_TEST_STALL 0x100
 
 /* Fill *opts with the defaults listed above. */
@@ -209,7 +244,8 @@ SEM_API int sem_ax(sem_handle* h, void* w, const void* u, int precision, int ass
 
 /* u <- QQ^T u in place, then u <- mask * u if apply_mask (Sec. II-A).  Copies
  * of a node are summed in ascending local index, so the result is
- * bit-reproducible.  u: device [n_local], double (SEM_FP64*) or float. */
+ * bit-reproducible.  u: device [n_local], double (every SEM_FP64* precision:
+ * FP64 sums) or float (SEM_FP32). */
 SEM_API int sem_gs(sem_handle* h, void* u, int precision, int apply_mask, cudaStream_t stream);
 
 /* w = B u (diagonal mass, B = rho rho rho J), then mask * QQ^T if assemble.
@@ -259,15 +295,21 @@ SEM_API int sem_get_jacobi(const sem_handle* h, double* minv, cudaStream_t strea
  * refinement.  x: [n_local] initial guess in, solution out; b: [n_local]
  * assembled right-hand side (equal on all copies of a node, 0 on Dirichlet
  * nodes).  Host or device pointers.  opts NULL = defaults; stats may be NULL.
- * Returns SEM_OK, SEM_ENOTCONV, SEM_EBREAKDOWN or SEM_ESTAGNATE (x holds the
- * last iterate), or an error.  Synchronises the stream. */
+ * Returns SEM_OK only when the true residual ||b - A x|| / ||b|| of the
+ * returned x, recomputed with SEM_FP64, is at most tol; else SEM_ENOTCONV,
+ * SEM_EBREAKDOWN (also for a non-finite initial residual: a NaN or Inf in x0
+ * or b) or SEM_ESTAGNATE (x holds the last iterate), or an error.
+ * Synchronises the stream. */
 SEM_API int sem_cg_solve(sem_handle* h, double* x, const double* b, const sem_solve_opts* opts,
                          sem_solve_stats* stats, cudaStream_t stream);
 
 /* All solves of a batch handle at once: x, b concatenated [n_local];
  * stats: host array of nsolve entries (may be NULL).  Every CG iteration
- * advances all unconverged solves with one set of launches.  Returns the
- * worst status over the batch. */
+ * advances all unconverged solves with one set of launches: the operator (one
+ * launch over the groups of every order, or one launch per order, whichever
+ * the first solve's autotuning measured faster on this handle; a variant
+ * pinned at set-up selects one launch per order), one gather-scatter and one
+ * vector update.  Returns the worst status over the batch. */
 SEM_API int sem_cg_solve_batch(sem_handle* h, double* x, const double* b,
                                const sem_solve_opts* opts, sem_solve_stats* stats,
                                cudaStream_t stream);

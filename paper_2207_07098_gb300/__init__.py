@@ -8,6 +8,6 @@ sem_destroy, sem_get_info, sem_get_offsets, sem_gll.
 """
 from ._lib import *  # noqa: F401,F403
 from ._lib import (SEM_EBREAKDOWN, SEM_ECUDA, SEM_EINVAL, SEM_ENOMEM, SEM_ENOTCONV, SEM_ESTAGNATE,
-                   SEM_ETIMEOUT, SEM_FP32, SEM_FP64, SEM_FP64_NATIVE, SEM_MODE_FP64, SEM_MODE_MIXED_IR,
+                   SEM_ETIMEOUT, SEM_FP32, SEM_FP64, SEM_FP64_NATIVE, SEM_FP64_PAIR, SEM_MODE_FP64, SEM_MODE_MIXED_IR,
                    SEM_OK, LIB_PATH, SemError, load, exported_symbols, SEM_FLAG_VARIANT, SEM_FLAG_TEST_STALL)
 from .build import build  # noqa: F401

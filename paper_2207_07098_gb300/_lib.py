@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsem.so")
 
 SEM_OK, SEM_EINVAL, SEM_ENOMEM, SEM_ECUDA, SEM_ENOTCONV, SEM_EBREAKDOWN, SEM_ESTAGNATE, SEM_ETIMEOUT = range(8)
-SEM_FP64, SEM_FP32, SEM_FP64_NATIVE = 0, 1, 2
+SEM_FP64, SEM_FP32, SEM_FP64_NATIVE, SEM_FP64_PAIR = 0, 1, 2, 3
 SEM_MODE_FP64, SEM_MODE_MIXED_IR = 0, 1
 
 
@@ -24,7 +24,8 @@ SEM_FLAG_TEST_STALL = 0x100
 
 
 def SEM_FLAG_VARIANT(v: int) -> int:
-    """Set-up flag pinning operator kernel variant v (0..4), as in sem.h."""
+    """Set-up flag pinning operator kernel variant v, as in sem.h: 0..4 for
+    SEM_FP64 and SEM_FP32, 5 or 6 for SEM_FP64_PAIR."""
     return (v + 1) & 0xF
 STATUS_NAMES = {0: "SEM_OK", 1: "SEM_EINVAL", 2: "SEM_ENOMEM", 3: "SEM_ECUDA", 4: "SEM_ENOTCONV",
                 5: "SEM_EBREAKDOWN", 6: "SEM_ESTAGNATE", 7: "SEM_ETIMEOUT"}
@@ -46,14 +47,14 @@ class sem_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mode", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("precision", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("graph_chunk", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("ir_carry", ctypes.c_int)]
+                ("ir_carry", ctypes.c_int), ("persistent", ctypes.c_int)]
 
 
 class sem_solve_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("outer_iterations", ctypes.c_int),
                 ("relres", ctypes.c_double), ("relres_recursive", ctypes.c_double), ("time_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("ax_ms", ctypes.c_double), ("ax_samples", ctypes.c_int),
-                ("ax_variant", ctypes.c_int)]
+                ("ax_variant", ctypes.c_int), ("launches_per_iteration", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

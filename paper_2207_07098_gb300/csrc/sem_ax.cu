@@ -19,11 +19,21 @@ namespace sem {
 
 int* device_error_word(sem_handle* h) { return reinterpret_cast<int*>(h->scratch + 8); }
 
-int ax_variant_for(const sem_handle* h, int lx, bool fp32) {
-    const int v = h->ax_variant[fp32 ? 1 : 0][lx];
-    if (v == kDfVariant) return (!fp32 && lx <= 12) ? v : 0;
-    if (v == kDflVariant) return (!fp32 && bulk_supported(lx)) ? v : 0;
-    return (v > 0 && bulk_fits(lx, v, fp32)) ? v : 0;
+int ax_variant_for(const sem_handle* h, int lx, int cls) {
+    const int v = h->ax_variant[cls][lx];
+    if (cls == kClsPair) {
+        // pinned 5 or 6 where it applies, else the line-transform form, else the
+        // general pair kernel; orders neither covers use the native FP64 kernels
+        if (v == kDflVariant && bulk_supported(lx)) return v;
+        if (v == kDfVariant && lx <= 12) return v;
+        if (bulk_supported(lx)) return kDflVariant;
+        return lx <= 12 ? kDfVariant : ax_variant_for(h, lx, kClsF64);
+    }
+    return (v > 0 && v <= kBulkVariantsMax && bulk_fits(lx, v, cls == kClsF32)) ? v : 0;
+}
+
+int ax_variant_of_precision(const sem_handle* h, int lx, int precision) {
+    return precision == SEM_FP64_NATIVE ? 0 : ax_variant_for(h, lx, precision_class(precision));
 }
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
@@ -87,7 +97,7 @@ int launch_ax_local(sem_handle* h, const void* u, void* w, int precision, cudaSt
             a.G = h->G32 + 6 * p.loc_off;
             a.D = h->D32[p.lx];
             a.E = p.E;
-            rc = dispatch_variant<float>(h, p.lx, a, false, ax_variant_for(h, p.lx, true), s);
+            rc = dispatch_variant<float>(h, p.lx, a, false, ax_variant_for(h, p.lx, kClsF32), s);
         } else {
             AxParams<double> a = {};
             a.u = (const double*)u + p.loc_off;
@@ -95,8 +105,7 @@ int launch_ax_local(sem_handle* h, const void* u, void* w, int precision, cudaSt
             a.G = h->G64 + 6 * p.loc_off;
             a.D = h->D64[p.lx];
             a.E = p.E;
-            const int v = precision == SEM_FP64_NATIVE ? 0 : ax_variant_for(h, p.lx, false);
-            rc = dispatch_variant<double>(h, p.lx, a, false, v, s);
+            rc = dispatch_variant<double>(h, p.lx, a, false, ax_variant_of_precision(h, p.lx, precision), s);
         }
         if (rc) return rc;
     }
@@ -118,7 +127,7 @@ int launch_cg_pupdate_ax(sem_handle* h, int precision, cudaStream_t s) {
         a.st = h->state + 1;
         a.partials = h->partials;
         a.counter = h->counters + 2;
-        return dispatch_variant<float>(h, p.lx, a, true, ax_variant_for(h, p.lx, true), s);
+        return dispatch_variant<float>(h, p.lx, a, true, ax_variant_for(h, p.lx, kClsF32), s);
     }
     AxParams<double> a = {};
     a.w = h->ws.w;
@@ -130,19 +139,18 @@ int launch_cg_pupdate_ax(sem_handle* h, int precision, cudaStream_t s) {
     a.st = h->state;
     a.partials = h->partials;
     a.counter = h->counters + 2;
-    const int v = precision == SEM_FP64_NATIVE ? 0 : ax_variant_for(h, p.lx, false);
-    return dispatch_variant<double>(h, p.lx, a, true, v, s);
+    return dispatch_variant<double>(h, p.lx, a, true, ax_variant_of_precision(h, p.lx, precision), s);
 }
 
 // Set kernel attributes and cache occupancies of the CG kernels of this
 // handle before any stream capture (those calls are kept out of captures).
 int prepare_cg_kernels(sem_handle* h) {
     for (const MeshPart& p : h->parts) {
-        for (int fp32 = 0; fp32 < 2; fp32++)
+        for (int cls = 0; cls < 3; cls++)
             for (int fused = 0; fused < 2; fused++) {
-                const int v = ax_variant_for(h, p.lx, fp32 != 0);
+                const int v = ax_variant_for(h, p.lx, cls);
                 int rc;
-                if (fp32) {
+                if (cls == kClsF32) {
                     AxParams<float> a = {};
                     a.dry = 1;
                     a.variant = v;
@@ -168,11 +176,13 @@ int prepare_cg_kernels(sem_handle* h) {
     return SEM_OK;
 }
 
-// Autotuner: time every operator variant that fits (shared-slab staging and
-// the bulk-staged (elements per CTA, stages) configurations) on this handle's
-// own factors with the plain kernel, a few launches each after a warm-up, and
-// keep the fastest per order for the precision.  The fused CG kernel uses the
-// same choice.  Runs once per handle and precision, outside any capture.
+// Autotuner: time every operator variant of the class that fits (shared-slab
+// staging and the bulk-staged (elements per CTA, stages) configurations) on
+// this handle's own factors with the plain kernel, a few launches each after a
+// warm-up, and keep the fastest per order (FP32 class, or native FP64 class).
+// The fused CG kernel uses the same choice.  Runs once per handle and class,
+// outside any capture.  The pair class needs no timing (its line-transform
+// form is the faster one wherever it applies).
 int autotune_ax(sem_handle* h, bool fp32, cudaStream_t s) {
     int rc = ensure_workspace(h, fp32);
     if (rc) return rc;
@@ -183,10 +193,8 @@ int autotune_ax(sem_handle* h, bool fp32, cudaStream_t s) {
         if (h->ax_variant[fp32][p.lx] >= 0) continue;
         float best = 1e30f;
         int best_v = 0;
-        for (int v = 0; v <= kDflVariant; v++) {
-            if (v > 0 && v < kDfVariant && !bulk_fits(p.lx, v, fp32)) continue;
-            if (v == kDfVariant && (fp32 || p.lx > 12)) continue;
-            if (v == kDflVariant && (fp32 || !bulk_supported(p.lx))) continue;
+        for (int v = 0; v <= kBulkVariantsMax; v++) {
+            if (v > 0 && !bulk_fits(p.lx, v, fp32)) continue;
             int rc2;
             auto run = [&](int dry) -> int {
                 if (fp32) {
@@ -262,8 +270,7 @@ extern "C" {
 
 SEM_API int sem_ax(sem_handle* h, void* w, const void* u, int precision, int assemble, cudaStream_t s) {
     if (!h || !w || !u) return fail(SEM_EINVAL, "null argument");
-    if (precision != SEM_FP64 && precision != SEM_FP32 && precision != SEM_FP64_NATIVE)
-        return fail(SEM_EINVAL, "unknown precision");
+    if (!valid_precision(precision)) return fail(SEM_EINVAL, "unknown precision");
     if (w == u) return fail(SEM_EINVAL, "w must not alias u");
     if (!aligned16(w) || !aligned16(u)) return fail(SEM_EINVAL, "u and w must be 16-byte aligned");
     int rc = launch_ax_local(h, u, w, precision, s);
@@ -276,7 +283,7 @@ SEM_API int sem_mass(sem_handle* h, void* w, const void* u, int precision, int a
     int rc;
     if (precision == SEM_FP32)
         rc = launch_mass32(h, (const float*)u, (float*)w, s);
-    else if (precision == SEM_FP64 || precision == SEM_FP64_NATIVE)
+    else if (valid_precision(precision))
         rc = launch_mass(h, (const double*)u, (double*)w, s);
     else
         return fail(SEM_EINVAL, "unknown precision");

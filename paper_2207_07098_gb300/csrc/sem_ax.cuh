@@ -70,6 +70,14 @@ struct AxSmem {
         sr = su + C::EPC * C::N3;
         ss = sr + C::EPC * C::N3;
     }
+    // D (padded rows) at d, the EPC element slots of u, wr, ws from `slots` on
+    __device__ __forceinline__ AxSmem(T* d, T* slots) {
+        using C = AxCfg<LX>;
+        sD = d;
+        su = slots;
+        sr = su + C::EPC * C::N3;
+        ss = sr + C::EPC * C::N3;
+    }
 };
 
 // Thread coordinates inside a CTA: element slot `el`, column (i, j).

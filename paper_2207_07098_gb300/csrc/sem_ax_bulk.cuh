@@ -315,7 +315,11 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
         __syncthreads();
     }
     if (abort_flag) {
-        // a copy never completed: report, let the other copies land, return
+        // a copy never completed: report, let the other copies land, return.
+        // No stage is issued after the failed wait (the loop breaks before its
+        // refill).  The drain is bounded and best-effort: each stage still in
+        // flight gets a quarter of the wait budget, after which the CTA exits
+        // whether or not its copies have landed.
         if (tid == 0) {
             atomicExch(a.err, 1);
             for (int s = 0; s < NST; s++) {

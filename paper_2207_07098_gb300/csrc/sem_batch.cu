@@ -285,15 +285,20 @@ __global__ void correct_batch_kernel(double* x, const float* d32, TileList tl, c
 
 static int epc_of(int lx) { return std::max(1, 256 / (lx * lx)); }
 
-static int batch_bulk_variant(const sem_handle* h, int lx);
 
 // Cuts every solve of order lx into groups of at most epc_for(lx) elements
 // (epc 0: no groups of that order), one list per order present, numbered
 // globally; fills the per-solve first group and group count on the device.
+struct UnifiedGroups {
+    std::vector<int64_t> loc;
+    std::vector<int> cnt, sol;
+    std::vector<uint8_t> lx;
+};
+
 template <typename EpcFor>
 static int build_group_lists(sem_handle* h, const std::vector<int>& lxs, EpcFor epc_for,
                              std::vector<LxGroups>& lists, int64_t* total, int** d_first,
-                             int** d_count, double** d_part) {
+                             int** d_count, double** d_part, UnifiedGroups* all = nullptr) {
     const int ns = h->nsolve;
     std::vector<int> sgfirst(ns, 0), sgcount(ns, 0);
     int64_t goff = 0;
@@ -328,6 +333,12 @@ static int build_group_lists(sem_handle* h, const std::vector<int>& lxs, EpcFor 
             SEM_CUDA_TRY(cudaMemcpy(gl.cnt, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice));
             SEM_CUDA_TRY(cudaMemcpy(gl.solve, sol.data(), sol.size() * sizeof(int), cudaMemcpyHostToDevice));
         }
+        if (all) {
+            all->loc.insert(all->loc.end(), loc.begin(), loc.end());
+            all->cnt.insert(all->cnt.end(), cnt.begin(), cnt.end());
+            all->sol.insert(all->sol.end(), sol.begin(), sol.end());
+            all->lx.insert(all->lx.end(), loc.size(), (uint8_t)lx);
+        }
         goff += g.ngroups;
     }
     *total = goff;
@@ -338,24 +349,32 @@ static int build_group_lists(sem_handle* h, const std::vector<int>& lxs, EpcFor 
     return SEM_OK;
 }
 
-static int build_plan(sem_handle* h) {
-    BatchPlan& bp = h->batch;
-    if (bp.ready) return SEM_OK;
-    const int ns = h->nsolve;
+static std::vector<int> orders_present(const sem_handle* h) {
     std::vector<int> lxs;
     for (auto& p : h->parts) lxs.push_back(p.lx);
     std::sort(lxs.begin(), lxs.end());
     lxs.erase(std::unique(lxs.begin(), lxs.end()), lxs.end());
-    int rc = build_group_lists(h, lxs, epc_of, bp.lxg, &bp.ngroups, &bp.sgfirst, &bp.sgcount, &bp.gpart);
-    if (!rc)
-        rc = build_group_lists(
-            h, lxs,
-            [&](int lx) {
-                const int v = batch_bulk_variant(h, lx);
-                return v > 0 ? kBulkCfg[v - 1][0] : 0;
-            },
-            bp.blxg, &bp.bngroups, &bp.bsgfirst, &bp.bsgcount, &bp.bgpart);
+    return lxs;
+}
+
+static int build_plan(sem_handle* h) {
+    BatchPlan& bp = h->batch;
+    if (bp.ready) return SEM_OK;
+    const int ns = h->nsolve;
+    const std::vector<int> lxs = orders_present(h);
+    UnifiedGroups all;
+    int rc = build_group_lists(h, lxs, epc_of, bp.lxg, &bp.ngroups, &bp.sgfirst, &bp.sgcount, &bp.gpart, &all);
     if (rc) return rc;
+    bp.multi_ok = lxs.back() <= kMultiMaxLx;
+    if ((rc = dalloc(h, &bp.uloc, all.loc.size())) || (rc = dalloc(h, &bp.ucnt, all.cnt.size())) ||
+        (rc = dalloc(h, &bp.usolve, all.sol.size())) || (rc = dalloc(h, &bp.ulx, all.lx.size())))
+        return rc;
+    if (!all.loc.empty()) {
+        SEM_CUDA_TRY(cudaMemcpy(bp.uloc, all.loc.data(), all.loc.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+        SEM_CUDA_TRY(cudaMemcpy(bp.ucnt, all.cnt.data(), all.cnt.size() * sizeof(int), cudaMemcpyHostToDevice));
+        SEM_CUDA_TRY(cudaMemcpy(bp.usolve, all.sol.data(), all.sol.size() * sizeof(int), cudaMemcpyHostToDevice));
+        SEM_CUDA_TRY(cudaMemcpy(bp.ulx, all.lx.data(), all.lx.size(), cudaMemcpyHostToDevice));
+    }
     std::vector<int64_t> tloc;
     std::vector<int> tlen, tsol, stfirst(ns), stcount(ns);
     for (int q = 0; q < ns; q++) {
@@ -392,104 +411,267 @@ static TileList tiles(sem_handle* h) {
 
 static int grid_tiles(sem_handle* h) { return grid_for(h, h->batch.ntiles * 256, 256, 8); }
 
-// FP64 batches use the FP32-pair line-transform operator for the orders it
-// covers unless a native variant (0..4) was pinned at set-up.
-static bool batch_uses_pair_arith(const sem_handle* h, int lx) {
-    const int v = h->ax_variant[0][lx];
-    return (lx % 2 == 0 && lx >= 4 && lx <= 12) && (v < 0 || v >= kDfVariant);
+// FP64 batches with SEM_FP64_PAIR use the FP32-pair line-transform operator
+// for the orders it covers; every other FP64 application (SEM_FP64, the true
+// residual) uses the native FP64 batch kernel.
+static bool batch_uses_pair_arith(int lx, int precision) {
+    return precision == SEM_FP64_PAIR && lx % 2 == 0 && lx >= 4 && lx <= 12;
 }
 
-// FP32 batches use the bulk-staged operator for order lx only when a bulk
-// variant was pinned at set-up, it fits, and every solve of that order starts
-// on a 16-byte boundary (bulk copies need it; the elements of an even order
-// keep it).  By default they use the slab kernel over the element-group
-// lists: on the 256-box batch (N in {5, 7, 9}) it was faster than every bulk
-// variant (mixed solve 2.97 s against 3.50-3.97 s).
-static int batch_bulk_variant(const sem_handle* h, int lx) {
+// Bulk-staged operator variant v (1..4) can serve order lx of an FP32 batch:
+// it fits, and every solve of that order starts on a 16-byte boundary (bulk
+// copies need it; the elements of an even order keep it).
+static bool batch_bulk_ok(const sem_handle* h, int lx, int v) {
+    if (v < 1 || v > kBulkVariantsMax || !bulk_fits(lx, v, true)) return false;
     for (const MeshPart& p : h->parts)
-        if (p.lx == lx && (p.loc_off % 4) != 0) return 0;
-    const int pinned = h->ax_variant[1][lx];
-    if (pinned > 0 && pinned <= kBulkVariantsMax && bulk_fits(lx, pinned, true)) return pinned;
-    return 0;
+        if (p.lx == lx && (p.loc_off % 4) != 0) return false;
+    return true;
 }
 
-// K-A over every order present: fused (CG state slot base `st`) or plain.
-static int batch_ax(sem_handle* h, bool fp32, bool fused, const void* u, CGState* st, cudaStream_t s) {
+static int bulk_set_index(int epc) { return epc == 1 ? 0 : epc == 2 ? 1 : 2; }
+
+// group lists cut to `epc` elements per group for every order present
+static int ensure_bulk_set(sem_handle* h, int epc) {
+    BatchPlan::BulkSet& bs = h->batch.bulk[bulk_set_index(epc)];
+    if (bs.built) return SEM_OK;
+    int rc = build_group_lists(h, orders_present(h), [&](int) { return epc; }, bs.lists, &bs.ngroups, &bs.sgfirst,
+                               &bs.sgcount, &bs.gpart);
+    if (rc) return rc;
+    bs.built = true;
+    return SEM_OK;
+}
+
+// K-A of one order lx (list index li) with operator variant v: fused (CG state
+// slot base `st`) or plain.  precision: SEM_FP32, SEM_FP64 or SEM_FP64_PAIR.
+static int batch_ax_order(sem_handle* h, int precision, size_t li, int v, bool fused, const void* u, CGState* st,
+                          cudaStream_t s) {
     BatchPlan& bp = h->batch;
+    const LxGroups& g = bp.lxg[li];
+    if (precision == SEM_FP32 && v > 0) {
+        const int epc = kBulkCfg[v - 1][0];
+        int rc = ensure_bulk_set(h, epc);
+        if (rc) return rc;
+        const BatchPlan::BulkSet& bs = bp.bulk[bulk_set_index(epc)];
+        const LxGroups& gb = bs.lists[li];
+        AxParams<float> a = {};
+        a.u = (const float*)u;
+        a.z = h->ws.z32;
+        a.p = h->ws.p32;
+        a.w = h->ws.w32;
+        a.G = h->G32;
+        a.D = h->D32[g.lx];
+        a.variant = v;
+        a.err = device_error_word(h);
+        a.wait_budget = h->test_stall ? 100000000LL : 4000000000LL;
+        a.tx_extra = h->test_stall ? 16u : 0u;
+        a.loc = gb.loc; a.cnt = gb.cnt; a.solve = gb.solve; a.ngroups = gb.ngroups; a.goff = gb.goff;
+        a.st = st; a.sgfirst = bs.sgfirst; a.sgcount = bs.sgcount; a.gpart = bs.gpart; a.scount = bp.scount;
+        return dispatch_ax_bulk_batch_f32(h, g.lx, a, fused, s);
+    }
+    if (precision == SEM_FP32) {
+        BatchAxParams<float> a = {};
+        a.u = (const float*)u;
+        a.z = h->ws.z32;
+        a.p = h->ws.p32;
+        a.w = h->ws.w32;
+        a.G = h->G32;
+        a.D = h->D32[g.lx];
+        a.loc = g.loc; a.cnt = g.cnt; a.solve = g.solve; a.ngroups = g.ngroups; a.goff = g.goff;
+        a.st = st; a.sgfirst = bp.sgfirst; a.sgcount = bp.sgcount; a.gpart = bp.gpart; a.scount = bp.scount;
+        return dispatch_ax_batch_f32(h, g.lx, a, fused, s);
+    }
+    if (batch_uses_pair_arith(g.lx, precision)) {
+        DflParams d = {};
+        d.u = (const double*)u;
+        d.z = h->ws.z;
+        d.p = h->ws.p;
+        d.w = h->ws.w;
+        d.G2 = h->G2;
+        d.loc = g.loc; d.cnt = g.cnt; d.solve = g.solve; d.ngroups = g.ngroups; d.goff = g.goff;
+        d.st = st; d.sgfirst = bp.sgfirst; d.sgcount = bp.sgcount; d.gpart = bp.gpart; d.scount = bp.scount;
+        return dispatch_ax_dfl_batch_entry(h, g.lx, d, fused, s);
+    }
+    BatchAxParams<double> a = {};
+    a.u = (const double*)u;
+    a.z = h->ws.z;
+    a.p = h->ws.p;
+    a.w = h->ws.w;
+    a.G = h->G64;
+    a.D = h->D64[g.lx];
+    a.loc = g.loc; a.cnt = g.cnt; a.solve = g.solve; a.ngroups = g.ngroups; a.goff = g.goff;
+    a.st = st; a.sgfirst = bp.sgfirst; a.sgcount = bp.sgcount; a.gpart = bp.gpart; a.scount = bp.scount;
+    return dispatch_ax_batch_f64(h, g.lx, a, fused, s);
+}
+
+// One slab launch over the groups of every order (SEM_FP32 or SEM_FP64).
+static int batch_ax_multi(sem_handle* h, int precision, bool fused, const void* u, CGState* st, cudaStream_t s,
+                          int dry = 0) {
+    BatchPlan& bp = h->batch;
+    bool present[kMaxLx + 1] = {};
+    for (const LxGroups& g : bp.lxg) present[g.lx] = true;
+    if (precision == SEM_FP32) {
+        BatchAxParams<float> a = {};
+        a.u = (const float*)u;
+        a.z = h->ws.z32;
+        a.p = h->ws.p32;
+        a.w = h->ws.w32;
+        a.G = h->G32;
+        a.loc = bp.uloc; a.cnt = bp.ucnt; a.solve = bp.usolve; a.ngroups = bp.ngroups; a.goff = 0;
+        a.st = st; a.sgfirst = bp.sgfirst; a.sgcount = bp.sgcount; a.gpart = bp.gpart; a.scount = bp.scount;
+        a.dry = dry;
+        MultiOrder<float> mo = {};
+        for (int lx = 2; lx <= kMultiMaxLx; lx++) mo.D[lx] = present[lx] ? h->D32[lx] : nullptr;
+        mo.lx = bp.ulx;
+        return launch_ax_batch_multi_f32(h, a, mo, multi_smem_bytes<float>(present), fused, s);
+    }
+    BatchAxParams<double> a = {};
+    a.u = (const double*)u;
+    a.z = h->ws.z;
+    a.p = h->ws.p;
+    a.w = h->ws.w;
+    a.G = h->G64;
+    a.loc = bp.uloc; a.cnt = bp.ucnt; a.solve = bp.usolve; a.ngroups = bp.ngroups; a.goff = 0;
+    a.st = st; a.sgfirst = bp.sgfirst; a.sgcount = bp.sgcount; a.gpart = bp.gpart; a.scount = bp.scount;
+    a.dry = dry;
+    MultiOrder<double> mo = {};
+    for (int lx = 2; lx <= kMultiMaxLx; lx++) mo.D[lx] = present[lx] ? h->D64[lx] : nullptr;
+    mo.lx = bp.ulx;
+    return launch_ax_batch_multi_f64(h, a, mo, multi_smem_bytes<double>(present), fused, s);
+}
+
+// K-A over every order present with the class's chosen configuration.
+static int batch_ax(sem_handle* h, int precision, bool fused, const void* u, CGState* st, cudaStream_t s) {
+    BatchPlan& bp = h->batch;
+    const int cls = precision == SEM_FP32 ? kClsF32 : kClsF64;
+    if (precision != SEM_FP64_PAIR && bp.kcfg[cls] == 1) return batch_ax_multi(h, precision, fused, u, st, s);
     for (size_t li = 0; li < bp.lxg.size(); li++) {
-        const LxGroups& g = bp.lxg[li];
-        int rc;
-        const int bv = batch_bulk_variant(h, g.lx);
-        if (fp32 && bv > 0) {
-            const LxGroups& gb = bp.blxg[li];
-            AxParams<float> a = {};
-            a.u = (const float*)u;
-            a.z = h->ws.z32;
-            a.p = h->ws.p32;
-            a.w = h->ws.w32;
-            a.G = h->G32;
-            a.D = h->D32[g.lx];
-            a.variant = bv;
-            a.err = device_error_word(h);
-            a.wait_budget = h->test_stall ? 100000000LL : 4000000000LL;
-            a.tx_extra = h->test_stall ? 16u : 0u;
-            a.loc = gb.loc; a.cnt = gb.cnt; a.solve = gb.solve; a.ngroups = gb.ngroups; a.goff = gb.goff;
-            a.st = st; a.sgfirst = bp.bsgfirst; a.sgcount = bp.bsgcount; a.gpart = bp.bgpart; a.scount = bp.scount;
-            rc = dispatch_ax_bulk_batch_f32(h, g.lx, a, fused, s);
-        } else if (fp32) {
-            BatchAxParams<float> a = {};
-            a.u = (const float*)u;
-            a.z = h->ws.z32;
-            a.p = h->ws.p32;
-            a.w = h->ws.w32;
-            a.G = h->G32;
-            a.D = h->D32[g.lx];
-            a.loc = g.loc; a.cnt = g.cnt; a.solve = g.solve; a.ngroups = g.ngroups; a.goff = g.goff;
-            a.st = st; a.sgfirst = bp.sgfirst; a.sgcount = bp.sgcount; a.gpart = bp.gpart; a.scount = bp.scount;
-            rc = dispatch_ax_batch_f32(h, g.lx, a, fused, s);
-        } else if (batch_uses_pair_arith(h, g.lx)) {
-            DflParams d = {};
-            d.u = (const double*)u;
-            d.z = h->ws.z;
-            d.p = h->ws.p;
-            d.w = h->ws.w;
-            d.G2 = h->G2;
-            d.loc = g.loc; d.cnt = g.cnt; d.solve = g.solve; d.ngroups = g.ngroups; d.goff = g.goff;
-            d.st = st; d.sgfirst = bp.sgfirst; d.sgcount = bp.sgcount; d.gpart = bp.gpart; d.scount = bp.scount;
-            rc = dispatch_ax_dfl_batch_entry(h, g.lx, d, fused, s);
-        } else {
-            BatchAxParams<double> a = {};
-            a.u = (const double*)u;
-            a.z = h->ws.z;
-            a.p = h->ws.p;
-            a.w = h->ws.w;
-            a.G = h->G64;
-            a.D = h->D64[g.lx];
-            a.loc = g.loc; a.cnt = g.cnt; a.solve = g.solve; a.ngroups = g.ngroups; a.goff = g.goff;
-            a.st = st; a.sgfirst = bp.sgfirst; a.sgcount = bp.sgcount; a.gpart = bp.gpart; a.scount = bp.scount;
-            rc = dispatch_ax_batch_f64(h, g.lx, a, fused, s);
-        }
+        const int v = precision == SEM_FP64_PAIR ? 0 : bp.ovar[cls][bp.lxg[li].lx];
+        int rc = batch_ax_order(h, precision, li, v, fused, u, st, s);
         if (rc) return rc;
     }
     return SEM_OK;
 }
 
+// K-A launches of one batched iteration
+static int batch_ka_launches(const sem_handle* h, int precision) {
+    const int cls = precision == SEM_FP32 ? kClsF32 : kClsF64;
+    return (precision != SEM_FP64_PAIR && h->batch.kcfg[cls] == 1) ? 1 : (int)h->batch.lxg.size();
+}
+
+// Operator configuration of a batch for class cls (FP32 or native FP64):
+// variants pinned at set-up are honoured (one launch per order); otherwise,
+// with autotuning, each order's candidates (slab; for FP32 the bulk-staged
+// (elements per CTA, stages) variants that fit and are aligned) are timed on
+// the handle's own data with the plain operator over that order's groups, and
+// the sum of the fastest per order is compared with one multi-order slab
+// launch over every group; without autotuning the multi-order launch is taken
+// where it applies.  Runs once per handle and class, outside any capture.
+static int batch_configure(sem_handle* h, int cls, bool autotune, cudaStream_t s) {
+    BatchPlan& bp = h->batch;
+    if (bp.kcfg[cls] >= 0) return SEM_OK;
+    const bool fp32 = cls == kClsF32;
+    const int precision = fp32 ? SEM_FP32 : SEM_FP64;
+    bool pinned = false;
+    for (const LxGroups& g : bp.lxg) {
+        const int v = h->ax_variant[cls][g.lx];
+        if (v >= 0 && v <= kBulkVariantsMax) {
+            pinned = true;
+            bp.ovar[cls][g.lx] = (fp32 && batch_bulk_ok(h, g.lx, v)) ? v : 0;
+        } else {
+            bp.ovar[cls][g.lx] = 0;
+        }
+    }
+    if (pinned) {
+        bp.kcfg[cls] = 0;
+        return SEM_OK;
+    }
+    if (!autotune) {
+        bp.kcfg[cls] = bp.multi_ok ? 1 : 0;
+        return SEM_OK;
+    }
+    int rc = ensure_workspace(h, fp32);
+    if (rc) return rc;
+    const void* u = fp32 ? (const void*)h->ws.z32 : (const void*)h->ws.z;
+    SEM_CUDA_TRY(cudaMemsetAsync(const_cast<void*>(u), 0, (fp32 ? 4 : 8) * (size_t)h->n_local, s));
+    cudaEvent_t e0, e1;
+    SEM_CUDA_TRY(cudaEventCreate(&e0));
+    SEM_CUDA_TRY(cudaEventCreate(&e1));
+    auto time_it = [&](auto&& launch, float* ms) -> int {
+        int r = launch();  // warm-up (also sets kernel attributes outside any capture)
+        if (r) return r;
+        cudaEventRecord(e0, s);
+        for (int k = 0; k < 3 && !r; k++) r = launch();
+        cudaEventRecord(e1, s);
+        if (r) return r;
+        if (cudaEventSynchronize(e1) != cudaSuccess) return cuda_fail(cudaGetLastError(), "batch tuning");
+        cudaEventElapsedTime(ms, e0, e1);
+        return SEM_OK;
+    };
+    float per_order = 0.0f;
+    for (size_t li = 0; li < bp.lxg.size() && !rc; li++) {
+        const int lx = bp.lxg[li].lx;
+        float best = 1e30f;
+        int best_v = 0;
+        for (int v = 0; v <= (fp32 ? kBulkVariantsMax : 0); v++) {
+            if (v > 0 && !batch_bulk_ok(h, lx, v)) continue;
+            float ms = 0.0f;
+            rc = time_it([&]() { return batch_ax_order(h, precision, li, v, false, u, nullptr, s); }, &ms);
+            if (rc) break;
+            if (ms < best) {
+                best = ms;
+                best_v = v;
+            }
+        }
+        bp.ovar[cls][lx] = best_v;
+        per_order += best;
+    }
+    int cfg = 0;
+    if (!rc && bp.multi_ok) {
+        float ms = 0.0f;
+        rc = time_it([&]() { return batch_ax_multi(h, precision, false, u, nullptr, s); }, &ms);
+        if (!rc && ms < per_order) cfg = 1;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    bp.kcfg[cls] = cfg;
+    return SEM_OK;
+}
+
 static int prepare_batch_kernels(sem_handle* h) {
-    for (const LxGroups& g : h->batch.lxg) {
+    BatchPlan& bp = h->batch;
+    // group lists of the bulk-staged variants in use (allocation is not allowed during capture)
+    for (const LxGroups& g : bp.lxg) {
+        const int v = bp.ovar[kClsF32][g.lx];
+        if (v > 0) {
+            int rc = ensure_bulk_set(h, kBulkCfg[v - 1][0]);
+            if (rc) return rc;
+        }
+    }
+    for (int cls = 0; cls < 2; cls++) {
+        if (bp.kcfg[cls] == 1) {
+            const int prec = cls == kClsF32 ? SEM_FP32 : SEM_FP64;
+            int rc = batch_ax_multi(h, prec, true, nullptr, nullptr, 0, 1);
+            if (!rc) rc = batch_ax_multi(h, prec, false, nullptr, nullptr, 0, 1);
+            if (rc) return rc;
+        }
+    }
+    for (const LxGroups& g : bp.lxg) {
         BatchAxParams<double> a = {};
         a.dry = 1;
         BatchAxParams<float> b = {};
         b.dry = 1;
         int rc = dispatch_ax_batch_f64(h, g.lx, a, true, 0);
         if (!rc) rc = dispatch_ax_batch_f64(h, g.lx, a, false, 0);
-        if (!rc && batch_bulk_variant(h, g.lx) > 0) {
+        const int bv = bp.ovar[kClsF32][g.lx];
+        if (!rc && bv > 0) {
             AxParams<float> c = {};
             c.dry = 1;
-            c.variant = batch_bulk_variant(h, g.lx);
+            c.variant = bv;
             rc = dispatch_ax_bulk_batch_f32(h, g.lx, c, true, 0);
             if (!rc) rc = dispatch_ax_bulk_batch_f32(h, g.lx, c, false, 0);
         }
-        if (!rc && batch_uses_pair_arith(h, g.lx)) {
+        if (!rc && batch_uses_pair_arith(g.lx, SEM_FP64_PAIR)) {
             DflParams d = {};
             d.dry = 1;
             rc = dispatch_ax_dfl_batch_entry(h, g.lx, d, true, 0);
@@ -556,7 +738,8 @@ static int ensure_segment_solves(sem_handle* h) {
 
 // K-B and K-C of one batched iteration (K-B leaves the segments of the
 // solves already done: their w is not used).
-static int batch_kb_kc(sem_handle* h, bool fp32, CGState* st, cudaStream_t s) {
+static int batch_kb_kc(sem_handle* h, int precision, CGState* st, cudaStream_t s) {
+    const bool fp32 = precision == SEM_FP32;
     void* w = fp32 ? (void*)h->ws.w32 : (void*)h->ws.w;
     int rc;
     if (h->batch.sid_ready) {
@@ -579,17 +762,18 @@ static int batch_kb_kc(sem_handle* h, bool fp32, CGState* st, cudaStream_t s) {
     return SEM_OK;
 }
 
-static int batch_iteration(sem_handle* h, bool fp32, CGState* st, cudaStream_t s) {
-    int rc = batch_ax(h, fp32, true, nullptr, st, s);
-    return rc ? rc : batch_kb_kc(h, fp32, st, s);
+static int batch_iteration(sem_handle* h, int precision, CGState* st, cudaStream_t s) {
+    int rc = batch_ax(h, precision, true, nullptr, st, s);
+    return rc ? rc : batch_kb_kc(h, precision, st, s);
 }
 
-static int batch_graph(sem_handle* h, bool fp32, CGState* st, int chunk, cudaGraphExec_t* out, int* per_launch) {
+static int batch_graph(sem_handle* h, int precision, CGState* st, int chunk, cudaGraphExec_t* out,
+                       int* per_launch) {
     GraphCache& g = h->graph;
-    const int key = 100 + (fp32 ? 1 : 0);
+    const int key = 100 + precision;
     if (g.exec && g.key_prec == key && g.key_chunk == chunk && g.key_ptr == st) {
         *out = g.exec;
-        *per_launch = (int)h->batch.lxg.size() + 2;
+        *per_launch = batch_ka_launches(h, precision) + 2;
         return SEM_OK;
     }
     if (g.exec) {
@@ -608,10 +792,10 @@ static int batch_graph(sem_handle* h, bool fp32, CGState* st, int chunk, cudaGra
     for (int it = 0; it < chunk && rc == SEM_OK; it++) {
         if (it == 0 && cudaEventRecordWithFlags(h->ax_ev[0], cs, cudaEventRecordExternal) != cudaSuccess)
             rc = fail(SEM_ECUDA, "event record");
-        if (!rc) rc = batch_ax(h, fp32, true, nullptr, st, cs);
+        if (!rc) rc = batch_ax(h, precision, true, nullptr, st, cs);
         if (it == 0 && !rc && cudaEventRecordWithFlags(h->ax_ev[1], cs, cudaEventRecordExternal) != cudaSuccess)
             rc = fail(SEM_ECUDA, "event record");
-        if (!rc) rc = batch_kb_kc(h, fp32, st, cs);
+        if (!rc) rc = batch_kb_kc(h, precision, st, cs);
     }
     h->launches = before;
     cudaGraph_t graph = nullptr;
@@ -631,19 +815,19 @@ static int batch_graph(sem_handle* h, bool fp32, CGState* st, int chunk, cudaGra
     g.key_chunk = chunk;
     g.key_ptr = st;
     *out = g.exec;
-    *per_launch = (int)h->batch.lxg.size() + 2;
+    *per_launch = batch_ka_launches(h, precision) + 2;
     return SEM_OK;
 }
 
 // Iterate until every state in [st, st + ns) is done.
-static int batch_loop(sem_handle* h, bool fp32, CGState* st, const sem_solve_opts& o, cudaStream_t s,
+static int batch_loop(sem_handle* h, int precision, CGState* st, const sem_solve_opts& o, cudaStream_t s,
                       std::vector<CGState>& hs, double* ax_ms_sum, int* ax_samples) {
     const int ns = h->nsolve;
     const int chunk = std::max(1, std::min(o.graph_chunk, 1024));
     cudaGraphExec_t exec = nullptr;
     int per_launch = 0;
     if (o.use_graph) {
-        int rc = batch_graph(h, fp32, st, chunk, &exec, &per_launch);
+        int rc = batch_graph(h, precision, st, chunk, &exec, &per_launch);
         if (rc) return rc;
     }
     auto read = [&]() -> int {
@@ -666,7 +850,7 @@ static int batch_loop(sem_handle* h, bool fp32, CGState* st, const sem_solve_opt
             h->launches += (int64_t)per_launch * chunk;
         } else {
             for (int it = 0; it < chunk; it++)
-                if ((rc = batch_iteration(h, fp32, st, s))) return rc;
+                if ((rc = batch_iteration(h, precision, st, s))) return rc;
         }
         if ((rc = read())) return rc;
         if (exec) {
@@ -683,8 +867,9 @@ static int batch_loop(sem_handle* h, bool fp32, CGState* st, const sem_solve_opt
     return SEM_OK;
 }
 
+// r = b - A x per solve with the native FP64 operator, <r,r> and <b,b> per solve
 static int batch_true_residual(sem_handle* h, cudaStream_t s) {
-    int rc = batch_ax(h, false, false, h->ws.x, nullptr, s);
+    int rc = batch_ax(h, SEM_FP64, false, h->ws.x, nullptr, s);
     if (!rc) rc = launch_gs(h, h->ws.w, false, true, s);
     if (rc) return rc;
     resid_batch_kernel<<<grid_tiles(h), 256, 0, s>>>(h->ws.b, h->ws.w, h->ws.r, h->mult, tiles(h), h->batch.rrbb);
@@ -706,6 +891,9 @@ static int solve_batch(sem_handle* h, double* x_user, const double* b_user, cons
                        sem_solve_stats* stats, cudaStream_t s) {
     int rc = ensure_workspace(h, o.mode == SEM_MODE_MIXED_IR);
     if (!rc) rc = build_plan(h);
+    // operator configuration of each class this solve uses (tuned once per handle)
+    if (!rc) rc = batch_configure(h, kClsF64, o.autotune != 0, s);
+    if (!rc && o.mode == SEM_MODE_MIXED_IR) rc = batch_configure(h, kClsF32, o.autotune != 0, s);
     if (rc) return rc;
     const int ns = h->nsolve;
     const int64_t n = h->n_local;
@@ -731,6 +919,8 @@ static int solve_batch(sem_handle* h, double* x_user, const double* b_user, cons
     };
     if ((rc = batch_true_residual(h, s))) return rc;
     if (o.mode == SEM_MODE_FP64) {
+        // SEM_FP64_NATIVE has no batched form of its own: the FP64 class serves it
+        const int prec64 = o.precision == SEM_FP64_PAIR ? SEM_FP64_PAIR : SEM_FP64;
         // CG with residual replacement per solve (see the single-mesh solver)
         std::vector<int> act(ns, 1);
         for (int restart = 0;; restart++) {
@@ -755,7 +945,7 @@ static int solve_batch(sem_handle* h, double* x_user, const double* b_user, cons
             }
             SEM_LAUNCH_CHECK("init_batch_kernel");
             h->launches++;
-            if ((rc = batch_loop(h, false, h->state, o, s, hs, &ax_sum, &ax_n))) return rc;
+            if ((rc = batch_loop(h, prec64, h->state, o, s, hs, &ax_sum, &ax_n))) return rc;
             for (int q = 0; q < ns; q++)
                 if (act[q]) {
                     status[q] = hs[q].status;
@@ -766,7 +956,7 @@ static int solve_batch(sem_handle* h, double* x_user, const double* b_user, cons
         std::vector<double> prev(ns, INFINITY);
         std::vector<int> act(ns, 0), fin(ns, 0);
         std::vector<double> itol(ns, o.inner_tol), carry(ns, 0.0), rn_prev(ns, 0.0);
-        std::vector<int> can_carry(ns, 0);
+        std::vector<int> can_carry(ns, 0), capped(ns, 0);
         if ((rc = read_rrbb())) return rc;
         CGState* inner = h->state + ns;
         for (int round = 0;; round++) {
@@ -779,7 +969,7 @@ static int solve_batch(sem_handle* h, double* x_user, const double* b_user, cons
                 if (!std::isfinite(rel)) { status[q] = SEM_EBREAKDOWN; fin[q] = 1; }
                 else if (bb == 0.0 || rel <= o.tol) { status[q] = SEM_OK; fin[q] = 1; }
                 else if (outer[q] >= o.max_outer) { status[q] = SEM_ENOTCONV; fin[q] = 1; }
-                else if (outer[q] > 0 && rel > 0.5 * prev[q]) { status[q] = SEM_ESTAGNATE; fin[q] = 1; }
+                else if (outer[q] > 0 && rel > 0.5 * prev[q] && !capped[q]) { status[q] = SEM_ESTAGNATE; fin[q] = 1; }
                 else {
                     act[q] = 1;
                     prev[q] = rel;
@@ -802,12 +992,14 @@ static int solve_batch(sem_handle* h, double* x_user, const double* b_user, cons
                                                                     o.max_iter, bp.carry);
             SEM_LAUNCH_CHECK("batch refinement prepare");
             h->launches += 2;
-            if ((rc = batch_loop(h, true, inner, o, s, hs, &ax_sum, &ax_n))) return rc;
+            if ((rc = batch_loop(h, SEM_FP32, inner, o, s, hs, &ax_sum, &ax_n))) return rc;
             for (int q = 0; q < ns; q++)
                 if (act[q]) {
                     iters[q] += hs[q].iter;
                     outer[q]++;
-                    can_carry[q] = hs[q].status == SEM_OK && hs[q].iter > 0;
+                    // a step stopped by max_iter is not judged for stagnation and keeps its direction
+                    capped[q] = hs[q].iter >= o.max_iter ? 1 : 0;
+                    can_carry[q] = (hs[q].status == SEM_OK || hs[q].status == SEM_ENOTCONV) && hs[q].iter > 0;
                 }
             correct_batch_kernel<<<grid_tiles(h), 256, 0, s>>>(h->ws.x, h->ws.d32, tiles(h), bp.act, bp.rrbb);
             SEM_LAUNCH_CHECK("correct_batch_kernel");
@@ -824,6 +1016,9 @@ static int solve_batch(sem_handle* h, double* x_user, const double* b_user, cons
     cudaEventDestroy(ev1);
     int worst = SEM_OK;
     for (int q = 0; q < ns; q++) {
+        // SEM_OK promises the tolerance on the true residual of the returned x
+        const double relq = relative_residual(rrbb[2 * q], rrbb[2 * q + 1]);
+        if (status[q] == SEM_OK && !(relq <= o.tol)) status[q] = std::isfinite(relq) ? SEM_ENOTCONV : SEM_EBREAKDOWN;
         if (status[q] != SEM_OK && (worst == SEM_OK || status[q] > worst)) worst = status[q];
         if (stats) {
             sem_solve_stats& st = stats[q];
@@ -838,6 +1033,11 @@ static int solve_batch(sem_handle* h, double* x_user, const double* b_user, cons
             st.kernel_launches = h->launches - launches0;
             st.ax_samples = ax_n;
             st.ax_ms = ax_n ? ax_sum / ax_n : 0.0;
+            const int itprec = o.mode == SEM_MODE_MIXED_IR ? SEM_FP32 : (o.precision == SEM_FP64_PAIR ? SEM_FP64_PAIR : SEM_FP64);
+            const int cls = itprec == SEM_FP32 ? kClsF32 : kClsF64;
+            st.launches_per_iteration = batch_ka_launches(h, itprec) + 2;
+            st.ax_variant = itprec == SEM_FP64_PAIR ? kDflVariant
+                            : bp.kcfg[cls] == 1 ? kMultiVariant : bp.ovar[cls][h->parts[q].lx];
         }
     }
     if (worst != SEM_OK) set_error("at least one solve of the batch did not converge (see per-solve stats)");
@@ -860,6 +1060,8 @@ SEM_API int sem_cg_solve_batch(sem_handle* h, double* x, const double* b, const 
         return fail(SEM_EINVAL, "bad solve options");
     if (o.mode == SEM_MODE_MIXED_IR && !(o.inner_tol > 0.0 && o.inner_tol < 1.0))
         return fail(SEM_EINVAL, "inner_tol must be in (0, 1)");
+    if (o.mode == SEM_MODE_FP64 && (!valid_precision(o.precision) || o.precision == SEM_FP32))
+        return fail(SEM_EINVAL, "FP64 mode takes SEM_FP64, SEM_FP64_NATIVE or SEM_FP64_PAIR");
     return solve_batch(h, x, b, o, stats, s);
 }
 

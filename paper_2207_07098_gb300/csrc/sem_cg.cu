@@ -241,9 +241,22 @@ __global__ void ir_correct_kernel(double* __restrict__ x, const float* __restric
         x[L] = fma(s, (double)d32[L], x[L]);
 }
 
+// v *= f (f a power of two: exact)
+__global__ void scale_kernel(double* __restrict__ v, double f, int64_t n) {
+    for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < n; L += (int64_t)gridDim.x * blockDim.x)
+        v[L] *= f;
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+
+static int launch_scale(sem_handle* h, double* v, double f, cudaStream_t s) {
+    scale_kernel<<<grid_for(h, h->n_local, 256, 8), 256, 0, s>>>(v, f, h->n_local);
+    SEM_LAUNCH_CHECK("scale_kernel");
+    h->launches++;
+    return SEM_OK;
+}
 
 int launch_cg_update(sem_handle* h, int precision, cudaStream_t s) {
     const int grid = grid_for(h, h->n_local / 4 + 1, 256, 8);
@@ -279,8 +292,8 @@ static int launch_iteration(sem_handle* h, int precision, cudaStream_t s) {
 
 static int get_graph(sem_handle* h, int precision, int chunk, cudaGraphExec_t* out) {
     GraphCache& g = h->graph;
-    const int variant = precision == SEM_FP64_NATIVE ? 0 : ax_variant_for(h, h->parts[0].lx, precision == SEM_FP32);
     // (the pair-form loop has its own precision code and always the line kernel)
+    const int variant = precision == kPairPrec ? kDflVariant : ax_variant_of_precision(h, h->parts[0].lx, precision);
     if (g.exec && g.key_prec == precision && g.key_chunk == chunk && g.key_variant == variant) {
         *out = g.exec;
         return SEM_OK;
@@ -387,7 +400,36 @@ static int run_cg_loop(sem_handle* h, int precision, const sem_solve_opts& o, in
     return SEM_OK;
 }
 
-// rr_bb[0] = ||b - A x||^2, rr_bb[1] = ||b||^2 (unique-node norm), r = b - A x
+// The CG loop of state slot `slot` as one persistent launch when the options
+// and the mesh allow it (opts.persistent: 1 forces it where available, -1
+// takes it below kPersistAutoPoints local points), else the graph loop.
+static bool use_persist(const sem_handle* h, const sem_solve_opts& o, int precision) {
+    if (o.persistent == 0 || precision == kPairPrec || precision == SEM_FP64_PAIR || !persist_available(h))
+        return false;
+    return o.persistent > 0 || h->n_local <= kPersistAutoPoints;
+}
+
+static int run_cg(sem_handle* h, int precision, const sem_solve_opts& o, int slot, cudaStream_t s, CGState* out,
+                  AxTiming* tm, bool* persisted) {
+    if (!use_persist(h, o, precision)) return run_cg_loop(h, precision, o, slot, s, out, tm);
+    *persisted = true;
+    int rc = launch_cg_persist(h, precision, slot, s);
+    if (rc) return rc;
+    SEM_CUDA_TRY(cudaMemcpyAsync(out, h->state + slot, sizeof(CGState), cudaMemcpyDeviceToHost, s));
+    SEM_CUDA_TRY(cudaStreamSynchronize(s));
+    int err_word = 0;
+    SEM_CUDA_TRY(cudaMemcpy(&err_word, device_error_word(h), sizeof(int), cudaMemcpyDeviceToHost));
+    if (err_word) {
+        cudaMemset(device_error_word(h), 0, sizeof(int));
+        cudaMemset(h->counters, 0, 16 * sizeof(unsigned));
+        return fail(SEM_ETIMEOUT, "a grid barrier of the persistent CG kernel expired");
+    }
+    if (!out->done) return fail(SEM_ETIMEOUT, "the persistent CG kernel ended before the solve did");
+    return SEM_OK;
+}
+
+// rr_bb[0] = ||b - A x||^2, rr_bb[1] = ||b||^2 (unique-node norm), r = b - A x,
+// with the native FP64 operator whatever the solve's iterations use
 static int true_residual(sem_handle* h, const double* x, const double* b, double* rr_bb, cudaStream_t s) {
     int rc = launch_ax_local(h, x, h->ws.w, SEM_FP64, s);
     if (!rc) rc = launch_gs(h, h->ws.w, false, true, s);
@@ -417,14 +459,21 @@ static bool is_host_ptr(const void* p) {
     return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
 }
 
+static int read_rrbb(sem_handle* h, double* hb, cudaStream_t s) {
+    SEM_CUDA_TRY(cudaMemcpyAsync(hb, h->scratch, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SEM_CUDA_TRY(cudaStreamSynchronize(s));
+    return SEM_OK;
+}
+
 static int solve_single(sem_handle* h, double* x_user, const double* b_user, const sem_solve_opts& o,
                         sem_solve_stats* stats, cudaStream_t s) {
     int rc = ensure_workspace(h, o.mode == SEM_MODE_MIXED_IR);
     if (rc) return rc;
+    const int prec = o.mode == SEM_MODE_MIXED_IR ? SEM_FP32 : o.precision;
     if (o.autotune) {
-        if (o.mode == SEM_MODE_MIXED_IR && (rc = autotune_ax(h, true, s))) return rc;
-        if ((o.mode == SEM_MODE_MIXED_IR || o.precision != SEM_FP64_NATIVE) && (rc = autotune_ax(h, false, s)))
-            return rc;
+        if (prec == SEM_FP32 && (rc = autotune_ax(h, true, s))) return rc;
+        // the FP64 class computes every true residual
+        if ((rc = autotune_ax(h, false, s))) return rc;
     }
     const int64_t n = h->n_local;
     const size_t bytes = sizeof(double) * n;
@@ -441,26 +490,36 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
     const int64_t launches0 = h->launches;
     CGState hs;
     int status = SEM_OK;
+    double hb[2] = {0.0, 0.0};  // ||b - A x||^2, ||b||^2 of the returned x (SEM_FP64 operator)
+    bool persisted = false;     // a CG loop ran as one persistent launch
     if (o.mode == SEM_MODE_FP64) {
         // CG with residual replacement: when the recursive residual says
         // "converged" but the true residual ||b - A x|| is still above tol
         // (rounding drift), CG restarts from the true residual, up to four times.
-        const int prec = o.precision == SEM_FP64_NATIVE ? SEM_FP64_NATIVE : SEM_FP64;
-        // with the line-transform FP32-pair operator, the CG vectors live as float pairs
-        const bool pair = prec == SEM_FP64 && pair_cg_available(h);
+        // With the line-transform FP32-pair operator the CG vectors live as
+        // float pairs, and x, b, r are scaled by a power of two (exactly) into
+        // the range the pair format represents.
+        const bool pair = prec == SEM_FP64_PAIR && pair_cg_available(h);
         if (pair && (rc = ensure_pair_workspace(h))) return rc;
+        double scale = 1.0;
         int used = 0;
         for (int restart = 0;; restart++) {
-            if (pair && restart > 0 && (rc = launch_pair_join_x(h, s))) return rc;
-            if ((rc = true_residual(h, h->ws.x, h->ws.b, rrbb, s))) return rc;
-            if (restart > 0) {
-                double hb[2];
-                SEM_CUDA_TRY(cudaMemcpyAsync(hb, rrbb, sizeof(hb), cudaMemcpyDeviceToHost, s));
-                SEM_CUDA_TRY(cudaStreamSynchronize(s));
-                const double rel = relative_residual(hb[0], hb[1]);
-                if (rel <= o.tol || status != SEM_OK || restart > 4 || used >= o.max_iter) break;
+            if ((rc = true_residual(h, h->ws.x, h->ws.b, rrbb, s)) || (rc = read_rrbb(h, hb, s))) return rc;
+            const double rel = relative_residual(hb[0], hb[1]);
+            if (!std::isfinite(rel)) {  // NaN or Inf in x0 or b, or a diverged iterate
+                status = SEM_EBREAKDOWN;
+                break;
             }
+            if (restart > 0 && (rel <= o.tol || status != SEM_OK || restart > 4 || used >= o.max_iter)) break;
             if (pair) {
+                if (restart == 0 && hb[1] > 0.0) {
+                    const int e = std::ilogb(std::sqrt(hb[1]));
+                    scale = (e > 16 || e < -16) ? std::ldexp(1.0, e) : 1.0;
+                }
+                if (scale != 1.0 && ((rc = launch_scale(h, h->ws.x, 1.0 / scale, s)) ||
+                                     (rc = launch_scale(h, h->ws.b, 1.0 / scale, s)) ||
+                                     (rc = launch_scale(h, h->ws.r, 1.0 / scale, s))))
+                    return rc;
                 if ((rc = launch_pair_split_x(h, s)) || (rc = launch_pair_init(h, o.tol, o.max_iter - used, s)))
                     return rc;
             } else {
@@ -470,8 +529,13 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
                 SEM_LAUNCH_CHECK("cg_init_kernel");
                 h->launches++;
             }
-            if ((rc = run_cg_loop(h, pair ? kPairPrec : prec, o, 0, s, &hs, &tm))) return rc;
-            if (pair && (rc = launch_pair_join_x(h, s))) return rc;
+            if ((rc = run_cg(h, pair ? kPairPrec : prec, o, 0, s, &hs, &tm, &persisted))) return rc;
+            if (pair) {
+                if ((rc = launch_pair_join_x(h, s))) return rc;
+                if (scale != 1.0 && ((rc = launch_scale(h, h->ws.x, scale, s)) ||
+                                     (rc = launch_scale(h, h->ws.b, scale, s))))
+                    return rc;
+            }
             used += hs.iter;
             st.relres_recursive = hs.bb > 0 ? std::sqrt(hs.rr / hs.bb) : 0.0;
             status = hs.status;
@@ -479,21 +543,20 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
         st.iterations = used;
     } else {
         // FP64 refinement around an FP32 inner CG; with ir_carry the inner CG
-        // keeps its direction across steps (residual replacement)
+        // keeps its direction across steps (residual replacement).  A step
+        // stopped by max_iter is not judged for stagnation (the CG residual
+        // norm is not monotone), and its direction is kept like any other.
         double prev = INFINITY, rn_prev = 0.0;
-        bool can_carry = false;
+        bool can_carry = false, capped_last = false;
         int outer = 0, inner = 0;
         for (;;) {
-            if ((rc = true_residual(h, h->ws.x, h->ws.b, rrbb, s))) return rc;
-            double hb[2];
-            SEM_CUDA_TRY(cudaMemcpyAsync(hb, rrbb, sizeof(hb), cudaMemcpyDeviceToHost, s));
-            SEM_CUDA_TRY(cudaStreamSynchronize(s));
+            if ((rc = true_residual(h, h->ws.x, h->ws.b, rrbb, s)) || (rc = read_rrbb(h, hb, s))) return rc;
             const double rel = relative_residual(hb[0], hb[1]);
             st.relres_recursive = rel;
             if (!std::isfinite(rel)) { status = SEM_EBREAKDOWN; break; }
             if (hb[1] == 0.0 || rel <= o.tol) { status = SEM_OK; break; }
             if (outer >= o.max_outer) { status = SEM_ENOTCONV; break; }
-            if (outer > 0 && rel > 0.5 * prev) { status = SEM_ESTAGNATE; break; }
+            if (outer > 0 && rel > 0.5 * prev && !capped_last) { status = SEM_ESTAGNATE; break; }
             prev = rel;
             // the inner right-hand side is r / ||r||: the kept direction's units
             // were ||r_prev|| / ||r|| times smaller than the new ones
@@ -506,9 +569,10 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
                 h->state + 1, h->partials, h->counters + 5, carry_c);
             SEM_LAUNCH_CHECK("ir prepare");
             h->launches += 2;
-            if ((rc = run_cg_loop(h, SEM_FP32, o, 1, s, &hs, &tm))) return rc;
+            if ((rc = run_cg(h, SEM_FP32, o, 1, s, &hs, &tm, &persisted))) return rc;
             inner += hs.iter;
-            can_carry = hs.status == SEM_OK && hs.iter > 0;
+            capped_last = hs.iter >= o.max_iter;
+            can_carry = (hs.status == SEM_OK || hs.status == SEM_ENOTCONV) && hs.iter > 0;
             rn_prev = rn;
             ir_correct_kernel<<<grid_for(h, n, 256, 8), 256, 0, s>>>(h->ws.x, h->ws.d32, rrbb, n);
             SEM_LAUNCH_CHECK("ir_correct_kernel");
@@ -518,10 +582,7 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
         st.iterations = inner;
         st.outer_iterations = outer;
     }
-    // true FP64 residual of the final iterate
-    if ((rc = true_residual(h, h->ws.x, h->ws.b, rrbb, s))) return rc;
-    double hb[2];
-    SEM_CUDA_TRY(cudaMemcpyAsync(hb, rrbb, sizeof(hb), cudaMemcpyDeviceToHost, s));
+    // hb holds the true residual of the final iterate (both loops end right after computing it)
     SEM_CUDA_TRY(cudaMemcpyAsync(x_user, h->ws.x, bytes, xh ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
     cudaEventRecord(ev1, s);
     SEM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -537,17 +598,20 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
         return fail(SEM_ETIMEOUT, "a staged operator kernel gave up waiting for its bulk copies");
     }
     st.relres = relative_residual(hb[0], hb[1]);
+    // SEM_OK promises the tolerance on the true residual, whatever the loop reported
+    if (status == SEM_OK && !(st.relres <= o.tol)) status = std::isfinite(st.relres) ? SEM_ENOTCONV : SEM_EBREAKDOWN;
     st.time_ms = ms;
-    st.ax_variant = o.mode == SEM_MODE_MIXED_IR ? ax_variant_for(h, h->parts[0].lx, true)
-                    : (o.precision == SEM_FP64_NATIVE ? 0 : ax_variant_for(h, h->parts[0].lx, false));
+    st.ax_variant = o.mode == SEM_MODE_MIXED_IR ? ax_variant_for(h, h->parts[0].lx, kClsF32)
+                                                : ax_variant_of_precision(h, h->parts[0].lx, prec);
     st.status = status;
+    st.launches_per_iteration = persisted ? 0 : 3;
     st.kernel_launches = h->launches - launches0;
     st.ax_samples = tm.samples;
     st.ax_ms = tm.samples ? tm.ms / tm.samples : 0.0;
     if (stats) *stats = st;
     if (status != SEM_OK) {
         const char* what = status == SEM_ENOTCONV   ? "not converged within max_iter / max_outer"
-                           : status == SEM_EBREAKDOWN ? "CG breakdown (p^T A p <= 0 or non-finite scalar)"
+                           : status == SEM_EBREAKDOWN ? "CG breakdown (p^T A p <= 0 or non-finite residual)"
                                                       : "refinement stagnated";
         set_error(what);
     }
@@ -571,6 +635,8 @@ SEM_API int sem_cg_solve(sem_handle* h, double* x, const double* b, const sem_so
         return fail(SEM_EINVAL, "bad solve options");
     if (o.mode == SEM_MODE_MIXED_IR && !(o.inner_tol > 0.0 && o.inner_tol < 1.0))
         return fail(SEM_EINVAL, "inner_tol must be in (0, 1)");
+    if (o.mode == SEM_MODE_FP64 && (!valid_precision(o.precision) || o.precision == SEM_FP32))
+        return fail(SEM_EINVAL, "FP64 mode takes SEM_FP64, SEM_FP64_NATIVE or SEM_FP64_PAIR");
     return solve_single(h, x, b, o, stats, s);
 }
 

@@ -246,7 +246,7 @@ __global__ void split_minv_kernel(const double* minv, float* mh, float* ml, int6
 // ---------------------------------------------------------------------------
 
 bool pair_cg_available(const sem_handle* h) {
-    return h->nsolve == 1 && ax_variant_for(h, h->parts[0].lx, false) == kDflVariant;
+    return h->nsolve == 1 && ax_variant_for(h, h->parts[0].lx, kClsPair) == kDflVariant;
 }
 
 int ensure_pair_workspace(sem_handle* h) {

@@ -10,76 +10,14 @@
 #include <algorithm>
 
 #include "sem_device.cuh"
+#include "sem_gs.cuh"
 #include "sem_internal.h"
 
 namespace sem {
 
 // One launch covers free segments of 2, 4 and 8 copies (index vectors), free
 // segments of other sizes (CSR), and either the zeroing of every Dirichlet copy
-// (apply_mask) or the sums over Dirichlet segments.  Copies are always summed
-// left to right in ascending local index.  The loads are latency-bound
-// (scattered 4- or 8-byte accesses), so each thread issues the index and value
-// loads of U segments before it sums and stores any.
-// segment t of a class belongs to a solve that is done (batched, skipping)
-__device__ __forceinline__ bool seg_done(const uint16_t* sid, const CGState* st, int64_t t) {
-    return sid && st[sid[t]].done;
-}
-
-template <typename T, int U>
-__device__ __forceinline__ void gs_pairs(T* __restrict__ u, const int2* __restrict__ idx, int64_t n, int64_t t0,
-                                         int64_t stride, const uint16_t* sid = nullptr, const CGState* st = nullptr) {
-    for (int64_t t = t0; t < n; t += stride * U) {
-        int2 q[U];
-        T a[U], b[U];
-#pragma unroll
-        for (int k = 0; k < U; k++)
-            q[k] = (t + k * stride < n && !seg_done(sid, st, t + k * stride)) ? idx[t + k * stride] : make_int2(-1, -1);
-#pragma unroll
-        for (int k = 0; k < U; k++)
-            if (q[k].x >= 0) {
-                a[k] = u[q[k].x];
-                b[k] = u[q[k].y];
-            }
-#pragma unroll
-        for (int k = 0; k < U; k++)
-            if (q[k].x >= 0) {
-                const T sum = a[k] + b[k];
-                u[q[k].x] = sum;
-                u[q[k].y] = sum;
-            }
-    }
-}
-
-template <typename T, int U>
-__device__ __forceinline__ void gs_quads(T* __restrict__ u, const int4* __restrict__ idx, int64_t n, int64_t t0,
-                                         int64_t stride, const uint16_t* sid = nullptr, const CGState* st = nullptr) {
-    for (int64_t t = t0; t < n; t += stride * U) {
-        int4 q[U];
-        T a[U][4];
-#pragma unroll
-        for (int k = 0; k < U; k++)
-            q[k] = (t + k * stride < n && !seg_done(sid, st, t + k * stride)) ? idx[t + k * stride]
-                                                                               : make_int4(-1, -1, -1, -1);
-#pragma unroll
-        for (int k = 0; k < U; k++)
-            if (q[k].x >= 0) {
-                a[k][0] = u[q[k].x];
-                a[k][1] = u[q[k].y];
-                a[k][2] = u[q[k].z];
-                a[k][3] = u[q[k].w];
-            }
-#pragma unroll
-        for (int k = 0; k < U; k++)
-            if (q[k].x >= 0) {
-                const T sum = ((a[k][0] + a[k][1]) + a[k][2]) + a[k][3];
-                u[q[k].x] = sum;
-                u[q[k].y] = sum;
-                u[q[k].z] = sum;
-                u[q[k].w] = sum;
-            }
-    }
-}
-
+// (apply_mask) or the sums over Dirichlet segments.
 // CTA ranges of the segment classes of one gather-scatter launch: the
 // classes touch disjoint local points, so they run side by side, each CTA on
 // one class (a thread walks one chain of dependent loads instead of one per
@@ -211,7 +149,7 @@ extern "C" {
 
 SEM_API int sem_gs(sem_handle* h, void* u, int precision, int apply_mask, cudaStream_t s) {
     if (!h || !u) return fail(SEM_EINVAL, "null argument");
-    if (precision != SEM_FP64 && precision != SEM_FP32 && precision != SEM_FP64_NATIVE)
+    if (!valid_precision(precision))
         return fail(SEM_EINVAL, "unknown precision");
     return launch_gs(h, u, precision == SEM_FP32, apply_mask != 0, s);
 }

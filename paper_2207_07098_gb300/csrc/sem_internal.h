@@ -19,6 +19,18 @@ constexpr int kMaxPartials = 4096;  // upper bound on CTAs of a reducing launch
 constexpr int kBulkVariantsMax = 4;  // operator variants 1..4 are bulk-staged
 constexpr int kDfVariant = 5;        // FP64 data, FP32-pair arithmetic (FP64 precisions only)
 constexpr int kDflVariant = 6;       // same, line-transform form with even/odd splitting (even lx)
+constexpr int kMultiVariant = 7;     // batches: one slab launch over the groups of every order
+// operator classes, each with its own tuned or pinned variant per order:
+// native FP64 (variants 0..4), FP32 (0..4), FP32-pair arithmetic on FP64 data (5, 6)
+constexpr int kClsF64 = 0, kClsF32 = 1, kClsPair = 2;
+// class of a sem_precision value (SEM_FP64_NATIVE: the FP64 class, variant 0)
+inline int precision_class(int precision) {
+    return precision == SEM_FP32 ? kClsF32 : precision == SEM_FP64_PAIR ? kClsPair : kClsF64;
+}
+inline bool valid_precision(int precision) {
+    return precision == SEM_FP64 || precision == SEM_FP32 || precision == SEM_FP64_NATIVE ||
+           precision == SEM_FP64_PAIR;
+}
 
 // ---------------------------------------------------------------------------
 // errors
@@ -152,13 +164,28 @@ struct BatchPlan {
     int* act = nullptr;       // [nsolve] solves taking part in an inner solve
     double* itol = nullptr;   // [nsolve] inner relative tolerance of each active solve
     double* carry = nullptr;  // [nsolve] refinement: rescaling of the kept direction (0 = restart)
-    // second group lists, cut to the element count of the FP32 bulk-staged
-    // operator (blxg[i] has the order of lxg[i]; no groups where it is unused)
-    std::vector<LxGroups> blxg;
-    int64_t bngroups = 0;
-    int* bsgfirst = nullptr;  // [nsolve]
-    int* bsgcount = nullptr;  // [nsolve]
-    double* bgpart = nullptr; // [bngroups]
+    // the slab groups above as one list for the multi-order launch (same global
+    // group numbering): local index, element count, solve and order of each group
+    int64_t* uloc = nullptr;
+    int* ucnt = nullptr;
+    int* usolve = nullptr;
+    uint8_t* ulx = nullptr;
+    bool multi_ok = false;    // every order present is within the multi-order kernel's range
+    // operator configuration per class [kClsF64 / kClsF32]: 1 = one multi-order
+    // launch, 0 = one launch per order with ovar[cls][lx] (0 slab, 1..4 bulk-staged,
+    // FP32 only), -1 = not chosen yet (autotuned at the first solve)
+    int kcfg[2] = {-1, -1};
+    int ovar[2][kMaxLx + 1] = {};
+    // group lists cut to the element count of a bulk-staged variant, per
+    // elements-per-CTA (index 0: 1, 1: 2, 2: 4); built when first needed
+    struct BulkSet {
+        std::vector<LxGroups> lists;  // one per order present, in lxg's order
+        int64_t ngroups = 0;
+        int* sgfirst = nullptr;   // [nsolve]
+        int* sgcount = nullptr;   // [nsolve]
+        double* gpart = nullptr;  // [ngroups]
+        bool built = false;
+    } bulk[3];
     // solve of every gather-scatter segment (batches of at most 65535 solves)
     uint16_t* sid[5] = {};
     bool sid_ready = false;
@@ -221,7 +248,7 @@ struct sem_handle {
     cudaEvent_t ax_ev[2] = {nullptr, nullptr};  // bracket one K-A per graph (single: 2nd, batch: 1st)
     int64_t launches = 0;                        // kernels launched by this handle
     int test_stall = 0;                          // SEM_FLAG_TEST_STALL: bulk copies never complete a stage
-    int ax_variant[2][sem::kMaxLx + 1];          // tuned operator variant per [fp32][lx], -1 = not tuned
+    int ax_variant[3][sem::kMaxLx + 1];          // tuned or pinned operator variant per [class][lx], -1 = not tuned
     size_t device_bytes = 0;
 };
 
@@ -275,7 +302,15 @@ int launch_pair_ka(sem_handle* h, cudaStream_t s);
 int launch_pair_rest(sem_handle* h, cudaStream_t s);
 int prepare_pair_kernels(sem_handle* h);
 int autotune_ax(sem_handle* h, bool fp32, cudaStream_t s);
-int ax_variant_for(const sem_handle* h, int lx, bool fp32);
+// whole CG in one cooperative launch (sem_cg_persist.cu): single-mesh handles, lx <= 10
+constexpr int kPersistMaxLx = 10;
+constexpr int64_t kPersistAutoPoints = (int64_t)1 << 20;  // automatic below this many local points
+bool persist_available(const sem_handle* h);
+int launch_cg_persist(sem_handle* h, int precision, int slot, cudaStream_t s);
+// operator variant of class cls (kClsF64 / kClsF32 / kClsPair) for order lx
+int ax_variant_for(const sem_handle* h, int lx, int cls);
+// variant a precision uses for order lx (SEM_FP64_NATIVE: 0)
+int ax_variant_of_precision(const sem_handle* h, int lx, int precision);
 int* device_error_word(sem_handle* h);
 double inner_tolerance(const sem_solve_opts& o, double rel);
 

@@ -101,6 +101,10 @@ SEM_API int sem_dot_noalloc(const sem_handle* h, const double* a, const double* 
     if (rc) return rc;
     for (int q = 0; q < h->nsolve; q++) {
         const MeshPart& p = h->parts[q];
+        if (p.n_local == 0) {  // no launch for an empty mesh: its product is 0
+            SEM_CUDA_TRY(cudaMemsetAsync(result + q, 0, sizeof(double), s));
+            continue;
+        }
         // the ticket counter must start at zero whatever an earlier call left there
         SEM_CUDA_TRY(cudaMemsetAsync(scratch + kNoAllocCounterSlot, 0, sizeof(unsigned int), s));
         const int grid = (int)((p.n_local + kNoAllocChunk - 1) / kNoAllocChunk);

@@ -326,10 +326,13 @@ static void free_handle(sem_handle* h) {
     for (auto& g : bp.lxg) {
         cudaFree(g.loc); cudaFree(g.cnt); cudaFree(g.solve);
     }
-    for (auto& g : bp.blxg) {
-        cudaFree(g.loc); cudaFree(g.cnt); cudaFree(g.solve);
+    for (auto& bs : bp.bulk) {
+        for (auto& g : bs.lists) {
+            cudaFree(g.loc); cudaFree(g.cnt); cudaFree(g.solve);
+        }
+        cudaFree(bs.sgfirst); cudaFree(bs.sgcount); cudaFree(bs.gpart);
     }
-    cudaFree(bp.bsgfirst); cudaFree(bp.bsgcount); cudaFree(bp.bgpart);
+    cudaFree(bp.uloc); cudaFree(bp.ucnt); cudaFree(bp.usolve); cudaFree(bp.ulx);
     for (auto* p : bp.sid) cudaFree(p);
     cudaFree(bp.sgfirst); cudaFree(bp.sgcount); cudaFree(bp.tloc); cudaFree(bp.tlen); cudaFree(bp.tsolve);
     cudaFree(bp.stfirst); cudaFree(bp.stcount); cudaFree(bp.gpart); cudaFree(bp.tpart); cudaFree(bp.scount);
@@ -389,8 +392,13 @@ static int setup_common(sem_handle** out, int nsolve, const sem_mesh_desc* meshe
     const int forced = (flags & 0xF) - 1;  // pinned operator variant, -1 = autotune
     if (forced > kDflVariant) return fail(SEM_EINVAL, "operator variant out of range");
     sem_handle* h = new sem_handle();
-    for (auto& row : h->ax_variant)
-        for (int& v : row) v = forced;
+    // a pinned variant 0..4 serves the FP64 and FP32 classes, 5 or 6 the pair class;
+    // the other classes stay autotuned
+    for (int cls = 0; cls < 3; cls++) {
+        const bool pair_pin = forced >= kDfVariant;
+        const bool applies = forced >= 0 && ((cls == kClsPair) == pair_pin);
+        for (int& v : h->ax_variant[cls]) v = applies ? forced : -1;
+    }
     h->test_stall = (flags & SEM_FLAG_TEST_STALL) ? 1 : 0;
     int rc = SEM_OK;
     auto bail = [&](int code) {
@@ -634,12 +642,13 @@ SEM_API void sem_solve_opts_default(sem_solve_opts* o) {
     o->max_iter = 100000;
     o->mode = SEM_MODE_FP64;
     o->inner_tol = 1e-5;
-    o->max_outer = 30;
+    o->max_outer = 100;
     o->precision = SEM_FP64;
     o->use_graph = 1;
     o->graph_chunk = 32;
     o->autotune = 1;
     o->ir_carry = 0;
+    o->persistent = -1;
 }
 
 SEM_API int sem_gll(int lx, double* xi, double* rho, double* D) {

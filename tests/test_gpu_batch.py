@@ -136,9 +136,10 @@ def test_batch_statuses_are_per_member():
 
 
 def test_batch_256_member_workload_sampled():
-    """The 256-member batch (nx, ny, nz ~ U{2..16}, N ~ U{5,7,9}): both modes
-    converge for every member; the oracle checks the true residual of a
-    sample of members."""
+    """The 256-member batch (nx, ny, nz ~ U{2..16}, N ~ U{5,7,9}): the FP64
+    solve (native and FP32-pair operator) and the mixed refinement converge
+    for every member; the oracle checks the true residual of a sample of
+    members."""
     import torch
     params = W.batch_params()
     members = []
@@ -150,15 +151,16 @@ def test_batch_256_member_workload_sampled():
         rng = np.random.default_rng(7)
         sample = sorted(set(rng.choice(len(members), size=6, replace=False).tolist()))
         small = sorted(range(len(members)), key=lambda q: members[q][0].n_local)[:2]
-        for mode in (S.SEM_MODE_FP64, S.SEM_MODE_MIXED_IR):
-            xs, st = _solve(h, members, mode=mode)
+        for mode, prec in ((S.SEM_MODE_FP64, S.SEM_FP64), (S.SEM_MODE_FP64, S.SEM_FP64_PAIR),
+                           (S.SEM_MODE_MIXED_IR, S.SEM_FP64)):
+            xs, st = _solve(h, members, mode=mode, precision=prec)
             assert all(s["status"] == S.SEM_OK and s["relres"] <= TOL for s in st)
             for q in sorted(set(sample) | set(small)):
                 m, h1, b = members[q]
                 if m.n_local > 3_000_000:
                     continue
                 P = oracle.Problem(m, h1)
-                assert _oracle_relres(P, xs[q], b) <= 1.05 * TOL, (mode, q)
+                assert _oracle_relres(P, xs[q], b) <= 1.05 * TOL, (mode, prec, q)
     finally:
         S.sem_destroy(h)
         torch.cuda.empty_cache()
@@ -223,3 +225,52 @@ def test_batch_misaligned_even_order_falls_back():
 def _setup_flags(members, flags):
     return S.sem_setup_batch([(m.E, m.lx, m.coords, m.gid, m.mask, h1) for m, h1, _ in members], flags)
 
+
+
+def test_batch_multi_order_launch_matches_per_order():
+    """One operator launch over the element groups of every order (variant 7,
+    taken without autotuning where every order is at most lx = 10) against
+    one slab launch per order (variant 0 pinned): the same arithmetic in the
+    same order, so every member's solution is bit-identical, in FP64 and in
+    the mixed refinement; the stats report the launches of one iteration."""
+    members = _members(5, count=10)
+    orders = {m.lx for m, _, _ in members}
+    assert max(orders) <= 10 and len(orders) >= 3
+    hm = _setup(members)
+    hp = _setup_flags(members, S.SEM_FLAG_VARIANT(0))
+    try:
+        for mode in (S.SEM_MODE_FP64, S.SEM_MODE_MIXED_IR):
+            xm, sm = _solve(hm, members, mode=mode, autotune=0)
+            xp, sp = _solve(hp, members, mode=mode)
+            assert all(s["ax_variant"] == 7 and s["launches_per_iteration"] == 3 for s in sm), sm[0]
+            assert all(s["launches_per_iteration"] == len(orders) + 2 for s in sp), sp[0]
+            for q, (m, h1, b) in enumerate(members):
+                assert sm[q]["status"] == S.SEM_OK and sm[q]["relres"] <= TOL, (mode, q, sm[q])
+                assert np.array_equal(xm[q], xp[q]), (mode, q)
+                assert sm[q]["iterations"] == sp[q]["iterations"], (mode, q)
+            P = oracle.Problem(*members[3][:2])
+            assert _oracle_relres(P, xm[3], members[3][2]) <= 1.05 * TOL
+    finally:
+        S.sem_destroy(hm)
+        S.sem_destroy(hp)
+
+
+def test_batch_autotuned_configuration_is_reported():
+    """With autotuning (the default) the batch times its operator
+    configurations at the first solve and reports the one it keeps: the
+    multi-order launch (variant 7, 3 launches per iteration) or one launch
+    per order with a slab or bulk-staged variant; either way every member
+    converges by the oracle's residual."""
+    members = _even_members(17, 6, orders=(5, 7, 9))
+    h = _setup(members)
+    try:
+        xs, st = _solve(h, members, mode=S.SEM_MODE_MIXED_IR)
+        for q, (m, h1, b) in enumerate(members):
+            s = st[q]
+            assert s["status"] == S.SEM_OK and s["relres"] <= TOL, (q, s)
+            assert (s["ax_variant"] == 7 and s["launches_per_iteration"] == 3) or \
+                (0 <= s["ax_variant"] <= 4 and s["launches_per_iteration"] == 5), s
+            P = oracle.Problem(m, h1)
+            assert _oracle_relres(P, xs[q], b) <= 1.05 * TOL, q
+    finally:
+        S.sem_destroy(h)

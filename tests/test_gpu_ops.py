@@ -14,6 +14,11 @@ pytestmark = pytest.mark.gpu
 
 TOL_AX64 = 1e-12     # relative, 2-norm and max-norm, per application
 TOL_AX32 = 5e-6      # FP32 operator vs FP64 oracle (reported; FP32 rounding of G, D, u)
+# SEM_FP64_PAIR (48-bit float pairs) where the element sums cancel: its unit
+# roundoff 2^-48 = 3.6e-15 times a cancellation factor of ~10^3 on a smooth
+# field (|D^T||G||D||u| against |A u|) gives a few 1e-12; the documented bar
+# of that precision on such fields is 2e-11 (on rough fields it keeps 1e-12)
+TOL_AX64_PAIR_SMOOTH = 2e-11
 
 
 def _case(kind, dims, N, seed=0):
@@ -78,7 +83,7 @@ def test_ax_fp64_local_and_assembled(kind, dims, N):
     P = oracle.Problem(m, h1)
     H = Handle(m, h1)
     u = W.random_local_field(m, 11)
-    for prec in (S.SEM_FP64, S.SEM_FP64_NATIVE):
+    for prec in (S.SEM_FP64, S.SEM_FP64_NATIVE, S.SEM_FP64_PAIR):
         e2, einf = rel_err(H.ax(u, prec, assemble=0), P.ax_local(u))
         assert e2 <= TOL_AX64 and einf <= TOL_AX64, (e2, einf)
     uc = W.random_local_field(m, 12, continuous=True)
@@ -156,33 +161,36 @@ DF_CASES = [("affine", (1, 1, 1), 1), ("jitter", (3, 3, 2), 3), ("deformed", (5,
 @pytest.mark.parametrize("variant", [5, 6])
 @pytest.mark.parametrize("kind,dims,N", DF_CASES)
 def test_ax_fp32_pair_variant(variant, kind, dims, N):
-    """FP64 data with FP32-pair arithmetic (variant 5; variant 6 = line
-    transforms with even/odd splitting, even lx): FP64 parity bar.  Orders the
-    variant does not cover fall back to the native FP64 kernel."""
+    """SEM_FP64_PAIR: FP64 data with FP32-pair arithmetic (variant 5; variant
+    6 = line transforms with even/odd splitting, even lx) holds the FP64 bar
+    on random fields.  Orders the variant does not cover fall back to the
+    native FP64 kernels, and SEM_FP64 on the same handle stays native."""
     m, h1 = _case(kind, dims, N)
     P = oracle.Problem(m, h1)
     H = Handle(m, h1, flags=S.SEM_FLAG_VARIANT(variant))
     u = W.random_local_field(m, 23)
-    e2, einf = rel_err(H.ax(u, S.SEM_FP64, assemble=0), P.ax_local(u))
+    e2, einf = rel_err(H.ax(u, S.SEM_FP64_PAIR, assemble=0), P.ax_local(u))
     assert e2 <= TOL_AX64 and einf <= TOL_AX64, (e2, einf)
     uc = W.random_local_field(m, 24, continuous=True)
-    e2, einf = rel_err(H.ax(uc, S.SEM_FP64, assemble=1), P.ax(uc))
+    e2, einf = rel_err(H.ax(uc, S.SEM_FP64_PAIR, assemble=1), P.ax(uc))
     assert e2 <= TOL_AX64 and einf <= TOL_AX64, (e2, einf)
-    # the native FP64 kernel is still reachable on the same handle
-    e2, _ = rel_err(H.ax(u, S.SEM_FP64_NATIVE, assemble=0), P.ax_local(u))
-    assert e2 <= TOL_AX64
+    for prec in (S.SEM_FP64, S.SEM_FP64_NATIVE):
+        e2, einf = rel_err(H.ax(u, prec, assemble=0), P.ax_local(u))
+        assert e2 <= TOL_AX64 and einf <= TOL_AX64, (prec, e2, einf)
 
 
 @pytest.mark.parametrize("field", ["smooth", "random"])
 @pytest.mark.parametrize("variant", [5, 6])
-def test_ax_fp64_pair_kernels_within_rounding_bound(variant, field):
-    """FP32-pair FP64 operators against the native FP64 kernel on the same
-    handle (same factors): every output within the running rounding bound of
-    the pair arithmetic, |w_pair - w_fp64| <= 64 (2^-48 + 2^-53) |D^T||h1 G||D||u|
-    (a float pair carries 48 of the 53 mantissa bits; ~36 sequential operations
-    per output; the magnitude operator comes from the oracle).  Against the
-    oracle, the native kernel holds the 1e-12 relative bar on both fields; a
-    smooth field (sums that cancel) takes the pair kernels to a few 1e-12."""
+def test_ax_fp64_default_and_pair_kernels_on_cancelling_fields(variant, field):
+    """The default SEM_FP64 operator (native FP64 arithmetic) holds the 1e-12
+    relative bar against the oracle on a smooth field, whose element sums
+    cancel, as on a random one.  The FP32-pair operators (SEM_FP64_PAIR)
+    against the native kernel on the same handle (same factors): every output
+    within the running rounding bound of the pair arithmetic,
+    |w_pair - w_fp64| <= 64 (2^-48 + 2^-53) |D^T||h1 G||D||u| (a float pair
+    carries 48 of the 53 mantissa bits; ~36 sequential operations per output;
+    the magnitude operator comes from the oracle); against the oracle, 1e-12
+    on the random field and the documented 2e-11 on the smooth one."""
     m, h1 = _case("deformed", (8, 8, 8), 7)
     P = oracle.Problem(m, h1)
     H = Handle(m, h1, flags=S.SEM_FLAG_VARIANT(variant))
@@ -193,15 +201,17 @@ def test_ax_fp64_pair_kernels_within_rounding_bound(variant, field):
     # operator's scale (the sin field is ~1e-47 at the corner x = y = z = 1) are
     # held to an absolute floor 2^-20 of the largest magnitude instead
     bound = 64.0 * (2.0 ** -48 + 2.0 ** -53) * (mag + 2.0 ** -20 * mag.max())
-    w_pair = H.ax(u, S.SEM_FP64, assemble=0)
+    w_pair = H.ax(u, S.SEM_FP64_PAIR, assemble=0)
     w_fp64 = H.ax(u, S.SEM_FP64_NATIVE, assemble=0)
     assert np.all(np.abs(w_pair - w_fp64) <= bound)
-    e2, einf = rel_err(H.ax(u, S.SEM_FP64_NATIVE, assemble=1), P.ax(u))
-    assert e2 <= TOL_AX64 and einf <= TOL_AX64, (e2, einf)
-    p2, pinf = rel_err(H.ax(u, S.SEM_FP64, assemble=1), P.ax(u))
+    ref = P.ax(u)
+    for prec in (S.SEM_FP64, S.SEM_FP64_NATIVE):
+        e2, einf = rel_err(H.ax(u, prec, assemble=1), ref)
+        assert e2 <= TOL_AX64 and einf <= TOL_AX64, (prec, e2, einf)
+    p2, pinf = rel_err(H.ax(u, S.SEM_FP64_PAIR, assemble=1), ref)
     print(f"{field}: native {e2:.2e} / {einf:.2e}, variant {variant} {p2:.2e} / {pinf:.2e} (2-norm / max)")
-    if field == "random":
-        assert p2 <= TOL_AX64 and pinf <= TOL_AX64, (p2, pinf)
+    bar = TOL_AX64 if field == "random" else TOL_AX64_PAIR_SMOOTH
+    assert p2 <= bar and pinf <= bar, (p2, pinf)
 
 
 def test_ax_deterministic():
@@ -215,7 +225,10 @@ def test_ax_deterministic():
 
 def test_ax_full_size_deformed_cube():
     """The 32^3-element, N = 7 deformed cube with h1 (16.8 M points): every
-    output of one assembled FP64 application against the oracle."""
+    output of one assembled FP64 application against the oracle: 1e-12 on a
+    random continuous field; on the smooth field sin(pi x) sin(pi y) sin(pi z),
+    whose element sums cancel, within the FP64 rounding bound of the
+    evaluation; FP32 on the random field."""
     m, h1, _ = W.deformed_cube(32, 7, seed=2)
     P = oracle.Problem(m, h1)
     H = Handle(m, h1)
@@ -224,6 +237,22 @@ def test_ax_full_size_deformed_cube():
     assert e2 <= TOL_AX64 and einf <= TOL_AX64, (e2, einf)
     e2, einf = rel_err(H.ax(u, S.SEM_FP32), P.ax(u))
     assert e2 <= 1e-5, e2
+    # the smooth field sin(pi x) sin(pi y) sin(pi z): on 32^3 elements its element
+    # sums cancel by a factor kappa = ||QQ^T |D^T||h1 G||D||u| || / ||A u|| of
+    # ~7e4 (measured), so every FP64 evaluation of A u (the oracle's included)
+    # carries a relative error of order 2^-53 kappa ~ 1e-11 and the 1e-12 bar is
+    # out of reach of FP64 arithmetic itself (measured: 7.4e-12); the FP64
+    # operator is held to 16 2^-53 kappa there (both sides' rounding, a few ulp
+    # of the terms each, plus their slightly different factors G)
+    us = W.forcing_sines(m)
+    ref = P.ax(us)
+    w = H.ax(us)
+    mag = P.gs(P.ax_local_abs(us), mask=True)
+    kappa = np.linalg.norm(mag) / np.linalg.norm(ref)
+    e2, einf = rel_err(w, ref)
+    print(f"smooth 32^3: kappa {kappa:.3e}, FP64 operator vs oracle {e2:.2e} / {einf:.2e} (2-norm / max)")
+    assert kappa > 1e4
+    assert e2 <= max(TOL_AX64, 16.0 * 2.0 ** -53 * kappa), (e2, kappa)
 
 
 def test_invalid_inputs_rejected():

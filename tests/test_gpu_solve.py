@@ -33,7 +33,7 @@ def _deformed_case(n=6, N=7):
 
 
 @pytest.mark.parametrize("case", ["cube", "deformed"])
-@pytest.mark.parametrize("precision", [S.SEM_FP64, S.SEM_FP64_NATIVE])
+@pytest.mark.parametrize("precision", [S.SEM_FP64, S.SEM_FP64_NATIVE, S.SEM_FP64_PAIR])
 def test_fp64_pcg(case, precision):
     m, h1, P, b = _cube_case() if case == "cube" else _deformed_case()
     H = Handle(m, h1)
@@ -90,17 +90,23 @@ def test_mixed_ir_carried_direction(inner_tol):
 
 @pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
 def test_solves_with_each_operator_variant(variant):
+    """A pinned variant 0..4 serves the FP64 and FP32 operators, 5 or 6 the
+    FP32-pair one (SEM_FP64_PAIR); every solve reaches 1e-10 by the oracle's
+    residual with the variant it reports."""
     m, h1, P, b = _deformed_case(5, 7)
     H = Handle(m, h1, flags=S.SEM_FLAG_VARIANT(variant))
-    for mode in (S.SEM_MODE_FP64, S.SEM_MODE_MIXED_IR):
-        x, st = H.solve(b, mode=mode, tol=TOL)
+    runs = [(S.SEM_MODE_FP64, S.SEM_FP64), (S.SEM_MODE_MIXED_IR, S.SEM_FP64), (S.SEM_MODE_FP64, S.SEM_FP64_PAIR)]
+    for mode, prec in runs:
+        x, st = H.solve(b, mode=mode, precision=prec, tol=TOL)
         assert st["status"] == S.SEM_OK and st["relres"] <= TOL, st
-        # a pinned bulk variant too large for FP64 shared memory falls back to 0;
-        # the FP32-pair variant 5 exists for FP64 data only
-        if mode == S.SEM_MODE_FP64:
-            assert st["ax_variant"] in (variant, 0)
+        if prec == S.SEM_FP64_PAIR:
+            # a pinned native variant leaves the pair class on its own default (6 for even lx)
+            assert st["ax_variant"] == (variant if variant >= 5 else 6)
+        elif mode == S.SEM_MODE_FP64:
+            # a pinned bulk variant too large for FP64 shared memory falls back to 0
+            assert st["ax_variant"] in ((variant, 0) if variant <= 4 else (0, 1, 2, 3, 4))
         else:
-            assert st["ax_variant"] == (variant if variant <= 4 else 0)
+            assert (st["ax_variant"] == variant) if variant <= 4 else (0 <= st["ax_variant"] <= 4)
         assert _oracle_relres(P, x, b) <= 1.05 * TOL
 
 
@@ -182,32 +188,39 @@ def test_annulus_periodic_solve():
 
 def test_full_size_solve_true_residual():
     """The 32^3-element deformed cube (16.8 M points), in the launch
-    configuration bench.py times: the mixed-precision and the FP64 (pair-form)
-    solves reach 1e-10, checked by the oracle's operator on the full mesh, and
-    agree with each other to solver accuracy."""
+    configuration bench.py times: the mixed-precision solve, the FP64 solve
+    (native operator) and the FP64 solve with the FP32-pair operator and
+    vectors reach 1e-10, checked by the oracle's operator on the full mesh,
+    and agree with each other to solver accuracy."""
     m, h1, b = W.deformed_cube(32, 7, seed=2)
     H = Handle(m, h1)
     P = oracle.Problem(m, h1)
     xs = {}
-    for mode in (S.SEM_MODE_MIXED_IR, S.SEM_MODE_FP64):
-        x, st = H.solve(b, tol=TOL, mode=mode)
-        assert st["status"] == S.SEM_OK and st["relres"] <= TOL, (mode, st)
-        assert _oracle_relres(P, x, b) <= 1.05 * TOL, mode
-        xs[mode] = x
-    assert rel_err(xs[S.SEM_MODE_MIXED_IR], xs[S.SEM_MODE_FP64])[0] <= 1e-6
+    for key, mode, prec in (("mixed", S.SEM_MODE_MIXED_IR, S.SEM_FP64), ("fp64", S.SEM_MODE_FP64, S.SEM_FP64),
+                            ("pair", S.SEM_MODE_FP64, S.SEM_FP64_PAIR)):
+        x, st = H.solve(b, tol=TOL, mode=mode, precision=prec, inner_tol=1e-2, ir_carry=1)
+        assert st["status"] == S.SEM_OK and st["relres"] <= TOL, (key, st)
+        assert _oracle_relres(P, x, b) <= 1.05 * TOL, key
+        xs[key] = x
+    assert rel_err(xs["mixed"], xs["fp64"])[0] <= 1e-6
+    assert rel_err(xs["pair"], xs["fp64"])[0] <= 1e-6
 
 
 def test_bounded_wait_expiry_reports_timeout_and_context_survives():
     """Failure detection without a fault: with SEM_FLAG_TEST_STALL the staged
     operator kernels announce more bytes than they copy, so their bounded
-    mbarrier waits expire (~50 ms); the kernels record the failure and
-    return, and the solve reports SEM_ETIMEOUT.  The context stays usable."""
+    mbarrier waits expire (~50 ms), and the persistent CG kernel's first CTA
+    skips a grid barrier, so the other CTAs' bounded barrier waits expire; the
+    kernels record the failure and return, and the solve reports
+    SEM_ETIMEOUT.  The context stays usable."""
     m, h1, P, b = _deformed_case(3, 7)
     H = Handle(m, h1, flags=S.SEM_FLAG_VARIANT(2) | S.SEM_FLAG_TEST_STALL)
+    # graph loop (bulk-staged operator) and persistent launch (grid barrier)
     for mode in (S.SEM_MODE_MIXED_IR, S.SEM_MODE_FP64):
-        with pytest.raises(S.SemError) as ei:
-            H.solve(b, mode=mode, tol=TOL, graph_chunk=2)
-        assert ei.value.status == S.SEM_ETIMEOUT
+        for persistent in (0, 1):
+            with pytest.raises(S.SemError) as ei:
+                H.solve(b, mode=mode, tol=TOL, graph_chunk=2, persistent=persistent)
+            assert ei.value.status == S.SEM_ETIMEOUT, (mode, persistent)
     H.close()
     H2 = Handle(m, h1, flags=S.SEM_FLAG_VARIANT(2))
     x, st = H2.solve(b, tol=TOL)
@@ -224,3 +237,96 @@ def test_non_finite_rhs_reports_breakdown():
         assert st["status"] in (S.SEM_EBREAKDOWN, S.SEM_ENOTCONV, S.SEM_ESTAGNATE), st
     x, st = H.solve(b, tol=TOL)
     assert st["status"] == S.SEM_OK
+
+
+@pytest.mark.parametrize("scale", [1e-30, 1e30])
+def test_rhs_far_outside_unit_scale(scale):
+    """A right-hand side scaled by 1e-30 or 1e30: the native FP64 solve, the
+    FP32-pair solve (whose format reads |u| < 2^-75 as 0; the solver rescales
+    x and b by a power of two) and the mixed refinement (which scales every
+    inner right-hand side to unit norm) reach the same relative residual and
+    the scaled solution, checked by the oracle."""
+    m, h1, P, b = _deformed_case(3, 7)
+    H = Handle(m, h1)
+    x1, s1 = H.solve(b, tol=TOL)
+    for mode, prec in ((S.SEM_MODE_FP64, S.SEM_FP64), (S.SEM_MODE_FP64, S.SEM_FP64_PAIR),
+                       (S.SEM_MODE_MIXED_IR, S.SEM_FP64)):
+        x, st = H.solve(b * scale, tol=TOL, mode=mode, precision=prec)
+        assert st["status"] == S.SEM_OK and st["relres"] <= TOL, (mode, prec, st)
+        assert _oracle_relres(P, x, b * scale) <= 1.05 * TOL, (mode, prec)
+        assert rel_err(x / scale, x1)[0] <= 1e-7, (mode, prec)
+
+
+def test_non_finite_initial_guess_reports_breakdown():
+    """A NaN in x0 makes the true initial residual non-finite: every mode
+    reports SEM_EBREAKDOWN with a NaN residual instead of hiding it (the pair
+    format alone would read the NaN as 0)."""
+    m, h1, P, b = _deformed_case(2, 5)
+    H = Handle(m, h1)
+    x0 = np.zeros(m.n_local)
+    x0[np.flatnonzero(m.mask)[5]] = np.nan
+    for mode, prec in ((S.SEM_MODE_FP64, S.SEM_FP64), (S.SEM_MODE_FP64, S.SEM_FP64_PAIR),
+                       (S.SEM_MODE_MIXED_IR, S.SEM_FP64)):
+        x, st = H.solve(b, x0=x0, tol=TOL, mode=mode, precision=prec)
+        assert st["status"] == S.SEM_EBREAKDOWN and not np.isfinite(st["relres"]), (mode, prec, st)
+
+
+def test_fp64_restarts_exhausted_report_not_converged():
+    """A tolerance below what the 48-bit pair arithmetic can reach: the
+    recursive residual keeps converging, the true residual does not, the
+    residual-replacement restarts run out, and the solve reports
+    SEM_ENOTCONV with the true residual above tol (never SEM_OK)."""
+    m, h1, P, b = _deformed_case(3, 7)
+    H = Handle(m, h1)
+    x, st = H.solve(b, tol=1e-16, mode=S.SEM_MODE_FP64, precision=S.SEM_FP64_PAIR, max_iter=5000)
+    assert st["status"] == S.SEM_ENOTCONV and st["relres"] > 1e-16, st
+    assert _oracle_relres(P, x, b) <= 1e-12
+
+
+def test_mixed_kept_direction_with_capped_steps_matches_oracle():
+    """Kept direction with every refinement step capped at 100 inner
+    iterations (ir_carry = 1, max_iter = 100) on a periodic annulus: capped
+    steps are not judged for stagnation and keep their direction, as in the
+    oracle's refinement with the same cap; the inner iteration count follows
+    the oracle's and beats the uncapped kept direction."""
+    m, f = W.annulus_case(N=7, n_theta=16, n_r=8, n_z=6)
+    P = oracle.Problem(m)
+    b = P.mass(f, assemble=True)
+    H = Handle(m)
+    x, st = H.solve(b, tol=TOL, mode=S.SEM_MODE_MIXED_IR, inner_tol=1e-3, ir_carry=1, max_iter=100,
+                    max_outer=60)
+    assert st["status"] == S.SEM_OK and st["relres"] <= TOL, st
+    assert _oracle_relres(P, x, b) <= 1.05 * TOL
+    _, ic = P.ir(b, tol=TOL, inner_tol=1e-3, carry=True, max_inner=100, max_outer=60)
+    _, i64 = P.pcg(b, tol=TOL)
+    assert abs(st["iterations"] - ic["inner"]) <= 0.15 * ic["inner"] + 10, (st, ic)
+    assert st["iterations"] <= 1.3 * i64["iters"], (st, i64)
+    _, su = H.solve(b, tol=TOL, mode=S.SEM_MODE_MIXED_IR, inner_tol=1e-3, ir_carry=1, max_outer=60)
+    assert su["status"] == S.SEM_OK and st["iterations"] < su["iterations"], (st, su)
+
+
+@pytest.mark.parametrize("case", ["cube", "annulus5"])
+def test_persistent_single_launch_cg(case):
+    """The whole CG as one cooperative launch with bounded grid barriers
+    (opts.persistent = 1) against the graph loop (0): FP64 and mixed solves
+    reach 1e-10 by the oracle's residual with the same iteration counts
+    (within rounding effects), report no per-iteration launches, and are
+    bit-reproducible."""
+    if case == "cube":
+        m, h1, P, b = _cube_case()
+    else:
+        m, f = W.annulus_case(N=4, n_theta=12, n_r=4, n_z=3)
+        h1, P = None, oracle.Problem(m)
+        b = P.mass(f, assemble=True)
+    H = Handle(m, h1)
+    for mode, prec in ((S.SEM_MODE_FP64, S.SEM_FP64), (S.SEM_MODE_FP64, S.SEM_FP64_NATIVE),
+                       (S.SEM_MODE_MIXED_IR, S.SEM_FP64)):
+        xg, sg = H.solve(b, tol=TOL, mode=mode, precision=prec, persistent=0)
+        xp, sp = H.solve(b, tol=TOL, mode=mode, precision=prec, persistent=1)
+        xq, sq = H.solve(b, tol=TOL, mode=mode, precision=prec, persistent=1)
+        assert sp["status"] == S.SEM_OK and sp["relres"] <= TOL, (mode, sp)
+        assert sp["launches_per_iteration"] == 0 and sg["launches_per_iteration"] == 3
+        assert _oracle_relres(P, xp, b) <= 1.05 * TOL, mode
+        assert abs(sp["iterations"] - sg["iterations"]) <= max(2, sg["iterations"] // 50), (mode, sp, sg)
+        assert rel_err(xp, xg)[0] <= 1e-7, mode
+        assert np.array_equal(xp, xq) and sp["iterations"] == sq["iterations"], mode
