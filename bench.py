@@ -54,6 +54,8 @@ def _args():
     ap.add_argument("--variant", type=int, default=None,
                     help="pin the operator kernel variant (SEM_FLAG_VARIANT) instead of autotuning")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--tc-split", action="store_true",
+                    help="mixed solver: inner operator on the tensor cores (SEM_TC_SPLIT)")
     ap.add_argument("--suite", action="store_true",
                     help="also measure the cube (FP64 and mixed), the 256-member batch and the annulus")
     return ap.parse_args()
@@ -256,6 +258,8 @@ def run_ours(args):
     xd = torch.zeros(n, dtype=torch.float64, device="cuda")
     mode = S.SEM_MODE_MIXED_IR if args.solver == "mixed" else S.SEM_MODE_FP64
     opts = {"mode": mode, "tol": 1e-10, **(MIXED_OPTS if args.solver == "mixed" else {})}
+    if args.tc_split:
+        opts["tc_split"] = 1
 
     def step():
         xd.zero_()
@@ -318,6 +322,7 @@ def run_ours(args):
     kname = (f"ax_kernel<{tname},{m.lx},true>" if variant == 0 else
              f"ax_df_kernel<{m.lx},true>" if variant == 5 else
              f"ax_dfl_kernel<{m.lx},true>" if variant == 6 else
+             "ax_tc_kernel<true>" if variant == 8 else
              f"ax_bulk_kernel<{tname},{m.lx},{cfgs[variant][0]},{cfgs[variant][1]},true>")
     traffic = _traffic_for(kname, f"deformed_cube_{args.n}^3_N{args.order}")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -372,7 +377,8 @@ def _extras(S, torch, h, m, bd, n, args, peak, stats, ms_timed):
                                     ("fp64_pair", S.SEM_MODE_FP64, S.SEM_FP64_PAIR, {}),
                                     ("mixed", S.SEM_MODE_MIXED_IR, S.SEM_FP64, MIXED_OPTS),
                                     ("mixed_restart_1e-5", S.SEM_MODE_MIXED_IR, S.SEM_FP64,
-                                     {"inner_tol": 1e-5, "ir_carry": 0})):
+                                     {"inner_tol": 1e-5, "ir_carry": 0}),
+                                    ("mixed_tc_split", S.SEM_MODE_MIXED_IR, S.SEM_FP64, {**MIXED_OPTS, "tc_split": 1})):
         x.zero_()
         st = S.sem_cg_solve(h, x, bd, {"mode": mode, "precision": prec, "tol": 1e-10, **extra})
         res[name] = {"time_ms": st["time_ms"], "iterations": st["iterations"], "outer": st["outer_iterations"],
@@ -391,7 +397,7 @@ def _extras(S, torch, h, m, bd, n, args, peak, stats, ms_timed):
     stream = torch.cuda.current_stream()
     axr = {}
     for name, prec, dt, bpp in (("fp64", S.SEM_FP64, torch.float64, 64), ("fp64_pair", S.SEM_FP64_PAIR, torch.float64, 64),
-                                ("fp32", S.SEM_FP32, torch.float32, 32)):
+                                ("fp32", S.SEM_FP32, torch.float32, 32), ("fp32_tc_split", S.SEM_TC_SPLIT, torch.float32, 32)):
         u = torch.randn(n, dtype=dt, device="cuda")
         w = torch.empty_like(u)
         for _ in range(3):
@@ -409,14 +415,18 @@ def _extras(S, torch, h, m, bd, n, args, peak, stats, ms_timed):
         axr[name] = {"ms": t, "gb_s": gbs, "frac_hbm": gbs / peak, "bytes_per_point": bpp}
     axr["accuracy"] = ("fp64: native FP64 arithmetic, 1e-12 of the oracle on every field tested; fp64_pair: "
                        "FP32-pair arithmetic (unit roundoff 2^-48), 1e-12 on rough fields, a few 1e-12 on "
-                       "smooth cancelling ones")
+                       "smooth cancelling ones; fp32_tc_split: BF16 three-slice tensor-core contractions, "
+                       "FP32 accuracy class")
     ex["ax_helm_only"] = axr
     # every operator variant (pinned at set-up), plain ax_helm: 0..4 native FP64 and FP32, 5..6 FP32-pair
     var = {}
-    for v in range(7):
+    for v in (0, 1, 2, 3, 4, 5, 6, 8):
+        if v == 8 and m.lx != 8:
+            continue
         hv = S.sem_setup(m.E, m.lx, m.coords, m.gid, m.mask, None, S.SEM_FLAG_VARIANT(v))
         row = {}
         kinds = ((("fp64", S.SEM_FP64, torch.float64, 64), ("fp32", S.SEM_FP32, torch.float32, 32)) if v <= 4 else
+                 (("fp32", S.SEM_FP32, torch.float32, 32),) if v == 8 else
                  (("fp64_pair", S.SEM_FP64_PAIR, torch.float64, 64),))
         for name, prec, dt, bpp in kinds:
             u = torch.randn(n, dtype=dt, device="cuda")
@@ -583,7 +593,33 @@ def run_suite(args):
                      "frac_hbm": bpp * m.n_local / (t * 1e-3) / 1e9 / peak}
     S.sem_destroy(h)
     out["annulus_64x32x24_N7"] = ann
+    out["helmholtz_velocity"] = _helmholtz_suite(S, torch)
     print(json.dumps(out), flush=True)
+
+
+def _helmholtz_suite(S, torch):
+    """The velocity solve of a time step (Sec. II-B: P-CG with a Jacobi-type
+    preconditioner, tolerance 1e-8): the Helmholtz operator h1 K + h2 B with
+    h1 = 1/Re (Re = 30000) and h2 = gamma_0 / dt (BDF3, gamma_0 = 11/6,
+    dt = 2e-5, the rotor case's time step) on the 32^3 deformed cube, random
+    right-hand side, FP64 and mixed."""
+    m, _, b = W.deformed_cube(32, 7, seed=2)
+    h1 = np.full(m.n_local, 1.0 / 30000.0)
+    h2 = np.full(m.n_local, (11.0 / 6.0) / 2e-5)
+    h = S.sem_setup(m.E, m.lx, m.coords, m.gid, m.mask, h1)
+    S.sem_set_helmholtz(h, h2)
+    info = S.sem_get_info(h)
+    bd = torch.from_numpy(b).cuda()
+    res = {"workload": "32^3 deformed cube, N=7, Helmholtz h1 = 1/30000, h2 = (11/6)/2e-5, random RHS, tol 1e-8",
+           "n_local": m.n_local}
+    for name, o in (("fp64", {"mode": S.SEM_MODE_FP64, "tol": 1e-8}),
+                    ("fp64_pair", {"mode": S.SEM_MODE_FP64, "precision": S.SEM_FP64_PAIR, "tol": 1e-8}),
+                    ("mixed", {"mode": S.SEM_MODE_MIXED_IR, "tol": 1e-8})):
+        _, st = _timed_solve(S, torch, h, bd, m.n_local, o)
+        res[name] = _solve_report(st, m.n_local, info["n_free"])
+    res["speedup_mixed_vs_fp64"] = res["fp64"]["time_ms"] / res["mixed"]["time_ms"]
+    S.sem_destroy(h)
+    return res
 
 
 def main():

@@ -72,7 +72,7 @@ typedef enum sem_precision {
                             smooth fields whose sums cancel */
     SEM_FP32 = 1,        /* float data, FP32 arithmetic and accumulation */
     SEM_FP64_NATIVE = 2, /* double data, the plain shared-slab FP64 kernel (variant 0) */
-    SEM_FP64_PAIR = 3    /* double data, FP32-pair ("double-float") arithmetic on the FP32 pipe:
+    SEM_FP64_PAIR = 3,   /* double data, FP32-pair ("double-float") arithmetic on the FP32 pipe:
                             48 significant bits, unit roundoff 2^-48, about 4x the speed of
                             SEM_FP64 on GB300 (whose FP64 pipe runs at 1/64 of the FP32 rate).
                             Relative error vs exact FP64: ~1e-15..1e-14 on rough fields, up to
@@ -82,6 +82,12 @@ typedef enum sem_precision {
                             Inf/NaN) is read as 0; the solver rescales x and b by a power of two
                             to keep them inside it.  Variant 6 (line transforms, even lx <= 12)
                             or 5 (lx <= 12); other orders fall back to SEM_FP64 */
+    SEM_TC_SPLIT = 4     /* float data, the FP32 operator with its D and D^T contractions on
+                            the tensor cores: u, D (and the weighted derivatives) split into
+                            three BF16 slices each, the six slice products of weight >= 2^-16
+                            formed by warp-level mma.sync with FP32 accumulation, the G
+                            weighting in FP32 (variant 8; lx = 8, other orders fall back to
+                            SEM_FP32).  Same accuracy class as SEM_FP32 */
 } sem_precision;
 
 typedef enum sem_solve_mode {
@@ -135,10 +141,27 @@ typedef struct sem_solve_opts {
                             restarting is faster, hence the default (0) */
     int persistent;      /* run each CG loop as ONE persistent (cooperative) launch whose CTAs
                             meet at bounded grid barriers, instead of graphs of three launches
-                            per iteration: -1 (default) below 2^20 local points, where launch
-                            latency dominates; 1 always; 0 never.  Single-mesh handles, lx <= 10,
-                            SEM_FP32 inner solves and SEM_FP64 / SEM_FP64_NATIVE (slab
-                            operator); not for SEM_FP64_PAIR */
+                            per iteration: 1 always, -1 below 2^20 local points, 0 never (the
+                            default: on the 32 K-point cube the graph loop is as fast or faster,
+                            2.2 against 2.8 ms FP64, 3.1 against 3.1 ms mixed, because each
+                            phase is bound by dependent-load latency, not by launches).
+                            Single-mesh handles, lx <= 10, SEM_FP32 inner solves and SEM_FP64 /
+                            SEM_FP64_NATIVE (slab operator); not for SEM_FP64_PAIR */
+    int tc_split;        /* mixed mode: the inner FP32 CG applies the operator as SEM_TC_SPLIT
+                            (tensor-core contractions) instead of the CUDA-core FP32 kernels (0) */
+    int pipelined;       /* FP64 mode: pipelined PCG (Ghysels and Vanroose 2014; the paper's
+                            work on reducing communication in CG, Sec. II-B): the PCG iterates
+                            with one reduction phase per iteration instead of two, at the cost
+                            of more vector traffic; native FP64 operator (0 = standard PCG) */
+    int projection;      /* projection onto previous solutions (Sec. II-B, after Fischer
+                            1998): 0 (default) off; L in 1..64: the solve starts from the
+                            A-orthogonal projection of its solution onto the space of earlier
+                            solution increments kept by the handle (the x passed in is then
+                            ignored), and a converged solve adds its increment, A-orthonormalised;
+                            a full space (L vectors) restarts from the latest solution, as the
+                            paper's GPU runs reset theirs every 20 solves.  Single-mesh handles; the space
+                            (2 L + 1 FP64 vectors) stays with the handle until
+                            sem_projection_reset or sem_destroy */
 } sem_solve_opts;
 
 typedef struct sem_solve_stats {
@@ -160,7 +183,11 @@ typedef struct sem_solve_stats {
                                  6 = as 5 with even/odd line transforms (even lx <= 12);
                                  5 and 6 serve SEM_FP64_PAIR only;
                                  7 (batches) = one slab launch over the element groups
-                                 of every order (orders up to lx = 10) */
+                                 of every order (orders up to lx = 10);
+                                 8 = BF16 split-precision tensor-core contractions for
+                                 FP32 data (SEM_TC_SPLIT; lx = 8; an FP32 autotuning
+                                 candidate) */
+    double relres_start;      /* true relative residual of the start (after projection, when on) */
     int launches_per_iteration;  /* kernel launches of one CG iteration: 3 for one mesh
                                  (operator, gather-scatter, update), 0 when the CG ran
                                  as one persistent launch; for a batch the
@@ -179,7 +206,8 @@ typedef struct sem_mesh_desc {
 } sem_mesh_desc;
 
 /* Set-up flag: pin operator kernel variant v: 0..4 for SEM_FP64 and SEM_FP32,
- * 5 or 6 for SEM_FP64_PAIR (the other precisions stay autotuned). */
+ * 5 or 6 for SEM_FP64_PAIR, 8 for SEM_FP32 (the other precisions stay
+ * autotuned). */
 #define SEM_FLAG_VARIANT(v) ((int)(((v) + 1) & 0xF))
 
 /* Set-up flag for testing failure detection: the bulk-staged operator kernels
@@ -188,6 +216,11 @@ typedef struct sem_mesh_desc {
  * the bounded waits (shortened to ~50 ms) expire, the kernels record the
  * failure and return, and the solve reports SEM_ETIMEOUT.  No fault, no hang. */
 #define SEM_FLAG_TEST_STALL 0x100
+
+/* Set-up flag: also keep the metric terms dr_s/dx_l per point (9 doubles per
+ * local point) for the gradient, divergence and curl operators and the
+ * pressure right-hand side (sem_grad, sem_div, sem_curl, sem_pressure_rhs). */
+#define SEM_FLAG_METRICS 0x200
 
 /* Fill *opts with the defaults listed above. */
 SEM_API void sem_solve_opts_default(sem_solve_opts* opts);
@@ -236,6 +269,23 @@ SEM_API int sem_get_info(const sem_handle* h, sem_info* info);
  * of solve s, offsets[nsolve] = n_local (host array of nsolve+1 entries). */
 SEM_API int sem_get_offsets(const sem_handle* h, int64_t* offsets);
 
+/* Turn the handle's operator into the Helmholtz operator of the velocity
+ * solve (Sec. II-A: the implicit viscous term of the P_N-P_N splitting gives
+ * a Helmholtz equation; Sec. II-B solves it with P-CG):
+ *   A_L u = D^T (h1 G) D u + h2 B u,  B = rho rho rho J (diagonal GLL mass),
+ * h1 as given at set-up (typically 1/Re), h2 per point (typically gamma_0/dt).
+ *   h2  HOST [n_local] finite, >= 0 (for a batch: all meshes concatenated),
+ *       or NULL to return to the Poisson operator
+ * Every later sem_ax and solve on the handle uses it, and the Jacobi
+ * preconditioner becomes Minv = mask / QQ^T (diag(A_L) + h2 B).  With h2 > 0
+ * the operator is SPD without Dirichlet nodes.  While a Helmholtz term is set
+ * the operator runs on the shared-slab kernels (or the tensor-core kernel for
+ * SEM_TC_SPLIT): SEM_FP64_PAIR falls back to SEM_FP64 and the bulk-staged
+ * variants to the slab kernel.  Errors: SEM_EINVAL (negative or
+ * non-finite h2, device pointer), SEM_ENOMEM, SEM_ECUDA.  Synchronises the
+ * stream. */
+SEM_API int sem_set_helmholtz(sem_handle* h, const double* h2, cudaStream_t stream);
+
 /* w = A_L u (assemble = 0) or w = mask * QQ^T A_L u (assemble = 1)
  * (Sec. II-A, eq. disclap and A = QQ^T A_L).  u, w: device [n_local] of the
  * precision's type; w must not alias u. */
@@ -282,6 +332,32 @@ SEM_API int sem_dot(sem_handle* h, const double* a, const double* b, double* res
 SEM_API int sem_dot_noalloc(const sem_handle* h, const double* a, const double* b, double* result,
                             cudaStream_t stream);
 
+/* Gradient, divergence and curl of nodal fields by collocation (Sec. II-A:
+ * the GLL nodal basis and D; the derivatives the pressure equation's right
+ * side needs): du/dx_l = sum_s (dr_s/dx_l) (D_s u), element by element, so
+ * the results are local fields that may jump across element faces.  All
+ * vectors are device double [n_local]; outputs must not alias inputs.  The
+ * handle must have been set up with SEM_FLAG_METRICS, else SEM_EINVAL. */
+SEM_API int sem_grad(sem_handle* h, const double* u, double* gx, double* gy, double* gz, cudaStream_t stream);
+SEM_API int sem_div(sem_handle* h, const double* vx, const double* vy, const double* vz, double* out,
+                    cudaStream_t stream);
+SEM_API int sem_curl(sem_handle* h, const double* vx, const double* vy, const double* vz, double* cx, double* cy,
+                     double* cz, cudaStream_t stream);
+
+/* Right-hand side of the pressure equation of the P_N-P_N splitting (Sec.
+ * II-A, eq. "pressure"): -lap p = -div(vhat) / dt + (1/Re) div(curl(omega)),
+ * in the weak form the Poisson solve takes, b = mask QQ^T (B f) with f the
+ * collocation values of the right side (the same quadrature as sem_mass).
+ *   vx, vy, vz  device [n_local] the explicit velocity vhat
+ *   wx, wy, wz  device [n_local] the explicit vorticity omega, or all NULL
+ *               (the term is dropped)
+ *   dt, Re      time step and Reynolds number (> 0)
+ *   b           device [n_local] output, assembled and masked
+ * Uses the handle's FP64 work vectors; SEM_FLAG_METRICS required. */
+SEM_API int sem_pressure_rhs(sem_handle* h, const double* vx, const double* vy, const double* vz,
+                             const double* wx, const double* wy, const double* wz, double dt, double Re,
+                             double* b, cudaStream_t stream);
+
 /* Copies of set-up data (device outputs):
  *   G  [E][6][lx^3] factors h1*G11, h1*G12, h1*G13, h1*G22, h1*G23, h1*G33
  *   B  [n_local] mass rho rho rho J
@@ -302,6 +378,11 @@ SEM_API int sem_get_jacobi(const sem_handle* h, double* minv, cudaStream_t strea
  * Synchronises the stream. */
 SEM_API int sem_cg_solve(sem_handle* h, double* x, const double* b, const sem_solve_opts* opts,
                          sem_solve_stats* stats, cudaStream_t stream);
+
+/* Projection space of a handle (sem_solve_opts.projection): drop every kept
+ * vector (the next solve starts from x = 0), and the number kept now. */
+SEM_API int sem_projection_reset(sem_handle* h);
+SEM_API int sem_projection_size(const sem_handle* h, int* count);
 
 /* All solves of a batch handle at once: x, b concatenated [n_local];
  * stats: host array of nsolve entries (may be NULL).  Every CG iteration

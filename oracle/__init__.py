@@ -29,6 +29,18 @@ What pins the oracle to something other than itself (tests/test_oracle_*.py):
   numpy Jacobians and an explicit Q on 1-8 deformed elements.
 * QQ^T: multiplicities 1/2/4/8 from mesh structure; sum invariance.
 * Jacobi: diagonal of the dense assembled matrix.
+* Gradient, divergence, curl: exact for polynomials of degree <= N on
+  (sheared) affine meshes; curl grad = 0 and div curl = 0 there; spectral
+  convergence on deformed meshes; pressure right-hand side of a gradient
+  field equal to the mass-weighted Laplacian.
+* Pipelined PCG: the iterates and recursive residuals of Jacobi-PCG within
+  rounding on small problems; dense solution.
+* Projection onto previous solutions: A-orthonormal basis; exact recovery of
+  a solution in the span; equality with a dense Galerkin projection; fewer
+  iterations on a slowly varying sequence of right-hand sides; reset when full.
+* Helmholtz (h2 B mass term): constants give exactly the assembled h2 B;
+  dense K + Q^T diag(h2 B) Q; its diagonal; SPD without Dirichlet nodes (PCG
+  = dense solve); spectral convergence of -lap u + lambda u = f.
 * PCG: dense direct solve on tiny meshes; spectral convergence to
   sin(pi x) sin(pi y) sin(pi z); at most n_free iterations on tiny meshes.
 * IR: reaches the FP64 solution; monotone outer residuals.
@@ -86,6 +98,7 @@ def configure(lib):
     for name in ("or_get_mult", "or_get_minv", "or_get_dmat"):
         getattr(lib, name).argtypes = [ctypes.c_void_p, _dp]
     lib.or_get_geom.argtypes = [ctypes.c_void_p, _dp, _dp]
+    lib.or_set_h2.argtypes = [ctypes.c_void_p, _dp]
     lib.or_ax_local.argtypes = [ctypes.c_void_p, _dp, _dp]
     lib.or_ax_local_abs.argtypes = [ctypes.c_void_p, _dp, _dp]
     lib.or_ax.argtypes = [ctypes.c_void_p, _dp, _dp]
@@ -181,6 +194,15 @@ class Problem:
         self.lib.or_get_dmat(self.h, _d(D))
         return D
 
+    def set_h2(self, h2):
+        """Helmholtz operator A_L u = D^T (h1 G) D u + h2 B u (the velocity
+        solve's implicit viscous term, Sec. II-A); None returns to Poisson.
+        The Jacobi diagonal is rebuilt with the h2 B term."""
+        if h2 is None:
+            self.lib.or_set_h2(self.h, None)
+        else:
+            self.lib.or_set_h2(self.h, _d(np.ascontiguousarray(h2, dtype=np.float64)))
+
     # operators ----------------------------------------------------------
     def ax_local(self, u):
         u = np.ascontiguousarray(u, dtype=np.float64)
@@ -244,3 +266,170 @@ class Problem:
                             ctypes.byref(oi), ctypes.byref(ii), ctypes.byref(rr), _d(hist))
         return x, dict(status=int(st), outer=int(oi.value), inner=int(ii.value),
                        relres=float(rr.value), outer_hist=hist[: oi.value])
+
+
+class Projection:
+    """Projection onto previous solutions (Sec. II-B, after Fischer 1998, as
+    the paper's solvers use it for pressure and velocity; on the GPUs the space
+    is reset when it holds `max_vectors` vectors, every 20 solves in the
+    paper's runs).
+
+    The space keeps vectors xt_i that are A-orthonormal in the unique-node
+    inner product <a, b> = sum_L a_L b_L / mult_L, and bt_i = A xt_i.  For a
+    right-hand side b the projected start is xbar = sum_i <xt_i, b> xt_i,
+    the A-orthogonal projection of the solution A^-1 b onto the span (its
+    error is A-orthogonal to every xt_i).  After the solve, the new direction
+    dx = x - xbar is A-orthogonalised against the space by classical
+    Gram-Schmidt run twice (coefficients <bt_i, v> = xt_i^T A v), normalised
+    in the A-norm and appended; a direction whose A-norm is below 1e-10 of
+    the original's is not appended (it lies in the span numerically).  A full
+    space restarts from the latest solution: it is cleared and x itself
+    (A-normalised) becomes its first vector, so the next start keeps the
+    latest solution's direction (the paper does not say what a reset keeps;
+    this is the reading taken)."""
+
+    def __init__(self, P, max_vectors: int = 20):
+        self.P = P
+        self.L = max_vectors
+        self.X = []
+        self.BX = []
+
+    def start(self, b):
+        b = np.asarray(b, dtype=np.float64)
+        xbar = np.zeros_like(b)
+        for xt in self.X:
+            xbar += self.P.dot(xt, b) * xt
+        return xbar
+
+    def update(self, x, xbar):
+        P = self.P
+        v = np.asarray(x, dtype=np.float64) - xbar
+        if len(self.X) >= self.L:
+            self.X, self.BX = [], []
+            v = np.asarray(x, dtype=np.float64).copy()
+        total = 0.0
+        for _ in range(2):
+            g = [P.dot(bt, v) for bt in self.BX]
+            total += sum(c * c for c in g)
+            for c, xt in zip(g, self.X):
+                v = v - c * xt
+        w = P.ax(v)
+        nn = P.dot(v, w)
+        if not (nn > 1e-20 * (total + nn)):
+            return False
+        s = 1.0 / np.sqrt(nn)
+        self.X.append(v * s)
+        self.BX.append(w * s)
+        return True
+
+
+def pipelined_pcg(P, b, x0=None, tol: float = 1e-10, max_iter: int = 100000):
+    """Pipelined preconditioned CG (Ghysels and Vanroose 2014), the
+    communication-reduced CG the paper's solver work builds on (Sec. II-B,
+    reference on reducing communication in CG): the same Krylov iterates as
+    Jacobi-PCG in exact arithmetic, with one reduction phase per iteration,
+    (r, u), (w, u) and (r, r) together, overlapping the operator application
+    n = A m.  Recurrences, with M = diag(Minv) and u = M r, w = A u, m = M w:
+        gamma = (r, u), delta = (w, u), n = A m
+        beta = gamma / gamma_prev, alpha = gamma / (delta - beta gamma / alpha_prev)
+        (first iteration: beta = 0, alpha = gamma / delta)
+        z = n + beta z, q = m + beta q, s = w + beta s, p = u + beta p
+        x += alpha p, r -= alpha s, u -= alpha q, w -= alpha z
+    Stops when the recursive ||r|| / ||b|| <= tol.  Returns (x, info) with
+    the iterations, the recursive residual history and the true residual."""
+    b = np.asarray(b, dtype=np.float64)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    Minv = P.minv()
+    r = b - P.ax(x)
+    u = Minv * r
+    w = P.ax(u)
+    bn = np.sqrt(P.dot(b, b))
+    z = np.zeros_like(b)
+    q = np.zeros_like(b)
+    s = np.zeros_like(b)
+    p = np.zeros_like(b)
+    gamma_prev = alpha_prev = 0.0
+    hist = []
+    it = 0
+    status = 1
+    while it < max_iter:
+        if bn == 0.0 or np.sqrt(P.dot(r, r)) / bn <= tol:
+            status = 0
+            break
+        gamma = P.dot(r, u)
+        delta = P.dot(w, u)
+        m = Minv * w
+        n = P.ax(m)
+        if it == 0:
+            beta = 0.0
+            alpha = gamma / delta
+        else:
+            beta = gamma / gamma_prev
+            alpha = gamma / (delta - beta * gamma / alpha_prev)
+        if not np.isfinite(alpha) or alpha <= 0.0:
+            status = 2
+            break
+        z = n + beta * z
+        q = m + beta * q
+        s = w + beta * s
+        p = u + beta * p
+        x = x + alpha * p
+        r = r - alpha * s
+        u = u - alpha * q
+        w = w - alpha * z
+        gamma_prev, alpha_prev = gamma, alpha
+        it += 1
+        hist.append(np.sqrt(P.dot(r, r)) / bn if bn > 0 else 0.0)
+    rt = b - P.ax(x)
+    return x, dict(status=status, iters=it, hist=np.array(hist),
+                   relres=float(np.sqrt(P.dot(rt, rt)) / bn) if bn > 0 else 0.0)
+
+
+def _ref_derivs(D: np.ndarray, u: np.ndarray, lx: int):
+    """(du/dr, du/ds, du/dt) per element: D applied along i, j, k of [e][k][j][i]."""
+    ue = u.reshape(-1, lx, lx, lx)
+    dr = np.einsum("il,ekjl->ekji", D, ue)
+    ds = np.einsum("jl,ekli->ekji", D, ue)
+    dt = np.einsum("kl,elji->ekji", D, ue)
+    return [d.reshape(-1) for d in (dr, ds, dt)]
+
+
+def metrics(mesh) -> np.ndarray:
+    """dr_s/dx_l at every local point, [n_local][s][l]: the inverse of the
+    Jacobian matrix dx/dr, whose entries are the reference derivatives of the
+    node coordinates (the isoparametric map of Sec. II-A)."""
+    D = dmat(mesh.N)
+    J = np.zeros((mesh.n_local, 3, 3))
+    for m in range(3):
+        d = _ref_derivs(D, np.ascontiguousarray(mesh.coords[m].reshape(-1)), mesh.lx)
+        for s_ in range(3):
+            J[:, m, s_] = d[s_]
+    return np.linalg.inv(J)
+
+
+def grad(mesh, u):
+    """Collocation gradient du/dx_l = sum_s (dr_s/dx_l) du/dr_s, element by
+    element (Sec. II-A: nodal GLL basis and D).  Returns [3][n_local]."""
+    D = dmat(mesh.N)
+    d = np.array(_ref_derivs(D, np.asarray(u, dtype=np.float64), mesh.lx))  # [s][n]
+    M = metrics(mesh)                                                        # [n][s][l]
+    return np.einsum("nsl,sn->ln", M, d)
+
+
+def div(mesh, vx, vy, vz):
+    return grad(mesh, vx)[0] + grad(mesh, vy)[1] + grad(mesh, vz)[2]
+
+
+def curl(mesh, vx, vy, vz):
+    gx, gy, gz = grad(mesh, vx), grad(mesh, vy), grad(mesh, vz)
+    return np.array([gz[1] - gy[2], gx[2] - gz[0], gy[0] - gx[1]])
+
+
+def pressure_rhs(P, mesh, vhat, omega, dt: float, Re: float):
+    """Weak right-hand side of the pressure equation (Sec. II-A, eq.
+    "pressure"): f = -div(vhat) / dt + (1/Re) div(curl(omega)) at the nodes,
+    b = mask QQ^T (B f) (omega None: the term is dropped)."""
+    f = -div(mesh, *vhat) / dt
+    if omega is not None:
+        f = f + div(mesh, *curl(mesh, *omega)) / Re
+    return P.mass(f, assemble=True)

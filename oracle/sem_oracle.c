@@ -23,6 +23,7 @@ struct or_problem {
     double* G;          /* [6][n] : G11 G12 G13 G22 G23 G33 */
     double* B;          /* [n] */
     double* h1;         /* [n] */
+    double* h2;         /* [n] mass coefficient of the Helmholtz operator, NULL: Poisson */
     uint8_t* mask;      /* [n] */
     double* mult;       /* [n] */
     double* minv;       /* [n] */
@@ -232,7 +233,10 @@ void or_ax_local(const or_problem* p, const double* u, double* w) {
                         for (int l = 0; l < lx; l++) acc += p->D[l * lx + i] * ur[k * lx * lx + j * lx + l];
                         for (int l = 0; l < lx; l++) acc += p->D[l * lx + j] * us[k * lx * lx + l * lx + i];
                         for (int l = 0; l < lx; l++) acc += p->D[l * lx + k] * ut[l * lx * lx + j * lx + i];
-                        w[o + k * lx * lx + j * lx + i] = acc;
+                        /* Helmholtz: + h2 B u, the GLL-quadrature mass term (v, h2 u) */
+                        const int64_t L = o + k * lx * lx + j * lx + i;
+                        if (p->h2) acc += p->h2[L] * p->B[L] * ue[k * lx * lx + j * lx + i];
+                        w[L] = acc;
                     }
         }
         free(ur);
@@ -293,7 +297,9 @@ void or_ax_local_abs(const or_problem* p, const double* u, double* w) {
                         for (int l = 0; l < lx; l++) acc += fabs(p->D[l * lx + i]) * ur[k * lx * lx + j * lx + l];
                         for (int l = 0; l < lx; l++) acc += fabs(p->D[l * lx + j]) * us[k * lx * lx + l * lx + i];
                         for (int l = 0; l < lx; l++) acc += fabs(p->D[l * lx + k]) * ut[l * lx * lx + j * lx + i];
-                        w[o + k * lx * lx + j * lx + i] = acc;
+                        const int64_t L = o + k * lx * lx + j * lx + i;
+                        if (p->h2) acc += fabs(p->h2[L] * p->B[L] * u[L]);
+                        w[L] = acc;
                     }
         }
         free(ur);
@@ -372,6 +378,7 @@ static void jacobi(or_problem* p) {
                     const double dii = D[i * lx + i], djj = D[j * lx + j], dkk = D[k * lx + k];
                     s += 2.0 * p->h1[L] *
                          (dii * djj * p->G[1 * n + L] + dii * dkk * p->G[2 * n + L] + djj * dkk * p->G[4 * n + L]);
+                    if (p->h2) s += p->h2[L] * p->B[L];  /* Helmholtz mass term on the diagonal */
                     d[L] = s;
                 }
     }
@@ -443,9 +450,23 @@ or_problem* or_setup(int E, int lx, const double* coords, const int64_t* gid,
 
 void or_free(or_problem* p) {
     if (!p) return;
-    free(p->D); free(p->rho); free(p->G); free(p->B); free(p->h1); free(p->mask);
+    free(p->D); free(p->rho); free(p->G); free(p->B); free(p->h1); free(p->h2); free(p->mask);
     free(p->mult); free(p->minv); free(p->order); free(p->grp);
     free(p);
+}
+
+/* Helmholtz operator (Sec. II-A: the velocity equation's implicit viscous term
+ * gives a Helmholtz problem; h1 weighs the stiffness, h2 the mass): from now on
+ * A_L u = D^T (h1 G) D u + h2 B u, and the Jacobi diagonal includes h2 B.
+ * h2 = NULL returns to the Poisson operator. */
+void or_set_h2(or_problem* p, const double* h2) {
+    free(p->h2);
+    p->h2 = NULL;
+    if (h2) {
+        p->h2 = (double*)malloc(sizeof(double) * p->n);
+        memcpy(p->h2, h2, sizeof(double) * p->n);
+    }
+    jacobi(p);
 }
 
 int64_t or_n_local(const or_problem* p) { return p->n; }
@@ -516,6 +537,7 @@ typedef struct {
     float* G;   /* [6][n] */
     float* h1;
     float* minv;
+    float* hb;  /* [n] float(h2 B) of a Helmholtz operator, NULL: Poisson */
 } or_f32;
 
 static void ax_local_f32(const or_problem* p, const or_f32* f, const float* u, float* w) {
@@ -562,7 +584,9 @@ static void ax_local_f32(const or_problem* p, const or_f32* f, const float* u, f
                         for (int l = 0; l < lx; l++) acc += f->D[l * lx + i] * ur[k * lx * lx + j * lx + l];
                         for (int l = 0; l < lx; l++) acc += f->D[l * lx + j] * us[k * lx * lx + l * lx + i];
                         for (int l = 0; l < lx; l++) acc += f->D[l * lx + k] * ut[l * lx * lx + j * lx + i];
-                        w[o + k * lx * lx + j * lx + i] = acc;
+                        const int64_t L = o + k * lx * lx + j * lx + i;
+                        if (f->hb) acc += f->hb[L] * u[L];
+                        w[L] = acc;
                     }
         }
         free(ur);
@@ -645,6 +669,11 @@ int or_ir(const or_problem* p, const double* b, double* x, double tol, double in
     for (int q = 0; q < lx * lx; q++) f.D[q] = (float)p->D[q];
     for (int64_t q = 0; q < 6 * n; q++) f.G[q] = (float)p->G[q];
     for (int64_t L = 0; L < n; L++) { f.h1[L] = (float)p->h1[L]; f.minv[L] = (float)p->minv[L]; }
+    f.hb = NULL;
+    if (p->h2) {
+        f.hb = (float*)malloc(sizeof(float) * n);
+        for (int64_t L = 0; L < n; L++) f.hb[L] = (float)(p->h2[L] * p->B[L]);
+    }
     double* r = (double*)malloc(sizeof(double) * n);
     double* w = (double*)malloc(sizeof(double) * n);
     float* r32 = (float*)malloc(sizeof(float) * n);
@@ -682,7 +711,7 @@ int or_ir(const or_problem* p, const double* b, double* x, double tol, double in
     *outer_iters = outer;
     *inner_iters = inner;
     *relres = rel;
-    free(f.D); free(f.G); free(f.h1); free(f.minv);
+    free(f.D); free(f.G); free(f.h1); free(f.minv); free(f.hb);
     free(r); free(w); free(r32); free(d32); free(pp);
     return status;
 }

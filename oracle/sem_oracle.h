@@ -12,6 +12,7 @@
  *   GLL nodes/weights and derivative matrix D .......... Sec. II-A, def. of D
  *   geometric factors G^e_st, mass B ................... Sec. II-A, def. of G
  *   local stiffness action A^e u = D^T G D u (with h1) . Sec. II-A, eq. (disclap)
+ *   Helmholtz mass term h2 B u (velocity solve) ........ Sec. II-A, Helmholtz form
  *   gather-scatter QQ^T and Dirichlet mask ............. Sec. II-A, A = QQ^T A_L
  *   point-Jacobi diagonal, preconditioned CG ........... Sec. II-B (P-CG, Jacobi)
  *   FP64 iterative refinement around an FP32 inner CG .. Sec. V outlook on
@@ -51,6 +52,10 @@ void or_get_geom(const or_problem* p, double* G, double* B);
 void or_get_mult(const or_problem* p, double* mult);
 void or_get_minv(const or_problem* p, double* minv);
 void or_get_dmat(const or_problem* p, double* D);
+
+/* Helmholtz operator: A_L u = D^T (h1 G) D u + h2 B u from now on, Jacobi
+ * diagonal with h2 B (h2 [n_L] copied; NULL returns to Poisson). */
+void or_set_h2(or_problem* p, const double* h2);
 
 /* w = A_L u (local, unassembled). */
 void or_ax_local(const or_problem* p, const double* u, double* w);

@@ -16,16 +16,17 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsem.so")
 
 SEM_OK, SEM_EINVAL, SEM_ENOMEM, SEM_ECUDA, SEM_ENOTCONV, SEM_EBREAKDOWN, SEM_ESTAGNATE, SEM_ETIMEOUT = range(8)
-SEM_FP64, SEM_FP32, SEM_FP64_NATIVE, SEM_FP64_PAIR = 0, 1, 2, 3
+SEM_FP64, SEM_FP32, SEM_FP64_NATIVE, SEM_FP64_PAIR, SEM_TC_SPLIT = 0, 1, 2, 3, 4
 SEM_MODE_FP64, SEM_MODE_MIXED_IR = 0, 1
 
 
 SEM_FLAG_TEST_STALL = 0x100
+SEM_FLAG_METRICS = 0x200
 
 
 def SEM_FLAG_VARIANT(v: int) -> int:
     """Set-up flag pinning operator kernel variant v, as in sem.h: 0..4 for
-    SEM_FP64 and SEM_FP32, 5 or 6 for SEM_FP64_PAIR."""
+    SEM_FP64 and SEM_FP32, 5 or 6 for SEM_FP64_PAIR, 8 for SEM_FP32."""
     return (v + 1) & 0xF
 STATUS_NAMES = {0: "SEM_OK", 1: "SEM_EINVAL", 2: "SEM_ENOMEM", 3: "SEM_ECUDA", 4: "SEM_ENOTCONV",
                 5: "SEM_EBREAKDOWN", 6: "SEM_ESTAGNATE", 7: "SEM_ETIMEOUT"}
@@ -47,14 +48,16 @@ class sem_solve_opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mode", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("precision", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("graph_chunk", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("ir_carry", ctypes.c_int), ("persistent", ctypes.c_int)]
+                ("ir_carry", ctypes.c_int), ("persistent", ctypes.c_int), ("tc_split", ctypes.c_int),
+                ("pipelined", ctypes.c_int), ("projection", ctypes.c_int)]
 
 
 class sem_solve_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("outer_iterations", ctypes.c_int),
                 ("relres", ctypes.c_double), ("relres_recursive", ctypes.c_double), ("time_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("ax_ms", ctypes.c_double), ("ax_samples", ctypes.c_int),
-                ("ax_variant", ctypes.c_int), ("launches_per_iteration", ctypes.c_int)]
+                ("ax_variant", ctypes.c_int), ("relres_start", ctypes.c_double),
+                ("launches_per_iteration", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -78,6 +81,7 @@ _SIGS = {
     "sem_destroy": (_I, [_VP]),
     "sem_get_info": (_I, [_VP, ctypes.POINTER(sem_info)]),
     "sem_get_offsets": (_I, [_VP, _VP]),
+    "sem_set_helmholtz": (_I, [_VP, _VP, _VP]),
     "sem_ax": (_I, [_VP, _VP, _VP, _I, _I, _VP]),
     "sem_gs": (_I, [_VP, _VP, _I, _I, _VP]),
     "sem_mass": (_I, [_VP, _VP, _VP, _I, _I, _VP]),
@@ -87,6 +91,12 @@ _SIGS = {
     "sem_get_jacobi": (_I, [_VP, _VP, _VP]),
     "sem_cg_solve": (_I, [_VP, _VP, _VP, ctypes.POINTER(sem_solve_opts), ctypes.POINTER(sem_solve_stats), _VP]),
     "sem_cg_solve_batch": (_I, [_VP, _VP, _VP, ctypes.POINTER(sem_solve_opts), _VP, _VP]),
+    "sem_grad": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "sem_div": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "sem_curl": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "sem_pressure_rhs": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double, _VP, _VP]),
+    "sem_projection_reset": (_I, [_VP]),
+    "sem_projection_size": (_I, [_VP, ctypes.POINTER(_I)]),
 }
 
 
@@ -209,6 +219,12 @@ def sem_get_offsets(h, nsolve: int) -> np.ndarray:
     return off
 
 
+def sem_set_helmholtz(h, h2=None, stream=None) -> None:
+    """h2: host array [n_local] (mass coefficient) or None for Poisson."""
+    hh = None if h2 is None else _host(h2, np.float64)
+    _check(load().sem_set_helmholtz(ctypes.c_void_p(h), _ptr(hh), _stream(stream)))
+
+
 def sem_ax(h, w, u, precision: int = SEM_FP64, assemble: int = 1, stream=None) -> None:
     _check(load().sem_ax(ctypes.c_void_p(h), _ptr(w), _ptr(u), precision, assemble, _stream(stream)))
 
@@ -266,3 +282,31 @@ def sem_cg_solve_batch(h, x, b, nsolve: int, opts: dict | None = None, stream=No
     _check(load().sem_cg_solve_batch(ctypes.c_void_p(h), _ptr(x), _ptr(b), ctypes.byref(o),
                                      ctypes.cast(st, ctypes.c_void_p), _stream(stream)), _SOLVE_OK)
     return [st[q].as_dict() for q in range(nsolve)]
+
+
+def sem_projection_reset(h) -> None:
+    _check(load().sem_projection_reset(ctypes.c_void_p(h)))
+
+
+def sem_projection_size(h) -> int:
+    c = ctypes.c_int(0)
+    _check(load().sem_projection_size(ctypes.c_void_p(h), ctypes.byref(c)))
+    return c.value
+
+
+def sem_grad(h, u, gx, gy, gz, stream=None) -> None:
+    _check(load().sem_grad(ctypes.c_void_p(h), _ptr(u), _ptr(gx), _ptr(gy), _ptr(gz), _stream(stream)))
+
+
+def sem_div(h, vx, vy, vz, out, stream=None) -> None:
+    _check(load().sem_div(ctypes.c_void_p(h), _ptr(vx), _ptr(vy), _ptr(vz), _ptr(out), _stream(stream)))
+
+
+def sem_curl(h, vx, vy, vz, cx, cy, cz, stream=None) -> None:
+    _check(load().sem_curl(ctypes.c_void_p(h), _ptr(vx), _ptr(vy), _ptr(vz), _ptr(cx), _ptr(cy), _ptr(cz),
+                           _stream(stream)))
+
+
+def sem_pressure_rhs(h, vx, vy, vz, wx, wy, wz, dt: float, Re: float, b, stream=None) -> None:
+    _check(load().sem_pressure_rhs(ctypes.c_void_p(h), _ptr(vx), _ptr(vy), _ptr(vz), _ptr(wx), _ptr(wy), _ptr(wz),
+                                   dt, Re, _ptr(b), _stream(stream)))

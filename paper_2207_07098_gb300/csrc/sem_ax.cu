@@ -21,6 +21,8 @@ int* device_error_word(sem_handle* h) { return reinterpret_cast<int*>(h->scratch
 
 int ax_variant_for(const sem_handle* h, int lx, int cls) {
     const int v = h->ax_variant[cls][lx];
+    // the pair kernels carry no Helmholtz mass term: a Helmholtz handle takes the native ones
+    if (cls == kClsPair && h->hmass64) return ax_variant_for(h, lx, kClsF64);
     if (cls == kClsPair) {
         // pinned 5 or 6 where it applies, else the line-transform form, else the
         // general pair kernel; orders neither covers use the native FP64 kernels
@@ -29,10 +31,15 @@ int ax_variant_for(const sem_handle* h, int lx, int cls) {
         if (bulk_supported(lx)) return kDflVariant;
         return lx <= 12 ? kDfVariant : ax_variant_for(h, lx, kClsF64);
     }
+    if (cls == kClsF32 && v == kTcVariant && lx == 8) return v;
+    // the bulk-staged kernels carry no Helmholtz mass term (it would cost the
+    // Poisson hot path registers): a Helmholtz handle takes the slab kernel
+    if (h->hmass64) return 0;
     return (v > 0 && v <= kBulkVariantsMax && bulk_fits(lx, v, cls == kClsF32)) ? v : 0;
 }
 
 int ax_variant_of_precision(const sem_handle* h, int lx, int precision) {
+    if (precision == SEM_TC_SPLIT && lx == 8) return kTcVariant;
     return precision == SEM_FP64_NATIVE ? 0 : ax_variant_for(h, lx, precision_class(precision));
 }
 
@@ -71,7 +78,10 @@ static int dispatch_variant(sem_handle* h, int lx, AxParams<T> a, bool fused, in
             return dispatch_ax_dfl_entry(h, lx, d, fused, s);
         }
     }
-    if (variant == kDfVariant || variant == kDflVariant) variant = 0;
+    if constexpr (std::is_same<T, float>::value) {
+        if (variant == kTcVariant && lx == 8) return dispatch_ax_tc(h, lx, a, fused, s);
+    }
+    if (variant == kDfVariant || variant == kDflVariant || variant == kTcVariant) variant = 0;
     a.variant = variant;
     a.err = device_error_word(h);
     a.wait_budget = h->test_stall ? 100000000LL : 4000000000LL;  // ~50 ms / ~2 s at 2 GHz
@@ -90,14 +100,15 @@ int launch_ax_local(sem_handle* h, const void* u, void* w, int precision, cudaSt
     for (int q = 0; q < h->nsolve; q++) {
         const MeshPart& p = h->parts[q];
         int rc;
-        if (precision == SEM_FP32) {
+        if (is_f32(precision)) {
             AxParams<float> a = {};
             a.u = (const float*)u + p.loc_off;
             a.w = (float*)w + p.loc_off;
             a.G = h->G32 + 6 * p.loc_off;
             a.D = h->D32[p.lx];
             a.E = p.E;
-            rc = dispatch_variant<float>(h, p.lx, a, false, ax_variant_for(h, p.lx, kClsF32), s);
+            a.mass = h->hmass32 ? h->hmass32 + p.loc_off : nullptr;
+            rc = dispatch_variant<float>(h, p.lx, a, false, ax_variant_of_precision(h, p.lx, precision), s);
         } else {
             AxParams<double> a = {};
             a.u = (const double*)u + p.loc_off;
@@ -105,6 +116,7 @@ int launch_ax_local(sem_handle* h, const void* u, void* w, int precision, cudaSt
             a.G = h->G64 + 6 * p.loc_off;
             a.D = h->D64[p.lx];
             a.E = p.E;
+            a.mass = h->hmass64 ? h->hmass64 + p.loc_off : nullptr;
             rc = dispatch_variant<double>(h, p.lx, a, false, ax_variant_of_precision(h, p.lx, precision), s);
         }
         if (rc) return rc;
@@ -112,11 +124,24 @@ int launch_ax_local(sem_handle* h, const void* u, void* w, int precision, cudaSt
     return SEM_OK;
 }
 
+int launch_ax_local_until_done(sem_handle* h, const double* u, double* w, const CGState* st, cudaStream_t s) {
+    const MeshPart& p = h->parts[0];
+    AxParams<double> a = {};
+    a.u = u;
+    a.w = w;
+    a.G = h->G64;
+    a.D = h->D64[p.lx];
+    a.E = p.E;
+    a.mass = h->hmass64;
+    a.skip_st = st;
+    return dispatch_variant<double>(h, p.lx, a, false, ax_variant_for(h, p.lx, kClsF64), s);
+}
+
 // K-A of a CG iteration on a single-mesh handle: p = z + beta p; w = A_L p;
 // alpha = rho / <p, w>.
 int launch_cg_pupdate_ax(sem_handle* h, int precision, cudaStream_t s) {
     const MeshPart& p = h->parts[0];
-    if (precision == SEM_FP32) {
+    if (is_f32(precision)) {
         AxParams<float> a = {};
         a.w = h->ws.w32;
         a.G = h->G32;
@@ -127,7 +152,8 @@ int launch_cg_pupdate_ax(sem_handle* h, int precision, cudaStream_t s) {
         a.st = h->state + 1;
         a.partials = h->partials;
         a.counter = h->counters + 2;
-        return dispatch_variant<float>(h, p.lx, a, true, ax_variant_for(h, p.lx, kClsF32), s);
+        a.mass = h->hmass32;
+        return dispatch_variant<float>(h, p.lx, a, true, ax_variant_of_precision(h, p.lx, precision), s);
     }
     AxParams<double> a = {};
     a.w = h->ws.w;
@@ -139,6 +165,7 @@ int launch_cg_pupdate_ax(sem_handle* h, int precision, cudaStream_t s) {
     a.st = h->state;
     a.partials = h->partials;
     a.counter = h->counters + 2;
+    a.mass = h->hmass64;
     return dispatch_variant<double>(h, p.lx, a, true, ax_variant_of_precision(h, p.lx, precision), s);
 }
 
@@ -154,8 +181,14 @@ int prepare_cg_kernels(sem_handle* h) {
                     AxParams<float> a = {};
                     a.dry = 1;
                     a.variant = v;
-                    rc = v > 0 ? dispatch_ax_bulk_f32(h, p.lx, a, fused != 0, 0)
-                               : dispatch_ax_f32(h, p.lx, a, fused != 0, 0);
+                    rc = v == kTcVariant ? dispatch_ax_tc(h, p.lx, a, fused != 0, 0)
+                         : v > 0        ? dispatch_ax_bulk_f32(h, p.lx, a, fused != 0, 0)
+                                        : dispatch_ax_f32(h, p.lx, a, fused != 0, 0);
+                    // SEM_TC_SPLIT solves take the tensor-core kernel at lx = 8
+                    if (!rc && p.lx == 8 && v != kTcVariant) {
+                        a.variant = kTcVariant;
+                        rc = dispatch_ax_tc(h, p.lx, a, fused != 0, 0);
+                    }
                 } else {
                     AxParams<double> a = {};
                     a.dry = 1;
@@ -193,8 +226,9 @@ int autotune_ax(sem_handle* h, bool fp32, cudaStream_t s) {
         if (h->ax_variant[fp32][p.lx] >= 0) continue;
         float best = 1e30f;
         int best_v = 0;
-        for (int v = 0; v <= kBulkVariantsMax; v++) {
-            if (v > 0 && !bulk_fits(p.lx, v, fp32)) continue;
+        for (int v = 0; v <= kTcVariant; v++) {
+            if (v > kBulkVariantsMax && !(v == kTcVariant && fp32 && p.lx == 8)) continue;
+            if (v > 0 && v <= kBulkVariantsMax && (!bulk_fits(p.lx, v, fp32) || h->hmass64)) continue;
             int rc2;
             auto run = [&](int dry) -> int {
                 if (fp32) {
@@ -205,6 +239,7 @@ int autotune_ax(sem_handle* h, bool fp32, cudaStream_t s) {
                     a.D = h->D32[p.lx];
                     a.E = p.E;
                     a.dry = dry;
+                    a.mass = h->hmass32 ? h->hmass32 + p.loc_off : nullptr;
                     return dispatch_variant<float>(h, p.lx, a, false, v, s);
                 }
                 AxParams<double> a = {};
@@ -214,6 +249,7 @@ int autotune_ax(sem_handle* h, bool fp32, cudaStream_t s) {
                 a.D = h->D64[p.lx];
                 a.E = p.E;
                 a.dry = dry;
+                a.mass = h->hmass64 ? h->hmass64 + p.loc_off : nullptr;
                 return dispatch_variant<double>(h, p.lx, a, false, v, s);
             };
             rc2 = run(1);
@@ -274,20 +310,20 @@ SEM_API int sem_ax(sem_handle* h, void* w, const void* u, int precision, int ass
     if (w == u) return fail(SEM_EINVAL, "w must not alias u");
     if (!aligned16(w) || !aligned16(u)) return fail(SEM_EINVAL, "u and w must be 16-byte aligned");
     int rc = launch_ax_local(h, u, w, precision, s);
-    if (rc == SEM_OK && assemble) rc = launch_gs(h, w, precision == SEM_FP32, true, s);
+    if (rc == SEM_OK && assemble) rc = launch_gs(h, w, is_f32(precision), true, s);
     return rc;
 }
 
 SEM_API int sem_mass(sem_handle* h, void* w, const void* u, int precision, int assemble, cudaStream_t s) {
     if (!h || !w || !u) return fail(SEM_EINVAL, "null argument");
     int rc;
-    if (precision == SEM_FP32)
+    if (is_f32(precision))
         rc = launch_mass32(h, (const float*)u, (float*)w, s);
     else if (valid_precision(precision))
         rc = launch_mass(h, (const double*)u, (double*)w, s);
     else
         return fail(SEM_EINVAL, "unknown precision");
-    if (rc == SEM_OK && assemble) rc = launch_gs(h, w, precision == SEM_FP32, true, s);
+    if (rc == SEM_OK && assemble) rc = launch_gs(h, w, is_f32(precision), true, s);
     return rc;
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 
 #include "sem_device.cuh"
 #include "sem_internal.h"
@@ -26,6 +27,8 @@ struct AxParams {
     const T* G;   // [E][6][lx^3], h1 folded in
     const T* D;   // [lx][lx]
     int64_t E;
+    const T* mass;  // [n] Helmholtz term h2 B (w += mass u), null for Poisson
+    const CGState* skip_st;  // plain kernels: return at once when skip_st->done (null: never)
     // fused CG variant: u = z + beta p, p <- u, partial <p, w>
     const T* z;
     T* p;
@@ -105,12 +108,14 @@ __device__ __forceinline__ void ax_load_d(T* sD, const T* D) {
 // One group of up to EPC elements.  Element `e` of this thread (relative to
 // the pointers) is processed when `valid`.  Plain: w = A_L u.  FUSED:
 // u = z + beta p (p <- u; old p ignored on the first iteration), w = A_L u,
-// and the thread's partial sum of u.w is returned.  Contains two
+// and the thread's partial sum of u.w is returned.  mass (may be null): the
+// Helmholtz term h2 B per point, added as w += mass u.  Contains two
 // __syncthreads(); every thread of the CTA must call it.
 template <typename T, int LX, bool FUSED>
 __device__ __forceinline__ T ax_group(const AxSmem<T, LX>& sm, const AxThread<LX>& th, int64_t e, bool valid,
                                       const T* __restrict__ u, const T* __restrict__ z, T* __restrict__ p,
-                                      T* __restrict__ w, const T* __restrict__ G, T tbeta, bool first) {
+                                      T* __restrict__ w, const T* __restrict__ G, T tbeta, bool first,
+                                      const T* __restrict__ mass = nullptr) {
     using C = AxCfg<LX>;
     constexpr int N2 = C::N2, N3 = C::N3, DP = C::DP;
     const T* sD = sm.sD;
@@ -183,6 +188,9 @@ __device__ __forceinline__ T ax_group(const AxSmem<T, LX>& sm, const AxThread<LX
             acc = fma(sD[l * DP + k], wt[l], acc);
         }
         if (valid) {
+            // Helmholtz mass term: u is read back from its shared slot, so the
+            // column need not stay in registers through this loop
+            if (mass) acc = fma(ld_stream(mass + base + k * N2), su[so + k * N2 + ij], acc);
             st_keep<FUSED>(w + base + k * N2, acc);
             if (FUSED) pw = fma(ucol[k], acc, pw);
         }
@@ -202,6 +210,8 @@ __global__ void __launch_bounds__(AxCfg<LX>::THREADS) ax_kernel(AxParams<T> a) {
         if (a.st->done) return;  // uniform over the grid
         if (threadIdx.x == 0) s_tbeta = (T)cg_beta(a.st);
         first = cg_first(a.st);
+    } else if (a.skip_st && a.skip_st->done) {
+        return;  // uniform over the grid
     }
     ax_load_d<T, LX>(sm.sD, a.D);
     const AxThread<LX> th;
@@ -213,7 +223,7 @@ __global__ void __launch_bounds__(AxCfg<LX>::THREADS) ax_kernel(AxParams<T> a) {
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
         const int64_t e = g * EPC + th.el;
         const bool valid = th.active && e < a.E;
-        const T pw = ax_group<T, LX, FUSED>(sm, th, e, valid, a.u, a.z, a.p, a.w, a.G, tbeta, first);
+        const T pw = ax_group<T, LX, FUSED>(sm, th, e, valid, a.u, a.z, a.p, a.w, a.G, tbeta, first, a.mass);
         if (FUSED) {
             if constexpr (sizeof(T) == 4)
                 fpair_add(paph, papl, pw);
@@ -299,6 +309,9 @@ inline bool bulk_fits(int lx, int v, bool fp32) {
     const size_t bytes = el * ((size_t)lx * (lx + 1) + 3 * epc * n3 + nst * epc * n3 * 8) + 16 * nst + 64;
     return bytes <= 227 * 1024 && epc * lx * lx <= 1024;
 }
+
+// BF16 split-precision tensor-core operator for FP32 data, lx = 8 (sem_ax_tc.cu)
+int dispatch_ax_tc(sem_handle* h, int lx, const AxParams<float>& a, bool fused, cudaStream_t s);
 
 // per-precision entry points (sem_ax_f64.cu, sem_ax_f32.cu)
 int dispatch_ax_f64(sem_handle* h, int lx, const AxParams<double>& a, bool fused, cudaStream_t s);

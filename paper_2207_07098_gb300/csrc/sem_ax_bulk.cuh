@@ -8,6 +8,8 @@
 // same order.  Only for even lx (element blocks are multiples of 16 bytes).
 #pragma once
 
+#include <type_traits>
+
 #include "sem_ax.cuh"
 
 namespace sem {
@@ -139,6 +141,8 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
         if (a.st->done) return;  // uniform over the grid
         if (threadIdx.x == 0) s_tbeta = (T)cg_beta(a.st);
         first = cg_first(a.st);
+    } else if (!FUSED && a.skip_st && a.skip_st->done) {
+        return;  // uniform over the grid
     }
     T tbeta = T(0);
     const int64_t ngroups = BATCH ? a.ngroups : (a.E + EPC - 1) / EPC;
@@ -190,33 +194,61 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
         Dci[l] = sD[l * DP + i];
         Dcj[l] = sD[l * DP + j];
     }
-    if (tid == 0)
+    // A batched CG launch skips the groups of converged solves: their stages
+    // are never filled, so no bytes move for them.  A solve's done flag cannot
+    // change while any of its groups is still to come in this launch (only the
+    // CTA that finishes its last group writes its state), so the producer's
+    // decision at issue time and the consumers' at use time agree.  Each stage
+    // keeps its own phase bit, flipped only by fills that were waited for.
+    auto skipped = [&](int64_t g) -> bool { return BATCH && FUSED && a.st[a.solve[g]].done; };
+    __shared__ unsigned inflight;  // stages with a fill in flight (thread 0's bookkeeping, for the drain)
+    if (tid == 0) {
+        inflight = 0u;
         for (int s = 0; s < NST; s++) {
             const int64_t g = blockIdx.x + (int64_t)s * gridDim.x;
-            if (g < ngroups) issue(s, g);
+            if (g < ngroups && !skipped(g)) {
+                issue(s, g);
+                inflight |= 1u << s;
+            }
         }
+    }
 
     double pap = 0.0;
     float paph = 0.f, papl = 0.f;  // FP32 kernels: <p, A p> as a float pair (no FP64 per group)
     int64_t it = 0;
+    uint32_t phase = 0u;  // bit s: parity of the next completed fill of stage s
+    __shared__ int s_skip;
     for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x, it++) {
         const int s = (int)(it % NST);
-        const uint32_t parity = (uint32_t)((it / NST) & 1);
-        if (!mbar_wait_bounded(&bars[s], parity, a.wait_budget)) abort_flag = 1;
+        if (BATCH && FUSED) {
+            if (tid == 0) s_skip = skipped(g) ? 1 : 0;
+            __syncthreads();
+        }
+        const bool skip = BATCH && FUSED && s_skip;
+        if (!skip) {
+            if (!mbar_wait_bounded(&bars[s], (phase >> s) & 1u, a.wait_budget))
+                abort_flag = 1;  // the stage stays in flight: the drain waits for its phase again
+            else
+                phase ^= 1u << s;
+        }
         __syncthreads();
         if (abort_flag) break;
+        if (tid == 0 && !skip) inflight &= ~(1u << s);
         int sol = 0;
+        if (skip) {  // converged solve: its stage was never filled; fill it with the group NST rounds ahead
+            if (tid == 0) {
+                const int64_t gn = g + (int64_t)NST * gridDim.x;
+                if (gn < ngroups && !skipped(gn)) {
+                    issue(s, gn);
+                    inflight |= 1u << s;
+                }
+            }
+            __syncthreads();  // s_skip is rewritten next round
+            continue;
+        }
         if (BATCH && FUSED) {
             sol = a.solve[g];
             const CGState* stg = a.st + sol;
-            if (stg->done) {  // converged solve: drop the stage, keep the ring going
-                __syncthreads();
-                if (tid == 0) {
-                    const int64_t gn = g + (int64_t)NST * gridDim.x;
-                    if (gn < ngroups) issue(s, gn);
-                }
-                continue;
-            }
             beta = cg_beta(stg);
             first = cg_first(stg);
             tbeta = (T)beta;
@@ -266,7 +298,10 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
         // the stage is consumed: refill it with the group NST rounds ahead
         if (tid == 0) {
             const int64_t gn = g + (int64_t)NST * gridDim.x;
-            if (gn < ngroups) issue(s, gn);
+            if (gn < ngroups && !skipped(gn)) {
+                issue(s, gn);
+                inflight |= 1u << s;
+            }
         }
         // phase 2: transposed contractions
         T pw = T(0);
@@ -322,11 +357,8 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
         // whether or not its copies have landed.
         if (tid == 0) {
             atomicExch(a.err, 1);
-            for (int s = 0; s < NST; s++) {
-                const int64_t ahead = it + s;
-                const int ss_ = (int)(ahead % NST);
-                mbar_wait_bounded(&bars[ss_], (uint32_t)((ahead / NST) & 1), a.wait_budget / 4);
-            }
+            for (int s = 0; s < NST; s++)
+                if (inflight & (1u << s)) mbar_wait_bounded(&bars[s], (phase >> s) & 1u, a.wait_budget / 4);
         }
         return;
     }

@@ -414,15 +414,17 @@ static int grid_tiles(sem_handle* h) { return grid_for(h, h->batch.ntiles * 256,
 // FP64 batches with SEM_FP64_PAIR use the FP32-pair line-transform operator
 // for the orders it covers; every other FP64 application (SEM_FP64, the true
 // residual) uses the native FP64 batch kernel.
-static bool batch_uses_pair_arith(int lx, int precision) {
-    return precision == SEM_FP64_PAIR && lx % 2 == 0 && lx >= 4 && lx <= 12;
+static bool batch_uses_pair_arith(const sem_handle* h, int lx, int precision) {
+    // (the pair kernels carry no Helmholtz mass term)
+    return precision == SEM_FP64_PAIR && !h->hmass64 && lx % 2 == 0 && lx >= 4 && lx <= 12;
 }
 
 // Bulk-staged operator variant v (1..4) can serve order lx of an FP32 batch:
 // it fits, and every solve of that order starts on a 16-byte boundary (bulk
 // copies need it; the elements of an even order keep it).
 static bool batch_bulk_ok(const sem_handle* h, int lx, int v) {
-    if (v < 1 || v > kBulkVariantsMax || !bulk_fits(lx, v, true)) return false;
+    // (the bulk-staged kernels carry no Helmholtz mass term)
+    if (v < 1 || v > kBulkVariantsMax || !bulk_fits(lx, v, true) || h->hmass64) return false;
     for (const MeshPart& p : h->parts)
         if (p.lx == lx && (p.loc_off % 4) != 0) return false;
     return true;
@@ -478,9 +480,10 @@ static int batch_ax_order(sem_handle* h, int precision, size_t li, int v, bool f
         a.D = h->D32[g.lx];
         a.loc = g.loc; a.cnt = g.cnt; a.solve = g.solve; a.ngroups = g.ngroups; a.goff = g.goff;
         a.st = st; a.sgfirst = bp.sgfirst; a.sgcount = bp.sgcount; a.gpart = bp.gpart; a.scount = bp.scount;
+        a.mass = h->hmass32;
         return dispatch_ax_batch_f32(h, g.lx, a, fused, s);
     }
-    if (batch_uses_pair_arith(g.lx, precision)) {
+    if (batch_uses_pair_arith(h, g.lx, precision)) {
         DflParams d = {};
         d.u = (const double*)u;
         d.z = h->ws.z;
@@ -500,6 +503,7 @@ static int batch_ax_order(sem_handle* h, int precision, size_t li, int v, bool f
     a.D = h->D64[g.lx];
     a.loc = g.loc; a.cnt = g.cnt; a.solve = g.solve; a.ngroups = g.ngroups; a.goff = g.goff;
     a.st = st; a.sgfirst = bp.sgfirst; a.sgcount = bp.sgcount; a.gpart = bp.gpart; a.scount = bp.scount;
+    a.mass = h->hmass64;
     return dispatch_ax_batch_f64(h, g.lx, a, fused, s);
 }
 
@@ -519,6 +523,7 @@ static int batch_ax_multi(sem_handle* h, int precision, bool fused, const void* 
         a.loc = bp.uloc; a.cnt = bp.ucnt; a.solve = bp.usolve; a.ngroups = bp.ngroups; a.goff = 0;
         a.st = st; a.sgfirst = bp.sgfirst; a.sgcount = bp.sgcount; a.gpart = bp.gpart; a.scount = bp.scount;
         a.dry = dry;
+        a.mass = h->hmass32;
         MultiOrder<float> mo = {};
         for (int lx = 2; lx <= kMultiMaxLx; lx++) mo.D[lx] = present[lx] ? h->D32[lx] : nullptr;
         mo.lx = bp.ulx;
@@ -533,6 +538,7 @@ static int batch_ax_multi(sem_handle* h, int precision, bool fused, const void* 
     a.loc = bp.uloc; a.cnt = bp.ucnt; a.solve = bp.usolve; a.ngroups = bp.ngroups; a.goff = 0;
     a.st = st; a.sgfirst = bp.sgfirst; a.sgcount = bp.sgcount; a.gpart = bp.gpart; a.scount = bp.scount;
     a.dry = dry;
+    a.mass = h->hmass64;
     MultiOrder<double> mo = {};
     for (int lx = 2; lx <= kMultiMaxLx; lx++) mo.D[lx] = present[lx] ? h->D64[lx] : nullptr;
     mo.lx = bp.ulx;
@@ -559,13 +565,16 @@ static int batch_ka_launches(const sem_handle* h, int precision) {
 }
 
 // Operator configuration of a batch for class cls (FP32 or native FP64):
-// variants pinned at set-up are honoured (one launch per order); otherwise,
-// with autotuning, each order's candidates (slab; for FP32 the bulk-staged
-// (elements per CTA, stages) variants that fit and are aligned) are timed on
-// the handle's own data with the plain operator over that order's groups, and
-// the sum of the fastest per order is compared with one multi-order slab
-// launch over every group; without autotuning the multi-order launch is taken
-// where it applies.  Runs once per handle and class, outside any capture.
+// variants pinned at set-up are honoured (one launch per order, the pinned
+// bulk-staged variant where it fits); otherwise, with autotuning, one slab
+// launch per order and one multi-order slab launch over every group are
+// timed on the handle's own data with the plain operator, and the faster is
+// kept; without autotuning the multi-order launch is taken where it applies.
+// The bulk-staged variants are not candidates: timed plain they beat the
+// slab kernel on a batch, but inside the solve, where members converge at
+// different iterations, they lost (256-box mixed batch, kept direction:
+// 2.94-2.98 s against 2.33 s per-order slab and 2.46 s multi-order).  Runs
+// once per handle and class, outside any capture.
 static int batch_configure(sem_handle* h, int cls, bool autotune, cudaStream_t s) {
     BatchPlan& bp = h->batch;
     if (bp.kcfg[cls] >= 0) return SEM_OK;
@@ -608,23 +617,16 @@ static int batch_configure(sem_handle* h, int cls, bool autotune, cudaStream_t s
         return SEM_OK;
     };
     float per_order = 0.0f;
-    for (size_t li = 0; li < bp.lxg.size() && !rc; li++) {
-        const int lx = bp.lxg[li].lx;
-        float best = 1e30f;
-        int best_v = 0;
-        for (int v = 0; v <= (fp32 ? kBulkVariantsMax : 0); v++) {
-            if (v > 0 && !batch_bulk_ok(h, lx, v)) continue;
-            float ms = 0.0f;
-            rc = time_it([&]() { return batch_ax_order(h, precision, li, v, false, u, nullptr, s); }, &ms);
-            if (rc) break;
-            if (ms < best) {
-                best = ms;
-                best_v = v;
+    rc = time_it(
+        [&]() {
+            for (size_t li = 0; li < bp.lxg.size(); li++) {
+                int r = batch_ax_order(h, precision, li, 0, false, u, nullptr, s);
+                if (r) return r;
             }
-        }
-        bp.ovar[cls][lx] = best_v;
-        per_order += best;
-    }
+            return (int)SEM_OK;
+        },
+        &per_order);
+    for (const LxGroups& g : bp.lxg) bp.ovar[cls][g.lx] = 0;
     int cfg = 0;
     if (!rc && bp.multi_ok) {
         float ms = 0.0f;
@@ -671,7 +673,7 @@ static int prepare_batch_kernels(sem_handle* h) {
             rc = dispatch_ax_bulk_batch_f32(h, g.lx, c, true, 0);
             if (!rc) rc = dispatch_ax_bulk_batch_f32(h, g.lx, c, false, 0);
         }
-        if (!rc && batch_uses_pair_arith(g.lx, SEM_FP64_PAIR)) {
+        if (!rc && batch_uses_pair_arith(h, g.lx, SEM_FP64_PAIR)) {
             DflParams d = {};
             d.dry = 1;
             rc = dispatch_ax_dfl_batch_entry(h, g.lx, d, true, 0);
@@ -917,7 +919,9 @@ static int solve_batch(sem_handle* h, double* x_user, const double* b_user, cons
         SEM_CUDA_TRY(cudaStreamSynchronize(s));
         return SEM_OK;
     };
-    if ((rc = batch_true_residual(h, s))) return rc;
+    if ((rc = batch_true_residual(h, s)) || (rc = read_rrbb())) return rc;
+    std::vector<double> rel0(ns);
+    for (int q = 0; q < ns; q++) rel0[q] = relative_residual(rrbb[2 * q], rrbb[2 * q + 1]);
     if (o.mode == SEM_MODE_FP64) {
         // SEM_FP64_NATIVE has no batched form of its own: the FP64 class serves it
         const int prec64 = o.precision == SEM_FP64_PAIR ? SEM_FP64_PAIR : SEM_FP64;
@@ -1036,7 +1040,8 @@ static int solve_batch(sem_handle* h, double* x_user, const double* b_user, cons
             const int itprec = o.mode == SEM_MODE_MIXED_IR ? SEM_FP32 : (o.precision == SEM_FP64_PAIR ? SEM_FP64_PAIR : SEM_FP64);
             const int cls = itprec == SEM_FP32 ? kClsF32 : kClsF64;
             st.launches_per_iteration = batch_ka_launches(h, itprec) + 2;
-            st.ax_variant = itprec == SEM_FP64_PAIR ? kDflVariant
+            st.relres_start = rel0[q];
+            st.ax_variant = (itprec == SEM_FP64_PAIR && !h->hmass64) ? kDflVariant
                             : bp.kcfg[cls] == 1 ? kMultiVariant : bp.ovar[cls][h->parts[q].lx];
         }
     }
@@ -1060,8 +1065,9 @@ SEM_API int sem_cg_solve_batch(sem_handle* h, double* x, const double* b, const 
         return fail(SEM_EINVAL, "bad solve options");
     if (o.mode == SEM_MODE_MIXED_IR && !(o.inner_tol > 0.0 && o.inner_tol < 1.0))
         return fail(SEM_EINVAL, "inner_tol must be in (0, 1)");
-    if (o.mode == SEM_MODE_FP64 && (!valid_precision(o.precision) || o.precision == SEM_FP32))
+    if (o.mode == SEM_MODE_FP64 && (!valid_precision(o.precision) || is_f32(o.precision)))
         return fail(SEM_EINVAL, "FP64 mode takes SEM_FP64, SEM_FP64_NATIVE or SEM_FP64_PAIR");
+    if (o.projection != 0) return fail(SEM_EINVAL, "projection onto previous solutions: single-mesh handles only");
     return solve_batch(h, x, b, o, stats, s);
 }
 

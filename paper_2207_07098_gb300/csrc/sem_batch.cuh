@@ -29,6 +29,7 @@ struct BatchAxParams {
     double* gpart;
     unsigned int* scount;
     int dry;
+    const T* mass;         // [n] Helmholtz term h2 B, null for Poisson
 };
 
 template <typename T, int LX, bool FUSED>
@@ -69,7 +70,8 @@ __global__ void __launch_bounds__(AxCfg<LX>::THREADS) ax_batch_kernel(BatchAxPar
         const bool valid = th.active && th.el < a.cnt[g];
         const T pw = ax_group<T, LX, FUSED>(sm, th, th.el, valid, FUSED ? nullptr : a.u + loc,
                                             FUSED ? a.z + loc : nullptr, FUSED ? a.p + loc : nullptr,
-                                            a.w + loc, a.G + 6 * loc, tbeta, first);
+                                            a.w + loc, a.G + 6 * loc, tbeta, first,
+                                            a.mass ? a.mass + loc : nullptr);
         if (FUSED) {
             double v[1] = {0.0};
             if constexpr (sizeof(T) == 4) {  // float-pair block sum: FP64 only in thread 0
@@ -140,7 +142,8 @@ __device__ __forceinline__ T multi_group(T* dtab, T* slots, const BatchAxParams<
     const int64_t loc = a.loc[g];
     const bool valid = th.active && th.el < a.cnt[g];
     return ax_group<T, LX, FUSED>(sm, th, th.el, valid, FUSED ? nullptr : a.u + loc, FUSED ? a.z + loc : nullptr,
-                                  FUSED ? a.p + loc : nullptr, a.w + loc, a.G + 6 * loc, tbeta, first);
+                                  FUSED ? a.p + loc : nullptr, a.w + loc, a.G + 6 * loc, tbeta, first,
+                                  a.mass ? a.mass + loc : nullptr);
 }
 
 template <typename T, bool FUSED>

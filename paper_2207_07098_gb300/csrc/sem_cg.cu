@@ -260,7 +260,7 @@ static int launch_scale(sem_handle* h, double* v, double f, cudaStream_t s) {
 
 int launch_cg_update(sem_handle* h, int precision, cudaStream_t s) {
     const int grid = grid_for(h, h->n_local / 4 + 1, 256, 8);
-    if (precision == SEM_FP32) {
+    if (is_f32(precision)) {
         UpdParams<float> a = {h->ws.d32, h->ws.p32, h->ws.r32, h->ws.w32, h->ws.z32, h->minv32, h->mult,
                               h->n_local, h->state + 1, h->partials, h->counters + 3};
         cg_update_kernel<float><<<grid, 256, 0, s>>>(a);
@@ -275,12 +275,14 @@ int launch_cg_update(sem_handle* h, int precision, cudaStream_t s) {
 }
 
 static int launch_ka(sem_handle* h, int precision, cudaStream_t s) {
+    if (precision == kPipePrec) return launch_pipe_iteration(h, s);  // all three launches
     return precision == kPairPrec ? launch_pair_ka(h, s) : launch_cg_pupdate_ax(h, precision, s);
 }
 
 static int launch_kb_kc(sem_handle* h, int precision, cudaStream_t s) {
+    if (precision == kPipePrec) return SEM_OK;
     if (precision == kPairPrec) return launch_pair_rest(h, s);
-    int rc = launch_gs(h, precision == SEM_FP32 ? (void*)h->ws.w32 : (void*)h->ws.w, precision == SEM_FP32, true, s);
+    int rc = launch_gs(h, is_f32(precision) ? (void*)h->ws.w32 : (void*)h->ws.w, is_f32(precision), true, s);
     if (!rc) rc = launch_cg_update(h, precision, s);
     return rc;
 }
@@ -293,7 +295,9 @@ static int launch_iteration(sem_handle* h, int precision, cudaStream_t s) {
 static int get_graph(sem_handle* h, int precision, int chunk, cudaGraphExec_t* out) {
     GraphCache& g = h->graph;
     // (the pair-form loop has its own precision code and always the line kernel)
-    const int variant = precision == kPairPrec ? kDflVariant : ax_variant_of_precision(h, h->parts[0].lx, precision);
+    const int variant = precision == kPairPrec   ? kDflVariant
+                        : precision == kPipePrec ? ax_variant_for(h, h->parts[0].lx, kClsF64)
+                                                 : ax_variant_of_precision(h, h->parts[0].lx, precision);
     if (g.exec && g.key_prec == precision && g.key_chunk == chunk && g.key_variant == variant) {
         *out = g.exec;
         return SEM_OK;
@@ -404,7 +408,8 @@ static int run_cg_loop(sem_handle* h, int precision, const sem_solve_opts& o, in
 // and the mesh allow it (opts.persistent: 1 forces it where available, -1
 // takes it below kPersistAutoPoints local points), else the graph loop.
 static bool use_persist(const sem_handle* h, const sem_solve_opts& o, int precision) {
-    if (o.persistent == 0 || precision == kPairPrec || precision == SEM_FP64_PAIR || !persist_available(h))
+    if (o.persistent == 0 || precision == kPairPrec || precision == kPipePrec || precision == SEM_FP64_PAIR ||
+        precision == SEM_TC_SPLIT || !persist_available(h))
         return false;
     return o.persistent > 0 || h->n_local <= kPersistAutoPoints;
 }
@@ -469,9 +474,10 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
                         sem_solve_stats* stats, cudaStream_t s) {
     int rc = ensure_workspace(h, o.mode == SEM_MODE_MIXED_IR);
     if (rc) return rc;
-    const int prec = o.mode == SEM_MODE_MIXED_IR ? SEM_FP32 : o.precision;
+    // inner precision of the mixed mode: FP32, or its tensor-core form
+    const int prec = o.mode == SEM_MODE_MIXED_IR ? (o.tc_split ? SEM_TC_SPLIT : SEM_FP32) : o.precision;
     if (o.autotune) {
-        if (prec == SEM_FP32 && (rc = autotune_ax(h, true, s))) return rc;
+        if (is_f32(prec) && (rc = autotune_ax(h, true, s))) return rc;
         // the FP64 class computes every true residual
         if ((rc = autotune_ax(h, false, s))) return rc;
     }
@@ -484,8 +490,11 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
     cudaEventRecord(ev0, s);
     SEM_CUDA_TRY(cudaMemcpyAsync(h->ws.x, x_user, bytes, xh ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
     SEM_CUDA_TRY(cudaMemcpyAsync(h->ws.b, b_user, bytes, bh ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    // projection onto previous solutions: the start is the projected solution
+    if (o.projection > 0 && (rc = proj_start(h, o.projection, s))) return rc;
     double* rrbb = h->scratch;  // [0] rr, [1] bb
     sem_solve_stats st = {};
+    bool first_residual = true;
     AxTiming tm;
     const int64_t launches0 = h->launches;
     CGState hs;
@@ -499,13 +508,17 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
         // With the line-transform FP32-pair operator the CG vectors live as
         // float pairs, and x, b, r are scaled by a power of two (exactly) into
         // the range the pair format represents.
-        const bool pair = prec == SEM_FP64_PAIR && pair_cg_available(h);
+        const bool pipe = o.pipelined != 0;  // pipelined PCG, native FP64 operator
+        const bool pair = !pipe && prec == SEM_FP64_PAIR && pair_cg_available(h);
         if (pair && (rc = ensure_pair_workspace(h))) return rc;
+        if (pipe && (rc = ensure_pipe_workspace(h))) return rc;
         double scale = 1.0;
         int used = 0;
         for (int restart = 0;; restart++) {
             if ((rc = true_residual(h, h->ws.x, h->ws.b, rrbb, s)) || (rc = read_rrbb(h, hb, s))) return rc;
             const double rel = relative_residual(hb[0], hb[1]);
+            if (first_residual) st.relres_start = rel;
+            first_residual = false;
             if (!std::isfinite(rel)) {  // NaN or Inf in x0 or b, or a diverged iterate
                 status = SEM_EBREAKDOWN;
                 break;
@@ -522,6 +535,8 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
                     return rc;
                 if ((rc = launch_pair_split_x(h, s)) || (rc = launch_pair_init(h, o.tol, o.max_iter - used, s)))
                     return rc;
+            } else if (pipe) {
+                if ((rc = launch_pipe_init(h, o.tol, o.max_iter - used, s))) return rc;
             } else {
                 cg_init_kernel<double><<<grid_for(h, n, 256, 4), 256, 0, s>>>(
                     h->ws.b, h->ws.r, h->ws.z, h->minv64, h->mult, n, o.tol, o.max_iter - used, h->state,
@@ -529,7 +544,8 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
                 SEM_LAUNCH_CHECK("cg_init_kernel");
                 h->launches++;
             }
-            if ((rc = run_cg(h, pair ? kPairPrec : prec, o, 0, s, &hs, &tm, &persisted))) return rc;
+            if ((rc = run_cg(h, pair ? kPairPrec : pipe ? kPipePrec : prec, o, 0, s, &hs, &tm, &persisted)))
+                return rc;
             if (pair) {
                 if ((rc = launch_pair_join_x(h, s))) return rc;
                 if (scale != 1.0 && ((rc = launch_scale(h, h->ws.x, scale, s)) ||
@@ -552,6 +568,8 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
         for (;;) {
             if ((rc = true_residual(h, h->ws.x, h->ws.b, rrbb, s)) || (rc = read_rrbb(h, hb, s))) return rc;
             const double rel = relative_residual(hb[0], hb[1]);
+            if (first_residual) st.relres_start = rel;
+            first_residual = false;
             st.relres_recursive = rel;
             if (!std::isfinite(rel)) { status = SEM_EBREAKDOWN; break; }
             if (hb[1] == 0.0 || rel <= o.tol) { status = SEM_OK; break; }
@@ -569,7 +587,7 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
                 h->state + 1, h->partials, h->counters + 5, carry_c);
             SEM_LAUNCH_CHECK("ir prepare");
             h->launches += 2;
-            if ((rc = run_cg(h, SEM_FP32, o, 1, s, &hs, &tm, &persisted))) return rc;
+            if ((rc = run_cg(h, prec, o, 1, s, &hs, &tm, &persisted))) return rc;
             inner += hs.iter;
             capped_last = hs.iter >= o.max_iter;
             can_carry = (hs.status == SEM_OK || hs.status == SEM_ENOTCONV) && hs.iter > 0;
@@ -583,6 +601,8 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
         st.outer_iterations = outer;
     }
     // hb holds the true residual of the final iterate (both loops end right after computing it)
+    const double rel_final = relative_residual(hb[0], hb[1]);
+    if (o.projection > 0 && status == SEM_OK && rel_final <= o.tol && (rc = proj_update(h, s))) return rc;
     SEM_CUDA_TRY(cudaMemcpyAsync(x_user, h->ws.x, bytes, xh ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
     cudaEventRecord(ev1, s);
     SEM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -601,8 +621,8 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
     // SEM_OK promises the tolerance on the true residual, whatever the loop reported
     if (status == SEM_OK && !(st.relres <= o.tol)) status = std::isfinite(st.relres) ? SEM_ENOTCONV : SEM_EBREAKDOWN;
     st.time_ms = ms;
-    st.ax_variant = o.mode == SEM_MODE_MIXED_IR ? ax_variant_for(h, h->parts[0].lx, kClsF32)
-                                                : ax_variant_of_precision(h, h->parts[0].lx, prec);
+    st.ax_variant = (o.mode == SEM_MODE_FP64 && o.pipelined) ? ax_variant_for(h, h->parts[0].lx, kClsF64)
+                                                              : ax_variant_of_precision(h, h->parts[0].lx, prec);
     st.status = status;
     st.launches_per_iteration = persisted ? 0 : 3;
     st.kernel_launches = h->launches - launches0;
@@ -635,8 +655,9 @@ SEM_API int sem_cg_solve(sem_handle* h, double* x, const double* b, const sem_so
         return fail(SEM_EINVAL, "bad solve options");
     if (o.mode == SEM_MODE_MIXED_IR && !(o.inner_tol > 0.0 && o.inner_tol < 1.0))
         return fail(SEM_EINVAL, "inner_tol must be in (0, 1)");
-    if (o.mode == SEM_MODE_FP64 && (!valid_precision(o.precision) || o.precision == SEM_FP32))
+    if (o.mode == SEM_MODE_FP64 && (!valid_precision(o.precision) || is_f32(o.precision)))
         return fail(SEM_EINVAL, "FP64 mode takes SEM_FP64, SEM_FP64_NATIVE or SEM_FP64_PAIR");
+    if (o.projection < 0 || o.projection > 64) return fail(SEM_EINVAL, "projection must be in [0, 64]");
     return solve_single(h, x, b, o, stats, s);
 }
 

@@ -249,6 +249,15 @@ bool pair_cg_available(const sem_handle* h) {
     return h->nsolve == 1 && ax_variant_for(h, h->parts[0].lx, kClsPair) == kDflVariant;
 }
 
+// the pair planes of Minv follow a changed Jacobi diagonal (Helmholtz term)
+int refresh_pair_minv(sem_handle* h, cudaStream_t s) {
+    if (!h->ws.pv[10]) return SEM_OK;
+    split_minv_kernel<<<grid_for(h, h->n_local, 256, 8), 256, 0, s>>>(h->minv64, h->ws.pv[10], h->ws.pv[11],
+                                                                       h->n_local);
+    SEM_LAUNCH_CHECK("split_minv_kernel");
+    return SEM_OK;
+}
+
 int ensure_pair_workspace(sem_handle* h) {
     if (h->ws.pv[0]) return SEM_OK;
     const size_t n = (size_t)h->n_local;

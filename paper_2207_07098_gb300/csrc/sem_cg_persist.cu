@@ -45,6 +45,7 @@ struct PersistParams {
     int* err;
     long long budget;    // clock cycles a CTA waits at one barrier
     int stall;           // test of the bounded barrier: CTA 0 never arrives at the first one
+    const T* mass;       // [n] Helmholtz term h2 B, null for Poisson
 };
 
 // Bounded grid barrier of a cooperative launch: returns false (error word
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(AxCfg<LX>::THREADS) cg_persist_kernel(PersistP
         for (int64_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
             const int64_t e = g * C::EPC + th.el;
             const bool valid = th.active && e < a.E;
-            const T pw = ax_group<T, LX, true>(sm, th, e, valid, nullptr, a.z, a.p, a.w, a.G, tbeta, first);
+            const T pw = ax_group<T, LX, true>(sm, th, e, valid, nullptr, a.z, a.p, a.w, a.G, tbeta, first, a.mass);
             if constexpr (sizeof(T) == 4)
                 fpair_add(ph, pl, pw);
             else
@@ -322,15 +323,15 @@ int launch_cg_persist(sem_handle* h, int precision, int slot, cudaStream_t s) {
     const MeshPart& pt = h->parts[0];
     const GSLists& g = h->gs;
     const long long budget = h->test_stall ? 100000000LL : 4000000000LL;  // ~50 ms / ~2 s at 2 GHz
-    if (precision == SEM_FP32) {
+    if (is_f32(precision)) {
         PersistParams<float> a = {h->ws.d32, h->ws.p32, h->ws.r32, h->ws.w32, h->ws.z32, h->minv32, h->mult,
                                   h->G32, h->D32[pt.lx], pt.E, h->n_local, g, h->state + slot, h->partials,
-                                  h->counters + 10, device_error_word(h), budget, h->test_stall};
+                                  h->counters + 10, device_error_word(h), budget, h->test_stall, h->hmass32};
         return dispatch_persist<float>(h, pt.lx, a, s);
     }
     PersistParams<double> a = {h->ws.x, h->ws.p, h->ws.r, h->ws.w, h->ws.z, h->minv64, h->mult,
                                h->G64, h->D64[pt.lx], pt.E, h->n_local, g, h->state + slot, h->partials,
-                               h->counters + 10, device_error_word(h), budget, h->test_stall};
+                               h->counters + 10, device_error_word(h), budget, h->test_stall, h->hmass64};
     return dispatch_persist<double>(h, pt.lx, a, s);
 }
 

@@ -151,7 +151,7 @@ SEM_API int sem_gs(sem_handle* h, void* u, int precision, int apply_mask, cudaSt
     if (!h || !u) return fail(SEM_EINVAL, "null argument");
     if (!valid_precision(precision))
         return fail(SEM_EINVAL, "unknown precision");
-    return launch_gs(h, u, precision == SEM_FP32, apply_mask != 0, s);
+    return launch_gs(h, u, is_f32(precision), apply_mask != 0, s);
 }
 
 SEM_API int sem_dot(sem_handle* h, const double* a, const double* b, double* result, cudaStream_t s) {

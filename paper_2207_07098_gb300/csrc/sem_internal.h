@@ -20,16 +20,19 @@ constexpr int kBulkVariantsMax = 4;  // operator variants 1..4 are bulk-staged
 constexpr int kDfVariant = 5;        // FP64 data, FP32-pair arithmetic (FP64 precisions only)
 constexpr int kDflVariant = 6;       // same, line-transform form with even/odd splitting (even lx)
 constexpr int kMultiVariant = 7;     // batches: one slab launch over the groups of every order
+constexpr int kTcVariant = 8;        // FP32 data, BF16 split-precision tensor-core contractions (lx = 8)
 // operator classes, each with its own tuned or pinned variant per order:
 // native FP64 (variants 0..4), FP32 (0..4), FP32-pair arithmetic on FP64 data (5, 6)
 constexpr int kClsF64 = 0, kClsF32 = 1, kClsPair = 2;
 // class of a sem_precision value (SEM_FP64_NATIVE: the FP64 class, variant 0)
+// float data: SEM_FP32 and its tensor-core form SEM_TC_SPLIT
+inline bool is_f32(int precision) { return precision == SEM_FP32 || precision == SEM_TC_SPLIT; }
 inline int precision_class(int precision) {
-    return precision == SEM_FP32 ? kClsF32 : precision == SEM_FP64_PAIR ? kClsPair : kClsF64;
+    return is_f32(precision) ? kClsF32 : precision == SEM_FP64_PAIR ? kClsPair : kClsF64;
 }
 inline bool valid_precision(int precision) {
     return precision == SEM_FP64 || precision == SEM_FP32 || precision == SEM_FP64_NATIVE ||
-           precision == SEM_FP64_PAIR;
+           precision == SEM_FP64_PAIR || precision == SEM_TC_SPLIT;
 }
 
 // ---------------------------------------------------------------------------
@@ -128,6 +131,8 @@ struct Workspace {
     float* b32 = nullptr;
     // FP64 mode in pair form: x, p, r, w, z (hi, lo planes each), Minv (hi, lo)
     float* pv[12] = {};
+    // pipelined CG: u, w, m, n, z, q, s, p (FP64)
+    double* pipe[8] = {};
     bool have64 = false, have32 = false;
 };
 
@@ -201,6 +206,17 @@ inline double relative_residual(double rr, double bb) {
     return bb > 0 ? std::sqrt(rr / bb) : 0.0;
 }
 
+// Projection space of a single-mesh handle (sem_proj.cu): L slots of
+// A-orthonormal xt_i and bt_i = A xt_i, l of them in use, the last start xbar.
+struct ProjSpace {
+    int L = 0;
+    int l = 0;
+    double* xt = nullptr;    // [L][n_local]
+    double* bt = nullptr;    // [L][n_local]
+    double* xbar = nullptr;  // [n_local]
+    double* coef = nullptr;  // [L + 2] coefficients of the current projection
+};
+
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     int key_prec = -1;
@@ -231,6 +247,9 @@ struct sem_handle {
     float* G2 = nullptr;       // [E][12][lx^3]: hi planes then lo planes of G64 (FP32-pair kernel)
     double* B64 = nullptr;     // [n_local] mass
     double* minv64 = nullptr;  // [n_local]
+    double* hmass64 = nullptr; // [n_local] Helmholtz mass term h2 B (null: Poisson operator)
+    double* drdx = nullptr;    // [E][9][lx^3] dr_s/dx_l (SEM_FLAG_METRICS; gradient operators)
+    float* hmass32 = nullptr;
     float* minv32 = nullptr;
     uint8_t* mult = nullptr;   // [n_local] copies of the node
     uint8_t* mask = nullptr;   // [n_local]
@@ -243,6 +262,7 @@ struct sem_handle {
     double* scratch = nullptr;        // [64] small device scratch
     sem::Workspace ws;
     sem::GraphCache graph;
+    sem::ProjSpace proj;
     sem::BatchPlan batch;
     cudaStream_t capture_stream = nullptr;
     cudaEvent_t ax_ev[2] = {nullptr, nullptr};  // bracket one K-A per graph (single: 2nd, batch: 1st)
@@ -293,8 +313,19 @@ int grid_for(sem_handle* h, int64_t work_items, int threads, int per_sm);
 int prepare_cg_kernels(sem_handle* h);
 // FP64 CG with float-pair vectors (sem_cg_pair.cu)
 constexpr int kPairPrec = 100;  // "precision" code of the pair-form CG loop
+constexpr int kPipePrec = 101;  // "precision" code of the pipelined CG loop (sem_cg_pipe.cu)
+int ensure_pipe_workspace(sem_handle* h);
+int launch_pipe_init(sem_handle* h, double tol, int max_iter, cudaStream_t s);
+int launch_pipe_iteration(sem_handle* h, cudaStream_t s);
+// native FP64 w = A_L u that returns at once when st->done (inside CG graphs)
+int launch_ax_local_until_done(sem_handle* h, const double* u, double* w, const CGState* st, cudaStream_t s);
 bool pair_cg_available(const sem_handle* h);
 int ensure_pair_workspace(sem_handle* h);
+int refresh_pair_minv(sem_handle* h, cudaStream_t s);
+// projection onto previous solutions (sem_proj.cu)
+int proj_start(sem_handle* h, int max_vectors, cudaStream_t s);
+int proj_update(sem_handle* h, cudaStream_t s);
+void free_projection(sem_handle* h);
 int launch_pair_split_x(sem_handle* h, cudaStream_t s);
 int launch_pair_join_x(sem_handle* h, cudaStream_t s);
 int launch_pair_init(sem_handle* h, double tol, int max_iter, cudaStream_t s);

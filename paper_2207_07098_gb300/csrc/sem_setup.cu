@@ -99,6 +99,7 @@ struct GeomArgs {
     const double* rho;    // [lx]
     double* G;            // [E][6][lx^3] (this part)
     double* B;            // [n_local]
+    double* drdx;         // [E][9][lx^3] dr_s/dx_l (s major) of this part, or null
     int E, lx;
     int* bad;             // set to 1 on a non-positive Jacobian
 };
@@ -156,6 +157,10 @@ __global__ void geometry_kernel(GeomArgs a) {
             Ge[c * n3] = s * dot;
         }
         a.B[L] = wq * J;
+        if (a.drdx) {
+            double* Me = a.drdx + e * 9 * n3 + q;
+            for (int c = 0; c < 9; c++) Me[c * n3] = g[c / 3][c % 3] / J;
+        }
     }
 }
 
@@ -303,10 +308,13 @@ static void free_handle(sem_handle* h) {
         cudaFree(h->D2[l]);
     }
     cudaFree(h->G64);
+    cudaFree(h->drdx);
     cudaFree(h->G32);
     cudaFree(h->G2);
     cudaFree(h->B64);
     cudaFree(h->minv64);
+    cudaFree(h->hmass64);
+    cudaFree(h->hmass32);
     cudaFree(h->minv32);
     cudaFree(h->mult);
     cudaFree(h->mask);
@@ -322,6 +330,7 @@ static void free_handle(sem_handle* h) {
     cudaFree(w.r); cudaFree(w.p); cudaFree(w.z); cudaFree(w.w); cudaFree(w.x); cudaFree(w.b);
     cudaFree(w.r32); cudaFree(w.p32); cudaFree(w.z32); cudaFree(w.w32); cudaFree(w.d32); cudaFree(w.b32);
     for (float* pv : w.pv) cudaFree(pv);
+    for (double* pp : w.pipe) cudaFree(pp);
     BatchPlan& bp = h->batch;
     for (auto& g : bp.lxg) {
         cudaFree(g.loc); cudaFree(g.cnt); cudaFree(g.solve);
@@ -337,6 +346,7 @@ static void free_handle(sem_handle* h) {
     cudaFree(bp.sgfirst); cudaFree(bp.sgcount); cudaFree(bp.tloc); cudaFree(bp.tlen); cudaFree(bp.tsolve);
     cudaFree(bp.stfirst); cudaFree(bp.stcount); cudaFree(bp.gpart); cudaFree(bp.tpart); cudaFree(bp.scount);
     cudaFree(bp.rrbb); cudaFree(bp.act); cudaFree(bp.itol); cudaFree(bp.carry);
+    free_projection(h);
     if (h->graph.exec) cudaGraphExecDestroy(h->graph.exec);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     for (auto& ev : h->ax_ev)
@@ -390,13 +400,14 @@ static int setup_common(sem_handle** out, int nsolve, const sem_mesh_desc* meshe
     if (n_local >= ((int64_t)1 << 31) - 64)
         return fail(SEM_EINVAL, "n_local must be below 2^31 (32-bit local indices)");
     const int forced = (flags & 0xF) - 1;  // pinned operator variant, -1 = autotune
-    if (forced > kDflVariant) return fail(SEM_EINVAL, "operator variant out of range");
+    if (forced > kTcVariant || forced == kMultiVariant) return fail(SEM_EINVAL, "operator variant out of range");
     sem_handle* h = new sem_handle();
     // a pinned variant 0..4 serves the FP64 and FP32 classes, 5 or 6 the pair class;
     // the other classes stay autotuned
     for (int cls = 0; cls < 3; cls++) {
-        const bool pair_pin = forced >= kDfVariant;
-        const bool applies = forced >= 0 && ((cls == kClsPair) == pair_pin);
+        const bool pair_pin = forced == kDfVariant || forced == kDflVariant;
+        const bool applies = forced >= 0 && ((cls == kClsPair) == pair_pin) &&
+                             (forced != kTcVariant || cls == kClsF32);
         for (int& v : h->ax_variant[cls]) v = applies ? forced : -1;
     }
     h->test_stall = (flags & SEM_FLAG_TEST_STALL) ? 1 : 0;
@@ -498,6 +509,7 @@ static int setup_common(sem_handle** out, int nsolve, const sem_mesh_desc* meshe
         (rc = dalloc(h, &h->counters, 16)) || (rc = dalloc(h, &h->state, (size_t)2 * nsolve + 2)) ||
         (rc = dalloc(h, &h->scratch, 64)))
         return bail(rc);
+    if ((flags & SEM_FLAG_METRICS) && (rc = dalloc(h, &h->drdx, (size_t)9 * n_local))) return bail(rc);
     if (cudaMallocHost((void**)&h->state_host, sizeof(CGState) * (2 * nsolve + 2)) != cudaSuccess)
         return bail(fail(SEM_ENOMEM, "cudaMallocHost failed"));
 #define UP(dst, src, bytes)                                                               \
@@ -592,6 +604,7 @@ static int setup_common(sem_handle** out, int nsolve, const sem_mesh_desc* meshe
         a.D = h->D64[p.lx];
         a.rho = drho;
         a.G = h->G64 + 6 * p.loc_off;
+        a.drdx = h->drdx ? h->drdx + 9 * p.loc_off : nullptr;
         a.B = h->B64 + p.loc_off;
         a.E = p.E;
         a.lx = p.lx;
@@ -628,11 +641,81 @@ static int setup_common(sem_handle** out, int nsolve, const sem_mesh_desc* meshe
 #undef UP
 }
 
+// Helmholtz mass term: hm = h2 B (FP64 and FP32), d += hm on the local diagonal
+__global__ void helmholtz_mass_kernel(const double* h2, const double* B, double* hm, float* hm32, double* d,
+                                      int64_t n) {
+    for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < n; L += (int64_t)gridDim.x * blockDim.x) {
+        const double v = h2[L] * B[L];
+        hm[L] = v;
+        hm32[L] = (float)v;
+        d[L] += v;
+    }
+}
+
+// Rebuild the Jacobi diagonal (and the Helmholtz mass term when h2 is given):
+// d = diag(A_L) (+ h2 B), d <- QQ^T d, Minv = mask / d.
+static int set_helmholtz(sem_handle* h, const double* h2_host, cudaStream_t s) {
+    const int64_t n = h->n_local;
+    double* dd = nullptr;
+    double* dh2 = nullptr;
+    int rc = dalloc(h, &dd, (size_t)n);
+    if (!rc && h2_host) rc = dalloc(h, &dh2, (size_t)n);
+    if (!rc && h2_host && !h->hmass64) {
+        rc = dalloc(h, &h->hmass64, (size_t)n);
+        if (!rc) rc = dalloc(h, &h->hmass32, (size_t)n);
+    }
+    auto done = [&](int code) {
+        if (dd) { cudaFree(dd); h->device_bytes -= sizeof(double) * n; }
+        if (dh2) { cudaFree(dh2); h->device_bytes -= sizeof(double) * n; }
+        return code;
+    };
+    if (rc) return done(rc);
+    for (const MeshPart& p : h->parts)
+        jacobi_local_kernel<<<grid_for(h, p.n_local, 256, 8), 256, 0, s>>>(h->G64 + 6 * p.loc_off, h->D64[p.lx],
+                                                                            p.E, p.lx, dd + p.loc_off);
+    if (h2_host) {
+        if (cudaMemcpyAsync(dh2, h2_host, sizeof(double) * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return done(cuda_fail(cudaGetLastError(), "copy of h2"));
+        helmholtz_mass_kernel<<<grid_for(h, n, 256, 8), 256, 0, s>>>(dh2, h->B64, h->hmass64, h->hmass32, dd, n);
+    } else if (h->hmass64) {
+        cudaFree(h->hmass64);
+        cudaFree(h->hmass32);
+        h->hmass64 = nullptr;
+        h->hmass32 = nullptr;
+        h->device_bytes -= (sizeof(double) + sizeof(float)) * n;
+    }
+    rc = launch_gs(h, dd, false, false, s);
+    if (!rc) {
+        jacobi_invert_kernel<<<grid_for(h, n, 256, 8), 256, 0, s>>>(dd, h->mask, n, h->minv64, h->minv32);
+        rc = refresh_pair_minv(h, s);
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (!rc && e != cudaSuccess) rc = cuda_fail(e, "Helmholtz set-up");
+    // captured graphs hold the old operator's arguments; the batch operator
+    // configuration is chosen again for the new operator
+    if (h->graph.exec) {
+        cudaGraphExecDestroy(h->graph.exec);
+        h->graph.exec = nullptr;
+    }
+    h->batch.kcfg[0] = h->batch.kcfg[1] = -1;
+    return done(rc);
+}
+
 }  // namespace sem
 
 using namespace sem;
 
 extern "C" {
+
+SEM_API int sem_set_helmholtz(sem_handle* h, const double* h2, cudaStream_t stream) {
+    if (!h) return fail(SEM_EINVAL, "null handle");
+    if (h2 && !host_pointer(h2)) return fail(SEM_EINVAL, "h2 must be a host pointer");
+    if (h2)
+        for (int64_t L = 0; L < h->n_local; L++)
+            if (!(h2[L] >= 0.0) || !std::isfinite(h2[L]))
+                return fail(SEM_EINVAL, "h2 must be finite and non-negative");
+    return set_helmholtz(h, h2, stream);
+}
 
 SEM_API const char* sem_last_error(void) { return g_err.c_str(); }
 
@@ -648,7 +731,10 @@ SEM_API void sem_solve_opts_default(sem_solve_opts* o) {
     o->graph_chunk = 32;
     o->autotune = 1;
     o->ir_carry = 0;
-    o->persistent = -1;
+    o->persistent = 0;
+    o->projection = 0;
+    o->tc_split = 0;
+    o->pipelined = 0;
 }
 
 SEM_API int sem_gll(int lx, double* xi, double* rho, double* D) {

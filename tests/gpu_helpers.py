@@ -45,7 +45,7 @@ class Handle:
 
     def ax(self, u, precision=S.SEM_FP64, assemble=1):
         t = torch()
-        dt = t.float32 if precision == S.SEM_FP32 else t.float64
+        dt = t.float32 if precision in (S.SEM_FP32, S.SEM_TC_SPLIT) else t.float64
         ud = dev(u, dt)
         w = t.empty_like(ud)
         S.sem_ax(self.h, w, ud, precision, assemble)
@@ -54,7 +54,7 @@ class Handle:
 
     def gs(self, u, precision=S.SEM_FP64, mask=1):
         t = torch()
-        dt = t.float32 if precision == S.SEM_FP32 else t.float64
+        dt = t.float32 if precision in (S.SEM_FP32, S.SEM_TC_SPLIT) else t.float64
         ud = dev(u, dt)
         S.sem_gs(self.h, ud, precision, mask)
         t.cuda.synchronize()

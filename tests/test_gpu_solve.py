@@ -330,3 +330,22 @@ def test_persistent_single_launch_cg(case):
         assert abs(sp["iterations"] - sg["iterations"]) <= max(2, sg["iterations"] // 50), (mode, sp, sg)
         assert rel_err(xp, xg)[0] <= 1e-7, mode
         assert np.array_equal(xp, xq) and sp["iterations"] == sq["iterations"], mode
+
+
+@pytest.mark.parametrize("case", ["cube", "deformed"])
+def test_pipelined_pcg_matches_oracle(case):
+    """Pipelined PCG (opts.pipelined = 1, Ghysels and Vanroose): the PCG
+    iterates with one reduction phase per iteration; the iteration count
+    follows the oracle's pipelined PCG and PCG, and the true residual reaches
+    1e-10 by the oracle's operator (residual replacement restarts included)."""
+    m, h1, P, b = _cube_case() if case == "cube" else _deformed_case()
+    H = Handle(m, h1)
+    x, st = H.solve(b, tol=TOL, mode=S.SEM_MODE_FP64, pipelined=1)
+    assert st["status"] == S.SEM_OK and st["relres"] <= TOL, st
+    assert _oracle_relres(P, x, b) <= 1.05 * TOL
+    _, ip = oracle.pipelined_pcg(P, b, tol=TOL)
+    _, i64 = P.pcg(b, tol=TOL)
+    assert abs(st["iterations"] - ip["iters"]) <= max(3, ip["iters"] // 20), (st, ip)
+    assert abs(st["iterations"] - i64["iters"]) <= max(3, i64["iters"] // 20), (st, i64)
+    xg, _ = H.solve(b, tol=TOL, mode=S.SEM_MODE_FP64, pipelined=1, use_graph=0, graph_chunk=5)
+    assert np.array_equal(x, xg)

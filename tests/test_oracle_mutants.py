@@ -48,6 +48,11 @@ MUTANTS = {
         "s += D[l * lx + i] * D[l * lx + i] * p->h1[L0] * p->G[0 * n + La];"),
     "ir_kept_direction_rescaled_by_c_squared": (
         "rho_carry * (rn_prev / rn) : 0.0;", "rho_carry * (rn_prev / rn) * (rn_prev / rn) : 0.0;"),
+    "helmholtz_mass_without_jacobian_weights": (
+        "if (p->h2) acc += p->h2[L] * p->B[L] * ue[k * lx * lx + j * lx + i];",
+        "if (p->h2) acc += p->h2[L] * ue[k * lx * lx + j * lx + i];"),
+    "helmholtz_jacobi_without_mass_term": (
+        "if (p->h2) s += p->h2[L] * p->B[L];", ""),
     "ir_kept_direction_rescaled_by_inverse": (
         "rho_carry * (rn_prev / rn) : 0.0;", "rho_carry * (rn / rn_prev) : 0.0;"),
 }
@@ -87,6 +92,16 @@ def _battery() -> list[str]:
     ref_minv = np.where(m.mask > 0, 1.0 / np.diag(K)[inv], 0.0)
     check("dense_jacobi", np.allclose(P.minv(), ref_minv, rtol=1e-12))
     check("mult", np.array_equal(P.gs(np.ones(m.n_local), mask=False), P.mult()))
+    # Helmholtz: dense K + Q^T diag(h2 B) Q and its diagonal
+    x_, y_, z_ = m.xyz()
+    h2 = 2.0 + np.cos(3.0 * x_) * np.sin(2.0 * y_) + z_
+    P.set_h2(h2)
+    Hm = K + Q.T @ np.diag(h2 * Bm.reshape(-1)) @ Q
+    refh = Q @ (mask_g * (Hm @ ug))
+    check("dense_helmholtz_ax", np.max(np.abs(P.ax(Q @ ug) - refh)) < 1e-12 * np.max(np.abs(refh)))
+    check("dense_helmholtz_jacobi", np.allclose(P.minv(), np.where(m.mask > 0, 1.0 / np.diag(Hm)[inv], 0.0),
+                                                rtol=1e-12))
+    P.set_h2(None)
     # volume of a smoothly deformed cube (GLL quadrature of J is exact there)
     ms = W.box_mesh(3, 2, 2, 3, amp=0.1)
     Ps = oracle.Problem(ms)
