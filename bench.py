@@ -46,7 +46,9 @@ def _args():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--solver", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--solver", choices=["mixed", "fp64", "fp64_pair"], default="mixed",
+                    help="mixed refinement (default), FP64 PCG with the native operator, or FP64 PCG in "
+                         "FP32-pair arithmetic (SEM_FP64_PAIR)")
     ap.add_argument("--n", type=int, default=32, help="elements per direction of the cube")
     ap.add_argument("--order", type=int, default=7)
     ap.add_argument("--no-extras", action="store_true", help="skip the comparison solves and ax-only bench")
@@ -152,7 +154,8 @@ def _workload(args):
 
 def _config(args, m, extra=None):
     c = {"workload": f"deformed_cube_{args.n}^3_N{args.order}", "elements": m.E, "lx": m.lx,
-         "n_local": m.n_local, "tol": 1e-10, "solver": "mixed_ir" if args.solver == "mixed" else "fp64_pcg",
+         "n_local": m.n_local, "tol": 1e-10,
+         "solver": {"mixed": "mixed_ir", "fp64": "fp64_pcg", "fp64_pair": "fp64_pair_pcg"}[args.solver],
          "preconditioner": "point Jacobi (exact assembled diagonal)", "l2": L2_NOTE}
     if extra:
         c.update(extra)
@@ -250,14 +253,17 @@ def run_ours(args):
     n = m.n_local
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
+    # SEM_FLAG_SCHWARZ: the handle also carries the GMRES preconditioner (timed in the extras)
     h = S.sem_setup(m.E, m.lx, m.coords, m.gid, m.mask, h1,
-                    0 if args.variant is None else S.SEM_FLAG_VARIANT(args.variant))
+                    S.SEM_FLAG_SCHWARZ | (0 if args.variant is None else S.SEM_FLAG_VARIANT(args.variant)))
     setup_s = time.perf_counter() - t0
     info = S.sem_get_info(h)
     bd = torch.from_numpy(b).cuda()
     xd = torch.zeros(n, dtype=torch.float64, device="cuda")
     mode = S.SEM_MODE_MIXED_IR if args.solver == "mixed" else S.SEM_MODE_FP64
     opts = {"mode": mode, "tol": 1e-10, **(MIXED_OPTS if args.solver == "mixed" else {})}
+    if args.solver == "fp64_pair":
+        opts["precision"] = S.SEM_FP64_PAIR
     if args.tc_split:
         opts["tc_split"] = 1
 
@@ -333,7 +339,7 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32+f64" if args.solver == "mixed" else "f64", "data": "synthetic",
+           "dtype": {"mixed": "f32+f64", "fp64": "f64", "fp64_pair": "f32x2+f64"}[args.solver], "data": "synthetic",
            "config": _config(args, m, {"inner_tol": MIXED_OPTS["inner_tol"] if args.solver == "mixed" else None,
                                        "refinement": ("inner CG direction kept across FP64 refinement steps"
                                                       if args.solver == "mixed" else None),
@@ -388,6 +394,19 @@ def _extras(S, torch, h, m, bd, n, args, peak, stats, ms_timed):
     res["speedup_mixed_vs_fp64"] = res["fp64"]["time_ms"] / res["mixed"]["time_ms"]
     res["speedup_mixed_vs_fp64_pair"] = res["fp64_pair"]["time_ms"] / res["mixed"]["time_ms"]
     ex["solves_to_1e-10"] = res
+    # the paper's pressure solver on the same handle: restarted FGMRES + two-level Schwarz
+    gm = {}
+    for name, extra in (("gmres_mixed", {"precision": S.SEM_FP32}),
+                        ("gmres_fp64_pair_pc32", {"precision": S.SEM_FP64_PAIR, "precond_precision": S.SEM_FP32}),
+                        ("gmres_fp64", {})):
+        for _ in range(2):  # the first solve allocates the Krylov basis
+            x.zero_()
+            st = S.sem_cg_solve(h, x, bd, {"mode": S.SEM_MODE_GMRES, "tol": 1e-10, **extra})
+        gm[name] = {"time_ms": st["time_ms"], "iterations": st["iterations"], "restarts": st["outer_iterations"],
+                    "relres": st["relres"], "status": st["status"]}
+    gm["speedup_gmres_mixed_vs_mixed_pcg"] = res["mixed"]["time_ms"] / gm["gmres_mixed"]["time_ms"]
+    gm["speedup_gmres_fp64_vs_fp64_pcg"] = res["fp64"]["time_ms"] / gm["gmres_fp64"]["time_ms"]
+    ex["gmres_schwarz_to_1e-10"] = gm
     for name, prec in (("cg200_fp64", S.SEM_FP64), ("cg200_fp64_pair", S.SEM_FP64_PAIR)):
         x.zero_()
         st = S.sem_cg_solve(h, x, bd, {"mode": S.SEM_MODE_FP64, "precision": prec, "tol": 1e-30, "max_iter": 200})
@@ -594,7 +613,124 @@ def run_suite(args):
     S.sem_destroy(h)
     out["annulus_64x32x24_N7"] = ann
     out["helmholtz_velocity"] = _helmholtz_suite(S, torch)
+    out["gmres_schwarz"] = _gmres_suite(S, torch)
+    out["time_step"] = _timestep_suite(S, torch)
     print(json.dumps(out), flush=True)
+
+
+def _gmres_suite(S, torch):
+    """The paper's pressure solver (Sec. II-B): restarted flexible GMRES with
+    the two-level Schwarz preconditioner, on the 4^3 cube and the 32^3
+    deformed cube, to 1e-10: FP64 (native operator and preconditioner), FP64
+    with the pair operator and an FP32 preconditioner, and the mixed form
+    (FP32 cycles inside FP64 restarts), beside Jacobi-PCG (FP64) and the
+    mixed CG refinement on the same handle."""
+    res = {}
+    for name, (m, h1, b) in (("cube_4^3_N7", _cube_problem()), ("deformed_cube_32^3_N7", W.deformed_cube(32, 7, seed=2))):
+        h = S.sem_setup(m.E, m.lx, m.coords, m.gid, m.mask, h1, S.SEM_FLAG_SCHWARZ)
+        info = S.sem_get_info(h)
+        bd = torch.from_numpy(b).cuda()
+        row = {"n_local": m.n_local}
+        for mode, o in (("gmres_fp64", {"mode": S.SEM_MODE_GMRES, "tol": 1e-10}),
+                        ("gmres_fp64_pair_pc32", {"mode": S.SEM_MODE_GMRES, "tol": 1e-10,
+                                                  "precision": S.SEM_FP64_PAIR, "precond_precision": S.SEM_FP32}),
+                        ("gmres_mixed", {"mode": S.SEM_MODE_GMRES, "tol": 1e-10, "precision": S.SEM_FP32}),
+                        ("fp64_pcg", {"mode": S.SEM_MODE_FP64, "tol": 1e-10}),
+                        ("mixed_pcg", {"mode": S.SEM_MODE_MIXED_IR, "tol": 1e-10, **MIXED_OPTS})):
+            _, st = _timed_solve(S, torch, h, bd, m.n_local, o, reps=2)
+            row[mode] = _solve_report(st, m.n_local, info["n_free"])
+        row["speedup_gmres_fp64_vs_fp64_pcg"] = row["fp64_pcg"]["time_ms"] / row["gmres_fp64"]["time_ms"]
+        row["speedup_gmres_mixed_vs_mixed_pcg"] = row["mixed_pcg"]["time_ms"] / row["gmres_mixed"]["time_ms"]
+        S.sem_destroy(h)
+        torch.cuda.empty_cache()
+        res[name] = row
+    return res
+
+
+def _timestep_suite(S, torch):
+    """The rest of a time step's solver work on the 32^3 deformed cube:
+    projection onto previous solutions over a sequence of 30 time-correlated
+    pressure right-hand sides (space of 20, the paper's reset interval on
+    GPUs), pipelined against standard FP64 PCG, and the pressure right-hand
+    side -div(vhat)/dt + (1/Re) div(curl(omega)) with the gradient kernels."""
+    m, h1, _ = W.deformed_cube(32, 7, seed=2)
+    h = S.sem_setup(m.E, m.lx, m.coords, m.gid, m.mask, h1, S.SEM_FLAG_METRICS)
+    n = m.n_local
+    x, y, z = m.xyz()
+    res = {"workload": "32^3 deformed cube, N=7; b_k = mask QQ^T B f(t_k), f = sin(pi(x+t)) sin(pi y) sin(pi z)(1+xy)"
+                       " + 0.3 cos(3 pi (y-t)) z, t_k = 0.03 k, k < 30", "n_local": n}
+    fd = torch.empty(n, dtype=torch.float64, device="cuda")
+    bs = []
+    for k in range(30):
+        t = 0.03 * k
+        f = np.sin(np.pi * (x + t)) * np.sin(np.pi * y) * np.sin(np.pi * z) * (1.0 + x * y) \
+            + 0.3 * np.cos(3 * np.pi * (y - t)) * z
+        fd.copy_(torch.from_numpy(f))
+        bk = torch.empty_like(fd)
+        S.sem_mass(h, bk, fd, S.SEM_FP64, 1)
+        bs.append(bk)
+    xd = torch.zeros(n, dtype=torch.float64, device="cuda")
+    for name, o in (("mixed", {"mode": S.SEM_MODE_MIXED_IR, "tol": 1e-10}),
+                    ("mixed_projection_20", {"mode": S.SEM_MODE_MIXED_IR, "tol": 1e-10, "projection": 20}),
+                    ("fp64_pair", {"mode": S.SEM_MODE_FP64, "precision": S.SEM_FP64_PAIR, "tol": 1e-10}),
+                    ("fp64_pair_projection_20", {"mode": S.SEM_MODE_FP64, "precision": S.SEM_FP64_PAIR,
+                                                 "tol": 1e-10, "projection": 20})):
+        S.sem_projection_reset(h)
+        xd.zero_()
+        S.sem_cg_solve(h, xd, bs[0], {**o, "projection": 0})  # warm-up (autotune, graphs)
+        its, ms, starts, ok = [], 0.0, [], True
+        for k in range(30):
+            xd.zero_()
+            st = S.sem_cg_solve(h, xd, bs[k], o)
+            its.append(st["iterations"])
+            starts.append(st["relres_start"])
+            ms += st["time_ms"]
+            ok = ok and st["status"] == S.SEM_OK and st["relres"] <= 1e-10
+        res[name] = {"total_ms": ms, "mean_iterations": float(np.mean(its)), "iterations": its,
+                     "start_residual_last": starts[-1], "all_converged": ok}
+    S.sem_projection_reset(h)
+    res["speedup_projection_mixed"] = res["mixed"]["total_ms"] / res["mixed_projection_20"]["total_ms"]
+    res["speedup_projection_fp64_pair"] = res["fp64_pair"]["total_ms"] / res["fp64_pair_projection_20"]["total_ms"]
+    # pipelined PCG against the standard loop (both native FP64)
+    pipe = {}
+    for name, o in (("fp64_pcg", {"mode": S.SEM_MODE_FP64, "tol": 1e-10}),
+                    ("fp64_pipelined", {"mode": S.SEM_MODE_FP64, "tol": 1e-10, "pipelined": 1})):
+        _, st = _timed_solve(S, torch, h, bs[5], n, o, reps=1)
+        pipe[name] = {"time_ms": st["time_ms"], "iterations": st["iterations"], "relres": st["relres"],
+                      "status": st["status"]}
+    res["pipelined"] = pipe
+    # pressure right-hand side and gradient (one call each, CUDA events, best of 10)
+    v = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in
+         (np.sin(np.pi * x) * np.cos(np.pi * y), np.cos(np.pi * y) * z, x * y * z)]
+    w = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (y * z, np.sin(np.pi * z), x * x)]
+    out = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(3)]
+    b = torch.empty(n, dtype=torch.float64, device="cuda")
+
+    def best_ms(fn):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = None
+        for _ in range(10):
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        return best
+
+    res["pressure_rhs_ms"] = best_ms(lambda: S.sem_pressure_rhs(h, *v, *w, 2e-5, 30000.0, b))
+    res["grad_ms"] = best_ms(lambda: S.sem_grad(h, v[0], *out))
+    res["grad_gb_s"] = n * (8 + 72 + 24) / (res["grad_ms"] * 1e-3) / 1e9
+    S.sem_destroy(h)
+    torch.cuda.empty_cache()
+    return res
+
+
+def _cube_problem():
+    m, f = W.cube_sines(4, 7)
+    import oracle
+    return m, None, oracle.Problem(m).mass(f, assemble=True)
 
 
 def _helmholtz_suite(S, torch):

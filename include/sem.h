@@ -92,7 +92,18 @@ typedef enum sem_precision {
 
 typedef enum sem_solve_mode {
     SEM_MODE_FP64 = 0,     /* plain FP64 Jacobi-PCG */
-    SEM_MODE_MIXED_IR = 1  /* FP64 refinement around an FP32 inner Jacobi-PCG */
+    SEM_MODE_MIXED_IR = 1, /* FP64 refinement around an FP32 inner Jacobi-PCG */
+    SEM_MODE_GMRES = 2     /* the paper's pressure solver (Sec. II-B): restarted flexible GMRES
+                              with a two-level additive Schwarz preconditioner (element-interior
+                              fast-diagonalisation solves, point Jacobi on inter-element nodes,
+                              a coarse grid on the element corners solved by 10 Jacobi-PCG
+                              iterations); handles set up with SEM_FLAG_SCHWARZ.  precision
+                              SEM_FP64 / SEM_FP64_NATIVE (native FP64 operator) or SEM_FP64_PAIR:
+                              FP64 Krylov vectors, the true residual checked at every restart.
+                              precision SEM_FP32: mixed form, every restart cycle an FP32
+                              flexible GMRES solve (operator, preconditioner, basis in FP32) of
+                              A d = r for the true FP64 residual r, x += d in FP64; a cycle stops
+                              at inner_tol of its start residual or at gmres_restart steps */
 } sem_solve_mode;
 
 typedef struct sem_info {
@@ -149,6 +160,7 @@ typedef struct sem_solve_opts {
                             SEM_FP64_NATIVE (slab operator); not for SEM_FP64_PAIR */
     int tc_split;        /* mixed mode: the inner FP32 CG applies the operator as SEM_TC_SPLIT
                             (tensor-core contractions) instead of the CUDA-core FP32 kernels (0) */
+    int gmres_restart;   /* GMRES mode: Krylov vectors per restart cycle (30) */
     int pipelined;       /* FP64 mode: pipelined PCG (Ghysels and Vanroose 2014; the paper's
                             work on reducing communication in CG, Sec. II-B): the PCG iterates
                             with one reduction phase per iteration instead of two, at the cost
@@ -162,6 +174,12 @@ typedef struct sem_solve_opts {
                             paper's GPU runs reset theirs every 20 solves.  Single-mesh handles; the space
                             (2 L + 1 FP64 vectors) stays with the handle until
                             sem_projection_reset or sem_destroy */
+    int precond_precision; /* GMRES mode with an FP64 precision: arithmetic of the Schwarz
+                            preconditioner's local solves, restriction and prolongation,
+                            SEM_FP64 (default) or SEM_FP32 (FP32 arithmetic on the FP64 vectors;
+                            the coarse CG stays FP64).  Flexible GMRES accepts any
+                            preconditioner: this changes iteration counts, not the accuracy
+                            the solve reaches */
 } sem_solve_opts;
 
 typedef struct sem_solve_stats {
@@ -190,7 +208,7 @@ typedef struct sem_solve_stats {
     double relres_start;      /* true relative residual of the start (after projection, when on) */
     int launches_per_iteration;  /* kernel launches of one CG iteration: 3 for one mesh
                                  (operator, gather-scatter, update), 0 when the CG ran
-                                 as one persistent launch; for a batch the
+                                 as one persistent launch, -1 for GMRES; for a batch the
                                  operator launches (1 with variant 7, else one per
                                  order) + 2 */
 } sem_solve_stats;
@@ -221,6 +239,12 @@ typedef struct sem_mesh_desc {
  * local point) for the gradient, divergence and curl operators and the
  * pressure right-hand side (sem_grad, sem_div, sem_curl, sem_pressure_rhs). */
 #define SEM_FLAG_METRICS 0x200
+
+/* Set-up flag (sem_setup only): build the two-level Schwarz preconditioner of
+ * the GMRES pressure solve (SEM_MODE_GMRES): box lengths and mean h1 of every
+ * element, a coarse handle on the element corners (lx = 2), the interior
+ * modes of the reference element. */
+#define SEM_FLAG_SCHWARZ 0x400
 
 /* Fill *opts with the defaults listed above. */
 SEM_API void sem_solve_opts_default(sem_solve_opts* opts);
@@ -378,6 +402,19 @@ SEM_API int sem_get_jacobi(const sem_handle* h, double* minv, cudaStream_t strea
  * Synchronises the stream. */
 SEM_API int sem_cg_solve(sem_handle* h, double* x, const double* b, const sem_solve_opts* opts,
                          sem_solve_stats* stats, cudaStream_t stream);
+
+/* z = M^-1 r with the two-level Schwarz preconditioner of SEM_MODE_GMRES
+ * (handle set up with SEM_FLAG_SCHWARZ): point Jacobi, the fast-
+ * diagonalisation solves of the element interiors, and the coarse-grid
+ * correction (10 Jacobi-PCG iterations on the element corners), masked.
+ * r, z: device double [n_local], r assembled; z must not alias r. */
+SEM_API int sem_schwarz_apply(sem_handle* h, const double* r, double* z, cudaStream_t stream);
+
+/* The same preconditioner on FP32 vectors with FP32 arithmetic in the local
+ * solves, restriction and prolongation (the coarse CG stays FP64): the form
+ * the mixed GMRES solve applies.  r, z: device float [n_local], r assembled;
+ * z must not alias r.  Errors: SEM_EINVAL (null, aliasing, no Schwarz data). */
+SEM_API int sem_schwarz_apply32(sem_handle* h, const float* r, float* z, cudaStream_t stream);
 
 /* Projection space of a handle (sem_solve_opts.projection): drop every kept
  * vector (the next solve starts from x = 0), and the number kept now. */

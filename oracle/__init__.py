@@ -33,6 +33,10 @@ What pins the oracle to something other than itself (tests/test_oracle_*.py):
   (sheared) affine meshes; curl grad = 0 and div curl = 0 there; spectral
   convergence on deformed meshes; pressure right-hand side of a gradient
   field equal to the mass-weighted Laplacian.
+* FGMRES with the two-level Schwarz preconditioner: the fast-diagonalisation
+  local solve equals the dense interior solve on box elements; prolongation
+  reproduces trilinear fields; FGMRES with the identity reaches the dense
+  solution; the preconditioner cuts iterations against Jacobi-PCG.
 * Pipelined PCG: the iterates and recursive residuals of Jacobi-PCG within
   rounding on small problems; dense solution.
 * Projection onto previous solutions: A-orthonormal basis; exact recovery of
@@ -433,3 +437,183 @@ def pressure_rhs(P, mesh, vhat, omega, dt: float, Re: float):
     if omega is not None:
         f = f + div(mesh, *curl(mesh, *omega)) / Re
     return P.mass(f, assemble=True)
+
+
+def _corner_index(lx: int) -> np.ndarray:
+    """Local indices of an element's 8 corner nodes in the [k][j][i] order of
+    an lx = 2 element (i fastest)."""
+    return np.array([(k * lx + j) * lx + i for k in (0, lx - 1) for j in (0, lx - 1) for i in (0, lx - 1)])
+
+
+class _CoarseMesh:
+    def __init__(self, mesh):
+        c = _corner_index(mesh.lx)
+        n3 = mesh.lx ** 3
+        sel = (np.arange(mesh.E)[:, None] * n3 + c[None, :]).reshape(-1)
+        self.E, self.lx = mesh.E, 2
+        self.coords = np.ascontiguousarray(mesh.coords.reshape(3, -1)[:, sel].reshape(3, mesh.E, 8))
+        self.gid = np.ascontiguousarray(mesh.gid[sel])
+        self.mask = np.ascontiguousarray(mesh.mask[sel])
+        self.sel = sel
+
+
+class SchwarzPrecond:
+    """Two-level additive Schwarz preconditioner of the pressure solve (Sec.
+    II-B: overlapping additive Schwarz with a coarse-grid solve of 10 P-CG
+    iterations, after Lottes and Fischer 2005).  The paper gives no further
+    detail; this is the reading taken, applied to an assembled residual r:
+      z = Minv r                             (point Jacobi, every node)
+      z_e,interior = A_box,e^-1 r_e,interior (each element's interior nodes,
+          homogeneous Dirichlet on its boundary, by fast diagonalisation of
+          the element approximated by a box with the mean lengths of its four
+          edges per direction and its mean h1: separable 1-D stiffness K and
+          mass W on [-1, 1], K S = W S Lambda, S^T W S = I, scaled to the box)
+      z += P A_c^-1 R r                      (coarse grid: the same elements
+          with N = 1 on their corner nodes; R r = QQ_c^T sum_L P^T r / mult,
+          P the trilinear interpolation to the GLL nodes; A_c^-1 approximated
+          by 10 Jacobi-PCG iterations from zero)
+      z <- mask z.
+    The subdomains do not overlap beyond the shared nodes (the coarse space
+    and the Jacobi part on inter-element nodes couple them); the exact
+    extended-element overlap of Lottes and Fischer is not reproduced."""
+
+    def __init__(self, P, mesh, h1=None, coarse_iters: int = 10):
+        lx, N = mesh.lx, mesh.lx - 1
+        n3 = lx ** 3
+        self.P, self.mesh, self.lx, self.E = P, mesh, lx, mesh.E
+        self.Minv = P.minv()
+        self.mult = P.mult()
+        self.mask = np.asarray(mesh.mask, dtype=np.float64)
+        self.coarse_iters = coarse_iters
+        xi, rho = gll(N)
+        D = dmat(N)
+        K = D.T @ np.diag(rho) @ D
+        self.ni = N - 1
+        if self.ni > 0:
+            Ki, Wi = K[1:N, 1:N], rho[1:N]
+            C = Ki / np.sqrt(Wi)[:, None] / np.sqrt(Wi)[None, :]
+            lam, V = np.linalg.eigh(C)
+            self.lam = lam
+            self.S = V / np.sqrt(Wi)[:, None]
+        X = mesh.coords.reshape(3, mesh.E, n3)
+        c = _corner_index(lx)
+        Xc = X[:, :, c]  # [3][E][8], corner (i, j, k) bits = (q & 1, q >> 1 & 1, q >> 2)
+        L = np.zeros((mesh.E, 3))
+        for d in range(3):
+            pairs = [(q, q | (1 << d)) for q in range(8) if not (q >> d) & 1]
+            L[:, d] = np.mean([np.linalg.norm(Xc[:, :, b] - Xc[:, :, a], axis=0) for a, b in pairs], axis=0)
+        self.L = L
+        hh = np.ones(mesh.n_local) if h1 is None else np.asarray(h1, dtype=np.float64)
+        self.h1m = hh.reshape(mesh.E, n3).mean(axis=1)
+        self.cm = _CoarseMesh(mesh)
+        self.Pc = Problem(self.cm, None if h1 is None else np.ascontiguousarray(hh[self.cm.sel]))
+        phi = np.array([(1.0 - xi) / 2.0, (1.0 + xi) / 2.0])  # [c][i]
+        i, j, k = np.meshgrid(np.arange(lx), np.arange(lx), np.arange(lx), indexing="xy")
+        kk, jj, ii = np.meshgrid(np.arange(lx), np.arange(lx), np.arange(lx), indexing="ij")
+        ii, jj, kk = ii.reshape(-1), jj.reshape(-1), kk.reshape(-1)
+        self.Pw = np.array([phi[q & 1][ii] * phi[(q >> 1) & 1][jj] * phi[(q >> 2) & 1][kk] for q in range(8)]).T
+
+    def local_solve(self, r):
+        """The fast-diagonalisation part alone: interior nodes of every element."""
+        lx, ni = self.lx, self.ni
+        out = np.zeros_like(r)
+        if ni <= 0:
+            return out
+        re = np.asarray(r).reshape(self.E, lx, lx, lx)
+        ri = re[:, 1:lx - 1, 1:lx - 1, 1:lx - 1]  # [e][k][j][i]
+        sc = np.sqrt(2.0 / self.L)                 # S_d = S sqrt(2 / L_d)
+        lam = self.lam[None, :] * (4.0 / self.L[:, :, None] ** 2)  # [e][d][m]
+        t = np.einsum("im,ekji->ekjm", self.S, ri) * sc[:, 0, None, None, None]
+        t = np.einsum("jm,ekji->ekmi", self.S, t) * sc[:, 1, None, None, None]
+        t = np.einsum("km,ekji->emji", self.S, t) * sc[:, 2, None, None, None]
+        den = lam[:, 2, :, None, None] + lam[:, 1, None, :, None] + lam[:, 0, None, None, :]
+        t = t / (den * self.h1m[:, None, None, None])
+        t = np.einsum("km,emji->ekji", self.S, t) * sc[:, 2, None, None, None]
+        t = np.einsum("jm,ekmi->ekji", self.S, t) * sc[:, 1, None, None, None]
+        t = np.einsum("im,ekjm->ekji", self.S, t) * sc[:, 0, None, None, None]
+        oe = out.reshape(self.E, lx, lx, lx)
+        oe[:, 1:lx - 1, 1:lx - 1, 1:lx - 1] = t
+        return out
+
+    def restrict(self, r):
+        rl = (np.asarray(r) / self.mult).reshape(self.E, -1) @ self.Pw  # [E][8]
+        return self.Pc.gs(np.ascontiguousarray(rl.reshape(-1)), mask=True)
+
+    def prolong(self, ec):
+        return (np.asarray(ec).reshape(self.E, 8) @ self.Pw.T).reshape(-1)
+
+    def __call__(self, r):
+        r = np.asarray(r, dtype=np.float64)
+        z = self.Minv * r
+        if self.ni > 0:
+            lx = self.lx
+            zi = self.local_solve(r).reshape(self.E, lx, lx, lx)
+            ze = z.reshape(self.E, lx, lx, lx)
+            ze[:, 1:lx - 1, 1:lx - 1, 1:lx - 1] = zi[:, 1:lx - 1, 1:lx - 1, 1:lx - 1]
+        ec, _ = self.Pc.pcg(self.restrict(r), tol=1e-300, max_iter=self.coarse_iters)
+        z = z + self.prolong(ec)
+        return z * self.mask
+
+
+def fgmres(P, b, precond=None, restart: int = 30, tol: float = 1e-10, max_iter: int = 2000, x0=None):
+    """Restarted flexible GMRES (Saad 1993) with right preconditioning, the
+    Krylov method of the paper's pressure solve (Sec. II-B: restarted GMRES,
+    Saad and Schultz 1986; flexible because the preconditioner's coarse solve
+    is a fixed number of CG iterations): Arnoldi with classical Gram-Schmidt
+    run twice in the unique-node inner product, Givens rotations on the
+    Hessenberg matrix, x = x0 + Z y at the end of a cycle.  Stops when the
+    rotated residual estimate |g_{j+1}| / ||b|| <= tol (checked against the
+    true residual at each restart).  precond None: the identity."""
+    b = np.asarray(b, dtype=np.float64)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    M = precond if precond is not None else (lambda v: v)
+    bn = np.sqrt(P.dot(b, b))
+    it, cycles, status = 0, 0, 1
+    while True:
+        r = b - P.ax(x)
+        beta = np.sqrt(P.dot(r, r))
+        if bn == 0.0 or beta / bn <= tol:
+            status = 0
+            break
+        if it >= max_iter:
+            break
+        cycles += 1
+        V = [r / beta]
+        Z = []
+        H = np.zeros((restart + 1, restart))
+        g = np.zeros(restart + 1)
+        g[0] = beta
+        cs, sn = np.zeros(restart), np.zeros(restart)
+        k = 0
+        for j in range(restart):
+            z = M(V[j])
+            Z.append(z)
+            w = P.ax(z)
+            h = np.zeros(j + 2)
+            for _ in range(2):
+                c = np.array([P.dot(w, V[i]) for i in range(j + 1)])
+                for i in range(j + 1):
+                    w = w - c[i] * V[i]
+                h[:j + 1] += c
+            h[j + 1] = np.sqrt(P.dot(w, w))
+            for i in range(j):
+                t = cs[i] * h[i] + sn[i] * h[i + 1]
+                h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1]
+                h[i] = t
+            den = np.hypot(h[j], h[j + 1])
+            cs[j], sn[j] = h[j] / den, h[j + 1] / den
+            h[j] = den
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            H[:j + 1, j] = h[:j + 1]
+            it += 1
+            k = j + 1
+            if abs(g[j + 1]) / bn <= tol or it >= max_iter or h[j + 1] == 0.0:
+                break
+            V.append(w / np.sqrt(P.dot(w, w)))
+        y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])
+        for i in range(k):
+            x = x + y[i] * Z[i]
+    rt = b - P.ax(x)
+    return x, dict(status=status, iters=it, cycles=cycles,
+                   relres=float(np.sqrt(P.dot(rt, rt)) / bn) if bn > 0 else 0.0)

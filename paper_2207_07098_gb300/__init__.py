@@ -10,7 +10,7 @@ sem_curl, sem_pressure_rhs.
 """
 from ._lib import *  # noqa: F401,F403
 from ._lib import (SEM_EBREAKDOWN, SEM_ECUDA, SEM_EINVAL, SEM_ENOMEM, SEM_ENOTCONV, SEM_ESTAGNATE,
-                   SEM_ETIMEOUT, SEM_FP32, SEM_FP64, SEM_FP64_NATIVE, SEM_FP64_PAIR, SEM_TC_SPLIT, SEM_MODE_FP64, SEM_MODE_MIXED_IR,
+                   SEM_ETIMEOUT, SEM_FP32, SEM_FP64, SEM_FP64_NATIVE, SEM_FP64_PAIR, SEM_TC_SPLIT, SEM_MODE_FP64, SEM_MODE_MIXED_IR, SEM_MODE_GMRES,
                    SEM_OK, LIB_PATH, SemError, load, exported_symbols, SEM_FLAG_VARIANT, SEM_FLAG_TEST_STALL,
-                   SEM_FLAG_METRICS)
+                   SEM_FLAG_METRICS, SEM_FLAG_SCHWARZ)
 from .build import build  # noqa: F401

@@ -17,11 +17,12 @@ LIB_PATH = os.path.join(_HERE, "libsem.so")
 
 SEM_OK, SEM_EINVAL, SEM_ENOMEM, SEM_ECUDA, SEM_ENOTCONV, SEM_EBREAKDOWN, SEM_ESTAGNATE, SEM_ETIMEOUT = range(8)
 SEM_FP64, SEM_FP32, SEM_FP64_NATIVE, SEM_FP64_PAIR, SEM_TC_SPLIT = 0, 1, 2, 3, 4
-SEM_MODE_FP64, SEM_MODE_MIXED_IR = 0, 1
+SEM_MODE_FP64, SEM_MODE_MIXED_IR, SEM_MODE_GMRES = 0, 1, 2
 
 
 SEM_FLAG_TEST_STALL = 0x100
 SEM_FLAG_METRICS = 0x200
+SEM_FLAG_SCHWARZ = 0x400
 
 
 def SEM_FLAG_VARIANT(v: int) -> int:
@@ -49,7 +50,8 @@ class sem_solve_opts(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("precision", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("graph_chunk", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("ir_carry", ctypes.c_int), ("persistent", ctypes.c_int), ("tc_split", ctypes.c_int),
-                ("pipelined", ctypes.c_int), ("projection", ctypes.c_int)]
+                ("gmres_restart", ctypes.c_int), ("pipelined", ctypes.c_int), ("projection", ctypes.c_int),
+                ("precond_precision", ctypes.c_int)]
 
 
 class sem_solve_stats(ctypes.Structure):
@@ -95,6 +97,8 @@ _SIGS = {
     "sem_div": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "sem_curl": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "sem_pressure_rhs": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_double, _VP, _VP]),
+    "sem_schwarz_apply": (_I, [_VP, _VP, _VP, _VP]),
+    "sem_schwarz_apply32": (_I, [_VP, _VP, _VP, _VP]),
     "sem_projection_reset": (_I, [_VP]),
     "sem_projection_size": (_I, [_VP, ctypes.POINTER(_I)]),
 }
@@ -310,3 +314,11 @@ def sem_curl(h, vx, vy, vz, cx, cy, cz, stream=None) -> None:
 def sem_pressure_rhs(h, vx, vy, vz, wx, wy, wz, dt: float, Re: float, b, stream=None) -> None:
     _check(load().sem_pressure_rhs(ctypes.c_void_p(h), _ptr(vx), _ptr(vy), _ptr(vz), _ptr(wx), _ptr(wy), _ptr(wz),
                                    dt, Re, _ptr(b), _stream(stream)))
+
+
+def sem_schwarz_apply(h, r, z, stream=None) -> None:
+    _check(load().sem_schwarz_apply(ctypes.c_void_p(h), _ptr(r), _ptr(z), _stream(stream)))
+
+
+def sem_schwarz_apply32(h, r, z, stream=None) -> None:
+    _check(load().sem_schwarz_apply32(ctypes.c_void_p(h), _ptr(r), _ptr(z), _stream(stream)))

@@ -435,7 +435,7 @@ static int run_cg(sem_handle* h, int precision, const sem_solve_opts& o, int slo
 
 // rr_bb[0] = ||b - A x||^2, rr_bb[1] = ||b||^2 (unique-node norm), r = b - A x,
 // with the native FP64 operator whatever the solve's iterations use
-static int true_residual(sem_handle* h, const double* x, const double* b, double* rr_bb, cudaStream_t s) {
+int true_residual(sem_handle* h, const double* x, const double* b, double* rr_bb, cudaStream_t s) {
     int rc = launch_ax_local(h, x, h->ws.w, SEM_FP64, s);
     if (!rc) rc = launch_gs(h, h->ws.w, false, true, s);
     if (rc) return rc;
@@ -453,6 +453,37 @@ static int true_residual(sem_handle* h, const double* x, const double* b, double
 double inner_tolerance(const sem_solve_opts& o, double rel) {
     const double need = 0.3 * o.tol / rel;
     return std::min(0.1, std::max(o.inner_tol, need));
+}
+
+// Jacobi-PCG for exactly `iters` iterations from x = 0 on the right-hand
+// side in ws.b (no host synchronisation; stops early only on a zero residual
+// or a breakdown): the coarse-grid solve of the Schwarz preconditioner.
+int coarse_pcg(sem_handle* hc, int iters, bool persist, cudaStream_t s) {
+    const int64_t n = hc->n_local;
+    SEM_CUDA_TRY(cudaMemsetAsync(hc->ws.x, 0, sizeof(double) * n, s));
+    SEM_CUDA_TRY(cudaMemcpyAsync(hc->ws.r, hc->ws.b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    cg_init_kernel<double><<<grid_for(hc, n, 256, 4), 256, 0, s>>>(hc->ws.b, hc->ws.r, hc->ws.z, hc->minv64, hc->mult,
+                                                                  n, 0.0, iters, hc->state, hc->partials,
+                                                                  hc->counters + 5, 0.0);
+    SEM_LAUNCH_CHECK("cg_init_kernel");
+    hc->launches++;
+    // one cooperative launch whose CTAs meet at bounded grid barriers, or
+    // three launches per iteration
+    if (persist && persist_available(hc)) return launch_cg_persist(hc, SEM_FP64, 0, s);
+    for (int it = 0; it < iters; it++) {
+        int rc = launch_iteration(hc, SEM_FP64, s);
+        if (rc) return rc;
+    }
+    return SEM_OK;
+}
+
+bool host_resident(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
 }
 
 static bool is_host_ptr(const void* p) {
@@ -651,13 +682,15 @@ SEM_API int sem_cg_solve(sem_handle* h, double* x, const double* b, const sem_so
     sem_solve_opts o;
     sem_solve_opts_default(&o);
     if (opts) o = *opts;
-    if (!(o.tol > 0.0) || o.max_iter < 0 || (o.mode != SEM_MODE_FP64 && o.mode != SEM_MODE_MIXED_IR))
+    if (!(o.tol > 0.0) || o.max_iter < 0 ||
+        (o.mode != SEM_MODE_FP64 && o.mode != SEM_MODE_MIXED_IR && o.mode != SEM_MODE_GMRES))
         return fail(SEM_EINVAL, "bad solve options");
     if (o.mode == SEM_MODE_MIXED_IR && !(o.inner_tol > 0.0 && o.inner_tol < 1.0))
         return fail(SEM_EINVAL, "inner_tol must be in (0, 1)");
     if (o.mode == SEM_MODE_FP64 && (!valid_precision(o.precision) || is_f32(o.precision)))
         return fail(SEM_EINVAL, "FP64 mode takes SEM_FP64, SEM_FP64_NATIVE or SEM_FP64_PAIR");
     if (o.projection < 0 || o.projection > 64) return fail(SEM_EINVAL, "projection must be in [0, 64]");
+    if (o.mode == SEM_MODE_GMRES) return solve_gmres(h, x, b, o, stats, s);
     return solve_single(h, x, b, o, stats, s);
 }
 

@@ -14,7 +14,7 @@
 //              and the next gamma = (r, u), delta = (w, u), rr = (r, r)
 // with u = Minv r, w = A u and m = Minv w kept as recurrences.  On one GPU the
 // reductions already sit inside the kernels, so the pipelined form only adds
-// vector traffic (19 vector accesses per point in the update against 8); it
+// vector traffic (20 vector accesses per point in the update against 8); it
 // exists for parity with the paper's solver family and as the single-exchange
 // form a multi-GPU build would overlap.  FP64 data, native FP64 operator.
 #include <algorithm>

@@ -217,6 +217,28 @@ struct ProjSpace {
     double* coef = nullptr;  // [L + 2] coefficients of the current projection
 };
 
+// Two-level Schwarz preconditioner and FGMRES storage (sem_gmres.cu; built
+// at set-up with SEM_FLAG_SCHWARZ, single-mesh handles)
+struct SchwarzData {
+    sem_handle* coarse = nullptr;  // the same elements at lx = 2 on their corner nodes
+    double* fac = nullptr;         // [E][6] sqrt(2 / L_d), h1m 4 / L_d^2 (box lengths L_d, mean h1)
+    float* fac32 = nullptr;
+    double* S = nullptr;           // [(lx-2)^2] interior modes of the reference element (node major)
+    double* lam = nullptr;         // [lx-2] their eigenvalues
+    double* Pw = nullptr;          // [lx^3][8] trilinear weights of the corners at the GLL nodes
+    float* S32 = nullptr;          // FP32 copies of S, lam, Pw, fac (FP32 preconditioner arithmetic)
+    float* lam32 = nullptr;
+    float* Pw32 = nullptr;
+    int m = 0;                     // FGMRES restart length of the storage below
+    int elem = 0;                  // bytes per entry of V and Z (8 FP64, 4 mixed)
+    int64_t ld = 0;                // their leading dimension (n_local rounded up to 4)
+    void* V = nullptr;             // [m + 1][n_local] Arnoldi basis
+    void* Z = nullptr;             // [m][n_local] preconditioned basis
+    double* coef = nullptr;        // Gram-Schmidt coefficients, norm and y on the device
+    double* gpart = nullptr;       // Gram-Schmidt block partials
+    unsigned int* gcount = nullptr;
+};
+
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     int key_prec = -1;
@@ -263,6 +285,7 @@ struct sem_handle {
     sem::Workspace ws;
     sem::GraphCache graph;
     sem::ProjSpace proj;
+    sem::SchwarzData sch;
     sem::BatchPlan batch;
     cudaStream_t capture_stream = nullptr;
     cudaEvent_t ax_ev[2] = {nullptr, nullptr};  // bracket one K-A per graph (single: 2nd, batch: 1st)
@@ -326,6 +349,15 @@ int refresh_pair_minv(sem_handle* h, cudaStream_t s);
 int proj_start(sem_handle* h, int max_vectors, cudaStream_t s);
 int proj_update(sem_handle* h, cudaStream_t s);
 void free_projection(sem_handle* h);
+// two-level Schwarz + FGMRES (sem_gmres.cu)
+void free_schwarz(sem_handle* h);
+int solve_gmres(sem_handle* h, double* x_user, const double* b_user, const sem_solve_opts& o,
+                sem_solve_stats* stats, cudaStream_t s);
+// pieces of the CG driver used by other solvers (sem_cg.cu)
+int true_residual(sem_handle* h, const double* x, const double* b, double* rr_bb, cudaStream_t s);
+// fixed iterations from x = 0 on ws.b; persist: one cooperative launch
+int coarse_pcg(sem_handle* hc, int iters, bool persist, cudaStream_t s);
+bool host_resident(const void* p);
 int launch_pair_split_x(sem_handle* h, cudaStream_t s);
 int launch_pair_join_x(sem_handle* h, cudaStream_t s);
 int launch_pair_init(sem_handle* h, double tol, int max_iter, cudaStream_t s);

@@ -347,6 +347,7 @@ static void free_handle(sem_handle* h) {
     cudaFree(bp.stfirst); cudaFree(bp.stcount); cudaFree(bp.gpart); cudaFree(bp.tpart); cudaFree(bp.scount);
     cudaFree(bp.rrbb); cudaFree(bp.act); cudaFree(bp.itol); cudaFree(bp.carry);
     free_projection(h);
+    free_schwarz(h);
     if (h->graph.exec) cudaGraphExecDestroy(h->graph.exec);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     for (auto& ev : h->ax_ev)
@@ -641,6 +642,155 @@ static int setup_common(sem_handle** out, int nsolve, const sem_mesh_desc* meshe
 #undef UP
 }
 
+// ---------------------------------------------------------------------------
+// Two-level Schwarz preconditioner set-up (host; the data for sem_gmres.cu)
+// ---------------------------------------------------------------------------
+
+// Eigenvalues and eigenvectors of a small symmetric matrix by cyclic Jacobi
+// rotations (Golub and Van Loan, Sec. 8.5): A (n x n, row major) is
+// overwritten; on return lam[m] and V[:, m] (V row major: V[i * n + m]).
+static void sym_eigen(int n, std::vector<double>& A, std::vector<double>& lam, std::vector<double>& V) {
+    V.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; i++) V[(size_t)i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 100; sweep++) {
+        double off = 0.0, diag = 0.0;
+        for (int p = 0; p < n; p++)
+            for (int q = 0; q < n; q++) (p == q ? diag : off) += A[(size_t)p * n + q] * A[(size_t)p * n + q];
+        if (off <= 1e-30 * diag) break;
+        for (int p = 0; p < n - 1; p++)
+            for (int q = p + 1; q < n; q++) {
+                const double apq = A[(size_t)p * n + q];
+                if (apq == 0.0) continue;
+                const double theta = (A[(size_t)q * n + q] - A[(size_t)p * n + p]) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < n; k++) {  // columns p, q of A
+                    const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+                    A[(size_t)k * n + p] = c * akp - sn * akq;
+                    A[(size_t)k * n + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < n; k++) {  // rows p, q
+                    const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+                    A[(size_t)p * n + k] = c * apk - sn * aqk;
+                    A[(size_t)q * n + k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < n; k++) {
+                    const double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+                    V[(size_t)k * n + p] = c * vkp - sn * vkq;
+                    V[(size_t)k * n + q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+    lam.resize(n);
+    for (int i = 0; i < n; i++) lam[i] = A[(size_t)i * n + i];
+}
+
+// SEM_FLAG_SCHWARZ: box lengths and mean h1 per element, the coarse handle on
+// the element corners, the reference interior modes (K S = W S Lambda,
+// S^T W S = I on the interior GLL nodes) and the trilinear corner weights.
+static int build_schwarz(sem_handle* h, const sem_mesh_desc& m, cudaStream_t s) {
+    SchwarzData& sc = h->sch;
+    const int lx = m.lx, N = lx - 1, n3 = lx * lx * lx, E = m.E;
+    const int64_t n = (int64_t)E * n3;
+    int corner[8];
+    for (int q = 0; q < 8; q++) {
+        const int i = (q & 1) ? N : 0, j = ((q >> 1) & 1) ? N : 0, k = ((q >> 2) & 1) ? N : 0;
+        corner[q] = (k * lx + j) * lx + i;
+    }
+    std::vector<double> L((size_t)E * 3), h1m((size_t)E), cc((size_t)3 * E * 8), ch1;
+    std::vector<int64_t> cg((size_t)E * 8);
+    std::vector<uint8_t> cm((size_t)E * 8);
+    if (m.h1) ch1.resize((size_t)E * 8);
+    for (int e = 0; e < E; e++) {
+        for (int q = 0; q < 8; q++) {
+            const int64_t Lq = (int64_t)e * n3 + corner[q];
+            for (int d = 0; d < 3; d++) cc[((size_t)d * E + e) * 8 + q] = m.coords[d * n + Lq];
+            cg[(size_t)e * 8 + q] = m.gid[Lq];
+            cm[(size_t)e * 8 + q] = m.mask[Lq];
+            if (m.h1) ch1[(size_t)e * 8 + q] = m.h1[Lq];
+        }
+        for (int d = 0; d < 3; d++) {  // mean length of the element's four edges along direction d
+            double acc = 0.0;
+            for (int q = 0; q < 8; q++) {
+                if ((q >> d) & 1) continue;
+                const int q2 = q | (1 << d);
+                double d2 = 0.0;
+                for (int c = 0; c < 3; c++) {
+                    const double dx = cc[((size_t)c * E + e) * 8 + q2] - cc[((size_t)c * E + e) * 8 + q];
+                    d2 += dx * dx;
+                }
+                acc += std::sqrt(d2);
+            }
+            L[(size_t)e * 3 + d] = acc / 4.0;
+        }
+        double hs = 0.0;
+        for (int q = 0; q < n3; q++) hs += m.h1 ? m.h1[(int64_t)e * n3 + q] : 1.0;
+        h1m[e] = hs / n3;
+    }
+    sem_mesh_desc cmd;
+    cmd.E = E;
+    cmd.lx = 2;
+    cmd.coords = cc.data();
+    cmd.gid = cg.data();
+    cmd.mask = cm.data();
+    cmd.h1 = m.h1 ? ch1.data() : nullptr;
+    int rc = setup_common(&sc.coarse, 1, &cmd, 0, s);
+    if (!rc) rc = ensure_workspace(sc.coarse, false);
+    if (rc) return rc;
+    // reference interior problem and trilinear weights
+    std::vector<double> xi(lx), rho(lx), D((size_t)lx * lx);
+    gll_basis(lx, xi.data(), rho.data(), D.data());
+    const int ni = lx - 2;
+    std::vector<double> S, lam;
+    if (ni > 0) {
+        std::vector<double> C((size_t)ni * ni);
+        for (int a = 0; a < ni; a++)
+            for (int b = 0; b < ni; b++) {
+                double kab = 0.0;  // K = D^T diag(rho) D on [-1, 1], interior rows and columns
+                for (int l = 0; l < lx; l++) kab += D[(size_t)l * lx + a + 1] * rho[l] * D[(size_t)l * lx + b + 1];
+                C[(size_t)a * ni + b] = kab / std::sqrt(rho[a + 1] * rho[b + 1]);
+            }
+        std::vector<double> Vm;
+        sym_eigen(ni, C, lam, Vm);
+        S.resize((size_t)ni * ni);
+        for (int a = 0; a < ni; a++)
+            for (int b = 0; b < ni; b++) S[(size_t)a * ni + b] = Vm[(size_t)a * ni + b] / std::sqrt(rho[a + 1]);
+    }
+    std::vector<double> Pw((size_t)n3 * 8);
+    for (int q = 0; q < n3; q++) {
+        const int i = q % lx, j = (q / lx) % lx, k = q / (lx * lx);
+        for (int c = 0; c < 8; c++) {
+            const double fi = (c & 1) ? (1.0 + xi[i]) / 2.0 : (1.0 - xi[i]) / 2.0;
+            const double fj = ((c >> 1) & 1) ? (1.0 + xi[j]) / 2.0 : (1.0 - xi[j]) / 2.0;
+            const double fk = ((c >> 2) & 1) ? (1.0 + xi[k]) / 2.0 : (1.0 - xi[k]) / 2.0;
+            Pw[(size_t)q * 8 + c] = fi * fj * fk;
+        }
+    }
+    // per-element factors of the fast-diagonalisation solve: sqrt(2 / L_d) for
+    // the three directions, then h1m 4 / L_d^2 (the box's 1-D stiffness scale)
+    std::vector<double> fac((size_t)E * 6);
+    for (int e = 0; e < E; e++)
+        for (int d = 0; d < 3; d++) {
+            const double Ld = L[(size_t)e * 3 + d];
+            fac[(size_t)e * 6 + d] = std::sqrt(2.0 / Ld);
+            fac[(size_t)e * 6 + 3 + d] = h1m[e] * 4.0 / (Ld * Ld);
+        }
+    if ((rc = dalloc(h, &sc.fac, fac.size())) || (rc = dalloc(h, &sc.fac32, fac.size())) ||
+        (rc = dalloc(h, &sc.Pw, Pw.size())) || (rc = dalloc(h, &sc.Pw32, Pw.size())) ||
+        (ni > 0 && ((rc = dalloc(h, &sc.S, S.size())) || (rc = dalloc(h, &sc.lam, lam.size())) ||
+                    (rc = dalloc(h, &sc.S32, S.size())) || (rc = dalloc(h, &sc.lam32, lam.size())))))
+        return rc;
+    auto put = [](double* d, float* d32, const std::vector<double>& v) -> int {
+        std::vector<float> f(v.begin(), v.end());
+        SEM_CUDA_TRY(cudaMemcpy(d, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice));
+        SEM_CUDA_TRY(cudaMemcpy(d32, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice));
+        return SEM_OK;
+    };
+    if ((rc = put(sc.fac, sc.fac32, fac)) || (rc = put(sc.Pw, sc.Pw32, Pw))) return rc;
+    if (ni > 0 && ((rc = put(sc.S, sc.S32, S)) || (rc = put(sc.lam, sc.lam32, lam)))) return rc;
+    return SEM_OK;
+}
+
 // Helmholtz mass term: hm = h2 B (FP64 and FP32), d += hm on the local diagonal
 __global__ void helmholtz_mass_kernel(const double* h2, const double* B, double* hm, float* hm32, double* d,
                                       int64_t n) {
@@ -735,6 +885,8 @@ SEM_API void sem_solve_opts_default(sem_solve_opts* o) {
     o->projection = 0;
     o->tc_split = 0;
     o->pipelined = 0;
+    o->gmres_restart = 30;
+    o->precond_precision = SEM_FP64;
 }
 
 SEM_API int sem_gll(int lx, double* xi, double* rho, double* D) {
@@ -753,7 +905,12 @@ SEM_API int sem_setup(sem_handle** h, int E, int lx, const double* coords, const
     m.gid = gid;
     m.mask = mask;
     m.h1 = h1;
-    return setup_common(h, 1, &m, flags, stream);
+    int rc = setup_common(h, 1, &m, flags & ~SEM_FLAG_SCHWARZ, stream);
+    if (rc == SEM_OK && (flags & SEM_FLAG_SCHWARZ) && (rc = build_schwarz(*h, m, stream)) != SEM_OK) {
+        free_handle(*h);
+        *h = nullptr;
+    }
+    return rc;
 }
 
 SEM_API int sem_setup_batch(sem_handle** h, int nsolve, const sem_mesh_desc* meshes, int flags,
