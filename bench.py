@@ -654,7 +654,7 @@ def _timestep_suite(S, torch):
     GPUs), pipelined against standard FP64 PCG, and the pressure right-hand
     side -div(vhat)/dt + (1/Re) div(curl(omega)) with the gradient kernels."""
     m, h1, _ = W.deformed_cube(32, 7, seed=2)
-    h = S.sem_setup(m.E, m.lx, m.coords, m.gid, m.mask, h1, S.SEM_FLAG_METRICS)
+    h = S.sem_setup(m.E, m.lx, m.coords, m.gid, m.mask, h1, S.SEM_FLAG_METRICS | S.SEM_FLAG_SCHWARZ)
     n = m.n_local
     x, y, z = m.xyz()
     res = {"workload": "32^3 deformed cube, N=7; b_k = mask QQ^T B f(t_k), f = sin(pi(x+t)) sin(pi y) sin(pi z)(1+xy)"
@@ -674,7 +674,10 @@ def _timestep_suite(S, torch):
                     ("mixed_projection_20", {"mode": S.SEM_MODE_MIXED_IR, "tol": 1e-10, "projection": 20}),
                     ("fp64_pair", {"mode": S.SEM_MODE_FP64, "precision": S.SEM_FP64_PAIR, "tol": 1e-10}),
                     ("fp64_pair_projection_20", {"mode": S.SEM_MODE_FP64, "precision": S.SEM_FP64_PAIR,
-                                                 "tol": 1e-10, "projection": 20})):
+                                                 "tol": 1e-10, "projection": 20}),
+                    ("gmres_mixed", {"mode": S.SEM_MODE_GMRES, "precision": S.SEM_FP32, "tol": 1e-10}),
+                    ("gmres_mixed_projection_20", {"mode": S.SEM_MODE_GMRES, "precision": S.SEM_FP32, "tol": 1e-10,
+                                                   "projection": 20})):
         S.sem_projection_reset(h)
         xd.zero_()
         S.sem_cg_solve(h, xd, bs[0], {**o, "projection": 0})  # warm-up (autotune, graphs)
@@ -691,6 +694,7 @@ def _timestep_suite(S, torch):
     S.sem_projection_reset(h)
     res["speedup_projection_mixed"] = res["mixed"]["total_ms"] / res["mixed_projection_20"]["total_ms"]
     res["speedup_projection_fp64_pair"] = res["fp64_pair"]["total_ms"] / res["fp64_pair_projection_20"]["total_ms"]
+    res["speedup_projection_gmres_mixed"] = res["gmres_mixed"]["total_ms"] / res["gmres_mixed_projection_20"]["total_ms"]
     # pipelined PCG against the standard loop (both native FP64)
     pipe = {}
     for name, o in (("fp64_pcg", {"mode": S.SEM_MODE_FP64, "tol": 1e-10}),

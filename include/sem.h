@@ -160,7 +160,7 @@ typedef struct sem_solve_opts {
                             SEM_FP64_NATIVE (slab operator); not for SEM_FP64_PAIR */
     int tc_split;        /* mixed mode: the inner FP32 CG applies the operator as SEM_TC_SPLIT
                             (tensor-core contractions) instead of the CUDA-core FP32 kernels (0) */
-    int gmres_restart;   /* GMRES mode: Krylov vectors per restart cycle (30) */
+    int gmres_restart;   /* GMRES mode: Krylov vectors per restart cycle (20) */
     int pipelined;       /* FP64 mode: pipelined PCG (Ghysels and Vanroose 2014; the paper's
                             work on reducing communication in CG, Sec. II-B): the PCG iterates
                             with one reduction phase per iteration instead of two, at the cost
@@ -180,6 +180,13 @@ typedef struct sem_solve_opts {
                             the coarse CG stays FP64).  Flexible GMRES accepts any
                             preconditioner: this changes iteration counts, not the accuracy
                             the solve reaches */
+    int gmres_orth;      /* GMRES mode: orthogonalisation of the Arnoldi basis.  2 (default):
+                            classical Gram-Schmidt twice, the second pass lagged into the next
+                            step, so every step reads the basis twice (dots, then one combined
+                            update; Swirydowicz et al. 2021); 3: classical Gram-Schmidt twice
+                            within each step (three passes over the basis); 1: once (two
+                            passes, less orthogonality; the true residual at each restart still
+                            decides convergence) */
 } sem_solve_opts;
 
 typedef struct sem_solve_stats {

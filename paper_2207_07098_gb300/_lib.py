@@ -51,7 +51,7 @@ class sem_solve_opts(ctypes.Structure):
                 ("use_graph", ctypes.c_int), ("graph_chunk", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("ir_carry", ctypes.c_int), ("persistent", ctypes.c_int), ("tc_split", ctypes.c_int),
                 ("gmres_restart", ctypes.c_int), ("pipelined", ctypes.c_int), ("projection", ctypes.c_int),
-                ("precond_precision", ctypes.c_int)]
+                ("precond_precision", ctypes.c_int), ("gmres_orth", ctypes.c_int)]
 
 
 class sem_solve_stats(ctypes.Structure):

@@ -211,11 +211,41 @@ inline double relative_residual(double rr, double bb) {
 struct ProjSpace {
     int L = 0;
     int l = 0;
-    double* xt = nullptr;    // [L][n_local]
-    double* bt = nullptr;    // [L][n_local]
-    double* xbar = nullptr;  // [n_local]
-    double* coef = nullptr;  // [L + 2] coefficients of the current projection
+    int64_t ld = 0;               // leading dimension of xt, bt (n_local rounded up to 4)
+    double* xt = nullptr;         // [L][ld]
+    double* bt = nullptr;         // [L][ld]
+    double* xbar = nullptr;       // [n_local]
+    double* coef = nullptr;       // [L + 2] coefficients of the current projection
+    double* gpart = nullptr;      // Gram-Schmidt block partials
+    unsigned int* gcount = nullptr;
 };
+
+// Assembled coarse matrix of the Schwarz preconditioner (sem_coarse.cu): CSR
+// over the free unique corner nodes, its Jacobi inverse, the corner-to-row map
+// and every row's element-corner copies, the CG vectors (x, r, z, p0, p1, q per
+// precision) and scalars
+struct CoarseCsr {
+    int nc = 0;
+    int* rowptr = nullptr;
+    int* col = nullptr;
+    double* val64 = nullptr;
+    float* val32 = nullptr;
+    double* dinv64 = nullptr;
+    float* dinv32 = nullptr;
+    int* cmap = nullptr;  // [E * 8] row of each element corner, -1 on Dirichlet nodes
+    int* gptr = nullptr;  // [nc + 1]
+    int* gidx = nullptr;  // element-corner copies of the rows
+    void* vec[2] = {};    // FP64, FP32: [6][nc]
+    double* st = nullptr;
+    double* partials = nullptr;
+    unsigned int* counter = nullptr;
+};
+int build_coarse_csr(sem_handle* h, const int64_t* cgid, const uint8_t* cmask);
+void free_coarse_csr(CoarseCsr& cc);
+template <typename T>
+int coarse_csr_solve(sem_handle* h, const T* rc_local, int iters, cudaStream_t s);  // iters Jacobi-PCG from 0
+template <typename T>
+const T* coarse_csr_x(const sem_handle* h);
 
 // Two-level Schwarz preconditioner and FGMRES storage (sem_gmres.cu; built
 // at set-up with SEM_FLAG_SCHWARZ, single-mesh handles)
@@ -237,6 +267,9 @@ struct SchwarzData {
     double* coef = nullptr;        // Gram-Schmidt coefficients, norm and y on the device
     double* gpart = nullptr;       // Gram-Schmidt block partials
     unsigned int* gcount = nullptr;
+    CoarseCsr csr;                 // the assembled coarse problem
+    cudaStream_t aux = nullptr;    // the coarse CG's stream (beside the local solves)
+    cudaEvent_t ev_restrict = nullptr, ev_coarse = nullptr;
 };
 
 struct GraphCache {
@@ -354,9 +387,15 @@ void free_schwarz(sem_handle* h);
 int solve_gmres(sem_handle* h, double* x_user, const double* b_user, const sem_solve_opts& o,
                 sem_solve_stats* stats, cudaStream_t s);
 // pieces of the CG driver used by other solvers (sem_cg.cu)
-int true_residual(sem_handle* h, const double* x, const double* b, double* rr_bb, cudaStream_t s);
+int true_residual(sem_handle* h, const double* x, const double* b, double* rr_bb, cudaStream_t s,
+                  int precision = SEM_FP64);
+// refinement and restart residuals of ws.x against ws.b into hb = {rr, bb}
+struct RefineResidual {
+    bool first = true, fast = false, native = true;
+    int compute(sem_handle* h, double tol, cudaStream_t s, double (&hb)[2]);
+    int make_native(sem_handle* h, cudaStream_t s, double (&hb)[2]);
+};
 // fixed iterations from x = 0 on ws.b; persist: one cooperative launch
-int coarse_pcg(sem_handle* hc, int iters, bool persist, cudaStream_t s);
 bool host_resident(const void* p);
 int launch_pair_split_x(sem_handle* h, cudaStream_t s);
 int launch_pair_join_x(sem_handle* h, cudaStream_t s);

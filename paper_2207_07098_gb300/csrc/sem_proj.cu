@@ -18,21 +18,9 @@
 #include <cmath>
 #include <vector>
 
-#include "sem_device.cuh"
-#include "sem_internal.h"
+#include "sem_krylov.cuh"
 
 namespace sem {
-
-// out = base + sign * sum_{i < l} coef[i] vec_i  (vec_i = vecs + i n; base may be null)
-__global__ void proj_combine_kernel(double* __restrict__ out, const double* __restrict__ base,
-                                    const double* __restrict__ vecs, const double* __restrict__ coef, int l,
-                                    double sign, int64_t n) {
-    for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < n; L += (int64_t)gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        for (int i = 0; i < l; i++) acc = fma(coef[i], vecs[(int64_t)i * n + L], acc);
-        out[L] = (base ? base[L] : 0.0) + sign * acc;
-    }
-}
 
 // dx = v / sqrt(nn), db = w / sqrt(nn)
 __global__ void proj_normalise_kernel(const double* __restrict__ v, const double* __restrict__ w,
@@ -55,28 +43,40 @@ static int ensure_space(sem_handle* h, int L) {
     ProjSpace& ps = h->proj;
     if (ps.L == L && ps.xt) return SEM_OK;
     free_projection(h);
-    const size_t n = (size_t)h->n_local;
-    int rc = dalloc(h, &ps.xt, (size_t)L * n);
-    if (!rc) rc = dalloc(h, &ps.bt, (size_t)L * n);
+    const size_t n = (size_t)h->n_local, ld = (n + 3) & ~(size_t)3;
+    int rc = dalloc(h, &ps.xt, (size_t)L * ld);
+    if (!rc) rc = dalloc(h, &ps.bt, (size_t)L * ld);
     if (!rc) rc = dalloc(h, &ps.xbar, n);
     if (!rc) rc = dalloc(h, &ps.coef, (size_t)L + 2);
+    if (!rc) rc = dalloc(h, &ps.gpart, (size_t)(kGmNV + 1) * kMaxPartials);
+    if (!rc && cudaMalloc(&ps.gcount, sizeof(unsigned int)) != cudaSuccess) {
+        cudaGetLastError();
+        ps.gcount = nullptr;
+        rc = fail(SEM_ENOMEM, "cudaMalloc of the projection counter failed");
+    }
+    if (!rc && cudaMemset(ps.gcount, 0, sizeof(unsigned int)) != cudaSuccess) rc = fail(SEM_ECUDA, "cudaMemset");
     if (rc) {
         free_projection(h);
         return rc;
     }
     ps.L = L;
     ps.l = 0;
+    ps.ld = (int64_t)ld;
     return SEM_OK;
 }
 
 void free_projection(sem_handle* h) {
     ProjSpace& ps = h->proj;
     const size_t n = (size_t)h->n_local;
-    if (ps.xt) h->device_bytes -= sizeof(double) * ((size_t)2 * ps.L * n + n + ps.L + 2);
+    if (ps.xt)
+        h->device_bytes -= sizeof(double) * ((size_t)2 * ps.L * (size_t)ps.ld + n + ps.L + 2 +
+                                             (size_t)(kGmNV + 1) * kMaxPartials);
     cudaFree(ps.xt);
     cudaFree(ps.bt);
     cudaFree(ps.xbar);
     cudaFree(ps.coef);
+    cudaFree(ps.gpart);
+    cudaFree(ps.gcount);
     ps = ProjSpace{};
 }
 
@@ -86,12 +86,13 @@ int proj_start(sem_handle* h, int L, cudaStream_t s) {
     if (rc) return rc;
     ProjSpace& ps = h->proj;
     const int64_t n = h->n_local;
-    for (int i = 0; i < ps.l; i++)
-        if ((rc = launch_dot(h, ps.xt + (int64_t)i * n, h->ws.b, ps.coef + i, s))) return rc;
-    proj_combine_kernel<<<grid_for(h, n, 256, 8), 256, 0, s>>>(h->ws.x, nullptr, ps.xt, ps.coef, ps.l, 1.0, n);
-    SEM_LAUNCH_CHECK("proj_combine_kernel");
+    SEM_CUDA_TRY(cudaMemsetAsync(h->ws.x, 0, sizeof(double) * n, s));
+    if (ps.l > 0 &&
+        ((rc = krylov_pass<double>(h, h->ws.b, ps.xt, ps.ld, 0, nullptr, ps.l, ps.coef, nullptr, ps.gpart,
+                                   ps.gcount, s)) ||
+         (rc = krylov_update<double>(h, h->ws.x, ps.xt, ps.ld, ps.coef, ps.l, s))))
+        return rc;
     SEM_CUDA_TRY(cudaMemcpyAsync(ps.xbar, h->ws.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    h->launches++;
     return SEM_OK;
 }
 
@@ -114,12 +115,13 @@ int proj_update(sem_handle* h, cudaStream_t s) {
     double gsum = 0.0;
     std::vector<double> g((size_t)ps.L + 2);
     int rc;
+    // classical Gram-Schmidt twice in the A inner product: g = bt^T v, v -= xt g
     for (int pass = 0; pass < 2 && ps.l > 0; pass++) {
-        for (int i = 0; i < ps.l; i++)
-            if ((rc = launch_dot(h, ps.bt + (int64_t)i * n, v, ps.coef + i, s))) return rc;
-        proj_combine_kernel<<<grid_for(h, n, 256, 8), 256, 0, s>>>(v, v, ps.xt, ps.coef, ps.l, -1.0, n);
-        SEM_LAUNCH_CHECK("proj_combine_kernel");
-        h->launches++;
+        if ((rc = krylov_pass<double>(h, v, ps.bt, ps.ld, 0, nullptr, ps.l, ps.coef, nullptr, ps.gpart, ps.gcount,
+                                      s)) ||
+            (rc = krylov_pass<double>(h, v, ps.xt, ps.ld, ps.l, ps.coef, 0, nullptr, nullptr, ps.gpart, ps.gcount,
+                                      s)))
+            return rc;
         SEM_CUDA_TRY(cudaMemcpyAsync(g.data(), ps.coef, sizeof(double) * ps.l, cudaMemcpyDeviceToHost, s));
         SEM_CUDA_TRY(cudaStreamSynchronize(s));
         for (int i = 0; i < ps.l; i++) gsum += g[i] * g[i];
@@ -132,8 +134,8 @@ int proj_update(sem_handle* h, cudaStream_t s) {
     SEM_CUDA_TRY(cudaStreamSynchronize(s));
     // a direction inside the span (numerically) is not appended
     if (!(nn > 1e-20 * (gsum + nn)) || !std::isfinite(nn)) return SEM_OK;
-    proj_normalise_kernel<<<grid_for(h, n, 256, 8), 256, 0, s>>>(v, w, ps.xt + (int64_t)ps.l * n,
-                                                                 ps.bt + (int64_t)ps.l * n, ps.coef + ps.L, n);
+    proj_normalise_kernel<<<grid_for(h, n, 256, 8), 256, 0, s>>>(v, w, ps.xt + (int64_t)ps.l * ps.ld,
+                                                                 ps.bt + (int64_t)ps.l * ps.ld, ps.coef + ps.L, n);
     SEM_LAUNCH_CHECK("proj_normalise_kernel");
     h->launches++;
     ps.l++;

@@ -736,6 +736,7 @@ static int build_schwarz(sem_handle* h, const sem_mesh_desc& m, cudaStream_t s) 
     cmd.h1 = m.h1 ? ch1.data() : nullptr;
     int rc = setup_common(&sc.coarse, 1, &cmd, 0, s);
     if (!rc) rc = ensure_workspace(sc.coarse, false);
+    if (!rc) rc = build_coarse_csr(h, cg.data(), cm.data());
     if (rc) return rc;
     // reference interior problem and trilinear weights
     std::vector<double> xi(lx), rho(lx), D((size_t)lx * lx);
@@ -885,8 +886,9 @@ SEM_API void sem_solve_opts_default(sem_solve_opts* o) {
     o->projection = 0;
     o->tc_split = 0;
     o->pipelined = 0;
-    o->gmres_restart = 30;
+    o->gmres_restart = 20;
     o->precond_precision = SEM_FP64;
+    o->gmres_orth = 2;
 }
 
 SEM_API int sem_gll(int lx, double* xi, double* rho, double* D) {

@@ -59,7 +59,7 @@ def test_gmres_schwarz_solve_matches_oracle(kind, n, N):
     x, st = H.solve(b, tol=TOL, mode=S.SEM_MODE_GMRES)
     assert st["status"] == S.SEM_OK and st["relres"] <= TOL, st
     assert _oracle_relres(P, x, b) <= 1.05 * TOL
-    _, info = oracle.fgmres(P, b, oracle.SchwarzPrecond(P, m, h1), tol=TOL)
+    _, info = oracle.fgmres(P, b, oracle.SchwarzPrecond(P, m, h1), restart=20, tol=TOL)
     assert abs(st["iterations"] - info["iters"]) <= max(3, info["iters"] // 10), (st, info)
     xo, _ = P.pcg(b, tol=1e-12)
     assert rel_err(x, xo)[0] <= 1e-8
@@ -162,7 +162,24 @@ def test_gmres_rejects_bad_precision_options():
     H = Handle(m, h1, flags=S.SEM_FLAG_SCHWARZ)
     b = W.random_global_rhs(m, 1)
     for bad in ({"precision": S.SEM_TC_SPLIT}, {"precond_precision": 7}, {"gmres_restart": 201},
-                {"precision": S.SEM_FP32, "inner_tol": 1.0}):
+                {"precision": S.SEM_FP32, "inner_tol": 1.0}, {"gmres_orth": 4}, {"gmres_orth": 0}):
         with pytest.raises(S.SemError) as ei:
             H.solve(b, tol=TOL, mode=S.SEM_MODE_GMRES, **bad)
         assert ei.value.status == S.SEM_EINVAL, bad
+
+
+@pytest.mark.parametrize("prec", [S.SEM_FP64, S.SEM_FP32])
+def test_gmres_gram_schmidt_forms(prec):
+    """gmres_orth = 1 (Gram-Schmidt once) and 3 (twice within each step)
+    reach the true 1e-10 within a few iterations of the default (twice, the
+    second pass lagged one step)."""
+    m, h1 = _case("deformed", 4, 7)
+    P = oracle.Problem(m, h1)
+    H = Handle(m, h1, flags=S.SEM_FLAG_SCHWARZ)
+    b = W.random_global_rhs(m, 9)
+    _, ref = H.solve(b, tol=TOL, mode=S.SEM_MODE_GMRES, precision=prec)
+    for extra in ({"gmres_orth": 1}, {"gmres_orth": 3}):
+        x, st = H.solve(b, tol=TOL, mode=S.SEM_MODE_GMRES, precision=prec, **extra)
+        assert st["status"] == S.SEM_OK and st["relres"] <= TOL, (extra, st)
+        assert _oracle_relres(P, x, b) <= 1.05 * TOL, extra
+        assert abs(st["iterations"] - ref["iterations"]) <= max(3, ref["iterations"] // 10), (extra, st, ref)

@@ -88,3 +88,29 @@ def test_batch_refuses_projection():
         assert ei.value.status == S.SEM_EINVAL
     finally:
         S.sem_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [S.SEM_FP64, S.SEM_FP32])
+def test_projection_with_the_gmres_pressure_solver(prec):
+    """The paper pairs projection with its GMRES pressure solve: the same
+    projected start residuals as the oracle's projection, solutions at the
+    true 1e-10, and fewer GMRES iterations once the space holds vectors."""
+    m = W.box_mesh(4, 3, 3, 7, amp=0.05)
+    h1 = W.h1_wavy(m)
+    P = oracle.Problem(m, h1)
+    H = Handle(m, h1, flags=S.SEM_FLAG_SCHWARZ)
+    pr = oracle.Projection(P, 4)
+    its = []
+    for k in range(6):
+        b = _sequence(m, P, k)
+        x, st = H.solve(b, tol=TOL, mode=S.SEM_MODE_GMRES, precision=prec, projection=4)
+        xbar = pr.start(b)
+        r0 = b - P.ax(xbar)
+        start = np.sqrt(P.dot(r0, r0) / P.dot(b, b))
+        xo, _ = P.pcg(b, x0=xbar, tol=TOL)
+        pr.update(xo, xbar)
+        assert st["status"] == S.SEM_OK and st["relres"] <= TOL, (k, st)
+        assert _oracle_relres(P, x, b) <= 1.05 * TOL, k
+        assert abs(st["relres_start"] - start) <= 0.05 * start + 1e-9, (k, st["relres_start"], start)
+        its.append(st["iterations"])
+    assert max(its[3:]) < its[0], its
