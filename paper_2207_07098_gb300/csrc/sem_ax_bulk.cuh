@@ -125,8 +125,8 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
     ax_bulk_kernel(AxParams<T> a) {
     using C = BulkCfg<T, LX, EPC, NST, FUSED>;
     constexpr int N2 = C::N2, N3 = C::N3, DP = C::DP;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    T* sD = reinterpret_cast<T*>(smem_raw);
+    extern __shared__ __align__(128) unsigned char smem_bulk[];
+    T* sD = reinterpret_cast<T*>(smem_bulk);
     T* su = sD + ((LX * DP + 3) & ~3);  // 16-byte aligned
     T* sr = su + EPC * N3;
     T* ss = sr + EPC * N3;

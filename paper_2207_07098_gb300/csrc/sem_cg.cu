@@ -434,62 +434,15 @@ static int run_cg(sem_handle* h, int precision, const sem_solve_opts& o, int slo
 }
 
 // rr_bb[0] = ||b - A x||^2, rr_bb[1] = ||b||^2 (unique-node norm), r = b - A x,
-// with the native FP64 operator whatever the solve's iterations use (or the
-// given FP64-class operator: see RefineResidual)
-int true_residual(sem_handle* h, const double* x, const double* b, double* rr_bb, cudaStream_t s, int precision) {
-    int rc = launch_ax_local(h, x, h->ws.w, precision, s);
+// with the native FP64 operator whatever the solve's iterations use
+int true_residual(sem_handle* h, const double* x, const double* b, double* rr_bb, cudaStream_t s) {
+    int rc = launch_ax_local(h, x, h->ws.w, SEM_FP64, s);
     if (!rc) rc = launch_gs(h, h->ws.w, false, true, s);
     if (rc) return rc;
     resid_kernel<<<grid_for(h, h->n_local, 256, 4), 256, 0, s>>>(b, h->ws.w, h->ws.r, h->mult, h->n_local,
                                                                  h->partials, h->counters + 4, rr_bb);
     SEM_LAUNCH_CHECK("resid_kernel");
     h->launches++;
-    return SEM_OK;
-}
-
-// The residual of a refinement (or restart) step.  The first one of a solve
-// uses the native FP64 operator; later ones use the FP32-pair operator (48-bit,
-// four times faster on this GPU) when the handle has it and ||b|| lies well
-// inside the pair format's range, and a residual that meets the tolerance is
-// recomputed with the native operator before it is believed: the residual a
-// solve reports and stops on is always the native FP64 one.
-int RefineResidual::compute(sem_handle* h, double tol, cudaStream_t s, double (&hb)[2]) {
-    int rc;
-    auto run = [&](int prec) -> int {
-        if ((rc = true_residual(h, h->ws.x, h->ws.b, h->scratch, s, prec))) return rc;
-        SEM_CUDA_TRY(cudaMemcpyAsync(hb, h->scratch, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-        SEM_CUDA_TRY(cudaStreamSynchronize(s));
-        return SEM_OK;
-    };
-    if (!fast) {
-        if ((rc = run(SEM_FP64))) return rc;
-        if (first) {
-            first = false;
-            const double bn = std::sqrt(hb[1]);
-            const int v = ax_variant_for(h, h->parts[0].lx, kClsPair);
-            fast = h->nsolve == 1 && (v == kDfVariant || v == kDflVariant) && bn > 0x1p-40 && bn < 0x1p80;
-        }
-        native = true;
-        return SEM_OK;
-    }
-    if ((rc = run(SEM_FP64_PAIR))) return rc;
-    native = false;
-    const double rel = relative_residual(hb[0], hb[1]);
-    if (rel <= tol || !std::isfinite(rel)) {
-        if ((rc = run(SEM_FP64))) return rc;
-        native = true;
-    }
-    return SEM_OK;
-}
-
-// the native FP64 residual of the current x, if the last one was not
-int RefineResidual::make_native(sem_handle* h, cudaStream_t s, double (&hb)[2]) {
-    if (native) return SEM_OK;
-    int rc = true_residual(h, h->ws.x, h->ws.b, h->scratch, s, SEM_FP64);
-    if (rc) return rc;
-    SEM_CUDA_TRY(cudaMemcpyAsync(hb, h->scratch, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    SEM_CUDA_TRY(cudaStreamSynchronize(s));
-    native = true;
     return SEM_OK;
 }
 
@@ -621,9 +574,8 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
         double prev = INFINITY, rn_prev = 0.0;
         bool can_carry = false, capped_last = false;
         int outer = 0, inner = 0;
-        RefineResidual rres;
         for (;;) {
-            if ((rc = rres.compute(h, o.tol, s, hb))) return rc;
+            if ((rc = true_residual(h, h->ws.x, h->ws.b, rrbb, s)) || (rc = read_rrbb(h, hb, s))) return rc;
             const double rel = relative_residual(hb[0], hb[1]);
             if (first_residual) st.relres_start = rel;
             first_residual = false;
@@ -654,7 +606,6 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
             h->launches++;
             outer++;
         }
-        if ((rc = rres.make_native(h, s, hb))) return rc;  // the reported residual is the native one
         st.iterations = inner;
         st.outer_iterations = outer;
     }

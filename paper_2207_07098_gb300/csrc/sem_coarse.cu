@@ -13,7 +13,8 @@
 // with the CG scalars in device memory and p double-buffered (a row reads its
 // neighbours' previous p).  The right-hand side is gathered from the
 // element-corner restriction (the sum of every node's copies, in ascending
-// local index) and the prolongation reads x through the corner-to-row map.
+// local index); the last iteration writes x back to the element corners for
+// the prolongation.
 // Deterministic: fixed-order row sums and grid reductions.
 #include <algorithm>
 #include <vector>
@@ -67,6 +68,7 @@ __global__ void __launch_bounds__(256) coarse_spmv_kernel(const int* __restrict_
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
         T acc = (T)0;
         // (the first iteration does not read p_prev: it holds the last solve's p)
+#pragma unroll 4
         for (int k = rowptr[i]; k < rowptr[i + 1]; k++) {
             const int j = col[k];
             acc = fma(val[k], first ? z[j] : fma(beta, p_prev[j], z[j]), acc);
@@ -79,11 +81,15 @@ __global__ void __launch_bounds__(256) coarse_spmv_kernel(const int* __restrict_
     gm_grid_sum<T, 1>(d, partials, counter, [&](const double* t) { st[kCsPq] = t[0]; });
 }
 
-// alpha = rho / <p, q>; x += alpha p; r -= alpha q; z = Dinv r; rho_old = rho; rho = <r, z>
+// alpha = rho / <p, q>; x += alpha p; r -= alpha q; z = Dinv r; rho_old = rho;
+// rho = <r, z>; the last iteration also writes x to the row's element-corner
+// copies in xl (xl != null; its Dirichlet corners stay zero)
 template <typename T>
 __global__ void __launch_bounds__(256) coarse_update_kernel(T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
                                                             const T* __restrict__ p, const T* __restrict__ q,
-                                                            const T* __restrict__ dinv, int nc, double* st,
+                                                            const T* __restrict__ dinv, int nc, T* __restrict__ xl,
+                                                            const int* __restrict__ gptr,
+                                                            const int* __restrict__ gidx, double* st,
                                                             double* partials, unsigned int* counter) {
     __shared__ T alpha_s;
     if (threadIdx.x == 0) {
@@ -94,7 +100,10 @@ __global__ void __launch_bounds__(256) coarse_update_kernel(T* __restrict__ x, T
     const T alpha = alpha_s;
     T d[1] = {(T)0};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
-        x[i] = fma(alpha, p[i], x[i]);
+        const T xi = fma(alpha, p[i], x[i]);
+        x[i] = xi;
+        if (xl)
+            for (int c = gptr[i]; c < gptr[i + 1]; c++) xl[gidx[c]] = xi;
         const T ri = fma(-alpha, q[i], r[i]);
         const T zi = dinv[i] * ri;
         r[i] = ri;
@@ -138,6 +147,7 @@ int coarse_csr_solve(sem_handle* h, const T* rc, int iters, cudaStream_t s) {
     T* p[2] = {csr_vec<T>(cc, 3), csr_vec<T>(cc, 4)};
     T* q = csr_vec<T>(cc, 5);
     const T* dinv = csr_dinv<T>(cc);
+    T* xl = static_cast<T*>(cc.xl[std::is_same<T, float>::value ? 1 : 0]);
     coarse_gather_kernel<T><<<grid, 256, 0, s>>>(rc, cc.gptr, cc.gidx, dinv, cc.nc, x, r, z, cc.st, cc.partials,
                                                  cc.counter);
     SEM_LAUNCH_CHECK("coarse_gather_kernel");
@@ -147,7 +157,8 @@ int coarse_csr_solve(sem_handle* h, const T* rc, int iters, cudaStream_t s) {
         coarse_spmv_kernel<T><<<grid, 256, 0, s>>>(cc.rowptr, cc.col, csr_val<T>(cc), z, p[it & 1], pn, q, cc.nc,
                                                    it == 0 ? 1 : 0, cc.st, cc.partials, cc.counter);
         SEM_LAUNCH_CHECK("coarse_spmv_kernel");
-        coarse_update_kernel<T><<<grid, 256, 0, s>>>(x, r, z, pn, q, dinv, cc.nc, cc.st, cc.partials, cc.counter);
+        coarse_update_kernel<T><<<grid, 256, 0, s>>>(x, r, z, pn, q, dinv, cc.nc, it == iters - 1 ? xl : nullptr,
+                                                     cc.gptr, cc.gidx, cc.st, cc.partials, cc.counter);
         SEM_LAUNCH_CHECK("coarse_update_kernel");
         h->launches += 2;
     }
@@ -157,8 +168,8 @@ template int coarse_csr_solve<double>(sem_handle*, const double*, int, cudaStrea
 template int coarse_csr_solve<float>(sem_handle*, const float*, int, cudaStream_t);
 
 template <typename T>
-const T* coarse_csr_x(const sem_handle* h) {
-    return csr_vec<T>(h->sch.csr, 0);
+const T* coarse_csr_x(const sem_handle* h) {  // element-corner values [E][8]
+    return static_cast<const T*>(h->sch.csr.xl[std::is_same<T, float>::value ? 1 : 0]);
 }
 template const double* coarse_csr_x<double>(const sem_handle*);
 template const float* coarse_csr_x<float>(const sem_handle*);
@@ -170,11 +181,12 @@ void free_coarse_csr(CoarseCsr& cc) {
     cudaFree(cc.val32);
     cudaFree(cc.dinv64);
     cudaFree(cc.dinv32);
-    cudaFree(cc.cmap);
     cudaFree(cc.gptr);
     cudaFree(cc.gidx);
     cudaFree(cc.vec[0]);
     cudaFree(cc.vec[1]);
+    cudaFree(cc.xl[0]);
+    cudaFree(cc.xl[1]);
     cudaFree(cc.st);
     cudaFree(cc.partials);
     cudaFree(cc.counter);
@@ -284,7 +296,7 @@ int build_coarse_csr(sem_handle* h, const int64_t* cgid, const uint8_t* cmask) {
     cc.nc = nc;
     if ((rc = upload(h, &cc.rowptr, rowptr)) || (rc = upload(h, &cc.col, col)) || (rc = upload(h, &cc.val64, val)) ||
         (rc = upload(h, &cc.val32, val32)) || (rc = upload(h, &cc.dinv64, dinv)) ||
-        (rc = upload(h, &cc.dinv32, dinv32)) || (rc = upload(h, &cc.cmap, cmap)) || (rc = upload(h, &cc.gptr, gptr)) ||
+        (rc = upload(h, &cc.dinv32, dinv32)) || (rc = upload(h, &cc.gptr, gptr)) ||
         (rc = upload(h, &cc.gidx, gidx)))
         return rc;
     const size_t nv = (size_t)6 * (size_t)std::max(nc, 1);
@@ -297,6 +309,13 @@ int build_coarse_csr(sem_handle* h, const int64_t* cgid, const uint8_t* cmask) {
     cc.vec[1] = v32;
     SEM_CUDA_TRY(cudaMemset(v64, 0, sizeof(double) * nv));
     SEM_CUDA_TRY(cudaMemset(v32, 0, sizeof(float) * nv));
+    double* xl64 = nullptr;
+    float* xl32 = nullptr;
+    if ((rc = dalloc(h, &xl64, (size_t)nl)) || (rc = dalloc(h, &xl32, (size_t)nl))) return rc;
+    cc.xl[0] = xl64;
+    cc.xl[1] = xl32;
+    SEM_CUDA_TRY(cudaMemset(xl64, 0, sizeof(double) * nl));  // Dirichlet corners stay zero
+    SEM_CUDA_TRY(cudaMemset(xl32, 0, sizeof(float) * nl));
     SEM_CUDA_TRY(cudaMalloc(&cc.counter, sizeof(unsigned int)));
     SEM_CUDA_TRY(cudaMemset(cc.counter, 0, sizeof(unsigned int)));
     return SEM_OK;

@@ -211,4 +211,35 @@ __device__ __forceinline__ double cg_beta(const CGState* st) {
     return cg_first(st) ? 0.0 : st->rho / st->rho_old;
 }
 
+// Bounded grid barrier of a cooperative launch: returns false (error word
+// set) when the other CTAs did not arrive within the budget.
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, int* err, long long budget, int* s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* gen = bar + 1;
+        const unsigned int g0 = *gen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            bar[0] = 0u;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g0) {
+                if (clock64() - t0 > budget) {
+                    ok = 0;
+                    atomicExch(err, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
 }  // namespace sem

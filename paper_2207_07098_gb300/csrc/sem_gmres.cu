@@ -365,30 +365,19 @@ __global__ void __launch_bounds__(sch_warps<LX, TC>() * 32)
     }
 }
 
-// z = mask (z + sum_c Pw[q][c] x_c), one warp per element: trilinear
-// interpolation of the element's corner values through the 1-D factors.  The
-// corner values are xc[e * 8 + c] (element-local), or xc[cmap[e * 8 + c]]
-// (rows of the assembled coarse problem; -1 marks a Dirichlet corner) when
-// cmap is given.
+// z = mask (z + sum_c Pw[q][c] xc[e][c]), one warp per element: trilinear
+// interpolation of the element's corner values through the 1-D factors
 template <int LX, typename TI, typename TC>
 __global__ void __launch_bounds__(256) prolong_kernel(TI* __restrict__ z, const TI* __restrict__ xc,
-                                                      const int* __restrict__ cmap, const TC* __restrict__ Pw,
-                                                      const uint8_t* __restrict__ mask, int64_t E) {
+                                                      const TC* __restrict__ Pw, const uint8_t* __restrict__ mask,
+                                                      int64_t E) {
     constexpr int N3 = LX * LX * LX;
     __shared__ TC F[2][LX];
     for (int t = threadIdx.x; t < 2 * LX; t += blockDim.x) F[t / LX][t % LX] = Pw[(t % LX) * 8 + t / LX];
     __syncthreads();
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int64_t e = (int64_t)blockIdx.x * nw + (threadIdx.x >> 5); e < E; e += (int64_t)gridDim.x * nw) {
-        TC xv = (TC)0;  // 8 conversions per element
-        if (lane < 8) {
-            if (cmap) {
-                const int row = cmap[e * 8 + lane];
-                xv = row >= 0 ? (TC)xc[row] : (TC)0;
-            } else {
-                xv = (TC)xc[e * 8 + lane];
-            }
-        }
+        const TC xv = lane < 8 ? (TC)xc[e * 8 + lane] : (TC)0;  // 8 conversions per element
         TC c8[8];
 #pragma unroll
         for (int c = 0; c < 8; c++) c8[c] = __shfl_sync(0xffffffffu, xv, c);
@@ -447,25 +436,25 @@ static int launch_local_t(sem_handle* h, int mode, const TI* r, const double* r_
 }
 
 template <int LX, typename TI, typename TC>
-static int launch_prolong_t(sem_handle* h, TI* z, const TI* xc, const int* cmap, cudaStream_t s) {
+static int launch_prolong_t(sem_handle* h, TI* z, const TI* xc, cudaStream_t s) {
     const SchwarzData& sc = h->sch;
     const int64_t E = h->parts[0].E;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((E + 7) / 8, (int64_t)h->sm_count * 8));
-    prolong_kernel<LX, TI, TC><<<grid, 256, 0, s>>>(z, xc, cmap, sch_table<TC>(sc, 0), h->mask, E);
+    prolong_kernel<LX, TI, TC><<<grid, 256, 0, s>>>(z, xc, sch_table<TC>(sc, 0), h->mask, E);
     SEM_LAUNCH_CHECK("prolong_kernel");
     h->launches++;
     return SEM_OK;
 }
 
 // phase kSchAll / kSchRestrict / kSchLocal: the local part (SchMode);
-// phase -1: the prolongation of xc (through cmap when given)
+// phase -1: the prolongation of the element-corner values xc
 template <typename TI, typename TC>
 static int launch_schwarz_phase(sem_handle* h, int phase, const TI* r, const double* r_norm2, TI* z, const TI* minv,
-                                const TI* xc, const int* cmap, cudaStream_t s) {
+                                const TI* xc, cudaStream_t s) {
 #define SEM_SCH_CASE(LXV)                                                                   \
     case LXV:                                                                                \
         return phase >= 0 ? launch_local_t<LXV, TI, TC>(h, phase, r, r_norm2, z, minv, s)  \
-                          : launch_prolong_t<LXV, TI, TC>(h, z, xc, cmap, s);
+                          : launch_prolong_t<LXV, TI, TC>(h, z, xc, s);
     switch (h->parts[0].lx) {
         SEM_SCH_CASE(2)
         SEM_SCH_CASE(3)
@@ -499,20 +488,22 @@ static int apply_schwarz(sem_handle* h, const TI* r, const double* r_norm2, TI* 
     const TI* xc = coarse_csr_x<TI>(h);
     int rc;
     if (!sc.aux) {  // one stream: local part with the restriction, coarse CG, prolongation
-        if ((rc = launch_schwarz_phase<TI, TC>(h, kSchAll, r, r_norm2, z, minv, nullptr, nullptr, s)) ||
+        if ((rc = launch_schwarz_phase<TI, TC>(h, kSchAll, r, r_norm2, z, minv, nullptr, s)) ||
             (rc = coarse_csr_solve<TI>(h, coarse_rhs<TI>(hc), 10, s)))
             return rc;
-        return launch_schwarz_phase<TI, TC>(h, -1, r, r_norm2, z, minv, xc, sc.csr.cmap, s);
+        return launch_schwarz_phase<TI, TC>(h, -1, r, r_norm2, z, minv, xc, s);
     }
     // the coarse CG on the handle's second stream, beside the local solves
-    if ((rc = launch_schwarz_phase<TI, TC>(h, kSchRestrict, r, r_norm2, z, minv, nullptr, nullptr, s))) return rc;
+    // (the local-solve kernel is queued first, so that it starts while the
+    // host is still queueing the coarse CG's launches)
+    if ((rc = launch_schwarz_phase<TI, TC>(h, kSchRestrict, r, r_norm2, z, minv, nullptr, s))) return rc;
     SEM_CUDA_TRY(cudaEventRecord(sc.ev_restrict, s));
+    if ((rc = launch_schwarz_phase<TI, TC>(h, kSchLocal, r, r_norm2, z, minv, nullptr, s))) return rc;
     SEM_CUDA_TRY(cudaStreamWaitEvent(sc.aux, sc.ev_restrict, 0));
     if ((rc = coarse_csr_solve<TI>(h, coarse_rhs<TI>(hc), 10, sc.aux))) return rc;
     SEM_CUDA_TRY(cudaEventRecord(sc.ev_coarse, sc.aux));
-    if ((rc = launch_schwarz_phase<TI, TC>(h, kSchLocal, r, r_norm2, z, minv, nullptr, nullptr, s))) return rc;
     SEM_CUDA_TRY(cudaStreamWaitEvent(s, sc.ev_coarse, 0));
-    return launch_schwarz_phase<TI, TC>(h, -1, r, r_norm2, z, minv, xc, sc.csr.cmap, s);
+    return launch_schwarz_phase<TI, TC>(h, -1, r, r_norm2, z, minv, xc, s);
 }
 
 // the second stream and its two events (created at the first GMRES solve; a
@@ -520,7 +511,11 @@ static int apply_schwarz(sem_handle* h, const TI* r, const double* r_norm2, TI* 
 static void ensure_aux_stream(sem_handle* h) {
     SchwarzData& sc = h->sch;
     if (sc.aux) return;
-    if (cudaStreamCreateWithFlags(&sc.aux, cudaStreamNonBlocking) != cudaSuccess ||
+    // the highest priority: its small kernels take SM slots as soon as blocks of
+    // the local-solve kernel finish
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (cudaStreamCreateWithPriority(&sc.aux, cudaStreamNonBlocking, greatest) != cudaSuccess ||
         cudaEventCreateWithFlags(&sc.ev_restrict, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&sc.ev_coarse, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
@@ -862,9 +857,10 @@ static int solve_gmres_t(sem_handle* h, const sem_solve_opts& o, sem_solve_stats
     double hb[2] = {0.0, 0.0};
     double rel_prev = INFINITY;
     int status = SEM_ENOTCONV, it = 0, cycles = 0, rc;
-    RefineResidual rres;  // pair-operator residuals between restarts, native ones to stop on
     for (;;) {
-        if ((rc = rres.compute(h, o.tol, s, hb)) || (rc = check_error_words(h, s))) return rc;
+        if ((rc = true_residual(h, h->ws.x, h->ws.b, h->scratch, s)) || (rc = read_scalars(hb, h->scratch, 2, s)) ||
+            (rc = check_error_words(h, s)))
+            return rc;
         const double rel = relative_residual(hb[0], hb[1]);
         if (cycles == 0) st->relres_start = rel;
         if (!std::isfinite(rel)) {
@@ -905,7 +901,6 @@ static int solve_gmres_t(sem_handle* h, const sem_solve_opts& o, sem_solve_stats
         }
         cycles++;
     }
-    if ((rc = rres.make_native(h, s, hb))) return rc;
     st->status = status;
     st->iterations = it;
     st->outer_iterations = cycles;

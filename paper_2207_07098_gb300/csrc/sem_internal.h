@@ -221,9 +221,9 @@ struct ProjSpace {
 };
 
 // Assembled coarse matrix of the Schwarz preconditioner (sem_coarse.cu): CSR
-// over the free unique corner nodes, its Jacobi inverse, the corner-to-row map
-// and every row's element-corner copies, the CG vectors (x, r, z, p0, p1, q per
-// precision) and scalars
+// over the free unique corner nodes, its Jacobi inverse, every row's
+// element-corner copies, the CG vectors (x, r, z, p0, p1, q per precision),
+// the solution at the element corners, and the CG scalars
 struct CoarseCsr {
     int nc = 0;
     int* rowptr = nullptr;
@@ -232,10 +232,10 @@ struct CoarseCsr {
     float* val32 = nullptr;
     double* dinv64 = nullptr;
     float* dinv32 = nullptr;
-    int* cmap = nullptr;  // [E * 8] row of each element corner, -1 on Dirichlet nodes
     int* gptr = nullptr;  // [nc + 1]
     int* gidx = nullptr;  // element-corner copies of the rows
     void* vec[2] = {};    // FP64, FP32: [6][nc]
+    void* xl[2] = {};     // FP64, FP32: the solution at the element corners [E][8]
     double* st = nullptr;
     double* partials = nullptr;
     unsigned int* counter = nullptr;
@@ -387,15 +387,7 @@ void free_schwarz(sem_handle* h);
 int solve_gmres(sem_handle* h, double* x_user, const double* b_user, const sem_solve_opts& o,
                 sem_solve_stats* stats, cudaStream_t s);
 // pieces of the CG driver used by other solvers (sem_cg.cu)
-int true_residual(sem_handle* h, const double* x, const double* b, double* rr_bb, cudaStream_t s,
-                  int precision = SEM_FP64);
-// refinement and restart residuals of ws.x against ws.b into hb = {rr, bb}
-struct RefineResidual {
-    bool first = true, fast = false, native = true;
-    int compute(sem_handle* h, double tol, cudaStream_t s, double (&hb)[2]);
-    int make_native(sem_handle* h, cudaStream_t s, double (&hb)[2]);
-};
-// fixed iterations from x = 0 on ws.b; persist: one cooperative launch
+int true_residual(sem_handle* h, const double* x, const double* b, double* rr_bb, cudaStream_t s);
 bool host_resident(const void* p);
 int launch_pair_split_x(sem_handle* h, cudaStream_t s);
 int launch_pair_join_x(sem_handle* h, cudaStream_t s);

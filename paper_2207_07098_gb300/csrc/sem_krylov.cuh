@@ -38,8 +38,9 @@ __device__ __forceinline__ void ld_mult(const uint8_t* m, uint8_t (&o)[P]) {
 }
 
 // Deterministic grid sum of K per-thread values of type T: warp sums in T,
-// block and grid sums in FP64 in a fixed order (last block to arrive); fin
-// receives the K sums in thread 0 of that block.
+// block and grid sums in FP64 in a fixed order (the last block to arrive adds
+// the block partials, a warp per value); fin receives the K sums in thread 0
+// of that block.
 template <typename T, int K, typename Fin>
 __device__ __forceinline__ void gm_grid_sum(T (&d)[K], double* partials, unsigned int* counter, Fin fin) {
     __shared__ double red[K][8];
@@ -65,18 +66,15 @@ __device__ __forceinline__ void gm_grid_sum(T (&d)[K], double* partials, unsigne
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    if (threadIdx.x < K) {
-        const double* pq = partials + threadIdx.x * kMaxPartials;
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        int q = 0;
-        for (; q + 4 <= (int)gridDim.x; q += 4) {
-            s0 += __ldcg(pq + q);
-            s1 += __ldcg(pq + q + 1);
-            s2 += __ldcg(pq + q + 2);
-            s3 += __ldcg(pq + q + 3);
-        }
-        for (; q < (int)gridDim.x; q++) s0 += __ldcg(pq + q);
-        tot[threadIdx.x] = (s0 + s1) + (s2 + s3);
+    // the last block: warp w sums the partials of values w, w + nw, ..., each
+    // lane a fixed stride of blocks, then a fixed shuffle tree
+    for (int q = wid; q < K; q += nw) {
+        const double* pq = partials + q * kMaxPartials;
+        double acc = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) acc += __ldcg(pq + b);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) tot[q] = acc;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
