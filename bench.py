@@ -46,9 +46,9 @@ def _args():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--solver", choices=["mixed", "fp64", "fp64_pair"], default="mixed",
-                    help="mixed refinement (default), FP64 PCG with the native operator, or FP64 PCG in "
-                         "FP32-pair arithmetic (SEM_FP64_PAIR)")
+    ap.add_argument("--solver", choices=["mixed", "fp64", "fp64_pair", "gmres"], default="mixed",
+                    help="mixed refinement (default), FP64 PCG with the native operator, FP64 PCG in "
+                         "FP32-pair arithmetic (SEM_FP64_PAIR), or the mixed GMRES + Schwarz solve")
     ap.add_argument("--n", type=int, default=32, help="elements per direction of the cube")
     ap.add_argument("--order", type=int, default=7)
     ap.add_argument("--no-extras", action="store_true", help="skip the comparison solves and ax-only bench")
@@ -155,8 +155,12 @@ def _workload(args):
 def _config(args, m, extra=None):
     c = {"workload": f"deformed_cube_{args.n}^3_N{args.order}", "elements": m.E, "lx": m.lx,
          "n_local": m.n_local, "tol": 1e-10,
-         "solver": {"mixed": "mixed_ir", "fp64": "fp64_pcg", "fp64_pair": "fp64_pair_pcg"}[args.solver],
-         "preconditioner": "point Jacobi (exact assembled diagonal)", "l2": L2_NOTE}
+         "solver": {"mixed": "mixed_ir", "fp64": "fp64_pcg", "fp64_pair": "fp64_pair_pcg",
+                    "gmres": "mixed_fgmres_schwarz"}[args.solver],
+         "preconditioner": ("two-level additive Schwarz: element-interior fast-diagonalisation solves, point "
+                            "Jacobi on shared nodes, corner coarse grid (10 Jacobi-PCG iterations)"
+                            if args.solver == "gmres" else "point Jacobi (exact assembled diagonal)"),
+         "l2": L2_NOTE}
     if extra:
         c.update(extra)
     return c
@@ -260,10 +264,12 @@ def run_ours(args):
     info = S.sem_get_info(h)
     bd = torch.from_numpy(b).cuda()
     xd = torch.zeros(n, dtype=torch.float64, device="cuda")
-    mode = S.SEM_MODE_MIXED_IR if args.solver == "mixed" else S.SEM_MODE_FP64
+    mode = {"mixed": S.SEM_MODE_MIXED_IR, "gmres": S.SEM_MODE_GMRES}.get(args.solver, S.SEM_MODE_FP64)
     opts = {"mode": mode, "tol": 1e-10, **(MIXED_OPTS if args.solver == "mixed" else {})}
     if args.solver == "fp64_pair":
         opts["precision"] = S.SEM_FP64_PAIR
+    if args.solver == "gmres":  # the paper's pressure solver, FP32 cycles inside FP64 restarts
+        opts["precision"] = S.SEM_FP32
     if args.tc_split:
         opts["tc_split"] = 1
 
@@ -319,11 +325,11 @@ def run_ours(args):
     # dominant kernel: the fused p-update + ax_helm launch (K-A) of the CG loop
     samples = [s["ax_ms"] for s in stats if s["ax_samples"] > 0]
     ax_ms = statistics.mean(samples) if samples else None
-    ka_bytes_pt = 9 * (4 if args.solver == "mixed" else 8)  # read z, p, 6 G; write p, w (h1 folded)
+    ka_bytes_pt = 9 * (4 if args.solver in ("mixed", "gmres") else 8)  # read z, p, 6 G; write p, w (h1 folded)
     ka_bytes = ka_bytes_pt * n
     achieved = ka_bytes / (ax_ms * 1e-3) / 1e9 if ax_ms else None
     variant = stats[-1].get("ax_variant", 0)
-    tname = "float" if args.solver == "mixed" else "double"
+    tname = "float" if args.solver in ("mixed", "gmres") else "double"
     cfgs = {1: (1, 3), 2: (2, 2), 3: (2, 3), 4: (4, 2)}
     kname = (f"ax_kernel<{tname},{m.lx},true>" if variant == 0 else
              f"ax_df_kernel<{m.lx},true>" if variant == 5 else
@@ -335,11 +341,16 @@ def run_ours(args):
                 "frac": achieved / peak if achieved else None,
                 "traffic": traffic, "kernel": kname, "algorithmic_bytes_per_launch": ka_bytes,
                 "launch_ms": ax_ms, "peak_kind": peak_kind}
+    if args.solver == "gmres":  # no live per-kernel sample in this mode: see the GMRES launch-list summary
+        roofline = {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None, "traffic": None,
+                    "kernel": "gm_lagged_update_kernel<float>", "peak_kind": peak_kind,
+                    "note": "GMRES iterations are not CG iterations: value counts points x GMRES iterations"}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": {"mixed": "f32+f64", "fp64": "f64", "fp64_pair": "f32x2+f64"}[args.solver], "data": "synthetic",
+           "dtype": {"mixed": "f32+f64", "fp64": "f64", "fp64_pair": "f32x2+f64", "gmres": "f32+f64"}[args.solver],
+           "data": "synthetic",
            "config": _config(args, m, {"inner_tol": MIXED_OPTS["inner_tol"] if args.solver == "mixed" else None,
                                        "refinement": ("inner CG direction kept across FP64 refinement steps"
                                                       if args.solver == "mixed" else None),

@@ -157,7 +157,9 @@ typedef struct sem_solve_opts {
                             2.2 against 2.8 ms FP64, 3.1 against 3.1 ms mixed, because each
                             phase is bound by dependent-load latency, not by launches).
                             Single-mesh handles, lx <= 10, SEM_FP32 inner solves and SEM_FP64 /
-                            SEM_FP64_NATIVE (slab operator); not for SEM_FP64_PAIR */
+                            SEM_FP64_NATIVE (slab operator); not for SEM_FP64_PAIR.  GMRES mode:
+                            nonzero runs the coarse CG of the Schwarz preconditioner as one
+                            cooperative launch with bounded grid barriers */
     int tc_split;        /* mixed mode: the inner FP32 CG applies the operator as SEM_TC_SPLIT
                             (tensor-core contractions) instead of the CUDA-core FP32 kernels (0) */
     int gmres_restart;   /* GMRES mode: Krylov vectors per restart cycle (20) */

@@ -523,7 +523,51 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
         if (pipe && (rc = ensure_pipe_workspace(h))) return rc;
         double scale = 1.0;
         int used = 0;
-        for (int restart = 0;; restart++) {
+        // Pipelined PCG in segments of kPipeSeg iterations with residual
+        // replacement between them: the recursively updated r, u, w, s, q, z of
+        // the pipelined recurrences drift from the vectors they stand for over
+        // hundreds of iterations (on the 32^3 workload the recurrence broke down
+        // at a true residual of 1e-4 after 1800 iterations), so every segment
+        // starts from the true residual and recomputes the others from x and the
+        // kept direction p (Cools and Vanroose's residual replacement).  A
+        // breakdown restarts from the true residual (at most four times).
+        int pipe_base = 0, pipe_breaks = 0;
+        bool pipe_live = false;
+        for (int seg = 0; pipe; seg++) {
+            if ((rc = true_residual(h, h->ws.x, h->ws.b, rrbb, s)) || (rc = read_rrbb(h, hb, s))) return rc;
+            const double rel = relative_residual(hb[0], hb[1]);
+            if (first_residual) st.relres_start = rel;
+            first_residual = false;
+            if (!std::isfinite(rel)) {
+                status = SEM_EBREAKDOWN;
+                break;
+            }
+            if (hb[1] == 0.0 || rel <= o.tol) {
+                status = SEM_OK;
+                break;
+            }
+            if (used >= o.max_iter) {
+                status = SEM_ENOTCONV;
+                break;
+            }
+            if (status == SEM_EBREAKDOWN) {
+                if (++pipe_breaks > 4) break;
+                pipe_live = false;
+            }
+            const int len = std::min(kPipeSeg, o.max_iter - used);
+            if (pipe_live) {
+                rc = launch_pipe_replace(h, len, s);
+            } else {
+                pipe_base = used;
+                rc = launch_pipe_init(h, o.tol, len, s);
+            }
+            if (rc || (rc = run_cg(h, kPipePrec, o, 0, s, &hs, &tm, &persisted))) return rc;
+            pipe_live = true;
+            used = pipe_base + hs.iter;
+            st.relres_recursive = hs.bb > 0 ? std::sqrt(hs.rr / hs.bb) : 0.0;
+            status = hs.status == SEM_ENOTCONV ? SEM_OK : hs.status;  // a segment ended: replace and go on
+        }
+        for (int restart = 0; !pipe; restart++) {
             if ((rc = true_residual(h, h->ws.x, h->ws.b, rrbb, s)) || (rc = read_rrbb(h, hb, s))) return rc;
             const double rel = relative_residual(hb[0], hb[1]);
             if (first_residual) st.relres_start = rel;
@@ -544,8 +588,6 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
                     return rc;
                 if ((rc = launch_pair_split_x(h, s)) || (rc = launch_pair_init(h, o.tol, o.max_iter - used, s)))
                     return rc;
-            } else if (pipe) {
-                if ((rc = launch_pipe_init(h, o.tol, o.max_iter - used, s))) return rc;
             } else {
                 cg_init_kernel<double><<<grid_for(h, n, 256, 4), 256, 0, s>>>(
                     h->ws.b, h->ws.r, h->ws.z, h->minv64, h->mult, n, o.tol, o.max_iter - used, h->state,
@@ -553,7 +595,7 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
                 SEM_LAUNCH_CHECK("cg_init_kernel");
                 h->launches++;
             }
-            if ((rc = run_cg(h, pair ? kPairPrec : pipe ? kPipePrec : prec, o, 0, s, &hs, &tm, &persisted)))
+            if ((rc = run_cg(h, pair ? kPairPrec : prec, o, 0, s, &hs, &tm, &persisted)))
                 return rc;
             if (pair) {
                 if ((rc = launch_pair_join_x(h, s))) return rc;

@@ -17,6 +17,8 @@
 // vector traffic (20 vector accesses per point in the update against 8); it
 // exists for parity with the paper's solver family and as the single-exchange
 // form a multi-GPU build would overlap.  FP64 data, native FP64 operator.
+// The solve runs in segments with residual replacement between them
+// (launch_pipe_replace; the loop is in sem_cg.cu).
 #include <algorithm>
 #include <cmath>
 
@@ -163,6 +165,38 @@ __global__ void __launch_bounds__(256) pipe_update_kernel(PipeVecs v) {
     });
 }
 
+// residual replacement, last step: m = Minv w and the reductions gamma = <r, u>,
+// delta = <w, u>, rr = <r, r> of the recomputed vectors; the scalars of the
+// previous iteration (gamma_prev, alpha_prev) stay, so the next update
+// continues the recurrence with the kept direction; seg more iterations
+__global__ void __launch_bounds__(256) pipe_replace_kernel(PipeVecs v, int seg) {
+    __shared__ double inv[256];
+    for (int m = threadIdx.x; m < 256; m += blockDim.x) inv[m] = m ? 1.0 / m : 0.0;
+    __syncthreads();
+    double acc3[3] = {0.0, 0.0, 0.0};
+    for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < v.nn; L += (int64_t)gridDim.x * blockDim.x) {
+        const double rv = v.r[L], uv = v.u[L], wv = v.w[L], iv = inv[v.mult[L]];
+        v.m[L] = v.minv[L] * wv;
+        acc3[0] = fma(rv * uv, iv, acc3[0]);
+        acc3[1] = fma(wv * uv, iv, acc3[1]);
+        acc3[2] = fma(rv * rv, iv, acc3[2]);
+    }
+    CGState* st = v.st;
+    grid_sum_finalize<3>(acc3, v.partials, v.counter, [&](double (&a)[3]) {
+        st->rho = a[0];
+        st->pap = a[1];
+        st->rr = a[2];
+        st->max_iter = st->iter + seg;
+        const bool conv = a[2] <= st->tol2;
+        st->done = (conv || seg <= 0) ? 1 : 0;
+        st->status = SEM_OK;
+        if (!conv && (!isfinite(a[0]) || !isfinite(a[1]) || !isfinite(a[2]))) {
+            st->done = 1;
+            st->status = SEM_EBREAKDOWN;
+        }
+    });
+}
+
 static PipeVecs pipe_vecs(sem_handle* h) {
     double** v = h->ws.pipe;
     return PipeVecs{h->ws.x, h->ws.r, v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7],
@@ -189,6 +223,29 @@ int launch_pipe_init(sem_handle* h, double tol, int max_iter, cudaStream_t s) {
     if (rc) return rc;
     pipe_init_kernel<<<grid_for(h, h->n_local, 256, 4), 256, 0, s>>>(v, tol, max_iter);
     SEM_LAUNCH_CHECK("pipe_init_kernel");
+    h->launches++;
+    return SEM_OK;
+}
+
+// residual replacement (ws.r = b - A x already computed): u = Minv r, w = A u,
+// s = A p, q = Minv s, z = A q, m = Minv w, the reductions, seg more iterations
+int launch_pipe_replace(sem_handle* h, int seg, cudaStream_t s) {
+    PipeVecs v = pipe_vecs(h);
+    const int grid = grid_for(h, h->n_local, 256, 8);
+    pipe_u_kernel<<<grid, 256, 0, s>>>(v.r, v.minv, v.u, v.nn);
+    SEM_LAUNCH_CHECK("pipe_u_kernel");
+    h->launches++;
+    int rc = launch_ax_local(h, v.u, v.w, SEM_FP64, s);
+    if (!rc) rc = launch_gs(h, v.w, false, true, s);
+    if (!rc) rc = launch_ax_local(h, v.p, v.s, SEM_FP64, s);
+    if (!rc) rc = launch_gs(h, v.s, false, true, s);
+    if (rc) return rc;
+    pipe_u_kernel<<<grid, 256, 0, s>>>(v.s, v.minv, v.q, v.nn);
+    SEM_LAUNCH_CHECK("pipe_u_kernel");
+    h->launches++;
+    if ((rc = launch_ax_local(h, v.q, v.z, SEM_FP64, s)) || (rc = launch_gs(h, v.z, false, true, s))) return rc;
+    pipe_replace_kernel<<<grid_for(h, h->n_local, 256, 4), 256, 0, s>>>(v, seg);
+    SEM_LAUNCH_CHECK("pipe_replace_kernel");
     h->launches++;
     return SEM_OK;
 }

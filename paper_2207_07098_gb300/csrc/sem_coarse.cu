@@ -15,7 +15,9 @@
 // element-corner restriction (the sum of every node's copies, in ascending
 // local index); the last iteration writes x back to the element corners for
 // the prolongation.
-// Deterministic: fixed-order row sums and grid reductions.
+// Deterministic: fixed-order row sums and grid reductions.  The whole CG can
+// also run as one cooperative launch with bounded grid barriers
+// (coarse_cg_persist_kernel, opts.persistent in GMRES mode).
 #include <algorithm>
 #include <vector>
 
@@ -116,6 +118,117 @@ __global__ void __launch_bounds__(256) coarse_update_kernel(T* __restrict__ x, T
     });
 }
 
+// The whole coarse CG (gather and `iters` iterations) as ONE cooperative
+// launch of at most one CTA per SM: the phases are separated by bounded grid
+// barriers (sem_device.cuh), each reduction is a block sum into a slot per
+// CTA, a barrier, and every CTA adding all slots in block order (so all CTAs
+// hold the same value; consecutive reductions alternate between two slot
+// arrays).  The arithmetic per row is that of the three kernels above.
+template <typename T>
+struct CoarseRun {
+    const int* rowptr;
+    const int* col;
+    const T* val;
+    const T* dinv;
+    const int* gptr;
+    const int* gidx;
+    const T* rc;
+    T *x, *r, *z, *p0, *p1, *q, *xl;
+    int nc, iters;
+    double* part;        // [2][kMaxPartials]
+    unsigned int* bar;   // [0] arrivals, [1] generation
+    int* err;
+    long long budget;
+};
+
+template <typename T>
+__device__ __forceinline__ bool coarse_allreduce(T v, double* slot, const CoarseRun<T>& a, double& out) {
+    __shared__ double red[8];
+    __shared__ double tot;
+    __shared__ int s_ok;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wid] = (double)v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < nw; w++) sum += red[w];
+        slot[blockIdx.x] = sum;
+        __threadfence();
+    }
+    if (!grid_barrier(a.bar, a.err, a.budget, &s_ok)) return false;
+    if (wid == 0) {
+        double acc = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) acc += __ldcg(slot + b);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) tot = acc;
+    }
+    __syncthreads();
+    out = tot;
+    __syncthreads();  // red and tot are rewritten by the next reduction
+    return true;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) coarse_cg_persist_kernel(CoarseRun<T> a) {
+    const int stride = gridDim.x * blockDim.x, i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    T d = (T)0;
+    for (int i = i0; i < a.nc; i += stride) {
+        T b = (T)0;
+        for (int c = a.gptr[i]; c < a.gptr[i + 1]; c++) b += a.rc[a.gidx[c]];
+        const T zi = a.dinv[i] * b;
+        a.x[i] = (T)0;
+        a.r[i] = b;
+        a.z[i] = zi;
+        d = fma(b, zi, d);
+    }
+    double rho = 0.0, rho_old = 0.0, pq = 0.0;
+    int k = 0;  // reductions so far: slot array k & 1
+    if (!coarse_allreduce(d, a.part + (size_t)(k++ & 1) * kMaxPartials, a, rho)) return;
+    const T* pp = a.p0;
+    T* pn = a.p1;
+    for (int it = 0; it < a.iters; it++) {
+        const bool first = it == 0;
+        const T beta = (!first && rho_old > 0.0) ? (T)(rho / rho_old) : (T)0;
+        d = (T)0;
+        for (int i = i0; i < a.nc; i += stride) {
+            T acc = (T)0;
+#pragma unroll 4
+            for (int kk = a.rowptr[i]; kk < a.rowptr[i + 1]; kk++) {
+                const int j = a.col[kk];
+                acc = fma(a.val[kk], first ? a.z[j] : fma(beta, pp[j], a.z[j]), acc);
+            }
+            const T pi = first ? a.z[i] : fma(beta, pp[i], a.z[i]);
+            pn[i] = pi;
+            a.q[i] = acc;
+            d = fma(pi, acc, d);
+        }
+        if (!coarse_allreduce(d, a.part + (size_t)(k++ & 1) * kMaxPartials, a, pq)) return;
+        const T alpha = pq > 0.0 ? (T)(rho / pq) : (T)0;
+        const bool last = it == a.iters - 1;
+        d = (T)0;
+        for (int i = i0; i < a.nc; i += stride) {
+            const T xi = fma(alpha, pn[i], a.x[i]);
+            a.x[i] = xi;
+            if (last)
+                for (int c = a.gptr[i]; c < a.gptr[i + 1]; c++) a.xl[a.gidx[c]] = xi;
+            const T ri = fma(-alpha, a.q[i], a.r[i]);
+            const T zi = a.dinv[i] * ri;
+            a.r[i] = ri;
+            a.z[i] = zi;
+            d = fma(ri, zi, d);
+        }
+        if (last) break;
+        rho_old = rho;
+        if (!coarse_allreduce(d, a.part + (size_t)(k++ & 1) * kMaxPartials, a, rho)) return;
+        T* t = const_cast<T*>(pp);
+        pp = pn;
+        pn = t;
+    }
+}
+
 template <typename T>
 static T* csr_vec(const CoarseCsr& cc, int which) {  // x, r, z, p0, p1, q
     T* base = static_cast<T*>(cc.vec[std::is_same<T, float>::value ? 1 : 0]);
@@ -136,11 +249,56 @@ static const T* csr_dinv(const CoarseCsr& cc) {
         return cc.dinv64;
 }
 
+// the coarse CG as one cooperative launch (coarse_cg_persist_kernel); false
+// when the device cannot launch it (the caller then takes the launch chain)
 template <typename T>
-int coarse_csr_solve(sem_handle* h, const T* rc, int iters, cudaStream_t s) {
+static bool coarse_csr_solve_coop(sem_handle* h, const T* rc, int iters, cudaStream_t s, int* rc_out) {
+    CoarseCsr& cc = h->sch.csr;
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        int coop = 0, nb = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
+        if (coop) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, coarse_cg_persist_kernel<T>, 256, 0);
+        per_sm = nb;
+    }
+    if (per_sm < 1) return false;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((cc.nc + 255) / 256, (int64_t)h->sm_count));
+    CoarseRun<T> a;
+    a.rowptr = cc.rowptr;
+    a.col = cc.col;
+    a.val = csr_val<T>(cc);
+    a.dinv = csr_dinv<T>(cc);
+    a.gptr = cc.gptr;
+    a.gidx = cc.gidx;
+    a.rc = rc;
+    a.x = csr_vec<T>(cc, 0);
+    a.r = csr_vec<T>(cc, 1);
+    a.z = csr_vec<T>(cc, 2);
+    a.p0 = csr_vec<T>(cc, 3);
+    a.p1 = csr_vec<T>(cc, 4);
+    a.q = csr_vec<T>(cc, 5);
+    a.xl = static_cast<T*>(cc.xl[std::is_same<T, float>::value ? 1 : 0]);
+    a.nc = cc.nc;
+    a.iters = iters;
+    a.part = cc.partials;
+    a.bar = cc.bar;
+    a.err = device_error_word(h->sch.coarse);
+    a.budget = h->test_stall ? 100000000LL : 4000000000LL;  // ~50 ms / ~2 s at 2 GHz
+    void* args[] = {&a};
+    const cudaError_t e = cudaLaunchCooperativeKernel((const void*)coarse_cg_persist_kernel<T>, grid, 256, args, 0, s);
+    *rc_out = e == cudaSuccess ? SEM_OK : cuda_fail(e, "cudaLaunchCooperativeKernel(coarse_cg_persist_kernel)");
+    h->launches++;
+    return true;
+}
+
+template <typename T>
+int coarse_csr_solve(sem_handle* h, const T* rc, int iters, bool coop, cudaStream_t s) {
     CoarseCsr& cc = h->sch.csr;
     if (cc.nc == 0) return SEM_OK;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((cc.nc + 255) / 256, (int64_t)h->sm_count * 4));
+    int crc = SEM_OK;
+    if (coop && coarse_csr_solve_coop<T>(h, rc, iters, s, &crc)) return crc;
+    // at most one CTA per SM: the launches fit beside the local-solve kernel
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((cc.nc + 255) / 256, (int64_t)h->sm_count));
     T* x = csr_vec<T>(cc, 0);
     T* r = csr_vec<T>(cc, 1);
     T* z = csr_vec<T>(cc, 2);
@@ -164,8 +322,8 @@ int coarse_csr_solve(sem_handle* h, const T* rc, int iters, cudaStream_t s) {
     }
     return SEM_OK;
 }
-template int coarse_csr_solve<double>(sem_handle*, const double*, int, cudaStream_t);
-template int coarse_csr_solve<float>(sem_handle*, const float*, int, cudaStream_t);
+template int coarse_csr_solve<double>(sem_handle*, const double*, int, bool, cudaStream_t);
+template int coarse_csr_solve<float>(sem_handle*, const float*, int, bool, cudaStream_t);
 
 template <typename T>
 const T* coarse_csr_x(const sem_handle* h) {  // element-corner values [E][8]
@@ -190,6 +348,7 @@ void free_coarse_csr(CoarseCsr& cc) {
     cudaFree(cc.st);
     cudaFree(cc.partials);
     cudaFree(cc.counter);
+    cudaFree(cc.bar);
     cc = CoarseCsr{};
 }
 
@@ -303,7 +462,7 @@ int build_coarse_csr(sem_handle* h, const int64_t* cgid, const uint8_t* cmask) {
     double* v64 = nullptr;
     float* v32 = nullptr;
     if ((rc = dalloc(h, &v64, nv)) || (rc = dalloc(h, &v32, nv)) || (rc = dalloc(h, &cc.st, 4)) ||
-        (rc = dalloc(h, &cc.partials, (size_t)kMaxPartials)))
+        (rc = dalloc(h, &cc.partials, (size_t)2 * kMaxPartials)))
         return rc;
     cc.vec[0] = v64;
     cc.vec[1] = v32;
@@ -318,6 +477,8 @@ int build_coarse_csr(sem_handle* h, const int64_t* cgid, const uint8_t* cmask) {
     SEM_CUDA_TRY(cudaMemset(xl32, 0, sizeof(float) * nl));
     SEM_CUDA_TRY(cudaMalloc(&cc.counter, sizeof(unsigned int)));
     SEM_CUDA_TRY(cudaMemset(cc.counter, 0, sizeof(unsigned int)));
+    SEM_CUDA_TRY(cudaMalloc(&cc.bar, 2 * sizeof(unsigned int)));
+    SEM_CUDA_TRY(cudaMemset(cc.bar, 0, 2 * sizeof(unsigned int)));
     return SEM_OK;
 }
 

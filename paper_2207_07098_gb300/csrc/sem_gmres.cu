@@ -418,7 +418,20 @@ static int launch_local_m(sem_handle* h, const TI* r, const double* r_norm2, TI*
     const SchwarzData& sc = h->sch;
     const int64_t E = h->parts[0].E;
     constexpr int W = sch_warps<LX, TC>();
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((E + W - 1) / W, (int64_t)h->sm_count * 16));
+    int64_t cap = (int64_t)h->sm_count * 16;
+    if (MODE == kSchLocal) {
+        // beside the coarse CG: one CTA slot per SM below this kernel's
+        // occupancy stays free, so the coarse launches (at most one CTA per SM)
+        // run while it does
+        static int per_sm = 0;
+        if (per_sm == 0) {
+            int nb = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, schwarz_local_kernel<LX, TI, TC, MODE>, W * 32, 0);
+            per_sm = nb > 1 ? nb - 1 : 1;
+        }
+        cap = (int64_t)h->sm_count * per_sm;
+    }
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((E + W - 1) / W, cap));
     schwarz_local_kernel<LX, TI, TC, MODE><<<grid, W * 32, 0, s>>>(
         r, r_norm2, z, minv, h->mult, sch_table<TC>(sc, 0), sch_table<TC>(sc, 1), sch_table<TC>(sc, 2),
         sch_table<TC>(sc, 3), coarse_rhs<TI>(sc.coarse), E);
@@ -477,7 +490,7 @@ static int launch_schwarz_phase(sem_handle* h, int phase, const TI* r, const dou
 // the precision of the data; the input is r / sqrt(*r_norm2) when r_norm2 (a
 // device scalar) is given
 template <typename TI, typename TC>
-static int apply_schwarz(sem_handle* h, const TI* r, const double* r_norm2, TI* z, cudaStream_t s) {
+static int apply_schwarz(sem_handle* h, const TI* r, const double* r_norm2, TI* z, bool coop, cudaStream_t s) {
     sem_handle* hc = h->sch.coarse;
     const TI* minv;
     if constexpr (std::is_same<TI, double>::value)
@@ -489,7 +502,7 @@ static int apply_schwarz(sem_handle* h, const TI* r, const double* r_norm2, TI* 
     int rc;
     if (!sc.aux) {  // one stream: local part with the restriction, coarse CG, prolongation
         if ((rc = launch_schwarz_phase<TI, TC>(h, kSchAll, r, r_norm2, z, minv, nullptr, s)) ||
-            (rc = coarse_csr_solve<TI>(h, coarse_rhs<TI>(hc), 10, s)))
+            (rc = coarse_csr_solve<TI>(h, coarse_rhs<TI>(hc), 10, coop, s)))
             return rc;
         return launch_schwarz_phase<TI, TC>(h, -1, r, r_norm2, z, minv, xc, s);
     }
@@ -500,7 +513,7 @@ static int apply_schwarz(sem_handle* h, const TI* r, const double* r_norm2, TI* 
     SEM_CUDA_TRY(cudaEventRecord(sc.ev_restrict, s));
     if ((rc = launch_schwarz_phase<TI, TC>(h, kSchLocal, r, r_norm2, z, minv, nullptr, s))) return rc;
     SEM_CUDA_TRY(cudaStreamWaitEvent(sc.aux, sc.ev_restrict, 0));
-    if ((rc = coarse_csr_solve<TI>(h, coarse_rhs<TI>(hc), 10, sc.aux))) return rc;
+    if ((rc = coarse_csr_solve<TI>(h, coarse_rhs<TI>(hc), 10, coop, sc.aux))) return rc;
     SEM_CUDA_TRY(cudaEventRecord(sc.ev_coarse, sc.aux));
     SEM_CUDA_TRY(cudaStreamWaitEvent(s, sc.ev_coarse, 0));
     return launch_schwarz_phase<TI, TC>(h, -1, r, r_norm2, z, minv, xc, s);
@@ -610,8 +623,9 @@ static int apply_operator(sem_handle* h, const T* z, T* w, int op_prec, cudaStre
     return rc ? rc : launch_gs(h, w, std::is_same<T, float>::value, true, s);
 }
 
-// A staged operator kernel that gave up a bounded wait set its handle's error
-// word and returned: the solve ends with SEM_ETIMEOUT, the context intact.
+// A staged operator kernel (fine handle) or the cooperative coarse CG (coarse
+// handle's word) that gave up a bounded wait set the error word and returned:
+// the solve ends with SEM_ETIMEOUT, the context intact.
 static int check_error_words(sem_handle* h, cudaStream_t s) {
     for (sem_handle* q : {h, h->sch.coarse}) {
         int word = 0;
@@ -620,6 +634,7 @@ static int check_error_words(sem_handle* h, cudaStream_t s) {
         if (word) {
             cudaMemset(device_error_word(q), 0, sizeof(int));
             cudaMemset(q->counters, 0, 16 * sizeof(unsigned));
+            if (q == h->sch.coarse) cudaMemset(h->sch.csr.bar, 0, 2 * sizeof(unsigned));
             return fail(SEM_ETIMEOUT, "a bounded device-side wait of the GMRES solve expired");
         }
     }
@@ -674,11 +689,12 @@ struct GmCycle {
 template <typename T>
 static int schwarz_step(sem_handle* h, const sem_solve_opts& o, const T* v, const double* v_norm2, T* z,
                         cudaStream_t s) {
+    const bool coop = o.persistent != 0;  // the coarse CG as one cooperative launch
     if constexpr (std::is_same<T, float>::value)
-        return apply_schwarz<float, float>(h, v, v_norm2, z, s);
+        return apply_schwarz<float, float>(h, v, v_norm2, z, coop, s);
     else
-        return o.precond_precision == SEM_FP32 ? apply_schwarz<double, float>(h, v, v_norm2, z, s)
-                                               : apply_schwarz<double, double>(h, v, v_norm2, z, s);
+        return o.precond_precision == SEM_FP32 ? apply_schwarz<double, float>(h, v, v_norm2, z, coop, s)
+                                               : apply_schwarz<double, double>(h, v, v_norm2, z, coop, s);
 }
 
 // One restart cycle with classical Gram-Schmidt once (orth 1) or twice in the
@@ -983,7 +999,7 @@ SEM_API int sem_schwarz_apply(sem_handle* h, const double* r, double* z, cudaStr
     if (r == z) return fail(SEM_EINVAL, "z must not alias r");
     if (h->nsolve != 1 || !h->sch.coarse) return fail(SEM_EINVAL, "the handle has no Schwarz preconditioner");
     int rc = ensure_workspace(h->sch.coarse, false);
-    return rc ? rc : apply_schwarz<double, double>(h, r, nullptr, z, s);
+    return rc ? rc : apply_schwarz<double, double>(h, r, nullptr, z, false, s);
 }
 
 SEM_API int sem_schwarz_apply32(sem_handle* h, const float* r, float* z, cudaStream_t s) {
@@ -991,7 +1007,7 @@ SEM_API int sem_schwarz_apply32(sem_handle* h, const float* r, float* z, cudaStr
     if (r == z) return fail(SEM_EINVAL, "z must not alias r");
     if (h->nsolve != 1 || !h->sch.coarse) return fail(SEM_EINVAL, "the handle has no Schwarz preconditioner");
     int rc = ensure_workspace(h->sch.coarse, true);
-    return rc ? rc : apply_schwarz<float, float>(h, r, nullptr, z, s);
+    return rc ? rc : apply_schwarz<float, float>(h, r, nullptr, z, false, s);
 }
 
 }  // extern "C"

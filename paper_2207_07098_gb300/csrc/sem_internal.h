@@ -239,11 +239,13 @@ struct CoarseCsr {
     double* st = nullptr;
     double* partials = nullptr;
     unsigned int* counter = nullptr;
+    unsigned int* bar = nullptr;  // grid barrier of the cooperative form: arrivals, generation
 };
 int build_coarse_csr(sem_handle* h, const int64_t* cgid, const uint8_t* cmask);
 void free_coarse_csr(CoarseCsr& cc);
 template <typename T>
-int coarse_csr_solve(sem_handle* h, const T* rc_local, int iters, cudaStream_t s);  // iters Jacobi-PCG from 0
+int coarse_csr_solve(sem_handle* h, const T* rc_local, int iters, bool coop,
+                     cudaStream_t s);  // iters Jacobi-PCG from 0; coop: one cooperative launch
 template <typename T>
 const T* coarse_csr_x(const sem_handle* h);
 
@@ -373,6 +375,10 @@ constexpr int kPipePrec = 101;  // "precision" code of the pipelined CG loop (se
 int ensure_pipe_workspace(sem_handle* h);
 int launch_pipe_init(sem_handle* h, double tol, int max_iter, cudaStream_t s);
 int launch_pipe_iteration(sem_handle* h, cudaStream_t s);
+// residual replacement of a pipelined solve in progress (ws.r = b - A x already
+// computed): the recurrence vectors recomputed from x and p, seg more iterations
+int launch_pipe_replace(sem_handle* h, int seg, cudaStream_t s);
+constexpr int kPipeSeg = 50;  // pipelined iterations between residual replacements
 // native FP64 w = A_L u that returns at once when st->done (inside CG graphs)
 int launch_ax_local_until_done(sem_handle* h, const double* u, double* w, const CGState* st, cudaStream_t s);
 bool pair_cg_available(const sem_handle* h);

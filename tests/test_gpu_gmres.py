@@ -172,14 +172,39 @@ def test_gmres_rejects_bad_precision_options():
 def test_gmres_gram_schmidt_forms(prec):
     """gmres_orth = 1 (Gram-Schmidt once) and 3 (twice within each step)
     reach the true 1e-10 within a few iterations of the default (twice, the
-    second pass lagged one step)."""
+    second pass lagged one step); so does the coarse CG as one cooperative
+    launch (opts.persistent)."""
     m, h1 = _case("deformed", 4, 7)
     P = oracle.Problem(m, h1)
     H = Handle(m, h1, flags=S.SEM_FLAG_SCHWARZ)
     b = W.random_global_rhs(m, 9)
     _, ref = H.solve(b, tol=TOL, mode=S.SEM_MODE_GMRES, precision=prec)
-    for extra in ({"gmres_orth": 1}, {"gmres_orth": 3}):
+    for extra in ({"gmres_orth": 1}, {"gmres_orth": 3}, {"persistent": 1}):
         x, st = H.solve(b, tol=TOL, mode=S.SEM_MODE_GMRES, precision=prec, **extra)
         assert st["status"] == S.SEM_OK and st["relres"] <= TOL, (extra, st)
         assert _oracle_relres(P, x, b) <= 1.05 * TOL, extra
         assert abs(st["iterations"] - ref["iterations"]) <= max(3, ref["iterations"] // 10), (extra, st, ref)
+
+
+def test_schwarz_two_stream_path_is_bit_identical():
+    """After a GMRES solve the handle applies the preconditioner with the coarse
+    CG on a second stream (restriction, local solves and coarse solve split over
+    two streams); the arithmetic is the one-stream path's, so the output is the
+    same to the bit, in FP64 and FP32."""
+    import torch
+    m, h1 = _case("deformed", 3, 7)
+    P = oracle.Problem(m, h1)
+    r = P.gs(W.random_local_field(m, 11), mask=True)
+    outs = {}
+    for warm in (False, True):
+        H = Handle(m, h1, flags=S.SEM_FLAG_SCHWARZ)
+        if warm:
+            H.solve(W.random_global_rhs(m, 2), tol=TOL, mode=S.SEM_MODE_GMRES, precision=S.SEM_FP32)
+        z64 = torch.empty(m.n_local, dtype=torch.float64, device="cuda")
+        z32 = torch.empty(m.n_local, dtype=torch.float32, device="cuda")
+        S.sem_schwarz_apply(H.h, dev(r, torch.float64), z64)
+        S.sem_schwarz_apply32(H.h, dev(r, torch.float32), z32)
+        torch.cuda.synchronize()
+        outs[warm] = (host(z64), host(z32))
+    assert np.array_equal(outs[False][0], outs[True][0])
+    assert np.array_equal(outs[False][1], outs[True][1])

@@ -189,21 +189,25 @@ def test_annulus_periodic_solve():
 def test_full_size_solve_true_residual():
     """The 32^3-element deformed cube (16.8 M points), in the launch
     configuration bench.py times: the mixed-precision solve, the FP64 solve
-    (native operator) and the FP64 solve with the FP32-pair operator and
-    vectors reach 1e-10, checked by the oracle's operator on the full mesh,
-    and agree with each other to solver accuracy."""
+    (native operator), the FP64 solve with the FP32-pair operator and vectors,
+    and the pipelined FP64 solve (whose recurrences need their residual
+    replacements at this size: ~1800 iterations) reach 1e-10, checked by the
+    oracle's operator on the full mesh, and agree with each other to solver
+    accuracy."""
     m, h1, b = W.deformed_cube(32, 7, seed=2)
     H = Handle(m, h1)
     P = oracle.Problem(m, h1)
     xs = {}
-    for key, mode, prec in (("mixed", S.SEM_MODE_MIXED_IR, S.SEM_FP64), ("fp64", S.SEM_MODE_FP64, S.SEM_FP64),
-                            ("pair", S.SEM_MODE_FP64, S.SEM_FP64_PAIR)):
-        x, st = H.solve(b, tol=TOL, mode=mode, precision=prec, inner_tol=1e-2, ir_carry=1)
+    for key, mode, prec, extra in (("mixed", S.SEM_MODE_MIXED_IR, S.SEM_FP64, {}),
+                                   ("fp64", S.SEM_MODE_FP64, S.SEM_FP64, {}),
+                                   ("pair", S.SEM_MODE_FP64, S.SEM_FP64_PAIR, {}),
+                                   ("pipelined", S.SEM_MODE_FP64, S.SEM_FP64, {"pipelined": 1})):
+        x, st = H.solve(b, tol=TOL, mode=mode, precision=prec, inner_tol=1e-2, ir_carry=1, **extra)
         assert st["status"] == S.SEM_OK and st["relres"] <= TOL, (key, st)
         assert _oracle_relres(P, x, b) <= 1.05 * TOL, key
         xs[key] = x
-    assert rel_err(xs["mixed"], xs["fp64"])[0] <= 1e-6
-    assert rel_err(xs["pair"], xs["fp64"])[0] <= 1e-6
+    for key in ("mixed", "pair", "pipelined"):
+        assert rel_err(xs[key], xs["fp64"])[0] <= 1e-6, key
 
 
 def test_bounded_wait_expiry_reports_timeout_and_context_survives():
