@@ -905,6 +905,9 @@ static int solve_gmres_t(sem_handle* h, const sem_solve_opts& o, sem_solve_stats
         rc = o.gmres_orth == 2 ? cycle_lagged<T>(h, o, it, stop, w, ls, &cyc, s)
                                : cycle_classic<T>(h, o, it, stop, w, ls, &cyc, s);
         if (rc) return rc;
+        // a kernel that gave up a bounded wait leaves unfinished vectors, which
+        // can end the cycle as a breakdown: the expired wait is what to report
+        if ((rc = check_error_words(h, s))) return rc;
         if (cyc.status == SEM_EBREAKDOWN) {
             status = SEM_EBREAKDOWN;
             break;

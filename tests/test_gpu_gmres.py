@@ -208,3 +208,48 @@ def test_schwarz_two_stream_path_is_bit_identical():
         outs[warm] = (host(z64), host(z32))
     assert np.array_equal(outs[False][0], outs[True][0])
     assert np.array_equal(outs[False][1], outs[True][1])
+
+
+@pytest.mark.parametrize("prec", [S.SEM_FP64, S.SEM_FP32])
+def test_gmres_edge_cases(prec):
+    """Zero right-hand side: SEM_OK at once, x = 0.  Right-hand sides scaled by
+    1e-30 and 1e30: the same 1e-10 by the oracle's operator (the Krylov
+    vectors are normalised, so the FP32 cycles see unit-sized data).  A NaN in
+    b: SEM_EBREAKDOWN.  max_iter too small: SEM_ENOTCONV with the true
+    residual above the tolerance."""
+    m, h1 = _case("deformed", 3, 5)
+    P = oracle.Problem(m, h1)
+    H = Handle(m, h1, flags=S.SEM_FLAG_SCHWARZ)
+    zero = np.zeros(m.n_local)
+    x, st = H.solve(zero, tol=TOL, mode=S.SEM_MODE_GMRES, precision=prec)
+    assert st["status"] == S.SEM_OK and st["iterations"] == 0 and not np.any(x), st
+    b = W.random_global_rhs(m, 17)
+    for scale in (1e-30, 1e30):
+        x, st = H.solve(b * scale, tol=TOL, mode=S.SEM_MODE_GMRES, precision=prec)
+        assert st["status"] == S.SEM_OK and st["relres"] <= TOL, (scale, st)
+        assert _oracle_relres(P, x, b * scale) <= 1.05 * TOL, scale
+    bad = b.copy()
+    bad[np.flatnonzero(m.mask)[4]] = np.nan
+    x, st = H.solve(bad, tol=TOL, mode=S.SEM_MODE_GMRES, precision=prec)
+    assert st["status"] == S.SEM_EBREAKDOWN, st
+    x, st = H.solve(b, tol=TOL, mode=S.SEM_MODE_GMRES, precision=prec, max_iter=5)
+    assert st["status"] == S.SEM_ENOTCONV and st["relres"] > TOL and st["iterations"] <= 5, st
+
+
+def test_gmres_bounded_wait_expiry_reports_timeout():
+    """Failure detection without a fault: with SEM_FLAG_TEST_STALL the
+    bulk-staged operator kernels announce more bytes than they copy, their
+    bounded waits expire (~50 ms), and the GMRES solve reports SEM_ETIMEOUT at
+    its next check; the context stays usable."""
+    m, h1 = _case("deformed", 3, 7)
+    P = oracle.Problem(m, h1)
+    b = W.random_global_rhs(m, 4)
+    H = Handle(m, h1, flags=S.SEM_FLAG_SCHWARZ | S.SEM_FLAG_VARIANT(2) | S.SEM_FLAG_TEST_STALL)
+    for prec in (S.SEM_FP64, S.SEM_FP32):
+        with pytest.raises(S.SemError) as ei:
+            H.solve(b, tol=TOL, mode=S.SEM_MODE_GMRES, precision=prec, gmres_restart=4, max_iter=8)
+        assert ei.value.status == S.SEM_ETIMEOUT, prec
+    H.close()
+    H2 = Handle(m, h1, flags=S.SEM_FLAG_SCHWARZ)
+    x, st = H2.solve(b, tol=TOL, mode=S.SEM_MODE_GMRES, precision=S.SEM_FP32)
+    assert st["status"] == S.SEM_OK and _oracle_relres(P, x, b) <= 1.05 * TOL
