@@ -10,7 +10,9 @@
 // six factors G are streamed once per point (coalesced along i), the
 // weighted derivatives wr, ws go back to shared memory and the transposed
 // contraction produces w.
+#include <algorithm>
 #include <type_traits>
+#include <vector>
 
 #include "sem_ax.cuh"
 #include "sem_ax_df.cuh"
@@ -224,52 +226,64 @@ int autotune_ax(sem_handle* h, bool fp32, cudaStream_t s) {
     SEM_CUDA_TRY(cudaEventCreate(&e1));
     for (const MeshPart& p : h->parts) {
         if (h->ax_variant[fp32][p.lx] >= 0) continue;
-        float best = 1e30f;
-        int best_v = 0;
+        // candidates: every variant that fits; each is warmed up, then all are
+        // timed in three interleaved rounds (best round per variant), so a
+        // clock ramp or a noisy launch does not decide the choice
+        auto run = [&](int v, int dry) -> int {
+            if (fp32) {
+                AxParams<float> a = {};
+                a.u = h->ws.z32 + p.loc_off;
+                a.w = h->ws.w32 + p.loc_off;
+                a.G = h->G32 + 6 * p.loc_off;
+                a.D = h->D32[p.lx];
+                a.E = p.E;
+                a.dry = dry;
+                a.mass = h->hmass32 ? h->hmass32 + p.loc_off : nullptr;
+                return dispatch_variant<float>(h, p.lx, a, false, v, s);
+            }
+            AxParams<double> a = {};
+            a.u = h->ws.z + p.loc_off;
+            a.w = h->ws.w + p.loc_off;
+            a.G = h->G64 + 6 * p.loc_off;
+            a.D = h->D64[p.lx];
+            a.E = p.E;
+            a.dry = dry;
+            a.mass = h->hmass64 ? h->hmass64 + p.loc_off : nullptr;
+            return dispatch_variant<double>(h, p.lx, a, false, v, s);
+        };
+        std::vector<int> cand;
         for (int v = 0; v <= kTcVariant; v++) {
             if (v > kBulkVariantsMax && !(v == kTcVariant && fp32 && p.lx == 8)) continue;
             if (v > 0 && v <= kBulkVariantsMax && (!bulk_fits(p.lx, v, fp32) || h->hmass64)) continue;
-            int rc2;
-            auto run = [&](int dry) -> int {
-                if (fp32) {
-                    AxParams<float> a = {};
-                    a.u = h->ws.z32 + p.loc_off;
-                    a.w = h->ws.w32 + p.loc_off;
-                    a.G = h->G32 + 6 * p.loc_off;
-                    a.D = h->D32[p.lx];
-                    a.E = p.E;
-                    a.dry = dry;
-                    a.mass = h->hmass32 ? h->hmass32 + p.loc_off : nullptr;
-                    return dispatch_variant<float>(h, p.lx, a, false, v, s);
-                }
-                AxParams<double> a = {};
-                a.u = h->ws.z + p.loc_off;
-                a.w = h->ws.w + p.loc_off;
-                a.G = h->G64 + 6 * p.loc_off;
-                a.D = h->D64[p.lx];
-                a.E = p.E;
-                a.dry = dry;
-                a.mass = h->hmass64 ? h->hmass64 + p.loc_off : nullptr;
-                return dispatch_variant<double>(h, p.lx, a, false, v, s);
-            };
-            rc2 = run(1);
-            if (rc2) {  // does not fit / cannot be resident: not a candidate
+            if (run(v, 1)) {  // does not fit / cannot be resident: not a candidate
                 set_error("");
                 continue;
             }
-            for (int w = 0; w < 2 && !rc2; w++) rc2 = run(0);
-            cudaEventRecord(e0, s);
-            for (int w = 0; w < 5 && !rc2; w++) rc2 = run(0);
-            cudaEventRecord(e1, s);
-            if (rc2) break;
-            SEM_CUDA_TRY(cudaEventSynchronize(e1));
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) {
-                best = ms;
-                best_v = v;
-            }
+            int rc2 = SEM_OK;
+            for (int w = 0; w < 2 && !rc2; w++) rc2 = run(v, 0);
+            if (rc2) return rc2;
+            cand.push_back(v);
         }
+        std::vector<float> best_ms(cand.size(), 1e30f);
+        for (int round = 0; round < 3; round++)
+            for (size_t c = 0; c < cand.size(); c++) {
+                int rc2 = SEM_OK;
+                cudaEventRecord(e0, s);
+                for (int w = 0; w < 5 && !rc2; w++) rc2 = run(cand[c], 0);
+                cudaEventRecord(e1, s);
+                if (rc2) return rc2;
+                SEM_CUDA_TRY(cudaEventSynchronize(e1));
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                best_ms[c] = std::min(best_ms[c], ms);
+            }
+        int best_v = 0;
+        float best = 1e30f;
+        for (size_t c = 0; c < cand.size(); c++)
+            if (best_ms[c] < best) {
+                best = best_ms[c];
+                best_v = cand[c];
+            }
         h->ax_variant[fp32][p.lx] = best_v;
     }
     cudaEventDestroy(e0);
