@@ -325,7 +325,7 @@ def run_ours(args):
     # dominant kernel: the fused p-update + ax_helm launch (K-A) of the CG loop
     samples = [s["ax_ms"] for s in stats if s["ax_samples"] > 0]
     ax_ms = statistics.mean(samples) if samples else None
-    ka_bytes_pt = 9 * (4 if args.solver in ("mixed", "gmres") else 8)  # read z, p, 6 G; write p, w (h1 folded)
+    ka_bytes_pt = 10 * (4 if args.solver in ("mixed", "gmres") else 8)  # read z, p, 6 G; write p, w (h1 folded)
     ka_bytes = ka_bytes_pt * n
     achieved = ka_bytes / (ax_ms * 1e-3) / 1e9 if ax_ms else None
     variant = stats[-1].get("ax_variant", 0)
@@ -335,6 +335,7 @@ def run_ours(args):
              f"ax_df_kernel<{m.lx},true>" if variant == 5 else
              f"ax_dfl_kernel<{m.lx},true>" if variant == 6 else
              "ax_tc_kernel<true>" if variant == 8 else
+             f"ax_ln_kernel<{m.lx},true>" if variant == 9 else
              f"ax_bulk_kernel<{tname},{m.lx},{cfgs[variant][0]},{cfgs[variant][1]},true>")
     traffic = _traffic_for(kname, f"deformed_cube_{args.n}^3_N{args.order}")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -448,15 +449,17 @@ def _extras(S, torch, h, m, bd, n, args, peak, stats, ms_timed):
                        "smooth cancelling ones; fp32_tc_split: BF16 three-slice tensor-core contractions, "
                        "FP32 accuracy class")
     ex["ax_helm_only"] = axr
-    # every operator variant (pinned at set-up), plain ax_helm: 0..4 native FP64 and FP32, 5..6 FP32-pair
+    # every operator variant (pinned at set-up), plain ax_helm: 0..4 native FP64 and FP32, 5..6 FP32-pair,
+    # 8 tensor-core FP32, 9 native FP64 line transforms
     var = {}
-    for v in (0, 1, 2, 3, 4, 5, 6, 8):
-        if v == 8 and m.lx != 8:
+    for v in (0, 1, 2, 3, 4, 5, 6, 8, 9):
+        if (v == 8 and m.lx != 8) or (v == 9 and m.lx % 2):
             continue
         hv = S.sem_setup(m.E, m.lx, m.coords, m.gid, m.mask, None, S.SEM_FLAG_VARIANT(v))
         row = {}
         kinds = ((("fp64", S.SEM_FP64, torch.float64, 64), ("fp32", S.SEM_FP32, torch.float32, 32)) if v <= 4 else
                  (("fp32", S.SEM_FP32, torch.float32, 32),) if v == 8 else
+                 (("fp64", S.SEM_FP64, torch.float64, 64),) if v == 9 else
                  (("fp64_pair", S.SEM_FP64_PAIR, torch.float64, 64),))
         for name, prec, dt, bpp in kinds:
             u = torch.randn(n, dtype=dt, device="cuda")

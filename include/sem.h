@@ -67,7 +67,7 @@ typedef enum sem_status {
 /* Arithmetic of one operator application or of the inner solve. */
 typedef enum sem_precision {
     SEM_FP64 = 0,        /* double data, FP64 arithmetic (unit roundoff 2^-53): the fastest of
-                            the native FP64 kernels (variants 0..4, autotuned per handle); holds
+                            the native FP64 kernels (variants 0..4 and 9, autotuned per handle); holds
                             the 1e-12 relative parity bar on every input tested, including
                             smooth fields whose sums cancel */
     SEM_FP32 = 1,        /* float data, FP32 arithmetic and accumulation */
@@ -213,7 +213,10 @@ typedef struct sem_solve_stats {
                                  of every order (orders up to lx = 10);
                                  8 = BF16 split-precision tensor-core contractions for
                                  FP32 data (SEM_TC_SPLIT; lx = 8; an FP32 autotuning
-                                 candidate) */
+                                 candidate);
+                                 9 = native FP64 with even/odd line transforms (even
+                                 lx <= 12; an FP64 autotuning candidate, not for
+                                 Helmholtz handles) */
     double relres_start;      /* true relative residual of the start (after projection, when on) */
     int launches_per_iteration;  /* kernel launches of one CG iteration: 3 for one mesh
                                  (operator, gather-scatter, update), 0 when the CG ran
@@ -233,8 +236,8 @@ typedef struct sem_mesh_desc {
 } sem_mesh_desc;
 
 /* Set-up flag: pin operator kernel variant v: 0..4 for SEM_FP64 and SEM_FP32,
- * 5 or 6 for SEM_FP64_PAIR, 8 for SEM_FP32 (the other precisions stay
- * autotuned). */
+ * 5 or 6 for SEM_FP64_PAIR, 8 for SEM_FP32, 9 for SEM_FP64 (the other
+ * precisions stay autotuned). */
 #define SEM_FLAG_VARIANT(v) ((int)(((v) + 1) & 0xF))
 
 /* Set-up flag for testing failure detection: the bulk-staged operator kernels

@@ -27,7 +27,8 @@ SEM_FLAG_SCHWARZ = 0x400
 
 def SEM_FLAG_VARIANT(v: int) -> int:
     """Set-up flag pinning operator kernel variant v, as in sem.h: 0..4 for
-    SEM_FP64 and SEM_FP32, 5 or 6 for SEM_FP64_PAIR, 8 for SEM_FP32."""
+    SEM_FP64 and SEM_FP32, 5 or 6 for SEM_FP64_PAIR, 8 for SEM_FP32, 9 for
+    SEM_FP64."""
     return (v + 1) & 0xF
 STATUS_NAMES = {0: "SEM_OK", 1: "SEM_EINVAL", 2: "SEM_ENOMEM", 3: "SEM_ECUDA", 4: "SEM_ENOTCONV",
                 5: "SEM_EBREAKDOWN", 6: "SEM_ESTAGNATE", 7: "SEM_ETIMEOUT"}

@@ -34,9 +34,11 @@ int ax_variant_for(const sem_handle* h, int lx, int cls) {
         return lx <= 12 ? kDfVariant : ax_variant_for(h, lx, kClsF64);
     }
     if (cls == kClsF32 && v == kTcVariant && lx == 8) return v;
-    // the bulk-staged kernels carry no Helmholtz mass term (it would cost the
-    // Poisson hot path registers): a Helmholtz handle takes the slab kernel
+    // the bulk-staged and line-transform kernels carry no Helmholtz mass term
+    // (it would cost the Poisson hot path registers): a Helmholtz handle
+    // takes the slab kernel
     if (h->hmass64) return 0;
+    if (cls == kClsF64 && v == kLnVariant && bulk_supported(lx)) return v;
     return (v > 0 && v <= kBulkVariantsMax && bulk_fits(lx, v, cls == kClsF32)) ? v : 0;
 }
 
@@ -80,10 +82,13 @@ static int dispatch_variant(sem_handle* h, int lx, AxParams<T> a, bool fused, in
             return dispatch_ax_dfl_entry(h, lx, d, fused, s);
         }
     }
+    if constexpr (std::is_same<T, double>::value) {
+        if (variant == kLnVariant && bulk_supported(lx) && !a.mass) return dispatch_ax_ln_entry(h, lx, a, fused, s);
+    }
     if constexpr (std::is_same<T, float>::value) {
         if (variant == kTcVariant && lx == 8) return dispatch_ax_tc(h, lx, a, fused, s);
     }
-    if (variant == kDfVariant || variant == kDflVariant || variant == kTcVariant) variant = 0;
+    if (variant == kDfVariant || variant == kDflVariant || variant == kTcVariant || variant == kLnVariant) variant = 0;
     a.variant = variant;
     a.err = device_error_word(h);
     a.wait_budget = h->test_stall ? 100000000LL : 4000000000LL;  // ~50 ms / ~2 s at 2 GHz
@@ -195,7 +200,7 @@ int prepare_cg_kernels(sem_handle* h) {
                     AxParams<double> a = {};
                     a.dry = 1;
                     a.G = h->G64;
-                    if (v == kDfVariant || v == kDflVariant) {
+                    if (v == kDfVariant || v == kDflVariant || v == kLnVariant) {
                         rc = dispatch_variant<double>(h, p.lx, a, fused != 0, v, 0);
                     } else {
                         a.variant = v;
@@ -212,7 +217,9 @@ int prepare_cg_kernels(sem_handle* h) {
 }
 
 // Autotuner: time every operator variant of the class that fits (shared-slab
-// staging and the bulk-staged (elements per CTA, stages) configurations) on
+// staging, the bulk-staged (elements per CTA, stages) configurations, the
+// tensor-core form (FP32, lx = 8) and the line-transform form (native FP64,
+// even lx <= 12)) on
 // this handle's own factors with the plain kernel, a few launches each after a
 // warm-up, and keep the fastest per order (FP32 class, or native FP64 class).
 // The fused CG kernel uses the same choice.  Runs once per handle and class,
@@ -252,8 +259,10 @@ int autotune_ax(sem_handle* h, bool fp32, cudaStream_t s) {
             return dispatch_variant<double>(h, p.lx, a, false, v, s);
         };
         std::vector<int> cand;
-        for (int v = 0; v <= kTcVariant; v++) {
-            if (v > kBulkVariantsMax && !(v == kTcVariant && fp32 && p.lx == 8)) continue;
+        for (int v = 0; v <= kLnVariant; v++) {
+            if (v > kBulkVariantsMax && !(v == kTcVariant && fp32 && p.lx == 8) &&
+                !(v == kLnVariant && !fp32 && bulk_supported(p.lx) && !h->hmass64))
+                continue;
             if (v > 0 && v <= kBulkVariantsMax && (!bulk_fits(p.lx, v, fp32) || h->hmass64)) continue;
             if (run(v, 1)) {  // does not fit / cannot be resident: not a candidate
                 set_error("");

@@ -310,11 +310,23 @@ __global__ void __launch_bounds__(BulkCfg<T, LX, EPC, NST, FUSED>::THREADS)
             T acc = T(0);
             T row[LX];
             load_row<T, LX>(sr + so + k * N2 + j * LX, row);
+            if constexpr (sizeof(T) == 4 && FUSED) {
+                // the three chains of ax_group's FP32 CG form, in its order
+                T ar = T(0), as = T(0), at = T(0);
 #pragma unroll
-            for (int l = 0; l < LX; l++) {
-                acc = fma(Dci[l], row[l], acc);
-                acc = fma(Dcj[l], ss[so + k * N2 + l * LX + i], acc);
-                acc = fma(bulk_d<T>(LX, l * LX + k), wt[l], acc);
+                for (int l = 0; l < LX; l++) {
+                    ar = fma(Dci[l], row[l], ar);
+                    as = fma(Dcj[l], ss[so + k * N2 + l * LX + i], as);
+                    at = fma(bulk_d<T>(LX, l * LX + k), wt[l], at);
+                }
+                acc = (ar + as) + at;
+            } else {
+#pragma unroll
+                for (int l = 0; l < LX; l++) {
+                    acc = fma(Dci[l], row[l], acc);
+                    acc = fma(Dcj[l], ss[so + k * N2 + l * LX + i], acc);
+                    acc = fma(bulk_d<T>(LX, l * LX + k), wt[l], acc);
+                }
             }
             if (valid) {
                 st_keep<FUSED>(a.w + base + k * N2, acc);

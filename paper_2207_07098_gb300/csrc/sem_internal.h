@@ -21,6 +21,7 @@ constexpr int kDfVariant = 5;        // FP64 data, FP32-pair arithmetic (FP64 pr
 constexpr int kDflVariant = 6;       // same, line-transform form with even/odd splitting (even lx)
 constexpr int kMultiVariant = 7;     // batches: one slab launch over the groups of every order
 constexpr int kTcVariant = 8;        // FP32 data, BF16 split-precision tensor-core contractions (lx = 8)
+constexpr int kLnVariant = 9;        // native FP64, line transforms with even/odd splitting (even lx <= 12)
 // operator classes, each with its own tuned or pinned variant per order:
 // native FP64 (variants 0..4), FP32 (0..4), FP32-pair arithmetic on FP64 data (5, 6)
 constexpr int kClsF64 = 0, kClsF32 = 1, kClsPair = 2;

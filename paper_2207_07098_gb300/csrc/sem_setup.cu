@@ -401,14 +401,14 @@ static int setup_common(sem_handle** out, int nsolve, const sem_mesh_desc* meshe
     if (n_local >= ((int64_t)1 << 31) - 64)
         return fail(SEM_EINVAL, "n_local must be below 2^31 (32-bit local indices)");
     const int forced = (flags & 0xF) - 1;  // pinned operator variant, -1 = autotune
-    if (forced > kTcVariant || forced == kMultiVariant) return fail(SEM_EINVAL, "operator variant out of range");
+    if (forced > kLnVariant || forced == kMultiVariant) return fail(SEM_EINVAL, "operator variant out of range");
     sem_handle* h = new sem_handle();
-    // a pinned variant 0..4 serves the FP64 and FP32 classes, 5 or 6 the pair class;
-    // the other classes stay autotuned
+    // a pinned variant 0..4 serves the FP64 and FP32 classes, 5 or 6 the pair
+    // class, 8 the FP32 class, 9 the FP64 class; the other classes stay autotuned
     for (int cls = 0; cls < 3; cls++) {
         const bool pair_pin = forced == kDfVariant || forced == kDflVariant;
         const bool applies = forced >= 0 && ((cls == kClsPair) == pair_pin) &&
-                             (forced != kTcVariant || cls == kClsF32);
+                             (forced != kTcVariant || cls == kClsF32) && (forced != kLnVariant || cls == kClsF64);
         for (int& v : h->ax_variant[cls]) v = applies ? forced : -1;
     }
     h->test_stall = (flags & SEM_FLAG_TEST_STALL) ? 1 : 0;
@@ -569,6 +569,16 @@ static int setup_common(sem_handle** out, int nsolve, const sem_mesh_desc* meshe
                         cf[((dir * 2 + 1) * 2 + 1) * P * P + i * P + m] = (float)(B - (double)Bh);
                     }
             if ((rc = dfl_set_coef(cf.data(), lx))) return bail(rc);
+            // the same tables in FP64 for the native line-transform operator: [dir][A/B][P][P]
+            std::vector<double> cd(4 * P * P);
+            for (int dir = 0; dir < 2; dir++)
+                for (int i = 0; i < P; i++)
+                    for (int m = 0; m < P; m++) {
+                        auto M = [&](int r, int c) { return dir == 0 ? Dh[r * lx + c] : Dh[c * lx + r]; };
+                        cd[(dir * 2 + 0) * P * P + i * P + m] = 0.5 * (M(i, m) - M(i, N - m));
+                        cd[(dir * 2 + 1) * P * P + i * P + m] = 0.5 * (M(i, m) + M(i, N - m));
+                    }
+            if ((rc = ln_set_coef(cd.data(), lx))) return bail(rc);
         }
     }
     // geometry, mass, Jacobi diagonal: one part at a time through a staging buffer

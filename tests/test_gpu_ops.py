@@ -214,6 +214,56 @@ def test_ax_fp64_default_and_pair_kernels_on_cancelling_fields(variant, field):
     assert p2 <= bar and pinf <= bar, (p2, pinf)
 
 
+LN_CASES = [("affine", (1, 1, 1), 3), ("jitter", (3, 3, 2), 3), ("deformed", (5, 3, 2), 5), ("jitter", (3, 3, 3), 7),
+            ("deformed", (5, 4, 3), 7), ("annulus", (8, 3, 2), 7), ("jitter", (2, 2, 3), 9), ("deformed", (2, 2, 1), 11),
+            ("deformed", (3, 2, 1), 6)]
+
+
+def _native_pointwise_bound(P, u):
+    # two FP64 evaluations of the same sums in different orders (direct
+    # contractions against even/odd line transforms): each output within a few
+    # dozen rounding errors of the magnitude |D^T||h1 G||D||u| of its terms
+    mag = P.ax_local_abs(u)
+    return 64.0 * 2.0 ** -53 * (mag + 2.0 ** -60 * mag.max())
+
+
+@pytest.mark.parametrize("kind,dims,N", LN_CASES)
+def test_ax_fp64_line_transform_variant(kind, dims, N):
+    """Variant 9 (native FP64 with even/odd line transforms; even lx, odd
+    orders fall back to the slab kernel): the 1e-12 bar against the oracle,
+    local and assembled, and every output within the FP64 rounding bound of
+    the slab kernel's (SEM_FP64_NATIVE on the same handle and factors)."""
+    m, h1 = _case(kind, dims, N)
+    P = oracle.Problem(m, h1)
+    H = Handle(m, h1, flags=S.SEM_FLAG_VARIANT(9))
+    u = W.random_local_field(m, 26)
+    w9 = H.ax(u, S.SEM_FP64, assemble=0)
+    e2, einf = rel_err(w9, P.ax_local(u))
+    assert e2 <= TOL_AX64 and einf <= TOL_AX64, (e2, einf)
+    w0 = H.ax(u, S.SEM_FP64_NATIVE, assemble=0)
+    assert np.all(np.abs(w9 - w0) <= _native_pointwise_bound(P, u))
+    if (N + 1) % 2 == 1:
+        assert np.array_equal(w9, w0)  # odd lx: the slab kernel itself
+    uc = W.random_local_field(m, 27, continuous=True)
+    e2, einf = rel_err(H.ax(uc, S.SEM_FP64, assemble=1), P.ax(uc))
+    assert e2 <= TOL_AX64 and einf <= TOL_AX64, (e2, einf)
+
+
+def test_ax_fp64_line_transform_on_cancelling_field():
+    """Variant 9 on the smooth field whose element sums cancel (8^3 deformed
+    elements, N = 7): the same 1e-12 bar as the slab kernel, and pointwise
+    within the FP64 rounding bound of it."""
+    m, h1 = _case("deformed", (8, 8, 8), 7)
+    P = oracle.Problem(m, h1)
+    H = Handle(m, h1, flags=S.SEM_FLAG_VARIANT(9))
+    u = W.forcing_sines(m)
+    w9 = H.ax(u, S.SEM_FP64, assemble=0)
+    assert np.all(np.abs(w9 - H.ax(u, S.SEM_FP64_NATIVE, assemble=0)) <= _native_pointwise_bound(P, u))
+    e2, einf = rel_err(H.ax(u, S.SEM_FP64, assemble=1), P.ax(u))
+    print(f"smooth 8^3: variant 9 vs oracle {e2:.2e} / {einf:.2e} (2-norm / max)")
+    assert e2 <= TOL_AX64 and einf <= TOL_AX64, (e2, einf)
+
+
 def test_ax_deterministic():
     m, h1 = _case("jitter", (4, 3, 3), 7)
     H = Handle(m, h1)
@@ -233,9 +283,10 @@ def test_ax_full_size_deformed_cube():
     P = oracle.Problem(m, h1)
     H = Handle(m, h1)
     u = W.random_local_field(m, 18, continuous=True)
-    e2, einf = rel_err(H.ax(u), P.ax(u))
+    ref_u = P.ax(u)
+    e2, einf = rel_err(H.ax(u), ref_u)
     assert e2 <= TOL_AX64 and einf <= TOL_AX64, (e2, einf)
-    e2, einf = rel_err(H.ax(u, S.SEM_FP32), P.ax(u))
+    e2, einf = rel_err(H.ax(u, S.SEM_FP32), ref_u)
     assert e2 <= 1e-5, e2
     # the smooth field sin(pi x) sin(pi y) sin(pi z): on 32^3 elements its element
     # sums cancel by a factor kappa = ||QQ^T |D^T||h1 G||D||u| || / ||A u|| of
@@ -252,6 +303,13 @@ def test_ax_full_size_deformed_cube():
     e2, einf = rel_err(w, ref)
     print(f"smooth 32^3: kappa {kappa:.3e}, FP64 operator vs oracle {e2:.2e} / {einf:.2e} (2-norm / max)")
     assert kappa > 1e4
+    assert e2 <= max(TOL_AX64, 16.0 * 2.0 ** -53 * kappa), (e2, kappa)
+    # the line-transform FP64 operator (variant 9) at full size, same bars
+    H9 = Handle(m, h1, flags=S.SEM_FLAG_VARIANT(9))
+    e2, einf = rel_err(H9.ax(u), ref_u)
+    assert e2 <= TOL_AX64 and einf <= TOL_AX64, (e2, einf)
+    e2, einf = rel_err(H9.ax(us), ref)
+    print(f"smooth 32^3: variant 9 vs oracle {e2:.2e} / {einf:.2e}")
     assert e2 <= max(TOL_AX64, 16.0 * 2.0 ** -53 * kappa), (e2, kappa)
 
 

@@ -88,11 +88,12 @@ def test_mixed_ir_carried_direction(inner_tol):
     assert st_r["iterations"] > st["iterations"], (st_r, st)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 9])
 def test_solves_with_each_operator_variant(variant):
     """A pinned variant 0..4 serves the FP64 and FP32 operators, 5 or 6 the
-    FP32-pair one (SEM_FP64_PAIR); every solve reaches 1e-10 by the oracle's
-    residual with the variant it reports."""
+    FP32-pair one (SEM_FP64_PAIR), 9 the FP64 one (native line transforms);
+    every solve reaches 1e-10 by the oracle's residual with the variant it
+    reports."""
     m, h1, P, b = _deformed_case(5, 7)
     H = Handle(m, h1, flags=S.SEM_FLAG_VARIANT(variant))
     runs = [(S.SEM_MODE_FP64, S.SEM_FP64), (S.SEM_MODE_MIXED_IR, S.SEM_FP64), (S.SEM_MODE_FP64, S.SEM_FP64_PAIR)]
@@ -101,10 +102,11 @@ def test_solves_with_each_operator_variant(variant):
         assert st["status"] == S.SEM_OK and st["relres"] <= TOL, st
         if prec == S.SEM_FP64_PAIR:
             # a pinned native variant leaves the pair class on its own default (6 for even lx)
-            assert st["ax_variant"] == (variant if variant >= 5 else 6)
+            assert st["ax_variant"] == (variant if variant in (5, 6) else 6)
         elif mode == S.SEM_MODE_FP64:
             # a pinned bulk variant too large for FP64 shared memory falls back to 0
-            assert st["ax_variant"] in ((variant, 0) if variant <= 4 else (0, 1, 2, 3, 4))
+            assert st["ax_variant"] in ((variant, 0) if variant <= 4 else (9,) if variant == 9 else
+                                        (0, 1, 2, 3, 4, 9))
         else:
             assert (st["ax_variant"] == variant) if variant <= 4 else (0 <= st["ax_variant"] <= 4)
         assert _oracle_relres(P, x, b) <= 1.05 * TOL
