@@ -292,8 +292,9 @@ static int launch_iteration(sem_handle* h, int precision, cudaStream_t s) {
     return rc ? rc : launch_kb_kc(h, precision, s);
 }
 
-static int get_graph(sem_handle* h, int precision, int chunk, cudaGraphExec_t* out) {
-    GraphCache& g = h->graph;
+// The CG loop graph of `chunk` iterations in cache `g`; with `events`, the
+// second K-A of the chunk is bracketed by the handle's timing events.
+static int get_graph(sem_handle* h, int precision, int chunk, cudaGraphExec_t* out, GraphCache& g, bool events) {
     // (the pair-form loop has its own precision code and always the line kernel)
     const int variant = precision == kPairPrec   ? kDflVariant
                         : precision == kPipePrec ? ax_variant_for(h, h->parts[0].lx, kClsF64)
@@ -318,7 +319,7 @@ static int get_graph(sem_handle* h, int precision, int chunk, cudaGraphExec_t* o
     int rc = SEM_OK;
     // the K-A that is timed: the second of the chunk (it follows K-C inside the
     // graph, as in steady state; the first one starts after the host check)
-    const int timed = chunk > 1 ? 1 : 0;
+    const int timed = !events ? -1 : chunk > 1 ? 1 : 0;
     for (int it = 0; it < chunk && rc == SEM_OK; it++) {
         if (it == timed && cudaEventRecordWithFlags(h->ax_ev[0], cs, cudaEventRecordExternal) != cudaSuccess)
             rc = fail(SEM_ECUDA, "event record");
@@ -353,36 +354,62 @@ struct AxTiming {
     int samples = 0;
 };
 
+// Iterations of the tail graph: the loop's predicted last iterations run in
+// graphs of this size, so a run that ends inside a chunk launches few
+// iterations past its end (kernels of a finished solve still launch, then
+// return at once).
+constexpr int kTailChunk = 4;
+
 // Run CG iterations on state slot `slot` until done.  Returns SEM_OK or an
 // error; the solve status is in the state.  With graphs, the duration of one
-// K-A of every graph launch (the second of the chunk) is added to `tm`; a
-// launch that ends the solve before that K-A ran adds nothing.
+// K-A of every full-chunk graph launch (the second of the chunk) is added to
+// `tm`; a launch that ends the solve before that K-A ran adds nothing.
+// `expect` > 0 predicts the iterations of this run (a refinement step takes
+// about as many as the one before): once fewer than a chunk remain by that
+// count, the loop launches just enough tail graphs to reach it; past the
+// predicted end it launches 1, 2, 4, ... tail graphs per check (up to a
+// chunk).  Each check reads the state and the device error word back with
+// one synchronisation.
 static int run_cg_loop(sem_handle* h, int precision, const sem_solve_opts& o, int slot, cudaStream_t s,
-                       CGState* out, AxTiming* tm) {
+                       CGState* out, AxTiming* tm, int expect) {
     const int chunk = std::max(1, std::min(o.graph_chunk, 1024));
-    cudaGraphExec_t exec = nullptr;
+    cudaGraphExec_t exec = nullptr, tail = nullptr;
     if (o.use_graph) {
-        int rc = get_graph(h, precision, chunk, &exec);
+        int rc = get_graph(h, precision, chunk, &exec, h->graph, true);
+        if (!rc && expect > 0 && chunk > kTailChunk) rc = get_graph(h, precision, kTailChunk, &tail, h->graph_tail, false);
         if (rc) return rc;
     }
-    SEM_CUDA_TRY(cudaMemcpyAsync(out, h->state + slot, sizeof(CGState), cudaMemcpyDeviceToHost, s));
+    LoopReadback* rb = h->loop_host;
+    SEM_CUDA_TRY(cudaMemcpyAsync(&rb->st, h->state + slot, sizeof(CGState), cudaMemcpyDeviceToHost, s));
     SEM_CUDA_TRY(cudaStreamSynchronize(s));
-    const int64_t max_rounds = (int64_t)out->max_iter / chunk + 3;
+    *out = rb->st;
+    const int iter0 = out->iter;
+    int over = 0;  // checks past the predicted end
+    const int64_t max_rounds = (int64_t)out->max_iter / (tail ? kTailChunk : chunk) + 3;
     for (int64_t round = 0; !out->done && round < max_rounds; round++) {
         const int iter_before = out->iter;
-        if (exec) {
+        const int left = expect - (out->iter - iter0);  // predicted iterations still to run
+        bool full = false;
+        if (tail && left < chunk) {
+            const int k = std::max(1, std::min(chunk / kTailChunk, left > 0 ? (left + kTailChunk - 1) / kTailChunk
+                                                                              : 1 << std::min(over++, 16)));
+            for (int q = 0; q < k; q++) SEM_CUDA_TRY(cudaGraphLaunch(tail, s));
+            h->launches += 3 * (int64_t)kTailChunk * k;
+        } else if (exec) {
             SEM_CUDA_TRY(cudaGraphLaunch(exec, s));
             h->launches += 3 * (int64_t)chunk;
+            full = true;
         } else {
             for (int it = 0; it < chunk; it++) {
                 int rc = launch_iteration(h, precision, s);
                 if (rc) return rc;
             }
         }
-        SEM_CUDA_TRY(cudaMemcpyAsync(out, h->state + slot, sizeof(CGState), cudaMemcpyDeviceToHost, s));
+        SEM_CUDA_TRY(cudaMemcpyAsync(&rb->st, h->state + slot, sizeof(CGState), cudaMemcpyDeviceToHost, s));
+        SEM_CUDA_TRY(cudaMemcpyAsync(&rb->err, device_error_word(h), sizeof(int), cudaMemcpyDeviceToHost, s));
         SEM_CUDA_TRY(cudaStreamSynchronize(s));
-        int err_word = 0;
-        SEM_CUDA_TRY(cudaMemcpy(&err_word, device_error_word(h), sizeof(int), cudaMemcpyDeviceToHost));
+        *out = rb->st;
+        const int err_word = rb->err;
         if (err_word) {
             // a staged kernel gave up waiting: its CTAs skipped the reductions, so
             // the counters are reset and the solve ends with SEM_ETIMEOUT
@@ -390,7 +417,7 @@ static int run_cg_loop(sem_handle* h, int precision, const sem_solve_opts& o, in
             cudaMemset(h->counters, 0, 16 * sizeof(unsigned));
             return fail(SEM_ETIMEOUT, "a staged operator kernel gave up waiting for its bulk copies");
         }
-        if (exec && tm && (chunk == 1 || out->iter - iter_before >= 2)) {
+        if (full && tm && (chunk == 1 || out->iter - iter_before >= 2)) {
             float ms = 0.0f;
             if (cudaEventElapsedTime(&ms, h->ax_ev[0], h->ax_ev[1]) == cudaSuccess) {
                 tm->ms += ms;
@@ -415,8 +442,8 @@ static bool use_persist(const sem_handle* h, const sem_solve_opts& o, int precis
 }
 
 static int run_cg(sem_handle* h, int precision, const sem_solve_opts& o, int slot, cudaStream_t s, CGState* out,
-                  AxTiming* tm, bool* persisted) {
-    if (!use_persist(h, o, precision)) return run_cg_loop(h, precision, o, slot, s, out, tm);
+                  AxTiming* tm, bool* persisted, int expect = 0) {
+    if (!use_persist(h, o, precision)) return run_cg_loop(h, precision, o, slot, s, out, tm, expect);
     *persisted = true;
     int rc = launch_cg_persist(h, precision, slot, s);
     if (rc) return rc;
@@ -615,7 +642,7 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
         // norm is not monotone), and its direction is kept like any other.
         double prev = INFINITY, rn_prev = 0.0;
         bool can_carry = false, capped_last = false;
-        int outer = 0, inner = 0;
+        int outer = 0, inner = 0, last_inner = 0;
         for (;;) {
             if ((rc = true_residual(h, h->ws.x, h->ws.b, rrbb, s)) || (rc = read_rrbb(h, hb, s))) return rc;
             const double rel = relative_residual(hb[0], hb[1]);
@@ -638,8 +665,9 @@ static int solve_single(sem_handle* h, double* x_user, const double* b_user, con
                 h->state + 1, h->partials, h->counters + 5, carry_c);
             SEM_LAUNCH_CHECK("ir prepare");
             h->launches += 2;
-            if ((rc = run_cg(h, prec, o, 1, s, &hs, &tm, &persisted))) return rc;
+            if ((rc = run_cg(h, prec, o, 1, s, &hs, &tm, &persisted, last_inner))) return rc;
             inner += hs.iter;
+            last_inner = hs.iter;
             capped_last = hs.iter >= o.max_iter;
             can_carry = (hs.status == SEM_OK || hs.status == SEM_ENOTCONV) && hs.iter > 0;
             rn_prev = rn;

@@ -275,6 +275,12 @@ struct SchwarzData {
     cudaEvent_t ev_restrict = nullptr, ev_coarse = nullptr;
 };
 
+// What the CG loop reads back after each graph launch, in one pinned block.
+struct LoopReadback {
+    CGState st;
+    int err;
+};
+
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     int key_prec = -1;
@@ -317,9 +323,11 @@ struct sem_handle {
     unsigned int* counters = nullptr; // [16]
     sem::CGState* state = nullptr;       // [2 nsolve + 2]: solve / outer states, then inner states
     sem::CGState* state_host = nullptr;  // pinned mirror
+    sem::LoopReadback* loop_host = nullptr;  // pinned: the CG loop's state and error word, read with one sync
     double* scratch = nullptr;        // [64] small device scratch
     sem::Workspace ws;
     sem::GraphCache graph;
+    sem::GraphCache graph_tail;  // kTailChunk iterations, no timing events: the predicted end of a CG run
     sem::ProjSpace proj;
     sem::SchwarzData sch;
     sem::BatchPlan batch;

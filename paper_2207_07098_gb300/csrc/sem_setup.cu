@@ -326,6 +326,7 @@ static void free_handle(sem_handle* h) {
     cudaFree(h->state);
     cudaFree(h->scratch);
     if (h->state_host) cudaFreeHost(h->state_host);
+    if (h->loop_host) cudaFreeHost(h->loop_host);
     Workspace& w = h->ws;
     cudaFree(w.r); cudaFree(w.p); cudaFree(w.z); cudaFree(w.w); cudaFree(w.x); cudaFree(w.b);
     cudaFree(w.r32); cudaFree(w.p32); cudaFree(w.z32); cudaFree(w.w32); cudaFree(w.d32); cudaFree(w.b32);
@@ -349,6 +350,7 @@ static void free_handle(sem_handle* h) {
     free_projection(h);
     free_schwarz(h);
     if (h->graph.exec) cudaGraphExecDestroy(h->graph.exec);
+    if (h->graph_tail.exec) cudaGraphExecDestroy(h->graph_tail.exec);
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     for (auto& ev : h->ax_ev)
         if (ev) cudaEventDestroy(ev);
@@ -511,7 +513,8 @@ static int setup_common(sem_handle** out, int nsolve, const sem_mesh_desc* meshe
         (rc = dalloc(h, &h->scratch, 64)))
         return bail(rc);
     if ((flags & SEM_FLAG_METRICS) && (rc = dalloc(h, &h->drdx, (size_t)9 * n_local))) return bail(rc);
-    if (cudaMallocHost((void**)&h->state_host, sizeof(CGState) * (2 * nsolve + 2)) != cudaSuccess)
+    if (cudaMallocHost((void**)&h->state_host, sizeof(CGState) * (2 * nsolve + 2)) != cudaSuccess ||
+        cudaMallocHost((void**)&h->loop_host, sizeof(LoopReadback)) != cudaSuccess)
         return bail(fail(SEM_ENOMEM, "cudaMallocHost failed"));
 #define UP(dst, src, bytes)                                                               \
     do {                                                                                  \
@@ -854,10 +857,11 @@ static int set_helmholtz(sem_handle* h, const double* h2_host, cudaStream_t s) {
     if (!rc && e != cudaSuccess) rc = cuda_fail(e, "Helmholtz set-up");
     // captured graphs hold the old operator's arguments; the batch operator
     // configuration is chosen again for the new operator
-    if (h->graph.exec) {
-        cudaGraphExecDestroy(h->graph.exec);
-        h->graph.exec = nullptr;
-    }
+    for (GraphCache* g : {&h->graph, &h->graph_tail})
+        if (g->exec) {
+            cudaGraphExecDestroy(g->exec);
+            g->exec = nullptr;
+        }
     h->batch.kcfg[0] = h->batch.kcfg[1] = -1;
     return done(rc);
 }

@@ -128,9 +128,17 @@ def test_solve_bit_reproducible_and_graph_equivalent():
     assert np.array_equal(x1, x2) and s1["iterations"] == s2["iterations"]
     x3, s3 = H.solve(b, tol=TOL, use_graph=0, graph_chunk=7)
     assert np.array_equal(x1, x3) and s1["iterations"] == s3["iterations"]
-    x4, _ = H.solve(b, tol=TOL, mode=S.SEM_MODE_MIXED_IR)
+    x4, s4 = H.solve(b, tol=TOL, mode=S.SEM_MODE_MIXED_IR)
     x5, _ = H.solve(b, tol=TOL, mode=S.SEM_MODE_MIXED_IR)
     assert np.array_equal(x4, x5)
+    # the refinement steps after the first launch graphs sized by the previous
+    # step's count (tail graphs of 4 iterations near the predicted end): the
+    # same iterations as one launch at a time and as another chunk size
+    x6, s6 = H.solve(b, tol=TOL, mode=S.SEM_MODE_MIXED_IR, use_graph=0)
+    assert np.array_equal(x4, x6) and s4["iterations"] == s6["iterations"]
+    x7, s7 = H.solve(b, tol=TOL, mode=S.SEM_MODE_MIXED_IR, graph_chunk=9)
+    assert np.array_equal(x4, x7) and s4["iterations"] == s7["iterations"]
+    assert s4["outer_iterations"] >= 2
 
 
 def test_host_buffers_and_warm_start():
