@@ -282,7 +282,9 @@ static int launch_ka(sem_handle* h, int precision, cudaStream_t s) {
 static int launch_kb_kc(sem_handle* h, int precision, cudaStream_t s) {
     if (precision == kPipePrec) return SEM_OK;
     if (precision == kPairPrec) return launch_pair_rest(h, s);
-    int rc = launch_gs(h, is_f32(precision) ? (void*)h->ws.w32 : (void*)h->ws.w, is_f32(precision), true, s);
+    // the state slot of the K-A and K-C of this precision (FP32 inner loop: 1)
+    const CGState* st = is_f32(precision) ? h->state + 1 : h->state;
+    int rc = launch_gs_until_done(h, is_f32(precision) ? (void*)h->ws.w32 : (void*)h->ws.w, is_f32(precision), st, s);
     if (!rc) rc = launch_cg_update(h, precision, s);
     return rc;
 }

@@ -202,8 +202,11 @@ struct GsPairRanges {
 };
 constexpr int kGsPairU = 4;
 
+// st: the pair CG's state; a graph launch past the end of the solve returns
+// at once (uniform over the grid)
 __global__ void __launch_bounds__(256) gs_pair_kernel(float* __restrict__ uh, float* __restrict__ ul, GSLists g,
-                                                      GsPairRanges rg) {
+                                                      GsPairRanges rg, const CGState* __restrict__ st) {
+    if (st->done) return;
     const int b = blockIdx.x;
     int c = 0;
     while (c < 4 && b >= rg.b[c]) c++;
@@ -335,7 +338,7 @@ int launch_pair_rest(sem_handle* h, cudaStream_t s) {
                           ctas(g.nzero, 1)};
         int acc = 0;
         for (int c = 0; c < 5; c++) rg.b[c] = (acc += n[c]);
-        gs_pair_kernel<<<acc, 256, 0, s>>>(v[6], v[7], g, rg);
+        gs_pair_kernel<<<acc, 256, 0, s>>>(v[6], v[7], g, rg, h->state);
         SEM_LAUNCH_CHECK("gs_pair_kernel");
         h->launches++;
     }

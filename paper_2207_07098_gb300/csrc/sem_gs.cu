@@ -26,11 +26,12 @@ struct GsRanges {
     int b[6];
 };
 constexpr int kGsThreads = 256;
-constexpr int kGsPairU = 4, kGsQuadU = 2, kGsZeroU = 4;
+constexpr int kGsPairU = 4, kGsQuadU = 4, kGsZeroU = 4;
 
 template <typename T>
 __global__ void __launch_bounds__(kGsThreads) gs_kernel(T* __restrict__ u, GSLists g, int apply_mask, GsRanges rg,
                                                         GsSkip sk) {
+    if (sk.done_st && sk.done_st->done) return;  // uniform over the grid
     const int b = blockIdx.x;
     int c = 0;
     while (c < 5 && b >= rg.b[c]) c++;
@@ -113,6 +114,12 @@ int launch_gs(sem_handle* h, void* u, bool fp32, bool apply_mask, cudaStream_t s
 
 int launch_gs_skip(sem_handle* h, void* u, bool fp32, const GsSkip& skip, cudaStream_t s) {
     return launch_gs_impl(h, u, fp32, true, skip, s);
+}
+
+int launch_gs_until_done(sem_handle* h, void* u, bool fp32, const CGState* st, cudaStream_t s) {
+    GsSkip sk;
+    sk.done_st = st;
+    return launch_gs_impl(h, u, fp32, true, sk, s);
 }
 
 // <a, b> = sum_L a_L b_L / mult_L in FP64, fixed-order grid reduction.

@@ -100,6 +100,10 @@ struct MeshPart {
 struct GsSkip {
     const uint16_t* sid[5] = {};  // pairs, quads, octets, other sizes, Dirichlet zero list
     const struct CGState* st = nullptr;
+    // single-mesh CG loop: the whole launch returns at once when this solve
+    // is done (a graph launch runs past the end of the solve; its operator and
+    // update kernels return at once too, and A p is recomputed before use)
+    const struct CGState* done_st = nullptr;
 };
 
 struct GSLists {
@@ -366,6 +370,8 @@ int launch_ax_local(sem_handle* h, const void* u, void* w, int precision, cudaSt
 int launch_gs(sem_handle* h, void* u, bool fp32, bool apply_mask, cudaStream_t s);
 // masked QQ^T of a batch that leaves the segments of solves already done
 int launch_gs_skip(sem_handle* h, void* u, bool fp32, const GsSkip& skip, cudaStream_t s);
+// QQ^T + mask that returns at once when the CG state `st` is done (CG loop)
+int launch_gs_until_done(sem_handle* h, void* u, bool fp32, const CGState* st, cudaStream_t s);
 // w = B u
 int launch_mass(sem_handle* h, const double* u, double* w, cudaStream_t s);
 int launch_mass32(sem_handle* h, const float* u, float* w, cudaStream_t s);
