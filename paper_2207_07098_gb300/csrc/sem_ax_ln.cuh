@@ -20,9 +20,10 @@
 // Thread (lo, hi) owns the column (i = lo, j = hi) of its element for the
 // loads, the G weighting and the output, and one line per direction in the
 // transforms: the r-line (k = hi, j = lo), the s-line (k = hi, i = lo) and
-// the t-line (j = hi, i = lo), which is its own column.  Element blocks live
-// in shared memory in four arrays (u, then ur/wr, us/ws, ut/wt) with padded
-// row and plane strides.  Even lx in {4, 6, 8, 10, 12}.
+// the t-line (j = hi, i = lo), which is its own column and stays in its
+// registers.  Element blocks live in shared memory in three arrays (u, then
+// w; ur/wr; us/ws) with padded row and plane strides.  Even lx in
+// {4, 6, 8, 10, 12}.
 #pragma once
 
 #include "sem_ax.cuh"
@@ -52,13 +53,13 @@ struct LnCfg {
     static constexpr int EPC = LX == 8 ? 2 : (256 / N2) > 0 ? (256 / N2) : 1;
     static constexpr int USED = EPC * N2;
     static constexpr int THREADS = ((USED + 31) / 32) * 32;
-    static constexpr size_t BYTES = sizeof(double) * 4 * (size_t)EPC * SLOT;
+    static constexpr size_t BYTES = sizeof(double) * 3 * (size_t)EPC * SLOT;
     // CTAs per SM the register allocation is held to.  The FP64 pipe (2
-    // thread-operations per cycle per SM) bounds the kernel; at lx = 8 three
-    // CTAs of 128 threads (12 warps, at most 170 registers) measured 2.3%
-    // faster than one of 256 threads at 187 registers and 1.3% faster than
-    // two of 256 at 128 (which spill); the other orders take what they need.
-    static constexpr int MINB = LX == 8 ? 3 : 1;
+    // thread-operations per cycle per SM) bounds the kernel.  At lx = 8 two
+    // CTAs of 128 threads, unconstrained (218 registers in the CG form, no
+    // spills): three at a 170-register cap spill and measured 0.9% slower;
+    // the other orders take what they need.
+    static constexpr int MINB = LX == 8 ? 2 : 1;
     static __host__ __device__ constexpr int at(int k, int j, int i) { return k * N2P + j * LXP + i; }
     static_assert(LX % 2 == 0 && LX >= 4 && LX <= 12, "line transforms need even lx in [4, 12]");
     static_assert(LXP >= LX && N2P >= LX * LXP, "padded strides must cover a plane");
@@ -96,6 +97,37 @@ __device__ __forceinline__ void ln_line(const double* x, int xst, double* y, int
     }
 }
 
+// The same transform on a line held in registers: y = M x, or with ACC
+// y = (y + S) + T, (y - ... ) as ln_line (the same operations in the same order).
+template <int LX, int CA, bool ACC>
+__device__ __forceinline__ void ln_line_reg(const double (&x)[LX], double (&y)[LX]) {
+    constexpr int P = LX / 2, N = LX - 1, PP = P * P;
+    const double* A = c_lncoef + CA;
+    const double* B = c_lncoef + CA + PP;
+    double e[P], o[P];
+#pragma unroll
+    for (int m = 0; m < P; m++) {
+        e[m] = x[m] + x[N - m];
+        o[m] = x[m] - x[N - m];
+    }
+#pragma unroll
+    for (int i = 0; i < P; i++) {
+        double S = A[i * P] * o[0], T = B[i * P] * e[0];
+#pragma unroll
+        for (int m = 1; m < P; m++) {
+            S = fma(A[i * P + m], o[m], S);
+            T = fma(B[i * P + m], e[m], T);
+        }
+        if (ACC) {
+            y[i] = (y[i] + S) + T;
+            y[N - i] = (y[N - i] + S) - T;
+        } else {
+            y[i] = S + T;
+            y[N - i] = S - T;
+        }
+    }
+}
+
 template <int LX, bool FUSED>
 __global__ void __launch_bounds__(LnCfg<LX>::THREADS, LnCfg<LX>::MINB) ax_ln_kernel(AxParams<double> a) {
     using C = LnCfg<LX>;
@@ -103,7 +135,7 @@ __global__ void __launch_bounds__(LnCfg<LX>::THREADS, LnCfg<LX>::MINB) ax_ln_ker
     constexpr int N2P = C::N2P, LXP = C::LXP;
     constexpr int CF = ln_coef_off(LX), CB = CF + 2 * P * P;  // forward (D) and backward (D^T) tables
     extern __shared__ __align__(16) unsigned char smem_ln[];
-    double* arr = reinterpret_cast<double*>(smem_ln);  // 4 arrays x EPC slots: u | r | s | t
+    double* arr = reinterpret_cast<double*>(smem_ln);  // 3 arrays x EPC slots: u | r | s
     __shared__ double sb_beta;
     bool first = false;
     if (FUSED) {
@@ -122,7 +154,6 @@ __global__ void __launch_bounds__(LnCfg<LX>::THREADS, LnCfg<LX>::MINB) ax_ln_ker
     double* su = arr + 0 * EPC * SLOT + slot;
     double* sr = arr + 1 * EPC * SLOT + slot;
     double* ss = arr + 2 * EPC * SLOT + slot;
-    double* st = arr + 3 * EPC * SLOT + slot;
     const int64_t ngroups = (a.E + EPC - 1) / EPC;
     double pap = 0.0;
     __syncthreads();
@@ -155,11 +186,13 @@ __global__ void __launch_bounds__(LnCfg<LX>::THREADS, LnCfg<LX>::MINB) ax_ln_ker
 #pragma unroll
         for (int c = 0; c < 6; c++) gc[c] = valid ? ld_stream(Ge + c * N3) : 0.0;
         __syncthreads();
-        // phase 1: derivative lines ur (along i), us (along j), ut (along k)
+        // phase 1: derivative lines ur (along i) and us (along j) through shared
+        // memory; ut along k is this thread's own column, from its registers
+        double tcol[LX];  // ut, then wt, of the column
         if (active) {
             ln_line<LX, CF, false>(su + C::at(hi, lo, 0), 1, sr + C::at(hi, lo, 0), 1);
             ln_line<LX, CF, false>(su + C::at(hi, 0, lo), LXP, ss + C::at(hi, 0, lo), LXP);
-            ln_line<LX, CF, false>(su + C::at(0, hi, lo), N2P, st + C::at(0, hi, lo), N2P);
+            ln_line_reg<LX, CF, false>(ud, tcol);
         }
         __syncthreads();
         // phase 2: (wr, ws, wt) = G (ur, us, ut) at the column's points, in
@@ -174,10 +207,10 @@ __global__ void __launch_bounds__(LnCfg<LX>::THREADS, LnCfg<LX>::MINB) ax_ln_ker
                     for (int c = 0; c < 6; c++) gn[c] = valid ? ld_stream(Ge + c * N3 + (k + 1) * N2) : 0.0;
                 }
                 const int q = C::at(k, hi, lo);
-                const double ur = sr[q], us = ss[q], ut = st[q];
+                const double ur = sr[q], us = ss[q], ut = tcol[k];
                 sr[q] = fma(gc[0], ur, fma(gc[1], us, gc[2] * ut));
                 ss[q] = fma(gc[1], ur, fma(gc[3], us, gc[4] * ut));
-                st[q] = fma(gc[2], ur, fma(gc[4], us, gc[5] * ut));
+                tcol[k] = fma(gc[2], ur, fma(gc[4], us, gc[5] * ut));
                 if (k + 1 < LX) {
 #pragma unroll
                     for (int c = 0; c < 6; c++) gc[c] = gn[c];
@@ -186,18 +219,23 @@ __global__ void __launch_bounds__(LnCfg<LX>::THREADS, LnCfg<LX>::MINB) ax_ln_ker
         }
         __syncthreads();
         // phase 3: w = D^T-lines of wr (into the u array), += those of ws,
-        // += those of wt; the t-line is this thread's own column, so its
-        // result needs no barrier before the store
+        // then += the D^T-line of wt along this thread's own column, in
+        // registers (its r and s sums read back once, no barrier needed)
         if (active) ln_line<LX, CB, false>(sr + C::at(hi, lo, 0), 1, su + C::at(hi, lo, 0), 1);
         __syncthreads();
         if (active) ln_line<LX, CB, true>(ss + C::at(hi, 0, lo), LXP, su + C::at(hi, 0, lo), LXP);
         __syncthreads();
-        if (active) ln_line<LX, CB, true>(st + C::at(0, hi, lo), N2P, su + C::at(0, hi, lo), N2P);
+        double wcol[LX];
+        if (active) {
+#pragma unroll
+            for (int k = 0; k < LX; k++) wcol[k] = su[C::at(k, hi, lo)];
+            ln_line_reg<LX, CB, true>(tcol, wcol);
+        }
         if (valid) {
             double pw = 0.0;
 #pragma unroll
             for (int k = 0; k < LX; k++) {
-                const double wv = su[C::at(k, hi, lo)];
+                const double wv = wcol[k];
                 st_keep<FUSED>(a.w + base + k * N2, wv);
                 if (FUSED) pw = fma(ud[k], wv, pw);
             }
