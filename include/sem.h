@@ -134,7 +134,11 @@ typedef struct sem_solve_opts {
                             are float pairs too where variant 6 applies).  The true residual
                             that decides convergence is always computed with SEM_FP64 */
     int use_graph;       /* capture the CG iterations in CUDA graphs (1) */
-    int graph_chunk;     /* CG iterations per graph launch between host checks (32) */
+    int graph_chunk;     /* CG iterations per graph launch between host checks (32).  Mixed
+                            mode: a refinement step after the first predicts its length from
+                            the step before and, once fewer than graph_chunk iterations remain
+                            by that count, launches graphs of 4 iterations instead (the
+                            iterates are the same) */
     int autotune;        /* time the operator-kernel variants on this handle's data at the
                             first solve of each precision and keep the fastest (1) */
     int ir_carry;        /* mixed mode: from the second refinement step on, the inner CG
