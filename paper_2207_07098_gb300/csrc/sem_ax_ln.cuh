@@ -98,7 +98,8 @@ __device__ __forceinline__ void ln_line(const double* x, int xst, double* y, int
 }
 
 // The same transform on a line held in registers: y = M x, or with ACC
-// y = (y + S) + T, (y - ... ) as ln_line (the same operations in the same order).
+// y_i = (y_i + S_i) + T_i and y_{N-i} = (y_{N-i} + S_i) - T_i, the same
+// operations in the same order as ln_line.
 template <int LX, int CA, bool ACC>
 __device__ __forceinline__ void ln_line_reg(const double (&x)[LX], double (&y)[LX]) {
     constexpr int P = LX / 2, N = LX - 1, PP = P * P;
