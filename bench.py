@@ -215,6 +215,15 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def ka_bytes_per_point(solver: str) -> int:
+    """Algorithmic bytes per local point of the fused CG operator kernel (K-A):
+    z, p and the six h1-folded factors read, p and w written, ten values of
+    the solve's inner precision (4 B for the FP32 inner solves of the mixed
+    and GMRES modes, 8 B otherwise)."""
+    reads, writes = 2 + 6, 2
+    return (reads + writes) * (4 if solver in ("mixed", "gmres") else 8)
+
+
 def _traffic_for(kernel: str, workload: str):
     """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
     summaries (a `traffic-record:` line in profiles/*.md), if the kernel's
@@ -325,8 +334,7 @@ def run_ours(args):
     # dominant kernel: the fused p-update + ax_helm launch (K-A) of the CG loop
     samples = [s["ax_ms"] for s in stats if s["ax_samples"] > 0]
     ax_ms = statistics.mean(samples) if samples else None
-    ka_bytes_pt = 10 * (4 if args.solver in ("mixed", "gmres") else 8)  # read z, p, 6 G; write p, w (h1 folded)
-    ka_bytes = ka_bytes_pt * n
+    ka_bytes = ka_bytes_per_point(args.solver) * n
     achieved = ka_bytes / (ax_ms * 1e-3) / 1e9 if ax_ms else None
     variant = stats[-1].get("ax_variant", 0)
     tname = "float" if args.solver in ("mixed", "gmres") else "double"

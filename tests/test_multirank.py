@@ -51,3 +51,4 @@ def test_two_gloo_ranks_combine_to_whole_job_figures():
 def test_single_rank_is_identity():
     import bench
     assert bench.combine_ranks(12.5, 7.0, None) == (12.5, 7.0)
+
