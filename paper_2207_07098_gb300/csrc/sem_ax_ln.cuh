@@ -56,7 +56,7 @@ struct LnCfg {
     static constexpr size_t BYTES = sizeof(double) * 3 * (size_t)EPC * SLOT;
     // CTAs per SM the register allocation is held to.  The FP64 pipe (2
     // thread-operations per cycle per SM) bounds the kernel.  At lx = 8 two
-    // CTAs of 128 threads, unconstrained (218 registers in the CG form, no
+    // CTAs of 128 threads, unconstrained (203 registers in the CG form, no
     // spills): three at a 170-register cap spill and measured 0.9% slower;
     // the other orders take what they need.
     static constexpr int MINB = LX == 8 ? 2 : 1;
@@ -133,7 +133,7 @@ template <int LX, bool FUSED>
 __global__ void __launch_bounds__(LnCfg<LX>::THREADS, LnCfg<LX>::MINB) ax_ln_kernel(AxParams<double> a) {
     using C = LnCfg<LX>;
     constexpr int P = C::P, N2 = C::N2, N3 = C::N3, EPC = C::EPC, SLOT = C::SLOT;
-    constexpr int N2P = C::N2P, LXP = C::LXP;
+    constexpr int LXP = C::LXP;
     constexpr int CF = ln_coef_off(LX), CB = CF + 2 * P * P;  // forward (D) and backward (D^T) tables
     extern __shared__ __align__(16) unsigned char smem_ln[];
     double* arr = reinterpret_cast<double*>(smem_ln);  // 3 arrays x EPC slots: u | r | s
